@@ -1,0 +1,594 @@
+"""CPU FP64 oracle for the particle-mesh kick with linear-response neutrinos.
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, obviously-correct
+restatement of what the GPU path computes.  Only the test-suite, the smoke
+check of ``__graft_entry__`` and the CPU-baseline leg of ``bench.py`` may
+import or run it.  The product path (the CUDA library and its Python binding)
+never imports it and never falls back to it; the two share no code.
+
+Paper: Ali-Haimoud & Bird, "An efficient implementation of massive neutrinos
+in non-linear structure formation simulations" (arXiv:1209.0461).  Every
+function names the section / equation it restates.
+
+Units (H0 = 1): lengths in Mpc/h, time in 1/H0, velocities u = a^2 dx/dt in
+units of H0 * Mpc/h (= 100 km/s), conformal time tau and superconformal time
+s = int dtau / a in 1/H0 (Sec. 3.2).  With c = 1 inside the free-streaming
+argument, x = k * (c/H0) * (s - s') * T_nu0 / m_nu (App. C: x = X T_nu0,
+X = k (s - s') / m from Eq. I.def / Eq. delta.final).
+
+Parity status: every function below is pinned by a test in
+``tests/test_oracle_*.py`` against closed forms, printed values, brute force or
+an independent route (see each function's docstring, "Pinned by").
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy import integrate, special
+
+# --------------------------------------------------------------------------
+# Constants (Sec. 2.1)
+# --------------------------------------------------------------------------
+T_NU0_EV = 1.68e-4          # Sec. 2.1: T_nu,0 = 1.95 K = 1.68e-4 eV (value as printed)
+OMEGA_NU_EV = 93.14         # Sec. 2.1: Omega_nu h^2 = sum m_nu / 93.14 eV
+C_OVER_H0 = 2997.92458      # c / H0 in Mpc/h
+WEIGHT_BITS = 16            # fixed-point CIC weight resolution per axis
+WEIGHT_ONE = 1 << WEIGHT_BITS
+MASS_ONE = WEIGHT_ONE ** 3  # 2^48: one particle's total deposit
+ZETA3 = float(special.zeta(3.0))
+
+
+def omega_nu_from_mass(m_nu_total_ev: float, h: float) -> float:
+    """Omega_nu = M_nu / (93.14 eV h^2) (Sec. 2.1, f_nu definition).
+
+    Pinned by: tests check the paper's printed f_nu ~ 0.022 for M_nu = 0.3 eV,
+    Omega_M h^2 = 0.147.
+    """
+    return m_nu_total_ev / (OMEGA_NU_EV * h * h)
+
+
+# --------------------------------------------------------------------------
+# Free-streaming kernel I(x)  (Eq. I.def; App. C series and Eq. fit)
+# --------------------------------------------------------------------------
+def nu_I(x) -> np.ndarray:
+    """Fermi-Dirac free-streaming kernel I(x), exact, from the App. C series
+
+        I(x) = 4 / (3 zeta(3)) * sum_{n>=1} (-1)^{n+1} n / (n^2 + x^2)^2,
+
+    which is the closed evaluation of Eq. I.def with f0 the relativistic
+    Fermi-Dirac distribution (Sec. 4.1, g = 2) and x = X T_nu0.
+
+    The alternating series is summed directly up to N terms (N well past the
+    peak of the terms at n ~ x / sqrt 3) and the remaining tail is taken by
+    repeated averaging of the last partial sums (Euler's transform of an
+    alternating series).  x values are grouped by magnitude so each group
+    uses only as many terms as it needs.
+
+    Pinned by: I(0) = 1; small-x slope 5 zeta(5) / (2 zeta(3)) and large-x
+    limit 1 / (3 zeta(3) x^4) (App. C); brute-force partial sums with 10^6
+    terms; quadrature of Eq. I.def; int_0^inf x I(x) dx = 2 ln 2 / (3 zeta 3)
+    (Sec. 3.3.2 with Eq. v2).
+    """
+    x = np.abs(np.asarray(x, dtype=np.float64))
+    out = np.empty_like(x)
+    flat_x = x.ravel()
+    flat_o = out.ravel()
+    # group by needed term count: N = 48 + 4 x, rounded up to a power of two
+    need = 48.0 + 4.0 * flat_x
+    grp = np.ceil(np.log2(need)).astype(np.int64)
+    n_avg = 20
+    for g in np.unique(grp):
+        sel = np.nonzero(grp == g)[0]
+        nterm = int(2 ** g) + n_avg
+        n = np.arange(1, nterm + 1, dtype=np.float64)
+        xs = flat_x[sel][:, None]
+        sign = np.where(n % 2 == 1, 1.0, -1.0)
+        terms = sign * n / (n * n + xs * xs) ** 2
+        nbase = nterm - n_avg
+        base = terms[:, :nbase].sum(axis=1)
+        # partial sums S_nbase .. S_nterm, then n_avg rounds of averaging
+        ps = base[:, None] + np.concatenate(
+            [np.zeros((len(sel), 1)), np.cumsum(terms[:, nbase:], axis=1)], axis=1)
+        for _ in range(n_avg):
+            ps = 0.5 * (ps[:, 1:] + ps[:, :-1])
+        flat_o[sel] = ps[:, 0]
+    return out * (4.0 / (3.0 * ZETA3))
+
+
+def nu_I_fit(x) -> np.ndarray:
+    """Fitting formula for I(x) (App. C, Eq. fit).
+
+    Pinned by: the paper's stated accuracy against the exact series
+    (absolute <~ 0.07%, relative <~ 1% on 0 <= x <= 2).
+    """
+    x = np.abs(np.asarray(x, dtype=np.float64))
+    x2 = x * x
+    num = 1.0 + 0.0168 * x2 + 0.0407 * x2 * x2
+    den = 1.0 + 2.1734 * x2 + 1.6787 * np.power(x, 4.1811) + 0.1467 * x2 ** 4
+    return num / den
+
+
+# --------------------------------------------------------------------------
+# Background (Sec. 3.2 superconformal time; Sec. 3.1 kick/drift)
+# --------------------------------------------------------------------------
+def hubble(a, omega_m: float):
+    """H(a)/H0 for flat matter + Lambda: sqrt(Om a^-3 + 1 - Om)."""
+    a = np.asarray(a, dtype=np.float64)
+    return np.sqrt(omega_m / a ** 3 + (1.0 - omega_m))
+
+
+_GL_X, _GL_W = np.polynomial.legendre.leggauss(64)
+
+
+def delta_s(a_lo, a_hi, omega_m: float):
+    """s(a_hi) - s(a_lo) = int_{a_lo}^{a_hi} da / (a^3 H)  (Sec. 3.2: ds = dtau/a,
+    dtau = da / (a^2 H)).
+
+    64-point Gauss-Legendre in ln a (integrand a^-2 / H, smooth); vectorised
+    over array arguments.  Computed directly as a difference-free integral so
+    that s - s' stays accurate when a' -> a.
+
+    Pinned by: scipy adaptive quad; Einstein-de Sitter closed form
+    2 (a_lo^-1/2 - a_hi^-1/2).
+    """
+    a_lo = np.asarray(a_lo, dtype=np.float64)
+    a_hi = np.asarray(a_hi, dtype=np.float64)
+    u0 = np.log(a_lo)[..., None]
+    # ln(a_hi / a_lo) via log1p of the exact difference: no cancellation when
+    # a_hi -> a_lo
+    half = 0.5 * np.log1p((a_hi - a_lo) / a_lo)[..., None]
+    u = u0 + half * (_GL_X + 1.0)
+    a = np.exp(u)
+    f = 1.0 / (a * a * hubble(a, omega_m))     # da/(a^3 H) = d ln a / (a^2 H)
+    return (half * (f * _GL_W)).sum(axis=-1)
+
+
+def s_of_a(a, a_init: float, omega_m: float):
+    """Superconformal time s(a) = int_{a_init}^{a} da / (a^3 H) (Sec. 3.2)."""
+    return delta_s(np.full_like(np.asarray(a, dtype=np.float64), a_init), a, omega_m)
+
+
+def kick_factor(a0: float, a1: float, omega_m: float) -> float:
+    """K = int_{a0}^{a1} dt = int da / (a H): the velocity u = a^2 dx/dt obeys
+    du/dt = -grad phi (Eq. dot.q.2 with q = m u).  Adaptive quadrature.
+
+    Pinned by: EdS closed form (2/3)(a1^{3/2} - a0^{3/2}).
+    """
+    val, _ = integrate.quad(lambda a: 1.0 / (a * float(hubble(a, omega_m))), a0, a1,
+                            epsabs=0.0, epsrel=1e-13, limit=200)
+    return val
+
+
+def drift_factor(a0: float, a1: float, omega_m: float) -> float:
+    """Delta s = int da / (a^3 H): dx/dt = u / a^2 (Sec. 3.1 definition of q)."""
+    val, _ = integrate.quad(lambda a: 1.0 / (a ** 3 * float(hubble(a, omega_m))), a0, a1,
+                            epsabs=0.0, epsrel=1e-13, limit=200)
+    return val
+
+
+def free_streaming_k(a: float, m_ev: float, omega_m: float) -> float:
+    """Free-streaming wavenumber k_fs(a) = (3/2 Omega_M(a) <v^-2>)^{1/2} a H in
+    h/Mpc (Eq. kfs-formal), with <v^-2> = 2 ln 2 / (3 zeta 3) (m a / T_nu0)^2
+    (Eq. v2, c = 1) and Omega_M(a) = Omega_M a^-3 / H^2.  Used only by tests
+    (small-scale limit of Sec. 3.3.2, App. A).
+
+    Pinned by: the numerical forms of Eq. kfs (0.08 h/Mpc) and Eq. v2
+    (810 km/s).
+    """
+    H = float(hubble(a, omega_m))
+    om_a = omega_m / a ** 3 / H ** 2
+    v2 = 2.0 * math.log(2.0) / (3.0 * ZETA3) * (m_ev * a / T_NU0_EV) ** 2
+    return math.sqrt(1.5 * om_a * v2) * a * H / C_OVER_H0
+
+
+# --------------------------------------------------------------------------
+# Particle quantisation and CIC deposit (Sec. 4.3 step (ii): the Fourier-
+# transformed CDM density needed for the long-range PM force)
+# --------------------------------------------------------------------------
+def quantise_positions_f64(pos: np.ndarray, box: float, ngrid: int):
+    """FP64 comoving positions [3, Np] -> (cell [3,Np] int64 in [0,N), w [3,Np]).
+
+    u = x / (L/N); c = floor(u); w = floor((u - c) * 2^16); c wrapped mod N.
+    """
+    delta = box / ngrid
+    u = np.asarray(pos, dtype=np.float64) / delta
+    c = np.floor(u)
+    o = u - c
+    w = np.floor(o * WEIGHT_ONE).astype(np.int64)
+    c = np.mod(c.astype(np.int64), ngrid)
+    return c, w
+
+
+def quantise_positions_cell(cell: np.ndarray, off: np.ndarray, ngrid: int):
+    """Cell-index + FP32-offset positions -> (cell mod N, w = floor(off * 2^16)).
+
+    Offsets must lie in [0, 1); raises ValueError otherwise.
+    """
+    off = np.asarray(off, dtype=np.float32)
+    if np.any(~np.isfinite(off)) or np.any(off < 0) or np.any(off >= 1):
+        raise ValueError("offsets must lie in [0, 1)")
+    w = np.floor(off.astype(np.float64) * WEIGHT_ONE).astype(np.int64)
+    c = np.mod(np.asarray(cell, dtype=np.int64), ngrid)
+    return c, w
+
+
+def _corner_weights(w):
+    """Per-axis fixed-point weights: (2^16 - w) at cell c, w at cell c + 1."""
+    return (WEIGHT_ONE - w, w)
+
+
+def cic_deposit(c: np.ndarray, w: np.ndarray, ngrid: int) -> np.ndarray:
+    """Fixed-point cloud-in-cell deposit: F[z, y, x] (int64), each particle
+    adding wx*wy*wz (product of per-axis 16-bit weights, total 2^48) to the 8
+    corner nodes.  Integer sums are exact, so the result is order-independent.
+
+    Pinned by: exact mass conservation sum F = Np 2^48; a hand-computed single
+    particle; brute-force per-particle loop.
+    """
+    n = ngrid
+    grid = np.zeros(n * n * n, dtype=np.int64)
+    wx, wy, wz = (_corner_weights(w[0]), _corner_weights(w[1]), _corner_weights(w[2]))
+    for dz in (0, 1):
+        iz = (c[2] + dz) % n
+        for dy in (0, 1):
+            iy = (c[1] + dy) % n
+            for dx in (0, 1):
+                ix = (c[0] + dx) % n
+                wt = wx[dx] * wy[dy] * wz[dz]
+                np.add.at(grid, (iz * n + iy) * n + ix, wt)
+    return grid.reshape(n, n, n)
+
+
+def density_contrast(F: np.ndarray, npart: int) -> np.ndarray:
+    """delta = F N^3 / (Np 2^48) - 1 in FP64 (mean particle count per node is
+    Np / N^3)."""
+    n = F.shape[0]
+    return F.astype(np.float64) * (float(n) ** 3 / (float(npart) * MASS_ONE)) - 1.0
+
+
+def forward_fft(delta: np.ndarray) -> np.ndarray:
+    """Unnormalised forward real 3-D DFT, half spectrum over x: spec[kz, ky, kx],
+    kx in [0, N/2].  numpy.fft.rfftn serves as the library step.
+
+    Pinned by: brute-force DFT at 8^3; Parseval.
+    """
+    return np.fft.rfftn(delta)
+
+
+# --------------------------------------------------------------------------
+# Power-spectrum bins (Sec. 4.2-4.3: P_cdm(k, tau) per |k| bin)
+# --------------------------------------------------------------------------
+def bin_thresholds(ngrid: int, n_kbins: int) -> np.ndarray:
+    """Integer n^2 thresholds T_b = ceil((e_b L / 2 pi)^2), b = 0..n_kbins, for
+    log-spaced edges e_b = k_min (k_max/k_min)^(b/nk), k_min = 2 pi / L,
+    k_max = sqrt(3) pi N / L (1 + 1e-12).  A mode with integer n^2 lies in bin
+    b iff T_b <= n^2 < T_{b+1}; a mode exactly on an edge goes to the upper
+    bin.  n^2 = 0 (the mean) is in no bin."""
+    r = math.sqrt(3.0) * ngrid / 2.0 * (1.0 + 1e-12)
+    b = np.arange(n_kbins + 1, dtype=np.float64)
+    return np.ceil(np.power(r, 2.0 * b / n_kbins)).astype(np.int64)
+
+
+def mode_indices(ngrid: int):
+    """Signed integer frequencies (iz, iy, ix) of the half spectrum, broadcastable."""
+    n = ngrid
+    f = np.fft.fftfreq(n, d=1.0 / n).astype(np.int64)   # 0..N/2-1, -N/2..-1
+    ix = np.arange(n // 2 + 1, dtype=np.int64)
+    return f[:, None, None], f[None, :, None], ix[None, None, :]
+
+
+def bin_power(spec: np.ndarray, box: float, n_kbins: int):
+    """Binned power spectrum of the half spectrum ``spec`` (Sec. 4.3 step (ii)).
+
+    Weight w = 1 on the kx = 0 and kx = N/2 planes, 2 elsewhere (each counts
+    a mode and its conjugate).  Returns dict with per-bin
+      count = sum w, ksum = sum w |k|, psum = sum w |delta_k|^2,
+      P = psum / count * L^3 / N^6   [(Mpc/h)^3],  k = ksum / count,
+      nonempty mask.
+
+    Pinned by: a single plane wave lands in one bin with known power; mode
+    counts equal a brute-force lattice enumeration.
+    """
+    n = spec.shape[0]
+    iz, iy, ix = mode_indices(n)
+    n2 = iz * iz + iy * iy + ix * ix
+    w = np.where((ix == 0) | (ix == n // 2), 1.0, 2.0) * np.ones_like(n2, dtype=np.float64)
+    T = bin_thresholds(n, n_kbins)
+    b = np.searchsorted(T, n2, side="right") - 1
+    valid = (n2 > 0) & (b >= 0) & (b < n_kbins)
+    bb = b[valid]
+    ww = w[valid]
+    kf = 2.0 * math.pi / box
+    kmag = kf * np.sqrt(n2[valid].astype(np.float64))
+    p2 = (np.abs(spec[valid]) ** 2)
+    count = np.bincount(bb, weights=ww, minlength=n_kbins)
+    ksum = np.bincount(bb, weights=ww * kmag, minlength=n_kbins)
+    psum = np.bincount(bb, weights=ww * p2, minlength=n_kbins)
+    ne = count > 0
+    P = np.zeros(n_kbins)
+    k = np.zeros(n_kbins)
+    P[ne] = psum[ne] / count[ne] * box ** 3 / float(n) ** 6
+    k[ne] = ksum[ne] / count[ne]
+    return dict(count=count, ksum=ksum, psum=psum, P=P, k=k, nonempty=ne, T=T)
+
+
+# --------------------------------------------------------------------------
+# Neutrino linear response (Eq. P-final, Eq. deltaI-nu, Sec. 4.3 (iii), App. B)
+# --------------------------------------------------------------------------
+@dataclass
+class Cosmo:
+    """Cosmology of the kick.  Omega_M = omega_cdm + omega_nu (baryons folded
+    into cdm); flat, Omega_L = 1 - Omega_M.  m_nu_ev lists the species masses."""
+    omega_cdm: float
+    omega_nu: float
+    h: float
+    m_nu_ev: tuple = ()
+    a_init: float = 0.02
+
+    @property
+    def omega_m(self) -> float:
+        return self.omega_cdm + self.omega_nu
+
+    @property
+    def f_nu(self) -> float:
+        return self.omega_nu / self.omega_m
+
+    def species_weights(self):
+        """Omega_nu,i / Omega_nu = m_i / M_nu (Sec. 2.1 per species)."""
+        m = np.asarray(self.m_nu_ev, dtype=np.float64)
+        tot = m.sum()
+        return m / tot if tot > 0 else np.zeros_like(m)
+
+
+def _interp_lna(lna_nodes, vals, lna):
+    """Piecewise-linear in ln a between nodes; constant before the first node.
+    vals: [n_nodes, nb]; lna: array -> [len(lna), nb]."""
+    lna = np.atleast_1d(lna)
+    out = np.empty((lna.size, vals.shape[1]))
+    for i, u in enumerate(lna):
+        if len(lna_nodes) == 1 or u <= lna_nodes[0]:
+            out[i] = vals[0]
+            continue
+        j = np.searchsorted(lna_nodes, u, side="right") - 1
+        j = min(max(j, 0), len(lna_nodes) - 2)
+        t = (u - lna_nodes[j]) / (lna_nodes[j + 1] - lna_nodes[j])
+        out[i] = vals[j] + (vals[j + 1] - vals[j]) * t
+    return out
+
+
+def response_integral(kb, a, cosmo: Cosmo, m_ev: float, a_nodes, h_nodes,
+                      I_func=nu_I, epsrel=1e-11):
+    """Integral term of Eq. P-final for one species:
+
+        J(k) = (3/2) Omega_M H0^2 int_{tau_i}^{tau} I[k (s - s') / m] (s - s')
+               P_M^{1/2}(k, tau') dtau',       dtau' = da' / (a'^2 H(a')),
+
+    with P_M^{1/2}(k, a') linear in ln a' through the nodes (a_nodes, h_nodes)
+    (h_nodes [n_nodes, nb]) and constant on [a_i, a_nodes[0]].  The last node
+    must be the current epoch a.  Integrated in ln a' by vector-valued
+    adaptive quadrature (scipy quad_vec, the nodes as break points) to
+    ``epsrel``.
+
+    Pinned by: EdS with I == 1 and constant P_M^{1/2} gives the closed form
+    3 c [ln(a/a_i) - 2 (1 - sqrt(a_i/a))]; a brute-force fine composite rule
+    in the superconformal-time variable; the small-scale limit (k_fs/k)^2.
+    """
+    kb = np.asarray(kb, dtype=np.float64)
+    om = cosmo.omega_m
+    kappa = kb * C_OVER_H0 * T_NU0_EV / m_ev            # x = kappa (s - s')
+    lna_nodes = np.log(np.asarray(a_nodes, dtype=np.float64))
+    h_nodes = np.asarray(h_nodes, dtype=np.float64)
+    ai = cosmo.a_init
+
+    def integrand(u):
+        ap = math.exp(u)
+        ds = float(delta_s(ap, a, om))
+        h = _interp_lna(lna_nodes, h_nodes, u)[0]
+        x = kappa * ds
+        return I_func(x) * ds * h / (ap * float(hubble(ap, om)))   # dtau'/dln a' = 1/(a' H)
+
+    u_lo, u_hi = math.log(ai), math.log(a)
+    if u_hi <= u_lo:
+        return np.zeros_like(kb)
+    inner = [u for u in lna_nodes if u_lo < u < u_hi]
+    val, _ = integrate.quad_vec(integrand, u_lo, u_hi, epsabs=0.0, epsrel=epsrel,
+                                norm="max", limit=200000, points=inner or None)
+    return 1.5 * om * val
+
+
+def ic_term(kb, a, cosmo: Cosmo, m_ev: float, sqrtPnu_init, theta_over_delta_init,
+            I_func=nu_I):
+    """Initial-condition term of Eq. P-final (Eq. deltaI-nu):
+    I_{s_i,s} P_nu,i^{1/2}(k) {1 - (s - s_i) a_i [theta/delta]_i(k)}."""
+    kb = np.asarray(kb, dtype=np.float64)
+    ds = float(delta_s(cosmo.a_init, a, cosmo.omega_m))
+    x = kb * C_OVER_H0 * T_NU0_EV / m_ev * ds
+    return I_func(x) * np.asarray(sqrtPnu_init) * (
+        1.0 - ds * cosmo.a_init * np.asarray(theta_over_delta_init))
+
+
+def nu_response(kb, sqrtPcdm, a, cosmo: Cosmo, a_hist, sqrtPM_hist,
+                sqrtPnu_init, theta_over_delta_init, sqrtPnu_prev=None,
+                iters: int = 1, I_func=nu_I, epsrel=1e-11):
+    """Neutrino response per |k| bin (Eq. P-final, Sec. 4.3 (iii)-(iv), App. B).
+
+    Inputs per bin b (arrays of length nb):
+      kb            representative |k| of the bin [h/Mpc]
+      sqrtPcdm      current P_cdm^{1/2}(k_b, a)
+      a_hist        [n_hist] scale factors of the stored spectra (strictly
+                    ascending, a_hist[0] >= a_i, a_hist[-1] < a)
+      sqrtPM_hist   [n_hist, nb] stored P_M^{1/2}(k_b, a_j)
+      sqrtPnu_init  [n_species, nb] P_nu,i^{1/2}(k_b)   (Eq. deltaI-nu)
+      theta_over_delta_init [n_species, nb]  [theta_nu/delta_nu]_i(k_b)
+      sqrtPnu_prev  [nb] P_nu^{1/2} of the previous step (None -> the
+                    species-weighted IC value)
+    The current node of P_M^{1/2} inside the integral is
+      (1 - f_nu) P_cdm^{1/2}(a) + f_nu P_nu^{1/2}(guess),
+    with the guess = sqrtPnu_prev for the first iteration (Sec. 4.3 (iii)) and
+    the previous iteration's result afterwards (App. B).  Species results are
+    weighted by Omega_nu,i / Omega_nu.
+
+    Returns dict(R, sqrtPnu, sqrtPM) where R = P_nu^{1/2} / P_cdm^{1/2} (0 for
+    empty bins, i.e. sqrtPcdm == 0) and sqrtPM = (1-f) P_cdm^{1/2} + f P_nu^{1/2}
+    (App. B first equation).
+    """
+    kb = np.asarray(kb, dtype=np.float64)
+    sqrtPcdm = np.asarray(sqrtPcdm, dtype=np.float64)
+    nb = kb.size
+    masses = np.asarray(cosmo.m_nu_ev, dtype=np.float64)
+    wts = cosmo.species_weights()
+    f = cosmo.f_nu
+    if cosmo.omega_nu <= 0 or masses.size == 0 or masses.sum() <= 0:
+        z = np.zeros(nb)
+        return dict(R=z, sqrtPnu=z.copy(), sqrtPM=sqrtPcdm.copy())
+    a_hist = np.asarray(a_hist, dtype=np.float64).reshape(-1)
+    sqrtPM_hist = np.asarray(sqrtPM_hist, dtype=np.float64).reshape(a_hist.size, nb)
+    Pi = np.asarray(sqrtPnu_init, dtype=np.float64).reshape(masses.size, nb)
+    Ti = np.asarray(theta_over_delta_init, dtype=np.float64).reshape(masses.size, nb)
+    if sqrtPnu_prev is None:
+        guess = (wts[:, None] * Pi).sum(axis=0)
+    else:
+        guess = np.asarray(sqrtPnu_prev, dtype=np.float64)
+    ic = np.zeros(nb)
+    for s, m in enumerate(masses):
+        if m > 0:
+            ic += wts[s] * ic_term(kb, a, cosmo, m, Pi[s], Ti[s], I_func)
+    if a < cosmo.a_init or (a_hist.size and (a_hist[0] < cosmo.a_init or a_hist[-1] >= a
+                                              or np.any(np.diff(a_hist) <= 0))):
+        raise ValueError("need a_i <= a_hist[0] < ... < a_hist[-1] < a")
+    a_nodes = np.concatenate([a_hist, [a]])
+    pnu = guess
+    for _ in range(max(1, iters)):
+        cur = (1.0 - f) * sqrtPcdm + f * pnu
+        h_nodes = np.vstack([sqrtPM_hist, cur[None, :]]) if a_hist.size else cur[None, :]
+        J = np.zeros(nb)
+        for s, m in enumerate(masses):
+            if m > 0:
+                J += wts[s] * response_integral(kb, a, cosmo, m, a_nodes, h_nodes,
+                                                I_func, epsrel)
+        pnu = ic + J
+    R = np.where(sqrtPcdm > 0, pnu / np.where(sqrtPcdm > 0, sqrtPcdm, 1.0), 0.0)
+    return dict(R=R, sqrtPnu=pnu, sqrtPM=(1.0 - f) * sqrtPcdm + f * pnu)
+
+
+# --------------------------------------------------------------------------
+# Green's function, gradient, inverse transform, interpolation, kick
+# (Eq. Poisson, Eq. phases, Sec. 4.3 (iv))
+# --------------------------------------------------------------------------
+def ratio_per_mode(kmag, kb, R, nonempty):
+    """R(|k|): linear in ln k between non-empty bin representatives k_b,
+    constant beyond the end bins (numpy.interp)."""
+    ne = np.asarray(nonempty, dtype=bool)
+    if not np.any(ne):
+        return np.zeros_like(kmag)
+    lk = np.log(np.where(kmag > 0, kmag, 1.0))
+    return np.interp(lk, np.log(np.asarray(kb)[ne]), np.asarray(R)[ne])
+
+
+def green_gradient(spec, box, a, cosmo: Cosmo, kb, R, nonempty, deconvolve=False):
+    """Acceleration spectra acc_c(k) = -i k_c phi(k), c = x, y, z, with
+    Poisson k^2 phi = -(3/2) Omega_M delta_M / a (Eq. Poisson, H0 = 1) and
+    delta_M = delta_cdm [(1 - f_nu) + f_nu R(|k|)]  (Eq. phases with the
+    total-matter sum of Sec. 4.3 (iv)).  k = 0 -> 0.  The gradient is the
+    4-point finite difference of ``gradient_operator`` (zero on the Nyquist
+    index).  Optional CIC deconvolution divides by prod_i sinc(k_i Delta/2)^4
+    (assignment and interpolation windows).
+
+    Pinned by: a single cosine density mode gives the analytic acceleration;
+    point mass against the Ewald-summed periodic 1/r^2 force.
+    """
+    n = spec.shape[0]
+    kf = 2.0 * math.pi / box
+    iz, iy, ix = mode_indices(n)
+    n2 = (iz * iz + iy * iy + ix * ix).astype(np.float64)
+    kmag = kf * np.sqrt(n2)
+    f = cosmo.f_nu
+    Rm = ratio_per_mode(kmag, kb, R, nonempty) if f > 0 else np.zeros_like(kmag)
+    fac = (1.0 - f) + f * Rm
+    with np.errstate(divide="ignore", invalid="ignore"):
+        G = np.where(n2 > 0, -1.5 * cosmo.omega_m / (a * kf * kf * np.where(n2 > 0, n2, 1.0)), 0.0)
+    G = G * fac
+    if deconvolve:
+        def sinc(i):
+            t = math.pi * i.astype(np.float64) / n
+            return np.where(i == 0, 1.0, np.sin(t) / np.where(i == 0, 1.0, t))
+        W = sinc(iz) * sinc(iy) * sinc(ix)
+        G = G / W ** 4
+    phi = G * spec
+    out = []
+    for comp in (ix, iy, iz):
+        out.append(-1j * gradient_operator(comp, n, box) * phi)
+    return out   # [acc_x, acc_y, acc_z] spectra
+
+
+def gradient_operator(i, ngrid, box):
+    """Fourier multiplier of the 4-point central finite-difference derivative
+    d/dx f ~ [8 (f(x+D) - f(x-D)) - (f(x+2D) - f(x-2D))] / (12 D), D = L/N,
+    on the periodic grid: i [8 sin(k D) - sin(2 k D)] / (6 D) with k D = 2 pi i / N.
+    (The paper's code computes the PM force by finite differences of the mesh
+    potential; it vanishes on the Nyquist index by construction.)"""
+    t = 2.0 * math.pi * np.asarray(i, dtype=np.float64) / ngrid
+    d = box / ngrid
+    return (8.0 * np.sin(t) - np.sin(2.0 * t)) / (6.0 * d)
+
+
+def inverse_fft(spec_c, ngrid):
+    """Normalised inverse real 3-D DFT (numpy.fft.irfftn)."""
+    return np.fft.irfftn(spec_c, s=(ngrid, ngrid, ngrid), axes=(0, 1, 2))
+
+
+def cic_interpolate(grid, c, w):
+    """Trilinear (CIC) gather with the deposit's fixed-point weights / 2^48."""
+    n = grid.shape[0]
+    wx, wy, wz = (_corner_weights(w[0]), _corner_weights(w[1]), _corner_weights(w[2]))
+    acc = np.zeros(c.shape[1])
+    for dz in (0, 1):
+        iz = (c[2] + dz) % n
+        for dy in (0, 1):
+            iy = (c[1] + dy) % n
+            for dx in (0, 1):
+                ix = (c[0] + dx) % n
+                wt = (wx[dx] * wy[dy] * wz[dz]).astype(np.float64) / MASS_ONE
+                acc += wt * grid[iz, iy, ix]
+    return acc
+
+
+@dataclass
+class KickResult:
+    F: np.ndarray
+    bins: dict
+    response: dict
+    acc: np.ndarray          # [3, Np]
+    vel: np.ndarray          # [3, Np] updated velocities
+    extras: dict = field(default_factory=dict)
+
+
+def pm_kick(c, w, vel, ngrid, box, a, kick, cosmo: Cosmo, n_kbins, a_hist, sqrtPM_hist,
+            sqrtPnu_init, theta_over_delta_init, sqrtPnu_prev=None, iters=1,
+            deconvolve=False, I_func=nu_I, epsrel=1e-11, keep_fields=False):
+    """One PM long-range kick with Fourier-space neutrinos, steps (ii)-(iv) of
+    Sec. 4.3 at one time step: deposit -> delta -> FFT -> P_cdm bins -> nu
+    response (Eq. P-final) -> delta_M, Green, gradient -> inverse FFTs -> CIC
+    interpolation -> u += acc * K."""
+    npart = c.shape[1]
+    F = cic_deposit(c, w, ngrid)
+    delta = density_contrast(F, npart)
+    spec = forward_fft(delta)
+    bins = bin_power(spec, box, n_kbins)
+    sqrtPcdm = np.sqrt(bins["P"])
+    resp = nu_response(bins["k"], sqrtPcdm, a, cosmo, a_hist, sqrtPM_hist, sqrtPnu_init,
+                       theta_over_delta_init, sqrtPnu_prev, iters, I_func, epsrel)
+    accs = green_gradient(spec, box, a, cosmo, bins["k"], resp["R"], bins["nonempty"],
+                          deconvolve)
+    acc = np.zeros((3, npart))
+    fields = []
+    for comp in range(3):
+        g = inverse_fft(accs[comp], ngrid)
+        if keep_fields:
+            fields.append(g)
+        acc[comp] = cic_interpolate(g, c, w)
+    vnew = np.asarray(vel, dtype=np.float64) + acc * kick
+    ex = dict(spec=spec, fields=fields) if keep_fields else {}
+    return KickResult(F=F, bins=bins, response=resp, acc=acc, vel=vnew, extras=ex)
