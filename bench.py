@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 PM kick with linear-response neutrinos.
+
+metric: particle-kicks/s including the neutrino response, N_p / t(kick),
+one kick = pm_deposit + pm_nu_response + pm_kick (CIC deposit, forward FFT,
+P_cdm bins, FP64 response integral, Green/gradient, 3 inverse FFTs, CIC
+interpolation and velocity update).
+
+Default workload: the precision form, 512^3 particles (int32 cell + FP32
+offset) on a 1024^3 FP32 grid, box 1 Gpc/h, M_nu = 0.06 eV (3 degenerate),
+256 log-k bins, 128-step FP64 history; seeded BBKS Gaussian field,
+Zel'dovich particles at a = 0.1 (synthetic stand-in for CAMB/N-GenICs).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+N > 1 runs under torchrun: independent boxes (seed + rank) per GPU, no
+collective on the data path ("replicas only"), max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1209_0461_gb300 import synth  # noqa: E402
+
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ------------------------------------------------------------------ helpers
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for i, nm in enumerate(names):
+                if f[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def stage_bytes(w, stage):
+    """Algorithmic (compulsory) HBM bytes of ONE launch of a stage: each pass
+    reads its inputs and writes its outputs once at stored precision."""
+    n = w.ngrid
+    M = n ** 3
+    Mc = n * n * (n // 2)                 # packed complex elements per field
+    r = 4 if w.precision == "fp32" else 8
+    c = 2 * r
+    p = 24                                 # position bytes per particle (both forms)
+    v = r
+    Np = w.npart
+    return {
+        "deposit": p * Np + 8 * M,                       # (one scatter launch)
+        "fft_x_fwd": 8 * M + c * Mc,
+        "fft_y_fwd": 2 * c * Mc,
+        "fft_z_fwd": 2 * c * Mc,
+        "bins": c * Mc,
+        "green": c * Mc + 3 * c * Mc,
+        "fft_z_inv": 3 * 2 * c * Mc,
+        "fft_y_inv": 3 * 2 * c * Mc,
+        "fft_x_inv": 3 * (c * Mc + r * M),
+        "interp": p * Np + min(3 * r * M, 24 * r * Np) + 2 * 3 * v * Np,
+    }.get(stage)
+
+
+def traffic_from_profiles(stage, workload):
+    """DRAM bytes per launch of `stage` from the committed ncu summary, if it
+    was taken on the current kernel sources (source hash recorded there)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for ln in open(path):
+        f = ln.split()
+        if len(f) >= 4 and f[0] == workload and f[1] == stage and f[2] == want:
+            return float(f[3])
+    return None
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1209_0461_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:12]
+
+
+# ------------------------------------------------------------------ oracle baseline
+def oracle_sample(w, seed_shift=0):
+    """A bounded CPU sample of the workload: same cosmology, bins, history and
+    particle:grid ratio, on a 128^3 grid with 64^3 particles (cell size kept)."""
+    scale = 128 / w.ngrid
+    s = synth.with_(w, name=w.name + "_sample", ngrid=128, npart_side=max(8, int(w.npart_side * scale)),
+                    box=w.box * scale, seed=w.seed + seed_shift)
+    return s
+
+
+def run_oracle_kick(s):
+    from oracle import pm_oracle as O
+    p = synth.particles(s)
+    ah, hh = synth.history(s)
+    pi, ti = synth.nu_initial(s)
+    cos = O.Cosmo(s.omega_cdm, s.omega_nu, s.h, s.masses, s.a_init)
+    if s.precision == "fp32":
+        cell, off = synth.split_cell_offset(synth.to_cell_offset(p["pos64"], s.box, s.ngrid))
+        c, q = O.quantise_positions_cell(cell, off, s.ngrid)
+    else:
+        c, q = O.quantise_positions_f64(p["pos64"], s.box, s.ngrid)
+    t0 = time.perf_counter()
+    O.pm_kick(c, q, p["vel"], s.ngrid, s.box, s.a_kick, 0.01, cos, s.n_kbins, ah, hh, pi, ti)
+    return time.perf_counter() - t0, s.npart
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, w, rank, world):
+    import torch
+    from paper_1209_0461_gb300 import build as b
+    from paper_1209_0461_gb300 import nupm
+    b.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    wr = synth.with_(w, seed=w.seed + rank)
+    t0 = time.time()
+    parts = synth.particles(wr)
+    a_hist, hist = synth.history(wr)
+    pi, ti = synth.nu_initial(wr)
+    fp32 = wr.precision == "fp32"
+    if fp32:
+        pos_h = torch.from_numpy(synth.to_cell_offset(parts["pos64"], wr.box, wr.ngrid))
+        vel_h = torch.from_numpy(parts["vel"].astype(np.float32))
+    else:
+        pos_h = torch.from_numpy(parts["pos64"])
+        vel_h = torch.from_numpy(parts["vel"])
+    del parts
+    pos_h, vel_h = pos_h.pin_memory(), vel_h.pin_memory()
+    gen_s = time.time() - t0
+    pos = pos_h.to(dev, non_blocking=True)
+    vel = vel_h.to(dev, non_blocking=True)
+    hist_d = torch.from_numpy(np.ascontiguousarray(hist)).to(dev)
+    nk = wr.n_kbins
+    out_R = torch.zeros(nk, dtype=torch.float64, device=dev)
+    out_Pm = torch.zeros(nk, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    pm = nupm.PM(wr.ngrid, wr.npart, wr.box, wr.omega_cdm, wr.omega_nu, wr.h, wr.m_nu_total,
+                 wr.n_species, a_init=wr.a_init, n_kbins=nk, n_hist_max=wr.n_hist,
+                 precision=wr.precision, sqrtPnu_init=pi, theta_over_delta_init=ti, stream=stream)
+    a = wr.a_kick
+    K = pm.kick_factor(a, a * 1.01)
+
+    def step(p_, v_):
+        pm.deposit(p_)
+        pm.nu_response(a, a_hist, hist_d, None, out_R, None, out_Pm)
+        pm.kick(p_, v_, a, K)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(pos, vel)
+    pm.check()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pm.timing(True)
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(pos, vel)
+        ev1.record(stream)
+        barrier()
+    stages = pm.get_timing()
+    pm.timing(False)
+    pm.check()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    # end to end through the same API with host buffers: H2D positions and
+    # velocities, the kick, D2H velocities, every step
+    e2e = None
+    if not args.no_e2e:
+        vel_out = torch.empty_like(vel_h).pin_memory()
+        for _ in range(1):
+            pos.copy_(pos_h, non_blocking=True)
+            vel.copy_(vel_h, non_blocking=True)
+            step(pos, vel)
+            vel_out.copy_(vel, non_blocking=True)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            pos.copy_(pos_h, non_blocking=True)
+            vel.copy_(vel_h, non_blocking=True)
+            step(pos, vel)
+            vel_out.copy_(vel, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        bi = pos_h.numel() * pos_h.element_size() + vel_h.numel() * vel_h.element_size()
+        bo = vel_out.numel() * vel_out.element_size()
+        e2e = {"value": world * wr.npart / (ems / 1e3), "unit": "particle-kicks/s",
+               "ms_per_step": ems, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
+    # roofline of the dominant kernel (largest total time among the HBM passes)
+    hbm, peak_kind = peaks()
+    cand = {k: v for k, v in stages.items() if k != "response" and v[1] > 0}
+    dom = max(cand, key=lambda k: cand[k][0])
+    tot_ms, launches, calls = stages[dom]
+    per_launch_ms = tot_ms / max(launches, 1)
+    if dom in ("deposit", "bins"):
+        per_launch_ms = tot_ms / max(calls, 1)     # memset/reduce ride along in the stage
+    alg = stage_bytes(wr, dom)
+    achieved = alg / (per_launch_ms / 1e3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+            "traffic": traffic_from_profiles(dom, wr.name), "alg_bytes_per_launch": int(alg),
+            "ms_per_launch": round(per_launch_ms, 4)}
+    total_launch = sum(v[1] for v in stages.values())
+    step_alg = sum(stage_bytes(wr, k) * (v[2] if k in ("deposit", "bins") else v[1])
+                   for k, v in stages.items() if k != "response") / args.steps
+    res = dict(value=world * wr.npart / (ms / 1e3), ms_per_step=ms, e2e=e2e, roofline=roof,
+               stages={k: {"ms_per_step": round(v[0] / args.steps, 4), "launches_per_step": v[1] // args.steps}
+                       for k, v in stages.items()},
+               gpu_launches=int(total_launch), clocks=clk.summary(), gen_s=round(gen_s, 1),
+               step_alg_gb=round(step_alg / 1e9, 2),
+               step_frac=round(step_alg / (ms / 1e3) / 1e9 / hbm, 4),
+               device_bytes=pm.device_bytes())
+    pm.close()
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="pm1024_p512_fp32", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--verbose", action="store_true")
+    args = ap.parse_args()
+    w = synth.WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dtype = "f32" if w.precision == "fp32" else "f64"
+    config = {"workload": w.name, "grid": w.ngrid, "particles": w.npart, "box_mpc_h": w.box,
+              "m_nu_ev": w.m_nu_total, "n_species": w.n_species, "n_kbins": w.n_kbins,
+              "n_hist": w.n_hist, "a": w.a_kick, "positions": "int32 cell + fp32 offset"
+              if w.precision == "fp32" else "fp64", "response": "fp64",
+              "l2": "inputs larger than L2 (each grid >= 4 GB)", "parallelism": f"replicas x{args.gpus}"}
+    base = {"metric": "particle-kicks/s incl. neutrino response", "unit": "particle-kicks/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic (seeded BBKS Gaussian field, Zel'dovich particles)", "config": config}
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        s = oracle_sample(w)
+        for _ in range(args.warmup):
+            run_oracle_kick(s)
+        ts = []
+        for _ in range(args.steps):
+            t, npart = run_oracle_kick(s)
+            ts.append(t)
+        t = sum(ts) / len(ts)
+        v = npart / t
+        sample = f"oracle kick on {s.ngrid}^3 grid / {s.npart_side}^3 particles, box {s.box:g}"
+        line = dict(base, impl="reference", value=v, ms_per_step=t * 1e3,
+                    cpu_baseline={"value": v, "unit": "particle-kicks/s", "cores": 1, "kind": "oracle",
+                                  "sample": sample},
+                    e2e={"value": v, "unit": "particle-kicks/s", "h2d_bytes_per_step": 0,
+                         "d2h_bytes_per_step": 0})
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    res = run_gpu(args, w, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(w)
+        t, npart = run_oracle_kick(s)
+        cpu = {"value": npart / t, "unit": "particle-kicks/s", "cores": 1, "kind": "oracle",
+               "sample": f"one oracle kick on a {s.ngrid}^3 grid with {s.npart_side}^3 particles "
+                         f"(box {s.box:g} Mpc/h, same cell size, bins and history), {t:.1f} s"}
+    line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"], e2e=res["e2e"],
+                roofline=res["roofline"], cpu_baseline=cpu, gpu_launches=res["gpu_launches"],
+                clocks=res["clocks"], step_model_gb=res["step_alg_gb"], step_hbm_frac=res["step_frac"],
+                stages_ms=res["stages"])
+    print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

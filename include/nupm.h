@@ -1,0 +1,227 @@
+/*
+ * nupm.h -- C ABI of the GB300 particle-mesh (PM) long-range kick with
+ * Fourier-space massive neutrinos (Ali-Haimoud & Bird, arXiv:1209.0461).
+ *
+ * One kick = the paper's Sec. 4.3 steps (ii)-(iv) at one time step:
+ *   pm_deposit      fixed-point CIC deposit of the CDM particles, density
+ *                   contrast, forward 3-D FFT and the binned P_cdm(k)
+ *                   (Sec. 4.3 (ii));
+ *   pm_nu_response  the neutrino linear response per |k| bin, Eq. P-final with
+ *                   the initial-condition term of Eq. deltaI-nu and the
+ *                   single-iteration implicit solve of Sec. 4.3 (iii)/App. B;
+ *   pm_kick         delta_nu(k) = (P_nu/P_cdm)^{1/2} delta_cdm(k) (Eq. phases),
+ *                   delta_M = (1-f_nu) delta_cdm + f_nu delta_nu (Sec. 4.3 (iv)),
+ *                   Poisson (Eq. Poisson), gradient, inverse FFTs, CIC
+ *                   interpolation and u += acc * K.
+ *
+ * Units: lengths in Mpc/h, time in 1/H0 (H0 = 1), velocities u = a^2 dx/dt in
+ * H0 Mpc/h (100 km/s); superconformal time s = int dtau/a (Sec. 3.2).
+ *
+ * Memory: every pointer argument says HOST or DEVICE.  The context owns its
+ * grids and tables (allocated at pm_init on the current device); the caller
+ * owns particles, velocities and the stored spectra.  All GPU work is issued
+ * on the stream given to pm_init and is asynchronous with respect to the
+ * host; host arrays passed in are consumed before the call returns.
+ *
+ * Errors: every int-returning call returns PM_OK (0) or a negative PM_ERR_*
+ * code; pm_last_error() gives a message.  Nothing throws across the ABI.
+ * Host-side argument checks are reported by the call itself; conditions that
+ * only the GPU can see (an offset outside [0,1), a non-finite position, a
+ * fixed-point overflow) are recorded in a device status word and reported by
+ * pm_check(), which synchronises the stream.
+ */
+#ifndef NUPM_H
+#define NUPM_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NUPM_API __attribute__((visibility("default")))
+#else
+#define NUPM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define PM_OK               0
+#define PM_ERR_INVALID     -1   /* bad argument (NULL, size, non-finite parameter) */
+#define PM_ERR_RANGE       -2   /* value outside its domain (offset not in [0,1), a < a_init, ...) */
+#define PM_ERR_OVERFLOW    -3   /* fixed-point deposit cannot hold the particle count */
+#define PM_ERR_CUDA        -4   /* a CUDA runtime call failed */
+#define PM_ERR_ALLOC       -5   /* device allocation failed */
+#define PM_ERR_TIMEOUT     -6   /* a bounded device wait gave up (reserved) */
+#define PM_ERR_ORDER       -7   /* calls out of order (kick before deposit/response at this a) */
+#define PM_ERR_UNSUPPORTED -8   /* grid size / option not built */
+
+/* ---- precision of the grids, FFTs, positions and velocities ---- */
+#define PM_FP64 0   /* positions: double[3][npart] comoving [Mpc/h]; grids FP64;   */
+                    /* velocities double[3][npart]                                 */
+#define PM_FP32 1   /* positions: int32 words [6][npart]: rows 0-2 the grid cell   */
+                    /* index (any integer, wrapped), rows 3-5 the FP32 offset in   */
+                    /* [0,1) stored bit-for-bit; grids FP32; velocities float[3][n] */
+
+/* ---- flags ---- */
+#define PM_I_FIT       0x1u  /* use the App. C fitting formula (Eq. fit) for I(x) */
+#define PM_DECONV_CIC  0x2u  /* divide the Green function by prod sinc^4 (CIC windows) */
+
+/*
+ * Problem statement (Sec. 4.3-4.4, Table 1).  Omega_M = omega_cdm + omega_nu
+ * (baryons folded into cdm), flat: Omega_Lambda = 1 - Omega_M.
+ *   omega_nu < 0       -> derived as m_nu_total_eV / (93.14 eV h^2) (Sec. 2.1)
+ *   n_species          number of massive species (0..3); 0 or m_nu_total 0 -> no neutrinos
+ *   m_nu_eV[i]         species masses; all zero -> degenerate m_nu_total / n_species
+ *   particle_mass      uniform CDM particle mass (it cancels in delta; must be > 0)
+ *   a_init             a_i of Eq. deltaI-nu (start of the response integral)
+ *   n_kbins            log-spaced |k| bins on [2 pi/L, sqrt(3) pi N/L]
+ *   n_hist_max         capacity the caller's stored-spectrum table may reach
+ *   iters              implicit-solve iterations (Sec. 4.3 (iii), App. B), >= 1
+ *   quad_nodes         Gauss-Legendre nodes per panel of the response integral (4..16)
+ */
+typedef struct {
+  int32_t ngrid;          /* N: grid points per side (16..1024, power of two) */
+  int64_t npart;          /* number of CDM particles */
+  double box;             /* L [Mpc/h] */
+  double particle_mass;
+  double omega_cdm, omega_nu, h;
+  double m_nu_total_eV;
+  int32_t n_species;
+  double m_nu_eV[3];
+  double a_init;
+  int32_t n_kbins;
+  int32_t n_hist_max;
+  int32_t precision;      /* PM_FP64 | PM_FP32 */
+  uint32_t flags;
+  int32_t iters;
+  int32_t quad_nodes;
+} pm_params;
+
+typedef struct pm_ctx pm_ctx;   /* opaque */
+
+/* Fill *p with defaults (iters 1, quad_nodes 8, precision PM_FP64, no flags). */
+NUPM_API void pm_default_params(pm_params* p);
+
+/*
+ * Create a context on the current CUDA device.
+ *   sqrtPnu_init           HOST double[n_species][n_kbins]: P_nu,i^{1/2}(k_b) at a_init
+ *                          (Eq. deltaI-nu), or NULL for unperturbed neutrinos at a_init
+ *   theta_over_delta_init  HOST double[n_species][n_kbins]: [theta_nu/delta_nu]_i(k_b)
+ *                          in units of H0 (Eq. P-final), or NULL for 0
+ *   cuda_stream            cudaStream_t to issue all work on (NULL = legacy default)
+ *   out                    receives the context; NULL on failure
+ * Allocates the grids: FP32 4 N^2 (N/2) complex float, FP64 the same in double.
+ */
+NUPM_API int pm_init(const pm_params* params, const double* sqrtPnu_init,
+            const double* theta_over_delta_init, void* cuda_stream, pm_ctx** out);
+
+/*
+ * Steps a1-a3 (Sec. 4.3 (ii)): CIC deposit of `pos` (DEVICE, layout by
+ * precision, see PM_FP64/PM_FP32), delta = rho/rho_bar - 1, forward real 3-D
+ * FFT and the binned CDM power spectrum (kept in the context).
+ * Offsets outside [0,1) or non-finite positions set PM_ERR_RANGE in the
+ * device status (see pm_check); their particles are skipped.
+ */
+NUPM_API int pm_deposit(pm_ctx* ctx, const void* pos);
+
+/*
+ * Step a4 (Eq. P-final, Eq. deltaI-nu, Sec. 4.3 (iii), App. B) at scale factor a
+ * for every |k| bin, in FP64 on the GPU.
+ *   a_hist        HOST double[n_hist]: scale factors of the stored spectra,
+ *                 strictly increasing, a_init <= a_hist[0], a_hist[n-1] < a
+ *   sqrtPM_hist   DEVICE double[n_hist][n_kbins]: stored P_M^{1/2}(k_b, a_j)
+ *   n_hist        0..n_hist_max (0: initial-condition term only)
+ *   sqrtPnu_prev  DEVICE double[n_kbins]: P_nu^{1/2} of the previous step (the
+ *                 first-iteration guess of Sec. 4.3 (iii)), or NULL for the
+ *                 species-weighted initial value
+ *   ratio_out, sqrtPnu_out, sqrtPM_out
+ *                 DEVICE double[n_kbins] or NULL: R_b = P_nu^{1/2}/P_cdm^{1/2},
+ *                 P_nu^{1/2}(k_b, a), P_M^{1/2} = (1-f_nu) P_cdm^{1/2} + f_nu P_nu^{1/2}
+ *                 (the row the caller appends to its history).  Empty bins give 0.
+ * Requires pm_deposit first.  PM_ERR_RANGE for a < a_init or a bad history.
+ */
+NUPM_API int pm_nu_response(pm_ctx* ctx, double a, const double* a_hist, const double* sqrtPM_hist,
+                   int32_t n_hist, const double* sqrtPnu_prev, double* ratio_out,
+                   double* sqrtPnu_out, double* sqrtPM_out);
+
+/*
+ * Steps a5-a7 (Eq. phases, Sec. 4.3 (iv), Eq. Poisson): Green function with the
+ * neutrino factor (1-f_nu) + f_nu R(|k|), 4-point finite-difference gradient,
+ * inverse FFTs, CIC interpolation with the deposit's weights and
+ * vel += acc * kick_factor.
+ *   pos          DEVICE, the same particles as the last pm_deposit
+ *   vel          DEVICE, updated in place (double or float [3][npart] by precision)
+ *   a            must equal the a of the last pm_nu_response (else PM_ERR_ORDER)
+ *   kick_factor  K = int dt = int da/(a H) over the kick (pm_kick_factor)
+ *   acc_out      DEVICE [3][npart] (precision's float type) or NULL
+ */
+NUPM_API int pm_kick(pm_ctx* ctx, const void* pos, void* vel, double a, double kick_factor,
+            void* acc_out);
+
+/* Synchronise the stream and report the first device-side error recorded
+ * since the previous pm_check (then clear it). */
+NUPM_API int pm_check(pm_ctx* ctx);
+
+NUPM_API void pm_free(pm_ctx* ctx);
+NUPM_API const char* pm_last_error(const pm_ctx* ctx);
+
+/* K = int_{a0}^{a1} da / (a H(a)) and Delta s = int da / (a^3 H(a)) of the
+ * context's background, host FP64 (16-point Gauss-Legendre on panels of
+ * width <= 1/8 in ln a); NaN on error. */
+NUPM_API double pm_kick_factor(const pm_ctx* ctx, double a0, double a1);
+NUPM_API double pm_drift_factor(const pm_ctx* ctx, double a0, double a1);
+
+/* ---- inspection (tests, checkpointing) ---- */
+
+/* Binned CDM spectrum of the last pm_deposit, HOST double[n_kbins] each (any may
+ * be NULL): mode count sum w, sum w |k|, sum w |delta_k|^2 (w = 1 on the kx = 0
+ * and kx = N/2 planes, 2 elsewhere).  Synchronises the stream. */
+NUPM_API int pm_get_bins(pm_ctx* ctx, double* count, double* ksum, double* psum);
+
+/* Integer n^2 thresholds of the bins, HOST int64[n_kbins + 1]. */
+NUPM_API int pm_get_thresholds(const pm_ctx* ctx, int64_t* thresholds);
+
+/* Copy an internal field to DEVICE memory `dst` (stream-ordered):
+ *   PM_FIELD_DEPOSIT   uint64[N][N][N] fixed-point deposit (valid after pm_deposit,
+ *                      until pm_kick overwrites it)
+ *   PM_FIELD_DELTA_K   the forward spectrum, complex[N][N][N/2+1] unpacked
+ *                      (numpy rfftn layout), valid after pm_deposit
+ *   PM_FIELD_ACC_X/Y/Z the real acceleration grids [N][N][N], valid after pm_kick
+ * Element type is the precision's float type (complex = 2 of them). */
+#define PM_FIELD_DEPOSIT 0
+#define PM_FIELD_DELTA_K 1
+#define PM_FIELD_ACC_X   2
+#define PM_FIELD_ACC_Y   3
+#define PM_FIELD_ACC_Z   4
+NUPM_API int pm_copy_field(pm_ctx* ctx, int32_t which, void* dst);
+
+/* ---- per-stage timing (CUDA events on the context's stream) ----
+ * Stages of one kick, in launch order. */
+#define PM_ST_DEPOSIT    0   /* memset + CIC scatter */
+#define PM_ST_FFT_X_FWD  1
+#define PM_ST_FFT_Y_FWD  2
+#define PM_ST_FFT_Z_FWD  3
+#define PM_ST_BINS       4   /* P_cdm bins + fixed-order reduction */
+#define PM_ST_RESPONSE   5   /* neutrino response + Green table */
+#define PM_ST_GREEN      6
+#define PM_ST_FFT_Z_INV  7
+#define PM_ST_FFT_Y_INV  8
+#define PM_ST_FFT_X_INV  9
+#define PM_ST_INTERP    10   /* CIC gather + kick */
+#define PM_NSTAGES      11
+/* enable != 0: record an event pair around every stage from now on and
+ * clear the totals; 0: stop recording. */
+NUPM_API int pm_timing(pm_ctx* ctx, int32_t enable);
+/* Synchronise, then return per-stage totals since pm_timing(ctx, 1): HOST
+ * ms[PM_NSTAGES] (elapsed GPU time), launches[PM_NSTAGES] (kernel launches),
+ * calls[PM_NSTAGES] (times the stage ran); any pointer may be NULL. */
+NUPM_API int pm_get_timing(pm_ctx* ctx, double* ms, int64_t* launches, int64_t* calls);
+
+/* Bytes of device memory the context holds. */
+NUPM_API int64_t pm_device_bytes(const pm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NUPM_H */

@@ -411,7 +411,7 @@ def ic_term(kb, a, cosmo: Cosmo, m_ev: float, sqrtPnu_init, theta_over_delta_ini
 
 def nu_response(kb, sqrtPcdm, a, cosmo: Cosmo, a_hist, sqrtPM_hist,
                 sqrtPnu_init, theta_over_delta_init, sqrtPnu_prev=None,
-                iters: int = 1, I_func=nu_I, epsrel=1e-11):
+                iters: int = 1, I_func=nu_I, epsrel=1e-11, nonempty=None):
     """Neutrino response per |k| bin (Eq. P-final, Sec. 4.3 (iii)-(iv), App. B).
 
     Inputs per bin b (arrays of length nb):
@@ -430,9 +430,9 @@ def nu_response(kb, sqrtPcdm, a, cosmo: Cosmo, a_hist, sqrtPM_hist,
     the previous iteration's result afterwards (App. B).  Species results are
     weighted by Omega_nu,i / Omega_nu.
 
-    Returns dict(R, sqrtPnu, sqrtPM) where R = P_nu^{1/2} / P_cdm^{1/2} (0 for
-    empty bins, i.e. sqrtPcdm == 0) and sqrtPM = (1-f) P_cdm^{1/2} + f P_nu^{1/2}
-    (App. B first equation).
+    Returns dict(R, sqrtPnu, sqrtPM) where R = P_nu^{1/2} / P_cdm^{1/2} (0 where
+    P_cdm = 0) and sqrtPM = (1-f) P_cdm^{1/2} + f P_nu^{1/2} (App. B first
+    equation).  With ``nonempty`` given, bins without modes return zeros.
     """
     kb = np.asarray(kb, dtype=np.float64)
     sqrtPcdm = np.asarray(sqrtPcdm, dtype=np.float64)
@@ -442,7 +442,7 @@ def nu_response(kb, sqrtPcdm, a, cosmo: Cosmo, a_hist, sqrtPM_hist,
     f = cosmo.f_nu
     if cosmo.omega_nu <= 0 or masses.size == 0 or masses.sum() <= 0:
         z = np.zeros(nb)
-        return dict(R=z, sqrtPnu=z.copy(), sqrtPM=sqrtPcdm.copy())
+        return dict(R=z, sqrtPnu=z.copy(), sqrtPM=(1.0 - f) * sqrtPcdm)
     a_hist = np.asarray(a_hist, dtype=np.float64).reshape(-1)
     sqrtPM_hist = np.asarray(sqrtPM_hist, dtype=np.float64).reshape(a_hist.size, nb)
     Pi = np.asarray(sqrtPnu_init, dtype=np.float64).reshape(masses.size, nb)
@@ -470,7 +470,11 @@ def nu_response(kb, sqrtPcdm, a, cosmo: Cosmo, a_hist, sqrtPM_hist,
                                                 I_func, epsrel)
         pnu = ic + J
     R = np.where(sqrtPcdm > 0, pnu / np.where(sqrtPcdm > 0, sqrtPcdm, 1.0), 0.0)
-    return dict(R=R, sqrtPnu=pnu, sqrtPM=(1.0 - f) * sqrtPcdm + f * pnu)
+    pm = (1.0 - f) * sqrtPcdm + f * pnu
+    if nonempty is not None:           # bins without modes carry no spectrum
+        ne = np.asarray(nonempty, dtype=bool)
+        R, pnu, pm = (np.where(ne, q, 0.0) for q in (R, pnu, pm))
+    return dict(R=R, sqrtPnu=pnu, sqrtPM=pm)
 
 
 # --------------------------------------------------------------------------
@@ -579,7 +583,8 @@ def pm_kick(c, w, vel, ngrid, box, a, kick, cosmo: Cosmo, n_kbins, a_hist, sqrtP
     bins = bin_power(spec, box, n_kbins)
     sqrtPcdm = np.sqrt(bins["P"])
     resp = nu_response(bins["k"], sqrtPcdm, a, cosmo, a_hist, sqrtPM_hist, sqrtPnu_init,
-                       theta_over_delta_init, sqrtPnu_prev, iters, I_func, epsrel)
+                       theta_over_delta_init, sqrtPnu_prev, iters, I_func, epsrel,
+                       nonempty=bins["nonempty"])
     accs = green_gradient(spec, box, a, cosmo, bins["k"], resp["R"], bins["nonempty"],
                           deconvolve)
     acc = np.zeros((3, npart))

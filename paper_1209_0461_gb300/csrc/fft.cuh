@@ -1,0 +1,364 @@
+// Hand-written 3-D real FFT for the PM grid (sm_103a).
+//
+// Layout.  The half spectrum of an N^3 real field is kept PACKED: rows of
+// M = N/2 complex values, spec[z][y][x2], x2 in [0, M).  Slot x2 = 0 holds
+// X[0] + i X[N/2] of the x-transform (both real for real input), so every
+// row, column and plane is a power-of-two length.  After the y and z passes
+// that slot holds A(ky,kz) + i B(ky,kz), A/B the 2-D spectra of the kx = 0 and
+// kx = N/2 planes; consumers unpack them with the Hermitian pair at -k.
+//
+// One pass = one kernel that streams the whole array once (HBM bound):
+//   x pass: rows of N reals <-> M complex (N/2-point complex FFT + split step)
+//   y / z pass: W consecutive x2-columns x N elements along a strided axis.
+// Inside a CTA each column is transformed by NT = N/E threads that hold E
+// elements in registers; radix-R1 x R2 (x R3) Stockham stages exchange data
+// through padded shared memory.  Twiddles come from FP64-accurate host tables.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "consts.cuh"
+
+namespace nupm {
+
+template <typename T>
+struct alignas(2 * sizeof(T)) cx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cconj(cx<T> a) { return {a.x, -a.y}; }
+template <typename T>
+__device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return {a.x * s, a.y * s}; }
+
+// a * exp(DIR * 2 pi i k / R) with a compile-time R and (after unrolling) k.
+template <int R, int DIR, typename T>
+__device__ __forceinline__ cx<T> twid_const(cx<T> a, int k) {
+  if (k == 0) return a;
+  if (4 * k == R) return DIR < 0 ? cx<T>{a.y, -a.x} : cx<T>{-a.y, a.x};
+  const int j = k * (64 / R);
+  const T c = (T)cos64(j);
+  const T s = (T)DIR * (T)cos64(j + 48);   // sin(t) = cos(t + 3 pi / 2)
+  return {a.x * c - a.y * s, a.x * s + a.y * c};
+}
+
+// In-register DFT of length R (power of two <= 64), recursive radix-2
+// decimation in time.  DIR = -1 forward (exp(-i...)), +1 inverse; unscaled.
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft(cx<T>* v) {
+  if constexpr (R == 1) {
+    return;
+  } else if constexpr (R == 2) {
+    const cx<T> a = v[0], b = v[1];
+    v[0] = a + b;
+    v[1] = a - b;
+  } else {
+    cx<T> e[R / 2], o[R / 2];
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    dft<R / 2, DIR>(e);
+    dft<R / 2, DIR>(o);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      const cx<T> t = twid_const<R, DIR>(o[k], k);
+      v[k] = e[k] + t;
+      v[k + R / 2] = e[k] - t;
+    }
+  }
+}
+
+// Twiddle W_N^m (forward table exp(-2 pi i m / N)); conjugated for DIR = +1.
+__device__ __forceinline__ cx<float> ldg_cx(const cx<float>* p) {
+  const float2 q = __ldg(reinterpret_cast<const float2*>(p));
+  return {q.x, q.y};
+}
+__device__ __forceinline__ cx<double> ldg_cx(const cx<double>* p) {
+  const double2 q = __ldg(reinterpret_cast<const double2*>(p));
+  return {q.x, q.y};
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ cx<T> twid_table(const cx<T>* __restrict__ tw, int m) {
+  cx<T> w = ldg_cx(tw + m);
+  if (DIR > 0) w.y = -w.y;
+  return w;
+}
+
+// Radix plan per (precision, length).  E = R1 elements per thread; R2, R3
+// divide R1; NT = L / R1 threads per transform.
+template <typename T, int L>
+struct Plan;
+#define NUPM_PLAN(TT, L_, A, B, C) \
+  template <>                      \
+  struct Plan<TT, L_> {            \
+    static constexpr int R1 = A, R2 = B, R3 = C; \
+  };
+NUPM_PLAN(float, 8, 8, 1, 1)
+NUPM_PLAN(float, 16, 4, 4, 1)
+NUPM_PLAN(float, 32, 8, 4, 1)
+NUPM_PLAN(float, 64, 8, 8, 1)
+NUPM_PLAN(float, 128, 16, 8, 1)
+NUPM_PLAN(float, 256, 16, 16, 1)
+NUPM_PLAN(float, 512, 32, 16, 1)
+NUPM_PLAN(float, 1024, 32, 32, 1)
+NUPM_PLAN(double, 8, 8, 1, 1)
+NUPM_PLAN(double, 16, 4, 4, 1)
+NUPM_PLAN(double, 32, 8, 4, 1)
+NUPM_PLAN(double, 64, 8, 8, 1)
+NUPM_PLAN(double, 128, 16, 8, 1)
+NUPM_PLAN(double, 256, 16, 16, 1)
+NUPM_PLAN(double, 512, 16, 8, 4)
+NUPM_PLAN(double, 1024, 16, 16, 4)
+#undef NUPM_PLAN
+
+// ---------------------------------------------------------------------------
+// Stockham stage on register data.  A transform of length L is split into
+// L/R butterflies j; butterfly j (k = j mod NS) reads in[j + i L/R], applies
+// W_{NS R}^{i k}, does a radix-R DFT and writes out[(j/NS) NS R + k + i NS].
+// Thread t owns butterflies j = t + NT b.  SM provides ld(e)/st(e, v) on the
+// thread's own transform in shared memory.
+// ---------------------------------------------------------------------------
+template <typename T, int L, int E, int NT, int R, int NS, int DIR, bool FIRST, bool LAST, class SM>
+__device__ __forceinline__ void stockham_stage(cx<T> (&v)[E], const SM& sm, int t,
+                                               const cx<T>* __restrict__ tw) {
+  static_assert(E % R == 0, "radix must divide the per-thread element count");
+  if constexpr (!FIRST) {
+    // gather this stage's inputs (previous stage wrote shared memory)
+#pragma unroll
+    for (int b = 0; b < E / R; ++b) {
+      const int j = t + NT * b;
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[b * R + i] = sm.ld(j + i * (L / R));
+    }
+    if constexpr (!LAST) __syncthreads();   // reads done before in-place writes
+  }
+#pragma unroll
+  for (int b = 0; b < E / R; ++b) {
+    const int j = t + NT * b;
+    const int k = j & (NS - 1);
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int i = 1; i < R; ++i)
+        v[b * R + i] = cmul(v[b * R + i], twid_table<DIR>(tw, i * k * (L / (NS * R))));
+    }
+    dft<R, DIR>(&v[b * R]);
+    if constexpr (!LAST) {
+      const int o0 = (j / NS) * NS * R + k;
+#pragma unroll
+      for (int i = 0; i < R; ++i) sm.st(o0 + i * NS, v[b * R + i]);
+    }
+  }
+  if constexpr (!LAST) __syncthreads();
+}
+
+// Full transform of length L held as E = R1 registers per thread.  On entry v
+// holds in[t + NT i] (i < E); on exit v[b R_last + i] holds
+// out[(t + NT b) + i (L / R_last)].
+template <typename T, int L, int DIR, class SM>
+__device__ __forceinline__ void fft_regs(cx<T> (&v)[Plan<T, L>::R1], const SM& sm, int t,
+                                         const cx<T>* __restrict__ tw) {
+  constexpr int R1 = Plan<T, L>::R1, R2 = Plan<T, L>::R2, R3 = Plan<T, L>::R3;
+  constexpr int E = R1, NT = L / R1;
+  if constexpr (R2 == 1) {
+    stockham_stage<T, L, E, NT, R1, 1, DIR, true, true>(v, sm, t, tw);
+  } else if constexpr (R3 == 1) {
+    stockham_stage<T, L, E, NT, R1, 1, DIR, true, false>(v, sm, t, tw);
+    stockham_stage<T, L, E, NT, R2, R1, DIR, false, true>(v, sm, t, tw);
+  } else {
+    stockham_stage<T, L, E, NT, R1, 1, DIR, true, false>(v, sm, t, tw);
+    stockham_stage<T, L, E, NT, R2, R1, DIR, false, false>(v, sm, t, tw);
+    stockham_stage<T, L, E, NT, R3, R1 * R2, DIR, false, true>(v, sm, t, tw);
+  }
+}
+
+template <typename T, int L>
+__host__ __device__ constexpr int last_radix() {
+  return Plan<T, L>::R3 > 1 ? Plan<T, L>::R3 : (Plan<T, L>::R2 > 1 ? Plan<T, L>::R2 : Plan<T, L>::R1);
+}
+
+// Shared-memory view of one column of a W-column tile: element e of column c
+// at e*W + c + (e >> 5) * PAD (PAD breaks bank conflicts of the stage writes).
+template <typename T, int W, int PAD>
+struct ColSmem {
+  cx<T>* base;
+  int c;
+  __device__ __forceinline__ cx<T> ld(int e) const { return base[e * W + c + (e >> 5) * PAD]; }
+  __device__ __forceinline__ void st(int e, cx<T> v) const { base[e * W + c + (e >> 5) * PAD] = v; }
+  static constexpr int words(int L) { return L * W + ((L + 31) >> 5) * PAD; }
+};
+
+// Shared-memory view of one row: element e at e + (e >> 5) (one pad per 32).
+template <typename T>
+struct RowSmem {
+  cx<T>* base;
+  __device__ __forceinline__ cx<T> ld(int e) const { return base[e + (e >> 5)]; }
+  __device__ __forceinline__ void st(int e, cx<T> v) const { base[e + (e >> 5)] = v; }
+  static constexpr int words(int L) { return L + ((L + 31) >> 5); }
+};
+
+// Column tile width (consecutive x2 columns per CTA) and pad per plan.
+template <typename T, int N>
+struct ColCfg {
+  static constexpr int M = N / 2;
+  static constexpr int W0 = sizeof(T) == 4 ? 8 : 4;     // >= 64 B per row segment
+  static constexpr int NT = N / Plan<T, N>::R1;
+  // widen small transforms so a CTA has >= 128 threads, never past M columns
+  static constexpr int Wt = (W0 * NT < 128) ? (128 / NT) : W0;
+  static constexpr int W = Wt > M ? M : Wt;
+  static constexpr int THREADS = W * NT;
+  static constexpr int PAD = sizeof(T) == 4 ? 8 : 4;
+  static constexpr int SMEM_WORDS = ColSmem<T, W, PAD>::words(N);
+};
+
+// Rows per CTA of the x pass.
+template <typename T, int N>
+struct RowCfg {
+  static constexpr int M = N / 2;
+  static constexpr int NT = M / Plan<T, M>::R1;
+  static constexpr int ROWS = (256 / NT) > 0 ? (256 / NT) : 1;
+  static constexpr int THREADS = ROWS * NT;
+  static constexpr int ROW_WORDS = RowSmem<T>::words(M);
+};
+
+// ---------------------------------------------------------------------------
+// y / z pass: transform along a strided axis, in place.
+//   data + field * field_stride + blockIdx.y * other_stride + x2 + e * elem_stride
+// grid = (M / W, N, nfields)
+// ---------------------------------------------------------------------------
+template <typename T, int N, int DIR>
+__global__ void __launch_bounds__(ColCfg<T, N>::THREADS)
+k_fft_col(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
+          int64_t field_stride, const cx<T>* __restrict__ tw) {
+  using Cfg = ColCfg<T, N>;
+  constexpr int E = Plan<T, N>::R1, NT = N / E, W = Cfg::W, RL = last_radix<T, N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = threadIdx.x % W;
+  const int t = threadIdx.x / W;
+  cx<T>* col = data + (int64_t)blockIdx.z * field_stride + (int64_t)blockIdx.y * other_stride +
+               (int64_t)blockIdx.x * W + c;
+  ColSmem<T, W, Cfg::PAD> sm{reinterpret_cast<cx<T>*>(smem_raw), c};
+  cx<T> v[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) v[i] = col[(int64_t)(t + NT * i) * elem_stride];
+  fft_regs<T, N, DIR>(v, sm, t, tw);
+#pragma unroll
+  for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+    for (int i = 0; i < RL; ++i)
+      col[(int64_t)(t + NT * b + i * (N / RL)) * elem_stride] = v[b * RL + i];
+}
+
+// ---------------------------------------------------------------------------
+// Forward x pass: fixed-point deposit rows -> delta -> packed half spectrum.
+//   z[n] = delta[2n] + i delta[2n+1];  Z = FFT_M(z);
+//   X[k] = (Z[k] + conj Z[M-k]) / 2 - (i/2) W_N^k (Z[k] - conj Z[M-k]),
+//   packed slot 0 = X[0] + i X[M] = (Re Z0 + Im Z0) + i (Re Z0 - Im Z0).
+// delta = F * scale - 1 in FP64, rounded to T.  tw_m: W_M^m (m < M);
+// tw_n: W_N^k (k < M).  grid = (N^2 / ROWS)
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(RowCfg<T, N>::THREADS)
+k_fft_x_fwd(const unsigned long long* __restrict__ grid, cx<T>* __restrict__ spec, double scale,
+            const cx<T>* __restrict__ tw_m, const cx<T>* __restrict__ tw_n) {
+  using Cfg = RowCfg<T, N>;
+  constexpr int M = N / 2, E = Plan<T, M>::R1, NT = M / E, RL = last_radix<T, M>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int t = threadIdx.x % NT;
+  const int r = threadIdx.x / NT;
+  const int64_t row = (int64_t)blockIdx.x * Cfg::ROWS + r;
+  RowSmem<T> sm{reinterpret_cast<cx<T>*>(smem_raw) + r * Cfg::ROW_WORDS};
+  const ulonglong2* src = reinterpret_cast<const ulonglong2*>(grid + row * N);
+  cx<T> v[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const ulonglong2 q = src[t + NT * i];
+    v[i] = {(T)((double)q.x * scale - 1.0), (T)((double)q.y * scale - 1.0)};
+  }
+  fft_regs<T, M, -1>(v, sm, t, tw_m);
+  // natural-order Z to shared memory for the split step
+  if constexpr (Plan<T, M>::R2 > 1) __syncthreads();   // previous stage's readers are done
+#pragma unroll
+  for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+    for (int i = 0; i < RL; ++i) sm.st(t + NT * b + i * (M / RL), v[b * RL + i]);
+  __syncthreads();
+  cx<T>* dst = spec + row * M;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int k = t + NT * i;
+    const cx<T> zk = sm.ld(k);
+    cx<T> out;
+    if (k == 0) {
+      out = {zk.x + zk.y, zk.x - zk.y};
+    } else {
+      const cx<T> zm = cconj(sm.ld(M - k));
+      const cx<T> ev = cscale(zk + zm, (T)0.5);
+      const cx<T> od = cscale(zk - zm, (T)0.5);           // = i O[k]
+      const cx<T> w = twid_table<-1>(tw_n, k);
+      const cx<T> wo = cmul(w, od);
+      out = {ev.x + wo.y, ev.y - wo.x};                     // ev - i * wo
+    }
+    dst[k] = out;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse x pass, in place: packed half-spectrum rows -> N reals (unscaled):
+//   Z'[k] = (X[k] + conj X[M-k]) + i W_N^{-k} (X[k] - conj X[M-k]),
+//   Z'[0] = (X0 + XM) + i (X0 - XM) with X0 = Re P0, XM = Im P0;
+//   z = IFFT_M(Z');  x[2n] = Re z[n], x[2n+1] = Im z[n].
+// grid = (rows / ROWS, 1, nfields); rows = N^2.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(RowCfg<T, N>::THREADS)
+k_fft_x_inv(cx<T>* __restrict__ data, int64_t field_stride, const cx<T>* __restrict__ tw_m,
+            const cx<T>* __restrict__ tw_n) {
+  using Cfg = RowCfg<T, N>;
+  constexpr int M = N / 2, E = Plan<T, M>::R1, NT = M / E, RL = last_radix<T, M>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int t = threadIdx.x % NT;
+  const int r = threadIdx.x / NT;
+  const int64_t row = (int64_t)blockIdx.x * Cfg::ROWS + r;
+  RowSmem<T> sm{reinterpret_cast<cx<T>*>(smem_raw) + r * Cfg::ROW_WORDS};
+  cx<T>* rowp = data + (int64_t)blockIdx.z * field_stride + row * M;
+#pragma unroll
+  for (int i = 0; i < E; ++i) sm.st(t + NT * i, rowp[t + NT * i]);
+  __syncthreads();
+  cx<T> v[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int k = t + NT * i;
+    const cx<T> xk = sm.ld(k);
+    if (k == 0) {
+      v[i] = {xk.x + xk.y, xk.x - xk.y};
+    } else {
+      const cx<T> xm = cconj(sm.ld(M - k));
+      const cx<T> s = xk + xm;
+      const cx<T> d = cmul(twid_table<+1>(tw_n, k), xk - xm);
+      v[i] = {s.x - d.y, s.y + d.x};                       // s + i d
+    }
+  }
+  __syncthreads();   // the stages reuse this row's shared memory
+  fft_regs<T, M, +1>(v, sm, t, tw_m);
+  T* out = reinterpret_cast<T*>(rowp);
+#pragma unroll
+  for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+      const int n = t + NT * b + i * (M / RL);
+      reinterpret_cast<cx<T>*>(out)[n] = v[b * RL + i];    // (x[2n], x[2n+1])
+    }
+}
+
+}  // namespace nupm

@@ -1,0 +1,150 @@
+// Launchers of the grid kernels for one precision.  Included by grid_f32.cu
+// and grid_f64.cu with NUPM_T set to float / double (one translation unit per
+// precision so the two compile in parallel).
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "grid_kernels.cuh"
+#include "nupm_internal.h"
+
+namespace nupm {
+namespace {
+
+using T = NUPM_T;
+using C = cx<T>;
+constexpr int kSMs = 152;
+
+// Opt the FFT kernels of size N into their dynamic shared memory (once per
+// process; every kernel of this size gets its attribute on first use).
+template <int N>
+void ensure_attrs() {
+  using RC = RowCfg<T, N>;
+  using CC = ColCfg<T, N>;
+  static bool done = false;
+  if (done) return;
+  const int row_smem = (int)((size_t)RC::ROWS * RC::ROW_WORDS * sizeof(C));
+  const int col_smem = (int)((size_t)CC::SMEM_WORDS * sizeof(C));
+  cudaFuncSetAttribute(k_fft_x_fwd<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
+  cudaFuncSetAttribute(k_fft_col<T, N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+  cudaFuncSetAttribute(k_fft_col<T, N, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+  cudaFuncSetAttribute(k_fft_x_inv<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
+  done = true;
+}
+
+// One FFT pass of size N (pass: kPassXFwd .. kPassXInv, see nupm_internal.h).
+template <int N>
+void fft_pass_n(const GridArgs& g, int pass, cudaStream_t s) {
+  constexpr int M = N / 2;
+  using RC = RowCfg<T, N>;
+  using CC = ColCfg<T, N>;
+  const size_t row_smem = (size_t)RC::ROWS * RC::ROW_WORDS * sizeof(C);
+  const size_t col_smem = (size_t)CC::SMEM_WORDS * sizeof(C);
+  ensure_attrs<N>();
+  const int64_t rows = (int64_t)N * N;
+  const C* twn = reinterpret_cast<const C*>(g.tw_n);
+  const C* twm = reinterpret_cast<const C*>(g.tw_m);
+  C* spec = reinterpret_cast<C*>(g.spec);
+  C* f = reinterpret_cast<C*>(g.g);
+  // y pass: columns (x2, z), element stride M; z pass: columns (x2, y), stride N M
+  switch (pass) {
+    case kPassXFwd:
+      k_fft_x_fwd<T, N><<<(unsigned)(rows / RC::ROWS), RC::THREADS, row_smem, s>>>(
+          reinterpret_cast<const unsigned long long*>(g.g), spec, g.scale, twm, twn);
+      break;
+    case kPassYFwd:
+      k_fft_col<T, N, -1><<<dim3(M / CC::W, N, 1), CC::THREADS, col_smem, s>>>(spec, (int64_t)N * M, (int64_t)M, 0, twn);
+      break;
+    case kPassZFwd:
+      k_fft_col<T, N, -1><<<dim3(M / CC::W, N, 1), CC::THREADS, col_smem, s>>>(spec, (int64_t)M, (int64_t)N * M, 0, twn);
+      break;
+    case kPassZInv:
+      k_fft_col<T, N, +1><<<dim3(M / CC::W, N, 3), CC::THREADS, col_smem, s>>>(f, (int64_t)M, (int64_t)N * M,
+                                                                             g.field_elems, twn);
+      break;
+    case kPassYInv:
+      k_fft_col<T, N, +1><<<dim3(M / CC::W, N, 3), CC::THREADS, col_smem, s>>>(f, (int64_t)N * M, (int64_t)M,
+                                                                             g.field_elems, twn);
+      break;
+    case kPassXInv:
+      k_fft_x_inv<T, N><<<dim3((unsigned)(rows / RC::ROWS), 1, 3), RC::THREADS, row_smem, s>>>(f, g.field_elems, twm, twn);
+      break;
+  }
+}
+
+#define NUPM_DISPATCH(fn)                                  \
+  switch (g.n) {                                           \
+    case 16: fn<16>(g, pass, s); break;                    \
+    case 32: fn<32>(g, pass, s); break;                    \
+    case 64: fn<64>(g, pass, s); break;                    \
+    case 128: fn<128>(g, pass, s); break;                  \
+    case 256: fn<256>(g, pass, s); break;                  \
+    case 512: fn<512>(g, pass, s); break;                  \
+    case 1024: fn<1024>(g, pass, s); break;                \
+    default: return PM_ERR_UNSUPPORTED;                    \
+  }
+
+int grid_blocks(int64_t work, int threads) {
+  int64_t b = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)kSMs * 16;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+#define NUPM_CAT2(a, b) a##b
+#define NUPM_CAT(a, b) NUPM_CAT2(a, b)
+#define NUPM_FN(name) NUPM_CAT(name, NUPM_SFX)
+
+int NUPM_FN(deposit)(const GridArgs& g, const void* pos, cudaStream_t s) {
+  cudaMemsetAsync(g.g, 0, (size_t)g.n * g.n * g.n * sizeof(unsigned long long), s);
+  if (g.np > 0)
+    k_deposit<T><<<grid_blocks(g.np, 256), 256, 0, s>>>(pos, g.np, g.n, g.delta,
+                                                       reinterpret_cast<unsigned long long*>(g.g), g.status);
+  return PM_OK;
+}
+
+int NUPM_FN(fft_pass)(const GridArgs& g, int pass, cudaStream_t s) {
+  NUPM_DISPATCH(fft_pass_n)
+  return PM_OK;
+}
+
+int NUPM_FN(bins)(const GridArgs& g, int nk, const long long* T_, double kf, double* partials, int nblk,
+                  double* out, cudaStream_t s) {
+  const size_t sh = 3 * (size_t)nk * sizeof(double) + (size_t)(nk + 1) * sizeof(long long);
+  k_bin_power<T><<<nblk, 256, sh, s>>>(reinterpret_cast<const C*>(g.spec), g.n, nk, T_, kf, partials);
+  k_bin_reduce<<<(3 * nk + 127) / 128, 128, 0, s>>>(partials, nblk, nk, out);
+  return PM_OK;
+}
+
+int NUPM_FN(green)(const GridArgs& g, const void* gtab, const void* dtab, const void* wtab, cudaStream_t s) {
+  const int64_t total = (int64_t)g.n * g.n * (g.n / 2);
+  k_green<T><<<grid_blocks(total, 256), 256, 0, s>>>(reinterpret_cast<const C*>(g.spec), reinterpret_cast<C*>(g.g),
+                                                    g.field_elems, g.n, reinterpret_cast<const T*>(gtab),
+                                                    reinterpret_cast<const T*>(dtab),
+                                                    reinterpret_cast<const T*>(wtab));
+  return PM_OK;
+}
+
+int NUPM_FN(interp)(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, cudaStream_t s) {
+  if (g.np > 0)
+    k_interp_kick<T><<<grid_blocks(g.np, 256), 256, 0, s>>>(pos, g.np, g.n, g.delta, reinterpret_cast<const T*>(g.g),
+                                                           2 * g.field_elems, reinterpret_cast<T*>(vel), (T)kick,
+                                                           reinterpret_cast<T*>(acc_out), g.status);
+  return PM_OK;
+}
+
+int NUPM_FN(unpack)(const GridArgs& g, void* dst, cudaStream_t s) {
+  const int64_t total = (int64_t)g.n * g.n * (g.n / 2 + 1);
+  k_unpack_spec<T><<<grid_blocks(total, 256), 256, 0, s>>>(reinterpret_cast<const C*>(g.spec),
+                                                          reinterpret_cast<C*>(dst), g.n);
+  return PM_OK;
+}
+
+#undef NUPM_FN
+#undef NUPM_CAT
+#undef NUPM_CAT2
+#undef NUPM_DISPATCH
+
+}  // namespace nupm

@@ -1,0 +1,294 @@
+// Particle and spectrum kernels of the PM kick (sm_103a), templated on the
+// grid precision T (float: PM_FP32, double: PM_FP64).
+//
+//   k_deposit      fixed-point CIC scatter (Sec. 4.3 (ii)), 64-bit integer atomics
+//   k_bin_power    per-|k|-bin sums of the forward spectrum (P_cdm, Sec. 4.3 (ii))
+//   k_green        delta_M = delta_cdm [(1-f) + f R(|k|)] (Eq. phases, Sec. 4.3 (iv)),
+//                  Poisson (Eq. Poisson), 4-point gradient -> 3 spectra
+//   k_interp_kick  CIC gather of the 3 force grids, u += acc * K
+//   k_unpack_spec  packed half spectrum -> rfftn layout (inspection only)
+#pragma once
+#include <stdint.h>
+
+#include "fft.cuh"
+#include "nupm_internal.h"
+
+namespace nupm {
+
+constexpr int kWeightBits = 16;
+constexpr int kWeightOne = 1 << kWeightBits;
+
+// Record the first device-side error (status 0 -> code).
+__device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+__device__ __forceinline__ int wrap_index(long long c, int n) {
+  long long r = c % n;
+  return (int)(r < 0 ? r + n : r);
+}
+
+// Quantised particle: cell (wrapped) and 16-bit weight per axis.  Returns
+// false (and records PM_ERR_RANGE) for an invalid particle.
+template <typename T>
+struct Quant;
+
+template <>
+struct Quant<double> {   // FP64 comoving positions, double[3][np]
+  __device__ static __forceinline__ bool get(const void* pos, int64_t np, int64_t p, int n,
+                                             double delta, int (&c)[3], int (&w)[3], int* status) {
+    const double* x = reinterpret_cast<const double*>(pos);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double u = x[d * np + p] / delta;          // same IEEE division as the definition
+      if (!(fabs(u) < 4503599627370496.0)) {           // non-finite or |u| >= 2^52
+        set_status(status, PM_ERR_RANGE);
+        return false;
+      }
+      const double cf = floor(u);
+      const double o = u - cf;                         // exact
+      w[d] = (int)floor(o * (double)kWeightOne);
+      c[d] = wrap_index((long long)cf, n);
+    }
+    return true;
+  }
+};
+
+template <>
+struct Quant<float> {    // int32 words [6][np]: cells rows 0-2, FP32 offsets rows 3-5
+  __device__ static __forceinline__ bool get(const void* pos, int64_t np, int64_t p, int n,
+                                             double, int (&c)[3], int (&w)[3], int* status) {
+    const int32_t* q = reinterpret_cast<const int32_t*>(pos);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float o = __int_as_float(q[(3 + d) * np + p]);
+      if (!(o >= 0.0f && o < 1.0f)) {
+        set_status(status, PM_ERR_RANGE);
+        return false;
+      }
+      w[d] = (int)floorf(o * (float)kWeightOne);       // exact scaling by 2^16
+      c[d] = wrap_index((long long)q[d * np + p], n);
+    }
+    return true;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// a1: CIC deposit.  Corner (dx,dy,dz) of cell c gets prod_d (dx ? w_d : 2^16 - w_d).
+// Integer addition is associative, so the grid is bit-exact in any order.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_deposit(const void* __restrict__ pos, int64_t np, int n, double delta,
+                          unsigned long long* __restrict__ grid, int* status) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int c[3], w[3];
+    if (!Quant<T>::get(pos, np, p, n, delta, c, w, status)) continue;
+    const unsigned long long wx[2] = {(unsigned long long)(kWeightOne - w[0]), (unsigned long long)w[0]};
+    const unsigned long long wy[2] = {(unsigned long long)(kWeightOne - w[1]), (unsigned long long)w[1]};
+    const unsigned long long wz[2] = {(unsigned long long)(kWeightOne - w[2]), (unsigned long long)w[2]};
+    const int x1 = c[0] + 1 == n ? 0 : c[0] + 1;
+    const int y1 = c[1] + 1 == n ? 0 : c[1] + 1;
+    const int z1 = c[2] + 1 == n ? 0 : c[2] + 1;
+    const int xs[2] = {c[0], x1}, ys[2] = {c[1], y1}, zs[2] = {c[2], z1};
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const unsigned long long wzy = wz[dz] * wy[dy];
+        const int64_t rowi = ((int64_t)zs[dz] * n + ys[dy]) * n;
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          const unsigned long long wt = wzy * wx[dx];
+          if (wt) atomicAdd(grid + rowi + xs[dx], wt);
+        }
+      }
+  }
+}
+
+// Signed frequency of index i on an n-point axis.
+__device__ __forceinline__ int signed_freq(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// Bin of integer n^2 (thresholds T[0..nk], T_b <= n2 < T_{b+1}); -1 if none.
+__device__ __forceinline__ int find_bin(const long long* T, int nk, long long n2) {
+  if (n2 < T[0] || n2 >= T[nk]) return -1;
+  int lo = 0, hi = nk;   // T[lo] <= n2 < T[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (T[mid] <= n2) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// a3: binned power of the packed spectrum.  Rows (z, y) are strided over the
+// grid; each CTA accumulates per-bin (count, ksum, psum) in shared memory and
+// writes one partial row; k_bin_reduce sums the partials in a fixed order.
+// The packed slot x2 = 0 is unpacked with the row at (-z, -y):
+//   A = (F(k) + conj F(-k)) / 2   (kx = 0),  B = (F(k) - conj F(-k)) / (2i)  (kx = N/2).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_bin_power(const cx<T>* __restrict__ spec, int n, int nk,
+                            const long long* __restrict__ thresholds, double kf,
+                            double* __restrict__ partials) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* acc = reinterpret_cast<double*>(smem_raw);             // [3][nk]
+  long long* thr = reinterpret_cast<long long*>(acc + 3 * nk);   // [nk + 1]
+  for (int i = threadIdx.x; i < 3 * nk; i += blockDim.x) acc[i] = 0.0;
+  for (int i = threadIdx.x; i <= nk; i += blockDim.x) thr[i] = thresholds[i];
+  __syncthreads();
+  const int m = n / 2;
+  const int64_t rows = (int64_t)n * n;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int iz = (int)(row / n), iy = (int)(row % n);
+    const long long kz = signed_freq(iz, n), ky = signed_freq(iy, n);
+    const long long base2 = kz * kz + ky * ky;
+    const cx<T>* r = spec + row * m;
+    for (int x2 = threadIdx.x; x2 < m; x2 += blockDim.x) {
+      const cx<T> f = r[x2];
+      if (x2 > 0) {
+        const long long n2 = base2 + (long long)x2 * x2;
+        const int b = find_bin(thr, nk, n2);
+        if (b >= 0) {
+          const double p = (double)f.x * f.x + (double)f.y * f.y;
+          atomicAdd(&acc[b], 2.0);
+          atomicAdd(&acc[nk + b], 2.0 * kf * sqrt((double)n2));
+          atomicAdd(&acc[2 * nk + b], 2.0 * p);
+        }
+      } else {
+        const int jz = (n - iz) % n, jy = (n - iy) % n;
+        const cx<T> g = spec[((int64_t)jz * n + jy) * m];
+        const double ax = 0.5 * ((double)f.x + g.x), ay = 0.5 * ((double)f.y - g.y);
+        const double bx = 0.5 * ((double)f.y + g.y), by = -0.5 * ((double)f.x - g.x);
+        const long long n2a = base2, n2b = base2 + (long long)m * m;
+        const int ba = find_bin(thr, nk, n2a);
+        if (ba >= 0) {
+          atomicAdd(&acc[ba], 1.0);
+          atomicAdd(&acc[nk + ba], kf * sqrt((double)n2a));
+          atomicAdd(&acc[2 * nk + ba], ax * ax + ay * ay);
+        }
+        const int bb = find_bin(thr, nk, n2b);
+        if (bb >= 0) {
+          atomicAdd(&acc[bb], 1.0);
+          atomicAdd(&acc[nk + bb], kf * sqrt((double)n2b));
+          atomicAdd(&acc[2 * nk + bb], bx * bx + by * by);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * nk; i += blockDim.x) partials[(int64_t)blockIdx.x * 3 * nk + i] = acc[i];
+}
+
+// ---------------------------------------------------------------------------
+// a5: Green function + gradient.  phi = G(n^2) [D^-4] delta_cdm with the
+// neutrino factor folded into G(n^2) (k_green_table), acc_c = -i D_c(k) phi.
+// grid-stride over all modes of the packed spectrum; writes 3 packed spectra.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out, int64_t field_stride,
+                        int n, const T* __restrict__ gtab, const T* __restrict__ dtab,
+                        const T* __restrict__ wtab /* 1/sinc^4 per index or nullptr */) {
+  const int m = n / 2;
+  const int64_t total = (int64_t)n * n * m;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int x2 = (int)(idx % m);
+    const int64_t row = idx / m;
+    const int iz = (int)(row / n), iy = (int)(row % n);
+    const long long kz = signed_freq(iz, n), ky = signed_freq(iy, n);
+    const long long base2 = kz * kz + ky * ky;
+    const T dy = dtab[iy], dz = dtab[iz];
+    const cx<T> f = spec[idx];
+    cx<T> o0, o1, o2;
+    if (x2 > 0) {
+      T g = gtab[base2 + (long long)x2 * x2];
+      if (wtab) g *= wtab[x2] * wtab[iy] * wtab[iz];
+      const cx<T> phi = cscale(f, g);
+      const T dx = dtab[x2];
+      o0 = {dx * phi.y, -dx * phi.x};
+      o1 = {dy * phi.y, -dy * phi.x};
+      o2 = {dz * phi.y, -dz * phi.x};
+    } else {
+      const int jz = (n - iz) % n, jy = (n - iy) % n;
+      const cx<T> h = spec[((int64_t)jz * n + jy) * m];
+      const cx<T> A = {(T)0.5 * (f.x + h.x), (T)0.5 * (f.y - h.y)};
+      const cx<T> B = {(T)0.5 * (f.y + h.y), (T)-0.5 * (f.x - h.x)};
+      T ga = gtab[base2], gb = gtab[base2 + (long long)m * m];
+      if (wtab) {
+        const T wyz = wtab[iy] * wtab[iz];
+        ga *= wtab[0] * wyz;
+        gb *= wtab[m] * wyz;
+      }
+      const cx<T> pa = cscale(A, ga), pb = cscale(B, gb);
+      const T dxa = dtab[0], dxb = dtab[m];
+      // acc spectra of the kx = 0 (a) and kx = N/2 (b) modes, repacked as a + i b
+      const cx<T> a0 = {dxa * pa.y, -dxa * pa.x}, b0 = {dxb * pb.y, -dxb * pb.x};
+      const cx<T> a1 = {dy * pa.y, -dy * pa.x}, b1 = {dy * pb.y, -dy * pb.x};
+      const cx<T> a2 = {dz * pa.y, -dz * pa.x}, b2 = {dz * pb.y, -dz * pb.x};
+      o0 = {a0.x - b0.y, a0.y + b0.x};
+      o1 = {a1.x - b1.y, a1.y + b1.x};
+      o2 = {a2.x - b2.y, a2.y + b2.x};
+    }
+    out[idx] = o0;
+    out[field_stride + idx] = o1;
+    out[2 * field_stride + idx] = o2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a7: CIC interpolation of the three real force grids (same quantised
+// weights as the deposit) and the kick u += acc * K.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_interp_kick(const void* __restrict__ pos, int64_t np, int n, double delta,
+                              const T* __restrict__ grids, int64_t field_stride, T* __restrict__ vel,
+                              T kick, T* __restrict__ acc_out, int* status) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int c[3], w[3];
+    if (!Quant<T>::get(pos, np, p, n, delta, c, w, status)) continue;
+    const T inv = (T)1.0 / (T)kWeightOne;
+    const T fx1 = (T)w[0] * inv, fy1 = (T)w[1] * inv, fz1 = (T)w[2] * inv;
+    const T fx0 = (T)1 - fx1, fy0 = (T)1 - fy1, fz0 = (T)1 - fz1;
+    const int x1 = c[0] + 1 == n ? 0 : c[0] + 1;
+    const int y1 = c[1] + 1 == n ? 0 : c[1] + 1;
+    const int z1 = c[2] + 1 == n ? 0 : c[2] + 1;
+    const int64_t r00 = ((int64_t)c[2] * n + c[1]) * n, r01 = ((int64_t)c[2] * n + y1) * n;
+    const int64_t r10 = ((int64_t)z1 * n + c[1]) * n, r11 = ((int64_t)z1 * n + y1) * n;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T* g = grids + d * field_stride;
+      const T v00 = fx0 * g[r00 + c[0]] + fx1 * g[r00 + x1];
+      const T v01 = fx0 * g[r01 + c[0]] + fx1 * g[r01 + x1];
+      const T v10 = fx0 * g[r10 + c[0]] + fx1 * g[r10 + x1];
+      const T v11 = fx0 * g[r11 + c[0]] + fx1 * g[r11 + x1];
+      const T a = fz0 * (fy0 * v00 + fy1 * v01) + fz1 * (fy0 * v10 + fy1 * v11);
+      vel[d * np + p] += a * kick;
+      if (acc_out) acc_out[d * np + p] = a;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inspection: packed [N][N][M] -> rfftn layout [N][N][M+1].
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_unpack_spec(const cx<T>* __restrict__ spec, cx<T>* __restrict__ dst, int n) {
+  const int m = n / 2;
+  const int64_t total = (int64_t)n * n * (m + 1);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(idx % (m + 1));
+    const int64_t row = idx / (m + 1);
+    if (kx > 0 && kx < m) {
+      dst[idx] = spec[row * m + kx];
+    } else {
+      const int iz = (int)(row / n), iy = (int)(row % n);
+      const int jz = (n - iz) % n, jy = (n - iy) % n;
+      const cx<T> f = spec[row * m], h = spec[((int64_t)jz * n + jy) * m];
+      if (kx == 0) dst[idx] = {(T)0.5 * (f.x + h.x), (T)0.5 * (f.y - h.y)};
+      else dst[idx] = {(T)0.5 * (f.y + h.y), (T)-0.5 * (f.x - h.x)};
+    }
+  }
+}
+
+}  // namespace nupm

@@ -1,0 +1,81 @@
+// Internal declarations shared by the host API and the kernel translation
+// units of libnupm.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nupm.h"
+
+namespace nupm {
+
+constexpr double kCOverH0 = 2997.92458;   // c / H0 [Mpc/h]
+constexpr double kTnu0eV = 1.68e-4;       // T_nu,0 [eV], Sec. 2.1 (value as printed)
+constexpr double kOmegaNuEv = 93.14;      // Omega_nu h^2 = sum m / 93.14 eV, Sec. 2.1
+constexpr int kMaxQuad = 16;
+constexpr int kMaxPanels = 320;           // history nodes + graded points + ends
+
+// Device inputs of the response kernels (one struct, passed by value).
+struct NuArgs {
+  int nk, ns, n_hist, quad, iters, use_fit, ngrid;
+  double a, ue, ui, s_end;        // a, ln a, ln a_i, s(a) - s(a_i)
+  double omega_m, omega_l, f_nu, a_init, box;
+  double kappa_scale[3];          // c/H0 * T_nu0 / m_s (x = kappa_scale k (s - s'))
+  double w_species[3];            // Omega_nu,s / Omega_nu
+  const double* bins;             // [3][nk] count, ksum, psum
+  const double* hist_u;           // [n_hist] ln a_j
+  const double* hist;             // [n_hist][nk] P_M^{1/2}
+  const double* prev;             // [nk] or nullptr
+  const double* pnu_init;         // [ns][nk]
+  const double* theta_init;       // [ns][nk]
+  const double* stab;             // s-table: [n_stab][2] (s, ds/du) on a uniform u grid
+  int n_stab;
+  double stab_u0, stab_inv_h, stab_h;
+  const double* gl;               // [2][quad] nodes, weights on [-1, 1]
+  double* parts;                  // [ns][nk][3] IC, J_hist, W_cur
+  double* R;                      // [nk]
+  double* pnu;                    // [nk]
+  double* pm;                     // [nk]
+  double* R_user;                 // optional copies
+  double* pnu_user;
+  double* pm_user;
+};
+
+void launch_nu_response(const NuArgs& a, cudaStream_t s);
+// Green table G(n^2), n^2 = 0..n2max, precision T; coeff = -1.5 Om / (a kf^2 N^3)
+void launch_green_table(bool fp64, void* gtab, long long n2max, double kf, double coeff,
+                        double f_nu, const double* R, const double* bins, int nk, cudaStream_t s);
+
+// FFT passes in launch order of one kick
+constexpr int kPassXFwd = 0, kPassYFwd = 1, kPassZFwd = 2, kPassZInv = 3, kPassYInv = 4, kPassXInv = 5;
+
+// precision-dispatched grid launchers (grid_f32.cu / grid_f64.cu)
+struct GridArgs {
+  int n;
+  int64_t np;
+  double box, delta, scale;       // scale = N^3 / (Np 2^48)
+  void* spec;                     // packed spectrum [N][N][M]
+  void* g;                        // 3 packed fields (deposit grid aliases the first two)
+  int64_t field_elems;            // N*N*M complex elements per field
+  const void* tw_n;               // W_N^m, m < N
+  const void* tw_m;               // W_M^m, m < M
+  int* status;
+};
+#define NUPM_DECLARE_GRID(SFX)                                                              \
+  int deposit##SFX(const GridArgs& g, const void* pos, cudaStream_t s);                     \
+  int fft_pass##SFX(const GridArgs& g, int pass, cudaStream_t s);                           \
+  int bins##SFX(const GridArgs& g, int nk, const long long* T, double kf, double* partials,  \
+                int nblk, double* out, cudaStream_t s);                                     \
+  int green##SFX(const GridArgs& g, const void* gtab, const void* dtab, const void* wtab,    \
+                 cudaStream_t s);                                                           \
+  int interp##SFX(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, \
+                  cudaStream_t s);                                                          \
+  int unpack##SFX(const GridArgs& g, void* dst, cudaStream_t s);
+NUPM_DECLARE_GRID(_f32)
+NUPM_DECLARE_GRID(_f64)
+#undef NUPM_DECLARE_GRID
+
+__global__ void k_bin_reduce(const double* __restrict__ partials, int nblk, int nk,
+                             double* __restrict__ out);
+
+
+}  // namespace nupm

@@ -1,0 +1,786 @@
+// Host side of the C ABI declared in include/nupm.h: argument checks,
+// context and device memory, FP64 host tables, and the launch sequence of
+// one kick (Sec. 4.3 steps (ii)-(iv) of the paper).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "nupm_internal.h"
+
+using namespace nupm;
+
+struct pm_ctx {
+  pm_params p{};
+  cudaStream_t stream = nullptr;
+  bool fp64 = true;
+  int n = 0, m = 0, nk = 0, ns = 0, quad = 8, iters = 1;
+  int64_t np = 0;
+  double box = 0, delta = 0, kf = 0, omega_m = 0, omega_l = 0, omega_nu = 0, f_nu = 0, a_init = 0;
+  double mass[3] = {0, 0, 0}, wsp[3] = {0, 0, 0};
+  int64_t n2max = 0, field_elems = 0;
+  size_t cplx = 0;            // bytes of one complex element
+  int nblk_bins = 0;
+  // device memory
+  void* spec = nullptr;       // packed spectrum
+  void* g = nullptr;          // 3 packed fields (deposit grid aliases the first two)
+  void* tw_n = nullptr;
+  void* tw_m = nullptr;
+  long long* d_thr = nullptr;
+  double* d_partials = nullptr;
+  double* d_bins = nullptr;   // [3][nk]
+  double* d_pi = nullptr;     // [ns][nk]
+  double* d_ti = nullptr;
+  double* d_stab = nullptr;
+  int n_stab = 0;
+  double stab_u0 = 0, stab_h = 0, stab_umax = 0;
+  double* d_hist_u = nullptr;
+  double* d_gl = nullptr;
+  double* d_parts = nullptr;  // [ns][nk][3]
+  double* d_R = nullptr;
+  double* d_pnu = nullptr;
+  double* d_pm = nullptr;
+  void* d_gtab = nullptr;
+  void* d_dtab = nullptr;
+  void* d_wtab = nullptr;
+  int* d_status = nullptr;
+  // pinned host staging
+  double* h_hist_u = nullptr;
+  int* h_status = nullptr;
+  // state
+  bool deposited = false, deposit_grid_valid = false, have_response = false, have_kick = false;
+  double a_response = 0;
+  int64_t bytes = 0;
+  std::vector<long long> thr;
+  std::string err;
+  // per-stage timing: pending (stage, start, stop) event triples
+  bool timing = false;
+  struct Rec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> spare;
+  double st_ms[PM_NSTAGES] = {};
+  int64_t st_launch[PM_NSTAGES] = {}, st_calls[PM_NSTAGES] = {};
+};
+
+namespace {
+
+int fail(pm_ctx* c, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(pm_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+int cuda_check(pm_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PM_OK;
+  return fail(c, PM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Host-side fault injection for tests: NUPM_FAIL_ALLOC_AT=k makes the k-th
+// device allocation of pm_init report failure.
+int g_alloc_counter = 0;
+
+int dalloc(pm_ctx* c, void** p, size_t bytes, const char* what) {
+  ++g_alloc_counter;
+  const char* inj = getenv("NUPM_FAIL_ALLOC_AT");
+  if (inj && atoi(inj) == g_alloc_counter)
+    return fail(c, PM_ERR_ALLOC, "allocation of %s (%zu bytes) failed (injected)", what, bytes);
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(c, PM_ERR_ALLOC, "cudaMalloc of %s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
+  }
+  c->bytes += (int64_t)bytes;
+  return PM_OK;
+}
+
+double hubble(const pm_ctx* c, double a) { return sqrt(c->omega_m / (a * a * a) + c->omega_l); }
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_q (long double).
+void gauss_legendre(int q, double* x, double* w) {
+  const long double pi = acosl(-1.0L);
+  for (int i = 0; i < q; ++i) {
+    long double z = cosl(pi * (i + 0.75L) / (q + 0.5L));
+    long double dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      long double p0 = 1, p1 = z;
+      for (int k = 2; k <= q; ++k) {
+        const long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (q == 1) { p1 = z; p0 = 1; }
+      dp = q * (z * p1 - p0) / (z * z - 1);
+      const long double dz = p1 / dp;
+      z -= dz;
+      if (fabsl(dz) < 1e-30L) break;
+    }
+    x[i] = (double)(-z);
+    w[i] = (double)(2 / ((1 - z * z) * dp * dp));
+  }
+}
+
+// int_{u0}^{u1} f(u) du by 16-point Gauss-Legendre on panels of width <= 1/8.
+template <class F>
+double integrate_u(double u0, double u1, F f) {
+  static double gx[16], gw[16];
+  static bool init = false;
+  if (!init) {
+    gauss_legendre(16, gx, gw);
+    init = true;
+  }
+  if (u1 == u0) return 0.0;
+  const int np = (int)ceil(fabs(u1 - u0) * 8.0) + 1;
+  const double h = (u1 - u0) / np;
+  double s = 0;
+  for (int p = 0; p < np; ++p) {
+    const double lo = u0 + p * h;
+    double ps = 0;
+    for (int i = 0; i < 16; ++i) ps += gw[i] * f(lo + 0.5 * h * (gx[i] + 1));
+    s += 0.5 * h * ps;
+  }
+  return s;
+}
+
+// s(u) table on u in [ln a_i, u_max], spacing 1/512: values and ds/du = 1/(a^2 H).
+int build_s_table(pm_ctx* c, double u_max) {
+  const double u0 = log(c->a_init);
+  const double h = 1.0 / 512.0;
+  int n = (int)ceil((u_max - u0) / h) + 2;
+  if (n < 4) n = 4;
+  std::vector<double> t(2 * (size_t)n);
+  double gx[8], gw[8];
+  gauss_legendre(8, gx, gw);
+  double s = 0, comp = 0;   // Kahan-compensated running sum
+  for (int i = 0; i < n; ++i) {
+    const double u = u0 + i * h;
+    const double a = exp(u);
+    if (i > 0) {
+      const double lo = u - h;
+      double cell = 0;
+      for (int k = 0; k < 8; ++k) {
+        const double uu = lo + 0.5 * h * (gx[k] + 1);
+        const double aa = exp(uu);
+        cell += gw[k] / (aa * aa * hubble(c, aa));
+      }
+      cell *= 0.5 * h;
+      const double y = cell - comp;
+      const double tt = s + y;
+      comp = (tt - s) - y;
+      s = tt;
+    }
+    t[2 * i] = s;
+    t[2 * i + 1] = 1.0 / (a * a * hubble(c, a));
+  }
+  if (c->d_stab) cudaFree(c->d_stab);
+  c->d_stab = nullptr;
+  if (cudaMalloc((void**)&c->d_stab, t.size() * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, PM_ERR_ALLOC, "s-table allocation failed");
+  }
+  if (cudaMemcpy(c->d_stab, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(c, PM_ERR_CUDA, "s-table upload failed");
+  c->n_stab = n;
+  c->stab_u0 = u0;
+  c->stab_h = h;
+  c->stab_umax = u0 + (n - 2) * h;
+  return PM_OK;
+}
+
+template <typename T>
+int upload_tables(pm_ctx* c) {
+  const int n = c->n, m = c->m;
+  const long double pi = acosl(-1.0L);
+  // twiddles W_N^k (k < N) and W_M^k (k < M), forward sign
+  std::vector<T> twn(2 * (size_t)n), twm(2 * (size_t)m);
+  for (int k = 0; k < n; ++k) {
+    const long double t = -2.0L * pi * k / n;
+    twn[2 * k] = (T)cosl(t);
+    twn[2 * k + 1] = (T)sinl(t);
+  }
+  for (int k = 0; k < m; ++k) {
+    const long double t = -2.0L * pi * k / m;
+    twm[2 * k] = (T)cosl(t);
+    twm[2 * k + 1] = (T)sinl(t);
+  }
+  // 4-point gradient multiplier per index (signed frequency), 0 at Nyquist
+  std::vector<T> dt(n), wt(n);
+  for (int i = 0; i < n; ++i) {
+    const int f = i < n / 2 ? i : i - n;
+    const long double th = 2.0L * pi * f / n;
+    long double d = (8.0L * sinl(th) - sinl(2.0L * th)) / (6.0L * (long double)c->delta);
+    if (i == n / 2 || i == 0) d = 0;
+    dt[i] = (T)d;
+    const long double x = pi * f / n;
+    const long double sc = f == 0 ? 1.0L : sinl(x) / x;
+    wt[i] = (T)(1.0L / (sc * sc * sc * sc));
+  }
+  cudaError_t e = cudaSuccess;
+  e = cudaMemcpy(c->tw_n, twn.data(), twn.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->tw_m, twm.data(), twm.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_dtab, dt.data(), dt.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_wtab, wt.data(), wt.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return cuda_check(c, e, "table upload");
+}
+
+cudaEvent_t take_event(pm_ctx* c) {
+  if (!c->spare.empty()) {
+    cudaEvent_t e = c->spare.back();
+    c->spare.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Stage scope: records an event pair around the launches of one stage when
+// timing is on, and counts the stage's kernel launches.
+struct Stage {
+  pm_ctx* c;
+  int stage;
+  cudaEvent_t a = nullptr;
+  Stage(pm_ctx* ctx, int st, int launches) : c(ctx), stage(st) {
+    c->st_launch[st] += launches;
+    c->st_calls[st] += 1;
+    if (c->timing) {
+      a = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~Stage() {
+    if (a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, c->stream);
+      c->pending.push_back({stage, a, b});
+    }
+  }
+};
+
+void drain_timing(pm_ctx* c) {
+  for (auto& r : c->pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) c->st_ms[r.stage] += ms;
+    c->spare.push_back(r.a);
+    c->spare.push_back(r.b);
+  }
+  c->pending.clear();
+  cudaGetLastError();
+}
+
+GridArgs grid_args(const pm_ctx* c) {
+  GridArgs g;
+  g.n = c->n;
+  g.np = c->np;
+  g.box = c->box;
+  g.delta = c->delta;
+  g.scale = (double)c->n * c->n * c->n / ((double)c->np * 281474976710656.0);   // N^3 / (Np 2^48)
+  g.spec = c->spec;
+  g.g = c->g;
+  g.field_elems = c->field_elems;
+  g.tw_n = c->tw_n;
+  g.tw_m = c->tw_m;
+  g.status = c->d_status;
+  return g;
+}
+
+void release(pm_ctx* c) {
+  void* ptrs[] = {c->spec, c->g, c->tw_n, c->tw_m, c->d_thr, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
+                  c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_gtab,
+                  c->d_dtab, c->d_wtab, c->d_status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_hist_u) cudaFreeHost(c->h_hist_u);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  for (auto& r : c->pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->spare) cudaEventDestroy(e);
+}
+
+bool finite_pos(double x) { return isfinite(x) && x > 0; }
+
+}  // namespace
+
+extern "C" {
+
+void pm_default_params(pm_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->ngrid = 32;
+  p->npart = 32 * 32 * 32;
+  p->box = 256.0;
+  p->particle_mass = 1.0;
+  p->omega_cdm = 0.3;
+  p->omega_nu = 0.0;
+  p->h = 0.7;
+  p->a_init = 0.02;
+  p->n_kbins = 32;
+  p->n_hist_max = 128;
+  p->precision = PM_FP64;
+  p->iters = 1;
+  p->quad_nodes = 8;
+}
+
+int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* theta_over_delta_init,
+            void* cuda_stream, pm_ctx** out) {
+  if (!out) return PM_ERR_INVALID;
+  *out = nullptr;
+  if (!params) return PM_ERR_INVALID;
+  pm_ctx* c = new pm_ctx();
+  c->p = *params;
+  const pm_params& p = *params;
+  int rc = PM_OK;
+  auto bad = [&](int code, const char* msg) {
+    c->err = msg;
+    rc = code;
+  };
+  const int n = p.ngrid;
+  if (!(n >= 16 && n <= 1024 && (n & (n - 1)) == 0)) bad(PM_ERR_UNSUPPORTED, "ngrid must be a power of two in [16, 1024]");
+  else if (p.npart < 1) bad(PM_ERR_INVALID, "npart must be >= 1");
+  else if (p.npart > 0x7fffffffLL) bad(PM_ERR_INVALID, "npart must be < 2^31");
+  else if (!finite_pos(p.box)) bad(PM_ERR_INVALID, "box must be finite and > 0");
+  else if (!finite_pos(p.particle_mass)) bad(PM_ERR_INVALID, "particle_mass must be finite and > 0");
+  else if (!(isfinite(p.omega_cdm) && p.omega_cdm > 0)) bad(PM_ERR_INVALID, "omega_cdm must be > 0");
+  else if (!finite_pos(p.h)) bad(PM_ERR_INVALID, "h must be > 0");
+  else if (!(isfinite(p.m_nu_total_eV) && p.m_nu_total_eV >= 0)) bad(PM_ERR_RANGE, "m_nu_total_eV must be >= 0");
+  else if (p.n_species < 0 || p.n_species > 3) bad(PM_ERR_INVALID, "n_species must be 0..3");
+  else if (!(isfinite(p.a_init) && p.a_init > 0 && p.a_init <= 1)) bad(PM_ERR_RANGE, "a_init must be in (0, 1]");
+  else if (p.n_kbins < 1 || p.n_kbins > 1024) bad(PM_ERR_INVALID, "n_kbins must be 1..1024");
+  else if (p.n_hist_max < 0 || p.n_hist_max > kMaxPanels - 64) bad(PM_ERR_INVALID, "n_hist_max must be 0..256");
+  else if (p.precision != PM_FP64 && p.precision != PM_FP32) bad(PM_ERR_INVALID, "precision must be PM_FP64 or PM_FP32");
+  else if (p.iters < 1 || p.iters > 16) bad(PM_ERR_INVALID, "iters must be 1..16");
+  else if (p.quad_nodes < 2 || p.quad_nodes > kMaxQuad) bad(PM_ERR_INVALID, "quad_nodes must be 2..16");
+  else if (p.flags & ~(PM_I_FIT | PM_DECONV_CIC)) bad(PM_ERR_INVALID, "unknown flag bits");
+  if (rc != PM_OK) {
+    // report through a context so pm_last_error works; caller still gets NULL
+    fprintf(stderr, "pm_init: %s\n", c->err.c_str());
+    delete c;
+    return rc;
+  }
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  c->fp64 = p.precision == PM_FP64;
+  c->n = n;
+  c->m = n / 2;
+  c->nk = p.n_kbins;
+  c->np = p.npart;
+  c->box = p.box;
+  c->delta = p.box / n;
+  c->kf = 2.0 * M_PI / p.box;
+  c->quad = p.quad_nodes;
+  c->iters = p.iters;
+  c->a_init = p.a_init;
+  // neutrinos (Sec. 2.1): Omega_nu from the total mass when not given
+  double mtot = p.m_nu_total_eV;
+  int ns = (mtot > 0) ? p.n_species : 0;
+  double ms[3] = {0, 0, 0};
+  if (ns > 0) {
+    double sum = 0;
+    for (int i = 0; i < ns; ++i) sum += p.m_nu_eV[i] > 0 ? p.m_nu_eV[i] : 0;
+    if (sum > 0) {
+      for (int i = 0; i < ns; ++i) ms[i] = p.m_nu_eV[i] > 0 ? p.m_nu_eV[i] : 0;
+      mtot = sum;
+    } else {
+      for (int i = 0; i < ns; ++i) ms[i] = mtot / ns;
+    }
+  }
+  double onu = p.omega_nu < 0 ? mtot / (kOmegaNuEv * p.h * p.h) : p.omega_nu;
+  if (ns == 0) onu = p.omega_nu > 0 ? p.omega_nu : 0.0;
+  if (!(isfinite(onu) && onu >= 0)) {
+    fprintf(stderr, "pm_init: bad omega_nu\n");
+    delete c;
+    return PM_ERR_RANGE;
+  }
+  c->omega_nu = onu;
+  c->omega_m = p.omega_cdm + onu;
+  c->omega_l = 1.0 - c->omega_m;
+  c->f_nu = onu / c->omega_m;
+  // massless species carry no weight; a species of mass 0 is skipped
+  int used = 0;
+  double wsum = 0;
+  for (int i = 0; i < ns; ++i) wsum += ms[i];
+  for (int i = 0; i < ns; ++i)
+    if (ms[i] > 0) {
+      c->mass[used] = ms[i];
+      c->wsp[used] = ms[i] / wsum;
+      ++used;
+    }
+  c->ns = used;
+  c->n2max = 3LL * (n / 2) * (n / 2);
+  c->field_elems = (int64_t)n * n * (n / 2);
+  c->cplx = c->fp64 ? 16 : 8;
+  const size_t real = c->fp64 ? 8 : 4;
+  c->nblk_bins = 152 * 4;
+
+  int nspec = c->ns > 0 ? c->ns : 1;
+  g_alloc_counter = 0;
+  const size_t fbytes = (size_t)c->field_elems * c->cplx;
+  if (rc == PM_OK) rc = dalloc(c, &c->spec, fbytes, "spectrum");
+  if (rc == PM_OK) rc = dalloc(c, &c->g, 3 * fbytes, "force fields");
+  if (rc == PM_OK) rc = dalloc(c, &c->tw_n, (size_t)n * c->cplx, "twiddles N");
+  if (rc == PM_OK) rc = dalloc(c, &c->tw_m, (size_t)(n / 2) * c->cplx, "twiddles M");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_thr, (size_t)(c->nk + 1) * sizeof(long long), "thresholds");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_partials, (size_t)c->nblk_bins * 3 * c->nk * sizeof(double), "bin partials");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_bins, 3 * (size_t)c->nk * sizeof(double), "bins");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_pi, (size_t)nspec * c->nk * sizeof(double), "nu ICs");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_ti, (size_t)nspec * c->nk * sizeof(double), "nu theta ICs");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_hist_u, (size_t)(p.n_hist_max + 1) * sizeof(double), "history ln a");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_gl, 2 * kMaxQuad * sizeof(double), "quadrature");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_parts, (size_t)nspec * c->nk * 3 * sizeof(double), "response parts");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_R, (size_t)c->nk * sizeof(double), "ratio");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_pnu, (size_t)c->nk * sizeof(double), "P_nu");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_pm, (size_t)c->nk * sizeof(double), "P_M");
+  if (rc == PM_OK) rc = dalloc(c, &c->d_gtab, (size_t)(c->n2max + 1) * real, "Green table");
+  if (rc == PM_OK) rc = dalloc(c, &c->d_dtab, (size_t)n * real, "gradient table");
+  if (rc == PM_OK) rc = dalloc(c, &c->d_wtab, (size_t)n * real, "deconvolution table");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_status, sizeof(int), "status");
+  if (rc == PM_OK && cudaMallocHost((void**)&c->h_hist_u, (size_t)(p.n_hist_max + 1) * sizeof(double)) != cudaSuccess)
+    rc = fail(c, PM_ERR_ALLOC, "pinned host allocation failed");
+  if (rc == PM_OK && cudaMallocHost((void**)&c->h_status, sizeof(int)) != cudaSuccess)
+    rc = fail(c, PM_ERR_ALLOC, "pinned host allocation failed");
+  if (rc == PM_OK) rc = c->fp64 ? upload_tables<double>(c) : upload_tables<float>(c);
+  if (rc == PM_OK) {
+    // bin thresholds T_b = ceil((e_b L / 2 pi)^2), e_b log-spaced on [kmin, kmax]
+    const double r = sqrt(3.0) * n / 2.0 * (1.0 + 1e-12);
+    c->thr.resize(c->nk + 1);
+    for (int b = 0; b <= c->nk; ++b) c->thr[b] = (long long)ceil(pow(r, 2.0 * b / c->nk));
+    rc = cuda_check(c, cudaMemcpy(c->d_thr, c->thr.data(), c->thr.size() * sizeof(long long),
+                                  cudaMemcpyHostToDevice), "thresholds upload");
+  }
+  if (rc == PM_OK) {
+    std::vector<double> gl(2 * kMaxQuad, 0.0);
+    gauss_legendre(c->quad, gl.data(), gl.data() + kMaxQuad);
+    rc = cuda_check(c, cudaMemcpy(c->d_gl, gl.data(), gl.size() * sizeof(double), cudaMemcpyHostToDevice),
+                    "quadrature upload");
+  }
+  if (rc == PM_OK) {
+    // neutrino ICs per species (zeros when not given)
+    std::vector<double> pi((size_t)nspec * c->nk, 0.0), ti((size_t)nspec * c->nk, 0.0);
+    int j = 0;
+    for (int i = 0; i < (ns > 0 ? ns : 0); ++i) {
+      if (ms[i] <= 0) continue;
+      for (int b = 0; b < c->nk; ++b) {
+        if (sqrtPnu_init) pi[(size_t)j * c->nk + b] = sqrtPnu_init[(size_t)i * c->nk + b];
+        if (theta_over_delta_init) ti[(size_t)j * c->nk + b] = theta_over_delta_init[(size_t)i * c->nk + b];
+        if (!isfinite(pi[(size_t)j * c->nk + b]) || !isfinite(ti[(size_t)j * c->nk + b])) {
+          rc = fail(c, PM_ERR_INVALID, "non-finite neutrino initial condition");
+        }
+      }
+      ++j;
+    }
+    if (rc == PM_OK)
+      rc = cuda_check(c, cudaMemcpy(c->d_pi, pi.data(), pi.size() * sizeof(double), cudaMemcpyHostToDevice), "IC upload");
+    if (rc == PM_OK)
+      rc = cuda_check(c, cudaMemcpy(c->d_ti, ti.data(), ti.size() * sizeof(double), cudaMemcpyHostToDevice), "IC upload");
+  }
+  if (rc == PM_OK) rc = build_s_table(c, 0.0 > log(c->a_init) ? 0.0 : log(c->a_init) + 1.0);
+  if (rc == PM_OK) rc = cuda_check(c, cudaMemset(c->d_status, 0, sizeof(int)), "status init");
+  if (rc == PM_OK) rc = cuda_check(c, cudaDeviceSynchronize(), "pm_init");
+  if (rc != PM_OK) {
+    fprintf(stderr, "pm_init: %s\n", c->err.c_str());
+    release(c);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return PM_OK;
+}
+
+int pm_deposit(pm_ctx* c, const void* pos) {
+  if (!c) return PM_ERR_INVALID;
+  if (!pos) return fail(c, PM_ERR_INVALID, "pm_deposit: pos is NULL");
+  GridArgs g = grid_args(c);
+  int rc = PM_OK;
+  {
+    Stage st(c, PM_ST_DEPOSIT, 1);
+    rc = c->fp64 ? deposit_f64(g, pos, c->stream) : deposit_f32(g, pos, c->stream);
+  }
+  const int fwd[3] = {kPassXFwd, kPassYFwd, kPassZFwd};
+  const int fst[3] = {PM_ST_FFT_X_FWD, PM_ST_FFT_Y_FWD, PM_ST_FFT_Z_FWD};
+  for (int i = 0; i < 3 && rc == PM_OK; ++i) {
+    Stage st(c, fst[i], 1);
+    rc = c->fp64 ? fft_pass_f64(g, fwd[i], c->stream) : fft_pass_f32(g, fwd[i], c->stream);
+  }
+  if (rc == PM_OK) {
+    Stage st(c, PM_ST_BINS, 2);
+    rc = c->fp64 ? bins_f64(g, c->nk, c->d_thr, c->kf, c->d_partials, c->nblk_bins, c->d_bins, c->stream)
+                 : bins_f32(g, c->nk, c->d_thr, c->kf, c->d_partials, c->nblk_bins, c->d_bins, c->stream);
+  }
+  if (rc != PM_OK) return fail(c, rc, "pm_deposit: unsupported grid");
+  rc = cuda_check(c, cudaGetLastError(), "pm_deposit launch");
+  if (rc != PM_OK) return rc;
+  c->deposited = true;
+  c->deposit_grid_valid = true;    // the fixed-point grid stays intact until pm_kick
+  c->have_response = false;
+  c->have_kick = false;
+  return PM_OK;
+}
+
+int pm_nu_response(pm_ctx* c, double a, const double* a_hist, const double* sqrtPM_hist, int32_t n_hist,
+                   const double* sqrtPnu_prev, double* ratio_out, double* sqrtPnu_out, double* sqrtPM_out) {
+  if (!c) return PM_ERR_INVALID;
+  if (!c->deposited) return fail(c, PM_ERR_ORDER, "pm_nu_response before pm_deposit");
+  if (!(isfinite(a) && a >= c->a_init)) return fail(c, PM_ERR_RANGE, "a must be finite and >= a_init");
+  if (n_hist < 0 || n_hist > c->p.n_hist_max) return fail(c, PM_ERR_INVALID, "n_hist outside 0..n_hist_max");
+  if (n_hist > 0 && (!a_hist || !sqrtPM_hist)) return fail(c, PM_ERR_INVALID, "history pointers are NULL");
+  for (int j = 0; j < n_hist; ++j) {
+    if (!isfinite(a_hist[j])) return fail(c, PM_ERR_RANGE, "non-finite a_hist");
+    if (j == 0 && a_hist[0] < c->a_init) return fail(c, PM_ERR_RANGE, "a_hist[0] < a_init");
+    if (j > 0 && !(a_hist[j] > a_hist[j - 1])) return fail(c, PM_ERR_RANGE, "a_hist not strictly increasing");
+  }
+  if (n_hist > 0 && !(a_hist[n_hist - 1] < a)) return fail(c, PM_ERR_RANGE, "a_hist[n-1] must be < a");
+  const double ue = log(a);
+  if (ue > c->stab_umax) {
+    const int rc = build_s_table(c, ue + 1.0);
+    if (rc != PM_OK) return rc;
+  }
+  for (int j = 0; j < n_hist; ++j) c->h_hist_u[j] = log(a_hist[j]);
+  if (n_hist > 0) {
+    const int rc = cuda_check(c, cudaMemcpyAsync(c->d_hist_u, c->h_hist_u, n_hist * sizeof(double),
+                                                 cudaMemcpyHostToDevice, c->stream), "history upload");
+    if (rc != PM_OK) return rc;
+  }
+  Stage stage(c, PM_ST_RESPONSE, (c->ns > 0 && c->f_nu > 0) ? 3 : 2);
+  if (c->ns > 0 && c->f_nu > 0) {
+    NuArgs A{};
+    A.nk = c->nk;
+    A.ns = c->ns;
+    A.n_hist = n_hist;
+    A.quad = c->quad;
+    A.iters = c->iters;
+    A.use_fit = (c->p.flags & PM_I_FIT) ? 1 : 0;
+    A.ngrid = c->n;
+    A.a = a;
+    A.ue = ue;
+    A.ui = log(c->a_init);
+    A.omega_m = c->omega_m;
+    A.omega_l = c->omega_l;
+    A.f_nu = c->f_nu;
+    A.a_init = c->a_init;
+    A.box = c->box;
+    for (int s = 0; s < c->ns; ++s) {
+      A.kappa_scale[s] = kCOverH0 * kTnu0eV / c->mass[s];
+      A.w_species[s] = c->wsp[s];
+    }
+    A.bins = c->d_bins;
+    A.hist_u = c->d_hist_u;
+    A.hist = sqrtPM_hist;
+    A.prev = sqrtPnu_prev;
+    A.pnu_init = c->d_pi;
+    A.theta_init = c->d_ti;
+    A.stab = c->d_stab;
+    A.n_stab = c->n_stab;
+    A.stab_u0 = c->stab_u0;
+    A.stab_h = c->stab_h;
+    A.stab_inv_h = 1.0 / c->stab_h;
+    A.gl = c->d_gl;
+    A.parts = c->d_parts;
+    A.R = c->d_R;
+    A.pnu = c->d_pnu;
+    A.pm = c->d_pm;
+    A.R_user = ratio_out;
+    A.pnu_user = sqrtPnu_out;
+    A.pm_user = sqrtPM_out;
+    launch_nu_response(A, c->stream);
+  } else {
+    // no neutrinos: R = 0, P_nu = 0, P_M^{1/2} = P_cdm^{1/2}
+    NuArgs A{};
+    A.nk = c->nk;
+    A.ns = 0;
+    A.iters = 1;
+    A.f_nu = 0;
+    A.ngrid = c->n;
+    A.box = c->box;
+    A.bins = c->d_bins;
+    A.parts = c->d_parts;
+    A.pnu_init = c->d_pi;
+    A.R = c->d_R;
+    A.pnu = c->d_pnu;
+    A.pm = c->d_pm;
+    A.R_user = ratio_out;
+    A.pnu_user = sqrtPnu_out;
+    A.pm_user = sqrtPM_out;
+    launch_nu_response(A, c->stream);   // zero items in the panel kernel; finish sets outputs
+  }
+  const double coeff = -1.5 * c->omega_m / (a * c->kf * c->kf * (double)c->n * c->n * c->n);
+  launch_green_table(c->fp64, c->d_gtab, c->n2max, c->kf, coeff, c->f_nu, c->d_R, c->d_bins, c->nk, c->stream);
+  const int rc = cuda_check(c, cudaGetLastError(), "pm_nu_response launch");
+  if (rc != PM_OK) return rc;
+  c->have_response = true;
+  c->a_response = a;
+  return PM_OK;
+}
+
+int pm_kick(pm_ctx* c, const void* pos, void* vel, double a, double kick_factor, void* acc_out) {
+  if (!c) return PM_ERR_INVALID;
+  if (!pos || !vel) return fail(c, PM_ERR_INVALID, "pm_kick: pos/vel is NULL");
+  if (!c->deposited || !c->have_response) return fail(c, PM_ERR_ORDER, "pm_kick needs pm_deposit and pm_nu_response first");
+  if (a != c->a_response) return fail(c, PM_ERR_ORDER, "pm_kick at a different a than pm_nu_response");
+  if (!isfinite(kick_factor)) return fail(c, PM_ERR_INVALID, "kick_factor must be finite");
+  GridArgs g = grid_args(c);
+  const void* wt = (c->p.flags & PM_DECONV_CIC) ? c->d_wtab : nullptr;
+  int rc = PM_OK;
+  {
+    Stage st(c, PM_ST_GREEN, 1);
+    rc = c->fp64 ? green_f64(g, c->d_gtab, c->d_dtab, wt, c->stream) : green_f32(g, c->d_gtab, c->d_dtab, wt, c->stream);
+  }
+  c->deposit_grid_valid = false;
+  const int inv[3] = {kPassZInv, kPassYInv, kPassXInv};
+  const int ist[3] = {PM_ST_FFT_Z_INV, PM_ST_FFT_Y_INV, PM_ST_FFT_X_INV};
+  for (int i = 0; i < 3 && rc == PM_OK; ++i) {
+    Stage st(c, ist[i], 1);
+    rc = c->fp64 ? fft_pass_f64(g, inv[i], c->stream) : fft_pass_f32(g, inv[i], c->stream);
+  }
+  if (rc == PM_OK) {
+    Stage st(c, PM_ST_INTERP, 1);
+    rc = c->fp64 ? interp_f64(g, pos, vel, kick_factor, acc_out, c->stream)
+                 : interp_f32(g, pos, vel, kick_factor, acc_out, c->stream);
+  }
+  if (rc != PM_OK) return fail(c, rc, "pm_kick: unsupported grid");
+  rc = cuda_check(c, cudaGetLastError(), "pm_kick launch");
+  if (rc == PM_OK) c->have_kick = true;
+  return rc;
+}
+
+int pm_check(pm_ctx* c) {
+  if (!c) return PM_ERR_INVALID;
+  int rc = cuda_check(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                      "status read");
+  if (rc == PM_OK) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "pm_check sync");
+  if (rc != PM_OK) return rc;
+  const int st = *c->h_status;
+  if (st != 0) {
+    cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+    cudaStreamSynchronize(c->stream);
+    return fail(c, st, st == PM_ERR_RANGE ? "device: particle offset outside [0,1) or non-finite position"
+                                          : "device: error recorded by a kernel");
+  }
+  return PM_OK;
+}
+
+void pm_free(pm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  release(c);
+  delete c;
+}
+
+const char* pm_last_error(const pm_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+double pm_kick_factor(const pm_ctx* c, double a0, double a1) {
+  if (!c || !(a0 > 0) || !(a1 > 0) || !isfinite(a0) || !isfinite(a1)) return NAN;
+  return integrate_u(log(a0), log(a1), [c](double u) { return 1.0 / hubble(c, exp(u)); });
+}
+
+double pm_drift_factor(const pm_ctx* c, double a0, double a1) {
+  if (!c || !(a0 > 0) || !(a1 > 0) || !isfinite(a0) || !isfinite(a1)) return NAN;
+  return integrate_u(log(a0), log(a1), [c](double u) {
+    const double a = exp(u);
+    return 1.0 / (a * a * hubble(c, a));
+  });
+}
+
+int pm_get_bins(pm_ctx* c, double* count, double* ksum, double* psum) {
+  if (!c) return PM_ERR_INVALID;
+  if (!c->deposited) return fail(c, PM_ERR_ORDER, "pm_get_bins before pm_deposit");
+  std::vector<double> h(3 * (size_t)c->nk);
+  int rc = cuda_check(c, cudaMemcpyAsync(h.data(), c->d_bins, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                         c->stream), "bins read");
+  if (rc == PM_OK) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "bins sync");
+  if (rc != PM_OK) return rc;
+  if (count) memcpy(count, h.data(), c->nk * sizeof(double));
+  if (ksum) memcpy(ksum, h.data() + c->nk, c->nk * sizeof(double));
+  if (psum) memcpy(psum, h.data() + 2 * c->nk, c->nk * sizeof(double));
+  return PM_OK;
+}
+
+int pm_get_thresholds(const pm_ctx* c, int64_t* t) {
+  if (!c || !t) return PM_ERR_INVALID;
+  for (size_t i = 0; i < c->thr.size(); ++i) t[i] = c->thr[i];
+  return PM_OK;
+}
+
+int pm_copy_field(pm_ctx* c, int32_t which, void* dst) {
+  if (!c || !dst) return PM_ERR_INVALID;
+  const int64_t n3 = (int64_t)c->n * c->n * c->n;
+  const size_t real = c->fp64 ? 8 : 4;
+  cudaError_t e = cudaSuccess;
+  switch (which) {
+    case PM_FIELD_DEPOSIT:
+      if (!c->deposit_grid_valid) return fail(c, PM_ERR_ORDER, "deposit grid not valid (no deposit, or a kick overwrote it)");
+      e = cudaMemcpyAsync(dst, c->g, (size_t)n3 * 8, cudaMemcpyDeviceToDevice, c->stream);
+      break;
+    case PM_FIELD_DELTA_K: {
+      if (!c->deposited) return fail(c, PM_ERR_ORDER, "no spectrum before pm_deposit");
+      GridArgs g = grid_args(c);
+      const int rc = c->fp64 ? unpack_f64(g, dst, c->stream) : unpack_f32(g, dst, c->stream);
+      if (rc != PM_OK) return fail(c, rc, "unpack failed");
+      e = cudaGetLastError();
+      break;
+    }
+    case PM_FIELD_ACC_X:
+    case PM_FIELD_ACC_Y:
+    case PM_FIELD_ACC_Z: {
+      if (!c->have_kick) return fail(c, PM_ERR_ORDER, "no force grids before pm_kick");
+      const int comp = which - PM_FIELD_ACC_X;
+      const char* src = reinterpret_cast<const char*>(c->g) + (size_t)comp * c->field_elems * c->cplx;
+      e = cudaMemcpyAsync(dst, src, (size_t)n3 * real, cudaMemcpyDeviceToDevice, c->stream);
+      break;
+    }
+    default:
+      return fail(c, PM_ERR_INVALID, "unknown field");
+  }
+  return cuda_check(c, e, "pm_copy_field");
+}
+
+int pm_timing(pm_ctx* c, int32_t enable) {
+  if (!c) return PM_ERR_INVALID;
+  const int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "pm_timing sync");
+  if (rc != PM_OK) return rc;
+  drain_timing(c);
+  for (int i = 0; i < PM_NSTAGES; ++i) {
+    c->st_ms[i] = 0;
+    c->st_launch[i] = 0;
+    c->st_calls[i] = 0;
+  }
+  c->timing = enable != 0;
+  return PM_OK;
+}
+
+int pm_get_timing(pm_ctx* c, double* ms, int64_t* launches, int64_t* calls) {
+  if (!c) return PM_ERR_INVALID;
+  const int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "pm_get_timing sync");
+  if (rc != PM_OK) return rc;
+  drain_timing(c);
+  for (int i = 0; i < PM_NSTAGES; ++i) {
+    if (ms) ms[i] = c->st_ms[i];
+    if (launches) launches[i] = c->st_launch[i];
+    if (calls) calls[i] = c->st_calls[i];
+  }
+  return PM_OK;
+}
+
+int64_t pm_device_bytes(const pm_ctx* c) { return c ? c->bytes : 0; }
+
+}  // extern "C"

@@ -1,0 +1,245 @@
+"""Thin ctypes binding of libnupm (include/nupm.h).
+
+Argument marshalling only: every step of the kick runs in the library's CUDA
+kernels.  Tensors are torch CUDA tensors (torch supplies device memory and the
+stream); host tables are numpy arrays.  The binding raises if the library is
+missing or a call fails; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnupm.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "nupm.h")
+
+PM_OK = 0
+ERRORS = {-1: "PM_ERR_INVALID", -2: "PM_ERR_RANGE", -3: "PM_ERR_OVERFLOW", -4: "PM_ERR_CUDA",
+          -5: "PM_ERR_ALLOC", -6: "PM_ERR_TIMEOUT", -7: "PM_ERR_ORDER", -8: "PM_ERR_UNSUPPORTED"}
+PM_FP64, PM_FP32 = 0, 1
+PM_I_FIT, PM_DECONV_CIC = 0x1, 0x2
+FIELD_DEPOSIT, FIELD_DELTA_K, FIELD_ACC_X, FIELD_ACC_Y, FIELD_ACC_Z = range(5)
+STAGES = ["deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_fwd", "bins", "response", "green",
+          "fft_z_inv", "fft_y_inv", "fft_x_inv", "interp"]
+
+
+class PmParams(C.Structure):
+    _fields_ = [("ngrid", C.c_int32), ("npart", C.c_int64), ("box", C.c_double),
+                ("particle_mass", C.c_double), ("omega_cdm", C.c_double), ("omega_nu", C.c_double),
+                ("h", C.c_double), ("m_nu_total_eV", C.c_double), ("n_species", C.c_int32),
+                ("m_nu_eV", C.c_double * 3), ("a_init", C.c_double), ("n_kbins", C.c_int32),
+                ("n_hist_max", C.c_int32), ("precision", C.c_int32), ("flags", C.c_uint32),
+                ("iters", C.c_int32), ("quad_nodes", C.c_int32)]
+
+
+class PMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libnupm.so (built in-tree by paper_1209_0461_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1209_0461_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, dp, i32, i64, d = C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "pm_default_params": (None, [C.POINTER(PmParams)]),
+        "pm_init": (C.c_int, [C.POINTER(PmParams), dp, dp, vp, C.POINTER(vp)]),
+        "pm_deposit": (C.c_int, [vp, vp]),
+        "pm_nu_response": (C.c_int, [vp, d, dp, vp, i32, vp, vp, vp, vp]),
+        "pm_kick": (C.c_int, [vp, vp, vp, d, d, vp]),
+        "pm_check": (C.c_int, [vp]),
+        "pm_free": (None, [vp]),
+        "pm_last_error": (C.c_char_p, [vp]),
+        "pm_kick_factor": (d, [vp, d, d]),
+        "pm_drift_factor": (d, [vp, d, d]),
+        "pm_get_bins": (C.c_int, [vp, dp, dp, dp]),
+        "pm_get_thresholds": (C.c_int, [vp, C.POINTER(C.c_int64)]),
+        "pm_copy_field": (C.c_int, [vp, i32, vp]),
+        "pm_device_bytes": (i64, [vp]),
+        "pm_timing": (C.c_int, [vp, i32]),
+        "pm_get_timing": (C.c_int, [vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def declared_symbols():
+    """Names of the functions include/nupm.h declares."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"NUPM_API\s+[\w\s\*]*?\b(pm_\w+)\s*\(", txt)))
+
+
+def _dptr(arr):
+    return arr.ctypes.data_as(C.POINTER(C.c_double)) if arr is not None else None
+
+
+def _tptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class PM:
+    """One PM context (pm_init .. pm_free) on the current CUDA device."""
+
+    def __init__(self, ngrid, npart, box, omega_cdm, omega_nu=-1.0, h=0.7, m_nu_total=0.0,
+                 n_species=3, m_nu=None, a_init=0.02, n_kbins=32, n_hist_max=128,
+                 precision="fp64", flags=0, iters=1, quad_nodes=8, sqrtPnu_init=None,
+                 theta_over_delta_init=None, stream=None, particle_mass=1.0):
+        import torch
+        L = lib()
+        p = PmParams()
+        L.pm_default_params(C.byref(p))
+        p.ngrid, p.npart, p.box = int(ngrid), int(npart), float(box)
+        p.particle_mass = float(particle_mass)
+        p.omega_cdm, p.omega_nu, p.h = float(omega_cdm), float(omega_nu), float(h)
+        p.m_nu_total_eV, p.n_species = float(m_nu_total), int(n_species)
+        for i, m in enumerate(m_nu or ()):
+            p.m_nu_eV[i] = float(m)
+        p.a_init = float(a_init)
+        p.n_kbins, p.n_hist_max = int(n_kbins), int(n_hist_max)
+        p.precision = PM_FP64 if precision == "fp64" else PM_FP32
+        p.flags, p.iters, p.quad_nodes = int(flags), int(iters), int(quad_nodes)
+        self.params = p
+        self.fp64 = p.precision == PM_FP64
+        self.dtype = torch.float64 if self.fp64 else torch.float32
+        self.nk = p.n_kbins
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        pi = None if sqrtPnu_init is None else np.ascontiguousarray(sqrtPnu_init, dtype=np.float64)
+        ti = None if theta_over_delta_init is None else np.ascontiguousarray(
+            theta_over_delta_init, dtype=np.float64)
+        for arr in (pi, ti):
+            if arr is not None and arr.size < max(1, n_species) * self.nk:
+                raise ValueError("initial-condition arrays must hold n_species x n_kbins values")
+        ctx = C.c_void_p()
+        rc = L.pm_init(C.byref(p), _dptr(pi), _dptr(ti), C.c_void_p(self.stream.cuda_stream),
+                       C.byref(ctx))
+        if rc != PM_OK:
+            raise PMError(rc, "pm_init failed (see stderr)")
+        self.ctx = ctx
+
+    # -- helpers
+    def _ok(self, rc, what):
+        if rc != PM_OK:
+            raise PMError(rc, f"{what}: {lib().pm_last_error(self.ctx).decode()}")
+
+    def _check_pos(self, pos):
+        import torch
+        n = self.params.npart
+        if not pos.is_cuda or not pos.is_contiguous():
+            raise ValueError("positions must be a contiguous CUDA tensor")
+        if self.fp64:
+            if pos.dtype != torch.float64 or tuple(pos.shape) != (3, n):
+                raise ValueError("PM_FP64 positions: float64 tensor [3, npart]")
+        elif pos.dtype != torch.int32 or tuple(pos.shape) != (6, n):
+            raise ValueError("PM_FP32 positions: int32 tensor [6, npart] (cells, offset bits)")
+
+    # -- the kick
+    def deposit(self, pos):
+        self._check_pos(pos)
+        self._ok(lib().pm_deposit(self.ctx, _tptr(pos)), "pm_deposit")
+
+    def nu_response(self, a, a_hist, sqrtPM_hist, sqrtPnu_prev=None, ratio=None, sqrtPnu=None,
+                    sqrtPM=None):
+        """a_hist: host array [n]; sqrtPM_hist: CUDA float64 [n, n_kbins] (or None for n = 0);
+        outputs: optional CUDA float64 [n_kbins] tensors filled in place."""
+        import torch
+        ah = np.ascontiguousarray(a_hist if a_hist is not None else [], dtype=np.float64)
+        n = int(ah.size)
+        if n:
+            if (sqrtPM_hist is None or sqrtPM_hist.dtype != torch.float64 or not sqrtPM_hist.is_cuda
+                    or sqrtPM_hist.numel() < n * self.nk or not sqrtPM_hist.is_contiguous()):
+                raise ValueError("sqrtPM_hist must be a contiguous CUDA float64 [n_hist, n_kbins]")
+        for t in (sqrtPnu_prev, ratio, sqrtPnu, sqrtPM):
+            if t is not None and (t.dtype != torch.float64 or not t.is_cuda or t.numel() < self.nk):
+                raise ValueError("per-bin vectors must be CUDA float64 [n_kbins]")
+        self._ok(lib().pm_nu_response(self.ctx, float(a), _dptr(ah) if n else None,
+                                      _tptr(sqrtPM_hist) if n else None, n, _tptr(sqrtPnu_prev),
+                                      _tptr(ratio), _tptr(sqrtPnu), _tptr(sqrtPM)), "pm_nu_response")
+
+    def kick(self, pos, vel, a, kick_factor, acc_out=None):
+        self._check_pos(pos)
+        n = self.params.npart
+        for t in (vel, acc_out):
+            if t is not None and (t.dtype != self.dtype or tuple(t.shape) != (3, n) or not t.is_cuda
+                                  or not t.is_contiguous()):
+                raise ValueError(f"velocities / accelerations: contiguous CUDA {self.dtype} [3, npart]")
+        self._ok(lib().pm_kick(self.ctx, _tptr(pos), _tptr(vel), float(a), float(kick_factor),
+                               _tptr(acc_out)), "pm_kick")
+
+    def check(self):
+        self._ok(lib().pm_check(self.ctx), "pm_check")
+
+    # -- background
+    def kick_factor(self, a0, a1):
+        return lib().pm_kick_factor(self.ctx, float(a0), float(a1))
+
+    def drift_factor(self, a0, a1):
+        return lib().pm_drift_factor(self.ctx, float(a0), float(a1))
+
+    # -- inspection
+    def bins(self):
+        cnt, ks, ps = (np.zeros(self.nk) for _ in range(3))
+        self._ok(lib().pm_get_bins(self.ctx, _dptr(cnt), _dptr(ks), _dptr(ps)), "pm_get_bins")
+        return cnt, ks, ps
+
+    def thresholds(self):
+        t = np.zeros(self.nk + 1, dtype=np.int64)
+        self._ok(lib().pm_get_thresholds(self.ctx, t.ctypes.data_as(C.POINTER(C.c_int64))),
+                 "pm_get_thresholds")
+        return t
+
+    def field(self, which):
+        import torch
+        n = self.params.ngrid
+        if which == FIELD_DEPOSIT:
+            out = torch.empty((n, n, n), dtype=torch.int64, device="cuda")
+        elif which == FIELD_DELTA_K:
+            out = torch.empty((n, n, n // 2 + 1), dtype=torch.complex128 if self.fp64 else torch.complex64,
+                              device="cuda")
+        else:
+            out = torch.empty((n, n, n), dtype=self.dtype, device="cuda")
+        self._ok(lib().pm_copy_field(self.ctx, int(which), _tptr(out)), "pm_copy_field")
+        return out
+
+    def timing(self, enable=True):
+        """Start (clear) or stop per-stage CUDA-event timing."""
+        self._ok(lib().pm_timing(self.ctx, 1 if enable else 0), "pm_timing")
+
+    def get_timing(self):
+        """{stage: (total ms, kernel launches, calls)} since timing(True)."""
+        ms = np.zeros(len(STAGES))
+        ln = np.zeros(len(STAGES), dtype=np.int64)
+        ca = np.zeros(len(STAGES), dtype=np.int64)
+        self._ok(lib().pm_get_timing(self.ctx, _dptr(ms), ln.ctypes.data_as(C.POINTER(C.c_int64)),
+                                     ca.ctypes.data_as(C.POINTER(C.c_int64))), "pm_get_timing")
+        return {name: (float(ms[i]), int(ln[i]), int(ca[i])) for i, name in enumerate(STAGES)}
+
+    def device_bytes(self):
+        return int(lib().pm_device_bytes(self.ctx))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().pm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

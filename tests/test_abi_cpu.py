@@ -1,0 +1,52 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads without a GPU,
+exports every function include/nupm.h declares, and rejects bad arguments
+before touching the device."""
+import ctypes as C
+
+import pytest
+
+from paper_1209_0461_gb300 import nupm
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1209_0461_gb300 import build as b
+    b.build()
+    return nupm.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = nupm.declared_symbols()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_params_struct_layout(L):
+    p = nupm.PmParams()
+    L.pm_default_params(C.byref(p))
+    assert C.sizeof(p) == 128
+    assert (p.ngrid, p.iters, p.quad_nodes, p.precision) == (32, 1, 8, nupm.PM_FP64)
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("ngrid", 17, -8), ("ngrid", 2048, -8), ("npart", 0, -1), ("box", -1.0, -1),
+    ("omega_cdm", 0.0, -1), ("a_init", 0.0, -2), ("n_kbins", 0, -1), ("iters", 0, -1),
+    ("quad_nodes", 1, -1), ("precision", 7, -1), ("m_nu_total_eV", -0.1, -2), ("flags", 0x80, -1),
+])
+def test_host_validation_without_gpu(L, field, value, code):
+    p = nupm.PmParams()
+    L.pm_default_params(C.byref(p))
+    setattr(p, field, value)
+    ctx = C.c_void_p(123)
+    assert L.pm_init(C.byref(p), None, None, None, C.byref(ctx)) == code
+    assert ctx.value is None
+
+
+def test_null_arguments(L):
+    assert L.pm_init(None, None, None, None, None) == -1
+    assert L.pm_deposit(None, None) == -1
+    assert L.pm_check(None) == -1
+    assert L.pm_get_timing(None, None, None, None) == -1
+    L.pm_free(None)
+    assert L.pm_last_error(None) == b"null context"

@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs.  Tolerances: deposit bit-exact; FP64 forces and response
+max-relative 1e-5; FP32 forces RMS-relative 2e-4 (as the kick's accuracy
+contract states)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import pm_oracle as O
+from paper_1209_0461_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+from gpu_common import build_lib, force_errors, gpu_kick, make_inputs, oracle_kick  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    build_lib()
+
+
+def _check_common(w, g, r, fp64):
+    # a1: bit-exact fixed-point deposit, exact mass conservation
+    assert np.array_equal(g["F"].astype(np.int64), r.F)
+    assert int(g["F"].astype(object).sum()) == g["acc"].shape[1] * 2 ** 48
+    # bins: identical thresholds and mode counts
+    assert np.array_equal(g["T"], r.bins["T"])
+    cnt, ks, ps = g["bins"]
+    assert np.array_equal(cnt, r.bins["count"])
+    assert np.allclose(ks, r.bins["ksum"], rtol=1e-13, atol=0)
+    tol_p = 1e-10 if fp64 else 2e-5
+    assert np.allclose(ps, r.bins["psum"], rtol=tol_p, atol=1e-300)
+    # spectrum
+    spec_ref = r.extras["spec"]
+    d = np.abs(g["spec"] - spec_ref)
+    scale = np.sqrt(np.mean(np.abs(spec_ref) ** 2))
+    if fp64:
+        assert d.max() < 1e-11 * scale
+    else:
+        assert np.sqrt(np.mean(d ** 2)) < 2e-6 * scale
+    # a4: response per bin
+    ne = r.bins["nonempty"]
+    for key, gk in (("R", "R"), ("sqrtPnu", "Pnu"), ("sqrtPM", "PM")):
+        ref = r.response[key]
+        got = g[gk]
+        rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+        assert np.all(rel[ne] < (1e-9 if fp64 else 1e-5)), (key, rel[ne].max())
+        assert np.all(got[~ne] == 0)
+    # a5-a7: forces and the kick
+    emax, erms = force_errors(g["acc"], r.acc)
+    if fp64:
+        assert emax < 1e-5, emax
+    else:
+        assert erms < 2e-4, erms
+    dv = g["vel"] - g["vel0"]
+    scale_v = np.max(np.abs(dv)) + 1e-300
+    assert np.max(np.abs(dv - g["acc"] * 0.01)) < (1e-12 if fp64 else 1e-5) * scale_v
+
+
+def test_plain_fp64_kick_32():
+    w = synth.WORKLOADS["pm32_fp64"]
+    inp = make_inputs(w)
+    g = gpu_kick(w, inp)
+    r = oracle_kick(w, inp)
+    _check_common(w, g, r, True)
+
+
+def test_fp32_kick_ragged_64():
+    # 64^3 grid, FP32 form, a particle count that is not a multiple of any block size
+    w = synth.with_(synth.WORKLOADS["pm32_fp64"], name="pm64_fp32", ngrid=64, npart_side=64,
+                    box=128.0, precision="fp32", n_hist=8, n_kbins=24)
+    inp = make_inputs(w, npart=64 ** 3 - 37)
+    g = gpu_kick(w, inp)
+    r = oracle_kick(w, inp)
+    _check_common(w, g, r, False)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 256])
+def test_fft_and_bins_sizes(n, prec):
+    # spectrum of the deposit at every built grid size, both precisions
+    w = synth.Workload(f"fft{n}", n, min(n, 64), 2.0 * n, 0.15, 3, 2, 12, prec)
+    inp = make_inputs(w)
+    g = gpu_kick(w, inp)
+    F = g["F"].astype(np.int64)
+    spec = O.forward_fft(O.density_contrast(F, inp["pos64"].shape[1]))
+    d = np.abs(g["spec"] - spec)
+    scale = np.sqrt(np.mean(np.abs(spec) ** 2))
+    if prec == "fp64":
+        assert d.max() < 1e-11 * scale
+    else:
+        assert np.sqrt(np.mean(d ** 2)) < 2e-6 * scale
+    b = O.bin_power(spec, w.box, w.n_kbins)
+    assert np.array_equal(g["bins"][0], b["count"])
+
+
+def test_inverse_fields_against_oracle():
+    w = synth.with_(synth.WORKLOADS["pm32_fp64"], n_hist=6)
+    inp = make_inputs(w)
+    g = gpu_kick(w, inp, keep_fields=True)
+    r = oracle_kick(w, inp, n_hist=6)
+    for c in range(3):
+        ref = r.extras["fields"][c]
+        assert np.max(np.abs(g["fields"][c] - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def test_options_iters_fit_deconv_nohist_prev():
+    w = synth.with_(synth.WORKLOADS["pm32_fp64"], n_hist=10)
+    inp = make_inputs(w)
+    prev = np.abs(inp["pi"][0]) * 1.7
+    for kw, okw in ((dict(iters=2), dict(iters=2)),
+                    (dict(flags=0x1), dict(I_func=O.nu_I_fit)),
+                    (dict(flags=0x2), dict(deconvolve=True)),
+                    (dict(n_hist=0), dict(n_hist=0)),
+                    (dict(prev=prev), dict(prev=prev))):
+        g = gpu_kick(w, inp, **kw)
+        r = oracle_kick(w, inp, **okw)
+        _check_common(w, g, r, True)
+
+
+def test_massless_neutrinos_cdm_only():
+    w = synth.with_(synth.WORKLOADS["pm32_fp64"], m_nu_total=0.0, n_hist=4)
+    inp = make_inputs(w)
+    g = gpu_kick(w, inp)
+    r = oracle_kick(w, inp)
+    assert np.all(g["R"] == 0) and np.all(g["Pnu"] == 0)
+    _check_common(w, g, r, True)
+
+
+def test_single_particle_and_boundaries():
+    # one particle in the last cell with offsets 0 and just below 1 (wraps)
+    w = synth.with_(synth.WORKLOADS["pm32_fp64"], n_hist=2)
+    inp = make_inputs(w)
+    L, n = w.box, w.ngrid
+    d = L / n
+    pos = np.array([[(n - 1) * d], [0.0], [L - 1e-9]])
+    one = dict(inp, pos64=pos, vel=np.zeros((3, 1)))
+    g = gpu_kick(w, one)
+    r = oracle_kick(w, one)
+    assert np.array_equal(g["F"].astype(np.int64), r.F)
+    emax, _ = force_errors(g["acc"], r.acc + 1e-300)
+    assert np.allclose(g["acc"], r.acc, rtol=1e-9, atol=1e-9 * np.abs(r.acc).max())
+
+
+def test_errors_reported():
+    from paper_1209_0461_gb300 import nupm
+    w = synth.WORKLOADS["pm32_fp64"]
+    inp = make_inputs(w)
+    dev = torch.device("cuda")
+    pm = nupm.PM(w.ngrid, w.npart, w.box, w.omega_cdm, w.omega_nu, w.h, w.m_nu_total, 3,
+                 a_init=w.a_init, n_kbins=w.n_kbins, precision="fp32")
+    cells = synth.to_cell_offset(inp["pos64"], w.box, w.ngrid)
+    bad = cells.copy()
+    bad[3, 5] = np.float32(1.0).view(np.int32)          # offset outside [0, 1)
+    pos = torch.from_numpy(bad).to(dev).contiguous()
+    vel = torch.zeros((3, w.npart), dtype=torch.float32, device=dev)
+    with pytest.raises(nupm.PMError) as e:
+        pm.kick(pos, vel, w.a_kick, 0.01)
+    assert e.value.code == -7                            # PM_ERR_ORDER
+    pm.deposit(pos)
+    with pytest.raises(nupm.PMError) as e:
+        pm.check()
+    assert e.value.code == -2                            # PM_ERR_RANGE
+    pm.check()                                           # cleared
+    with pytest.raises(nupm.PMError) as e:
+        pm.nu_response(0.5 * w.a_init, [], None)
+    assert e.value.code == -2
+    with pytest.raises(nupm.PMError) as e:
+        pm.nu_response(w.a_kick, [w.a_kick * 2], torch.zeros((1, w.n_kbins), dtype=torch.float64,
+                                                             device=dev))
+    assert e.value.code == -2
+    pm.nu_response(w.a_kick, [], None)
+    with pytest.raises(nupm.PMError) as e:
+        pm.kick(pos, vel, w.a_kick * 1.01, 0.01)
+    assert e.value.code == -7
+    pm.close()
+
+
+def test_kick_and_drift_factors():
+    from paper_1209_0461_gb300 import nupm
+    w = synth.WORKLOADS["pm32_fp64"]
+    pm = nupm.PM(w.ngrid, w.npart, w.box, w.omega_cdm, w.omega_nu, w.h, w.m_nu_total, 3)
+    for a0, a1 in ((0.02, 0.1), (0.1, 0.1003), (0.5, 1.0)):
+        assert abs(pm.kick_factor(a0, a1) / O.kick_factor(a0, a1, w.omega_m) - 1) < 1e-13
+        assert abs(pm.drift_factor(a0, a1) / O.drift_factor(a0, a1, w.omega_m) - 1) < 1e-13
+    pm.close()
+    eds = nupm.PM(32, 8, 64.0, 1.0, 0.0, 0.7, 0.0, 0)
+    assert abs(eds.kick_factor(0.1, 0.4) - 2 / 3 * (0.4 ** 1.5 - 0.1 ** 1.5)) < 1e-14
+    eds.close()
+
+
+def test_deposit_deterministic_under_shuffle():
+    w = synth.WORKLOADS["pm32_fp64"]
+    inp = make_inputs(w)
+    perm = np.random.default_rng(3).permutation(w.npart)
+    shuf = dict(inp, pos64=inp["pos64"][:, perm].copy(), vel=inp["vel"][:, perm].copy())
+    g1 = gpu_kick(w, inp)
+    g2 = gpu_kick(w, shuf)
+    g3 = gpu_kick(w, inp)
+    assert np.array_equal(g1["F"], g2["F"]) and np.array_equal(g1["F"], g3["F"])
+    assert np.allclose(g1["acc"][:, perm], g2["acc"], rtol=0, atol=1e-12 * np.abs(g1["acc"]).max())
