@@ -112,8 +112,13 @@ int NUPM_FN(fft_pass)(const GridArgs& g, int pass, cudaStream_t s) {
 
 int NUPM_FN(bins)(const GridArgs& g, int nk, const long long* T_, double kf, double* partials, int nblk,
                   double* out, cudaStream_t s) {
-  const size_t sh = 3 * (size_t)nk * sizeof(double) + (size_t)(nk + 1) * sizeof(long long);
-  k_bin_power<T><<<nblk, 256, sh, s>>>(reinterpret_cast<const C*>(g.spec), g.n, nk, T_, kf, partials);
+  const size_t sh = kBinWarps * 3 * (size_t)nk * sizeof(double) + (size_t)(nk + 1) * sizeof(long long);
+  static size_t attr = 48 * 1024;
+  if (sh > attr) {
+    cudaFuncSetAttribute(k_bin_power<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    attr = sh;
+  }
+  k_bin_power<T><<<nblk, kBinWarps * 32, sh, s>>>(reinterpret_cast<const C*>(g.spec), g.n, nk, T_, kf, partials);
   k_bin_reduce<<<(3 * nk + 127) / 128, 128, 0, s>>>(partials, nblk, nk, out);
   return PM_OK;
 }

@@ -21,10 +21,8 @@ constexpr int kWeightOne = 1 << kWeightBits;
 // Record the first device-side error (status 0 -> code).
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
-__device__ __forceinline__ int wrap_index(long long c, int n) {
-  long long r = c % n;
-  return (int)(r < 0 ? r + n : r);
-}
+// Periodic wrap onto [0, n), n a power of two (two's complement mask).
+__device__ __forceinline__ int wrap_index(long long c, int n) { return (int)(c & (long long)(n - 1)); }
 
 // Quantised particle: cell (wrapped) and 16-bit weight per axis.  Returns
 // false (and records PM_ERR_RANGE) for an invalid particle.
@@ -119,63 +117,107 @@ __device__ __forceinline__ int find_bin(const long long* T, int nk, long long n2
 }
 
 // ---------------------------------------------------------------------------
-// a3: binned power of the packed spectrum.  Rows (z, y) are strided over the
-// grid; each CTA accumulates per-bin (count, ksum, psum) in shared memory and
-// writes one partial row; k_bin_reduce sums the partials in a fixed order.
+// a3: binned power of the packed spectrum, deterministic.  One warp per row
+// (z, y); lanes take consecutive x2.  Along a row n^2 = kz^2 + ky^2 + x2^2 grows
+// with x2, so the bins of a 32-lane chunk are contiguous lane segments: a
+// segmented shuffle scan sums each segment and its last lane adds the sums
+// to the warp's private accumulator (one writer per bin, no atomics).  Warps
+// and CTAs are then summed in a fixed order (k_bin_reduce).
 // The packed slot x2 = 0 is unpacked with the row at (-z, -y):
 //   A = (F(k) + conj F(-k)) / 2   (kx = 0),  B = (F(k) - conj F(-k)) / (2i)  (kx = N/2).
+// Shared memory: [kBinWarps][3][nk] doubles, then the nk + 1 thresholds.
 // ---------------------------------------------------------------------------
+constexpr int kBinWarps = 4;
+constexpr int kBinBatch = 8;   // chunks loaded per batch (bytes in flight)
+
 template <typename T>
-__global__ void k_bin_power(const cx<T>* __restrict__ spec, int n, int nk,
-                            const long long* __restrict__ thresholds, double kf,
-                            double* __restrict__ partials) {
+__global__ void __launch_bounds__(kBinWarps * 32)
+k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const long long* __restrict__ thresholds,
+            double kf, double* __restrict__ partials) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* acc = reinterpret_cast<double*>(smem_raw);             // [3][nk]
-  long long* thr = reinterpret_cast<long long*>(acc + 3 * nk);   // [nk + 1]
-  for (int i = threadIdx.x; i < 3 * nk; i += blockDim.x) acc[i] = 0.0;
+  double* all = reinterpret_cast<double*>(smem_raw);
+  long long* thr = reinterpret_cast<long long*>(all + kBinWarps * 3 * nk);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* acc = all + warp * 3 * nk;
+  for (int i = threadIdx.x; i < kBinWarps * 3 * nk; i += blockDim.x) all[i] = 0.0;
   for (int i = threadIdx.x; i <= nk; i += blockDim.x) thr[i] = thresholds[i];
   __syncthreads();
+  const unsigned full = 0xffffffffu;
   const int m = n / 2;
   const int64_t rows = (int64_t)n * n;
-  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+  for (int64_t row = (int64_t)blockIdx.x * kBinWarps + warp; row < rows;
+       row += (int64_t)gridDim.x * kBinWarps) {
     const int iz = (int)(row / n), iy = (int)(row % n);
     const long long kz = signed_freq(iz, n), ky = signed_freq(iy, n);
     const long long base2 = kz * kz + ky * ky;
     const cx<T>* r = spec + row * m;
-    for (int x2 = threadIdx.x; x2 < m; x2 += blockDim.x) {
-      const cx<T> f = r[x2];
-      if (x2 > 0) {
-        const long long n2 = base2 + (long long)x2 * x2;
-        const int b = find_bin(thr, nk, n2);
-        if (b >= 0) {
-          const double p = (double)f.x * f.x + (double)f.y * f.y;
-          atomicAdd(&acc[b], 2.0);
-          atomicAdd(&acc[nk + b], 2.0 * kf * sqrt((double)n2));
-          atomicAdd(&acc[2 * nk + b], 2.0 * p);
+    for (int x0 = 0; x0 < m; x0 += 32 * kBinBatch) {
+      cx<T> f[kBinBatch];
+#pragma unroll
+      for (int j = 0; j < kBinBatch; ++j) {
+        const int x2 = x0 + 32 * j + lane;
+        f[j] = x2 < m ? r[x2] : cx<T>{(T)0, (T)0};
+      }
+#pragma unroll
+      for (int j = 0; j < kBinBatch; ++j) {
+        const int x2 = x0 + 32 * j + lane;
+        if (x0 + 32 * j >= m) break;                     // warp-uniform
+        double p = 0.0, kk = 0.0, w = 0.0;
+        int b = -1;
+        if (x2 > 0 && x2 < m) {
+          const long long n2 = base2 + (long long)x2 * x2;
+          b = find_bin(thr, nk, n2);
+          p = 2.0 * ((double)f[j].x * f[j].x + (double)f[j].y * f[j].y);
+          kk = 2.0 * kf * sqrt((double)n2);
+          w = 2.0;
+        } else if (x2 == 0) {
+          const int jz = (n - iz) & (n - 1), jy = (n - iy) & (n - 1);
+          const cx<T> g = spec[((int64_t)jz * n + jy) * m];
+          const double ax = 0.5 * ((double)f[j].x + g.x), ay = 0.5 * ((double)f[j].y - g.y);
+          const double bx = 0.5 * ((double)f[j].y + g.y), by = -0.5 * ((double)f[j].x - g.x);
+          b = find_bin(thr, nk, base2);                  // kx = 0 mode joins the scan
+          p = ax * ax + ay * ay;
+          kk = kf * sqrt((double)base2);
+          w = 1.0;
+          const long long n2b = base2 + (long long)m * m;   // kx = N/2 mode: added directly
+          const int bb = find_bin(thr, nk, n2b);
+          if (bb >= 0) {
+            acc[bb] += 1.0;
+            acc[nk + bb] += kf * sqrt((double)n2b);
+            acc[2 * nk + bb] += bx * bx + by * by;
+          }
         }
-      } else {
-        const int jz = (n - iz) % n, jy = (n - iy) % n;
-        const cx<T> g = spec[((int64_t)jz * n + jy) * m];
-        const double ax = 0.5 * ((double)f.x + g.x), ay = 0.5 * ((double)f.y - g.y);
-        const double bx = 0.5 * ((double)f.y + g.y), by = -0.5 * ((double)f.x - g.x);
-        const long long n2a = base2, n2b = base2 + (long long)m * m;
-        const int ba = find_bin(thr, nk, n2a);
-        if (ba >= 0) {
-          atomicAdd(&acc[ba], 1.0);
-          atomicAdd(&acc[nk + ba], kf * sqrt((double)n2a));
-          atomicAdd(&acc[2 * nk + ba], ax * ax + ay * ay);
+        if (b < 0) p = kk = w = 0.0;
+        __syncwarp();
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const double p2 = __shfl_up_sync(full, p, off);
+          const double k2 = __shfl_up_sync(full, kk, off);
+          const double w2 = __shfl_up_sync(full, w, off);
+          const int b2 = __shfl_up_sync(full, b, off);
+          if (lane >= off && b2 == b) {
+            p += p2;
+            kk += k2;
+            w += w2;
+          }
         }
-        const int bb = find_bin(thr, nk, n2b);
-        if (bb >= 0) {
-          atomicAdd(&acc[bb], 1.0);
-          atomicAdd(&acc[nk + bb], kf * sqrt((double)n2b));
-          atomicAdd(&acc[2 * nk + bb], bx * bx + by * by);
+        const int bn = __shfl_down_sync(full, b, 1);
+        if (b >= 0 && (lane == 31 || bn != b)) {
+          acc[b] += w;
+          acc[nk + b] += kk;
+          acc[2 * nk + b] += p;
         }
+        __syncwarp();
       }
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 3 * nk; i += blockDim.x) partials[(int64_t)blockIdx.x * 3 * nk + i] = acc[i];
+  for (int i = threadIdx.x; i < 3 * nk; i += blockDim.x) {
+    double sum = 0.0;
+#pragma unroll
+    for (int wi = 0; wi < kBinWarps; ++wi) sum += all[wi * 3 * nk + i];
+    partials[(int64_t)blockIdx.x * 3 * nk + i] = sum;
+  }
 }
 
 // ---------------------------------------------------------------------------

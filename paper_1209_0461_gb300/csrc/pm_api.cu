@@ -413,21 +413,44 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   c->omega_l = 1.0 - c->omega_m;
   c->f_nu = onu / c->omega_m;
   // massless species carry no weight; a species of mass 0 is skipped
-  int used = 0;
+  // Species of equal mass and identical initial conditions give identical
+  // responses: merge them into one species carrying their summed weight.
+  const int nkb = p.n_kbins;
+  std::vector<std::vector<double>> sp_pi, sp_ti;
   double wsum = 0;
   for (int i = 0; i < ns; ++i) wsum += ms[i];
-  for (int i = 0; i < ns; ++i)
-    if (ms[i] > 0) {
+  int used = 0;
+  for (int i = 0; i < ns; ++i) {
+    if (ms[i] <= 0) continue;
+    std::vector<double> pi(nkb, 0.0), ti(nkb, 0.0);
+    for (int b = 0; b < nkb; ++b) {
+      if (sqrtPnu_init) pi[b] = sqrtPnu_init[(size_t)i * nkb + b];
+      if (theta_over_delta_init) ti[b] = theta_over_delta_init[(size_t)i * nkb + b];
+      if (!isfinite(pi[b]) || !isfinite(ti[b])) {
+        fprintf(stderr, "pm_init: non-finite neutrino initial condition\n");
+        delete c;
+        return PM_ERR_INVALID;
+      }
+    }
+    int match = -1;
+    for (int j = 0; j < used; ++j)
+      if (c->mass[j] == ms[i] && sp_pi[j] == pi && sp_ti[j] == ti) match = j;
+    if (match >= 0) {
+      c->wsp[match] += ms[i] / wsum;
+    } else {
       c->mass[used] = ms[i];
       c->wsp[used] = ms[i] / wsum;
+      sp_pi.push_back(pi);
+      sp_ti.push_back(ti);
       ++used;
     }
+  }
   c->ns = used;
   c->n2max = 3LL * (n / 2) * (n / 2);
   c->field_elems = (int64_t)n * n * (n / 2);
   c->cplx = c->fp64 ? 16 : 8;
   const size_t real = c->fp64 ? 8 : 4;
-  c->nblk_bins = 152 * 4;
+  c->nblk_bins = 152 * 8;
 
   int nspec = c->ns > 0 ? c->ns : 1;
   g_alloc_counter = 0;
@@ -471,22 +494,14 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
                     "quadrature upload");
   }
   if (rc == PM_OK) {
-    // neutrino ICs per species (zeros when not given)
+    // neutrino ICs per (merged) species
     std::vector<double> pi((size_t)nspec * c->nk, 0.0), ti((size_t)nspec * c->nk, 0.0);
-    int j = 0;
-    for (int i = 0; i < (ns > 0 ? ns : 0); ++i) {
-      if (ms[i] <= 0) continue;
+    for (int j = 0; j < c->ns; ++j)
       for (int b = 0; b < c->nk; ++b) {
-        if (sqrtPnu_init) pi[(size_t)j * c->nk + b] = sqrtPnu_init[(size_t)i * c->nk + b];
-        if (theta_over_delta_init) ti[(size_t)j * c->nk + b] = theta_over_delta_init[(size_t)i * c->nk + b];
-        if (!isfinite(pi[(size_t)j * c->nk + b]) || !isfinite(ti[(size_t)j * c->nk + b])) {
-          rc = fail(c, PM_ERR_INVALID, "non-finite neutrino initial condition");
-        }
+        pi[(size_t)j * c->nk + b] = sp_pi[j][b];
+        ti[(size_t)j * c->nk + b] = sp_ti[j][b];
       }
-      ++j;
-    }
-    if (rc == PM_OK)
-      rc = cuda_check(c, cudaMemcpy(c->d_pi, pi.data(), pi.size() * sizeof(double), cudaMemcpyHostToDevice), "IC upload");
+    rc = cuda_check(c, cudaMemcpy(c->d_pi, pi.data(), pi.size() * sizeof(double), cudaMemcpyHostToDevice), "IC upload");
     if (rc == PM_OK)
       rc = cuda_check(c, cudaMemcpy(c->d_ti, ti.data(), ti.size() * sizeof(double), cudaMemcpyHostToDevice), "IC upload");
   }

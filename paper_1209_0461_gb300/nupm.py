@@ -123,8 +123,10 @@ class PM:
         pi = None if sqrtPnu_init is None else np.ascontiguousarray(sqrtPnu_init, dtype=np.float64)
         ti = None if theta_over_delta_init is None else np.ascontiguousarray(
             theta_over_delta_init, dtype=np.float64)
+        if m_nu_total <= 0 or n_species <= 0:
+            pi = ti = None                     # no massive species: nothing to initialise
         for arr in (pi, ti):
-            if arr is not None and arr.size < max(1, n_species) * self.nk:
+            if arr is not None and arr.size < n_species * self.nk:
                 raise ValueError("initial-condition arrays must hold n_species x n_kbins values")
         ctx = C.c_void_p()
         rc = L.pm_init(C.byref(p), _dptr(pi), _dptr(ti), C.c_void_p(self.stream.cuda_stream),

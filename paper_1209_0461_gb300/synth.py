@@ -82,6 +82,9 @@ WORKLOADS = {
     "pm256_fp32_m030": Workload("pm256_fp32_m030", 256, 256, 512.0, 0.30, 3, 64, 128, "fp32"),
     "pm1024_p512_fp32": Workload("pm1024_p512_fp32", 1024, 512, 1000.0, 0.06, 3, 128, 256, "fp32"),
     "pm1024_p512_fp64": Workload("pm1024_p512_fp64", 1024, 512, 1000.0, 0.06, 3, 128, 256, "fp64"),
+    # smaller analogue of the precision form (same cell size and particle:grid
+    # ratio; every grid still larger than L2) for detailed profiling
+    "pm512_p256_fp32": Workload("pm512_p256_fp32", 512, 256, 500.0, 0.06, 3, 128, 256, "fp32"),
 }
 
 
