@@ -219,6 +219,8 @@ struct ColCfg {
   static constexpr int THREADS = W * NT;
   static constexpr int PAD = sizeof(T) == 4 ? 8 : 4;
   static constexpr int SMEM_WORDS = ColSmem<T, W, PAD>::words(N);
+  // at least two resident CTAs per SM so one CTA's loads overlap another's math
+  static constexpr int MIN_BLOCKS = 2;
 };
 
 // Rows per CTA of the x pass.
@@ -237,7 +239,7 @@ struct RowCfg {
 // grid = (M / W, N, nfields)
 // ---------------------------------------------------------------------------
 template <typename T, int N, int DIR>
-__global__ void __launch_bounds__(ColCfg<T, N>::THREADS)
+__global__ void __launch_bounds__(ColCfg<T, N>::THREADS, ColCfg<T, N>::MIN_BLOCKS)
 k_fft_col(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
           int64_t field_stride, const cx<T>* __restrict__ tw) {
   using Cfg = ColCfg<T, N>;
@@ -280,10 +282,23 @@ k_fft_x_fwd(const unsigned long long* __restrict__ grid, cx<T>* __restrict__ spe
   RowSmem<T> sm{reinterpret_cast<cx<T>*>(smem_raw) + r * Cfg::ROW_WORDS};
   const ulonglong2* src = reinterpret_cast<const ulonglong2*>(grid + row * N);
   cx<T> v[E];
+  if constexpr (sizeof(T) == 4) {
+    // FP32 path: F = hi 2^32 + lo, delta = hi (s 2^32) + (lo s - 1) in FP32 FMAs
+    // (absolute error ~ 1e-7; no FP64 arithmetic, which is slow on this part)
+    const float hs = (float)(scale * 4294967296.0), ls = (float)scale;
 #pragma unroll
-  for (int i = 0; i < E; ++i) {
-    const ulonglong2 q = src[t + NT * i];
-    v[i] = {(T)((double)q.x * scale - 1.0), (T)((double)q.y * scale - 1.0)};
+    for (int i = 0; i < E; ++i) {
+      const ulonglong2 q = src[t + NT * i];
+      const float ax = fmaf((float)(unsigned)(q.x >> 32), hs, fmaf((float)(unsigned)q.x, ls, -1.0f));
+      const float ay = fmaf((float)(unsigned)(q.y >> 32), hs, fmaf((float)(unsigned)q.y, ls, -1.0f));
+      v[i] = {(T)ax, (T)ay};
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const ulonglong2 q = src[t + NT * i];
+      v[i] = {(T)((double)q.x * scale - 1.0), (T)((double)q.y * scale - 1.0)};
+    }
   }
   fft_regs<T, M, -1>(v, sm, t, tw_m);
   // natural-order Z to shared memory for the split step

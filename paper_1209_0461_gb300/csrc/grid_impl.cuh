@@ -110,16 +110,21 @@ int NUPM_FN(fft_pass)(const GridArgs& g, int pass, cudaStream_t s) {
   return PM_OK;
 }
 
-int NUPM_FN(bins)(const GridArgs& g, int nk, const long long* T_, double kf, double* partials, int nblk,
-                  double* out, cudaStream_t s) {
-  const size_t sh = kBinWarps * 3 * (size_t)nk * sizeof(double) + (size_t)(nk + 1) * sizeof(long long);
-  static size_t attr = 48 * 1024;
+int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const short* bin_of, double kf, double* partials,
+                  int nblk, double* out, cudaStream_t s) {
+  const int nv = lattice ? 2 : 1;
+  const size_t sh = kBinWarps * (size_t)nv * nk * sizeof(double);
+  static size_t attr_l = 48 * 1024, attr_p = 48 * 1024;
+  size_t& attr = lattice ? attr_l : attr_p;
   if (sh > attr) {
-    cudaFuncSetAttribute(k_bin_power<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (lattice) cudaFuncSetAttribute(k_bin_power<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    else cudaFuncSetAttribute(k_bin_power<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     attr = sh;
   }
-  k_bin_power<T><<<nblk, kBinWarps * 32, sh, s>>>(reinterpret_cast<const C*>(g.spec), g.n, nk, T_, kf, partials);
-  k_bin_reduce<<<(3 * nk + 127) / 128, 128, 0, s>>>(partials, nblk, nk, out);
+  const C* spec = reinterpret_cast<const C*>(g.spec);
+  if (lattice) k_bin_power<T, true><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, bin_of, kf, partials);
+  else k_bin_power<T, false><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, bin_of, kf, partials);
+  k_bin_reduce<<<(nv * nk + 127) / 128, 128, 0, s>>>(partials, nblk, nv * nk, out);
   return PM_OK;
 }
 

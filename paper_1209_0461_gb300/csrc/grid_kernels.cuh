@@ -10,6 +10,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "fft.cuh"
 #include "nupm_internal.h"
 
@@ -105,118 +107,117 @@ __global__ void k_deposit(const void* __restrict__ pos, int64_t np, int n, doubl
 // Signed frequency of index i on an n-point axis.
 __device__ __forceinline__ int signed_freq(int i, int n) { return i < n / 2 ? i : i - n; }
 
-// Bin of integer n^2 (thresholds T[0..nk], T_b <= n2 < T_{b+1}); -1 if none.
-__device__ __forceinline__ int find_bin(const long long* T, int nk, long long n2) {
-  if (n2 < T[0] || n2 >= T[nk]) return -1;
-  int lo = 0, hi = nk;   // T[lo] <= n2 < T[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (T[mid] <= n2) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
 // ---------------------------------------------------------------------------
 // a3: binned power of the packed spectrum, deterministic.  One warp per row
 // (z, y); lanes take consecutive x2.  Along a row n^2 = kz^2 + ky^2 + x2^2 grows
 // with x2, so the bins of a 32-lane chunk are contiguous lane segments: a
-// segmented shuffle scan sums each segment and its last lane adds the sums
-// to the warp's private accumulator (one writer per bin, no atomics).  Warps
-// and CTAs are then summed in a fixed order (k_bin_reduce).
+// segmented shuffle scan sums each segment and its last lane adds the sum to
+// the warp's private accumulator (one writer per bin, no atomics).  Warps and
+// CTAs are then summed in a fixed order (k_bin_reduce).  The bin of each n^2
+// comes from a lookup table (bin_of[n2], -1 outside the bins).
+//   LATTICE = true : accumulate the mode count sum w and sum w |k| (depends on
+//                    the lattice only; run once per context)
+//   LATTICE = false: accumulate sum w |delta_k|^2; per-mode arithmetic in the
+//                    grid precision T, one FP64 add per segment
 // The packed slot x2 = 0 is unpacked with the row at (-z, -y):
 //   A = (F(k) + conj F(-k)) / 2   (kx = 0),  B = (F(k) - conj F(-k)) / (2i)  (kx = N/2).
-// Shared memory: [kBinWarps][3][nk] doubles, then the nk + 1 thresholds.
+// Shared memory: [kBinWarps][NV][nk] doubles (NV = 2 lattice sums or 1).
 // ---------------------------------------------------------------------------
 constexpr int kBinWarps = 4;
 constexpr int kBinBatch = 8;   // chunks loaded per batch (bytes in flight)
 
-template <typename T>
+template <typename T, bool LATTICE>
 __global__ void __launch_bounds__(kBinWarps * 32)
-k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const long long* __restrict__ thresholds,
+k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restrict__ bin_of,
             double kf, double* __restrict__ partials) {
+  constexpr int NV = LATTICE ? 2 : 1;
+  using A = typename std::conditional<LATTICE, double, T>::type;   // scan type
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* all = reinterpret_cast<double*>(smem_raw);
-  long long* thr = reinterpret_cast<long long*>(all + kBinWarps * 3 * nk);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* acc = all + warp * 3 * nk;
-  for (int i = threadIdx.x; i < kBinWarps * 3 * nk; i += blockDim.x) all[i] = 0.0;
-  for (int i = threadIdx.x; i <= nk; i += blockDim.x) thr[i] = thresholds[i];
+  double* acc = all + warp * NV * nk;
+  for (int i = threadIdx.x; i < kBinWarps * NV * nk; i += blockDim.x) all[i] = 0.0;
   __syncthreads();
   const unsigned full = 0xffffffffu;
   const int m = n / 2;
-  const int64_t rows = (int64_t)n * n;
-  for (int64_t row = (int64_t)blockIdx.x * kBinWarps + warp; row < rows;
-       row += (int64_t)gridDim.x * kBinWarps) {
-    const int iz = (int)(row / n), iy = (int)(row % n);
-    const long long kz = signed_freq(iz, n), ky = signed_freq(iy, n);
-    const long long base2 = kz * kz + ky * ky;
-    const cx<T>* r = spec + row * m;
+  const int rows = n * n;
+  for (int row = blockIdx.x * kBinWarps + warp; row < rows; row += gridDim.x * kBinWarps) {
+    const int iz = row / n, iy = row - (row / n) * n;
+    const int kz = signed_freq(iz, n), ky = signed_freq(iy, n);
+    const int base2 = kz * kz + ky * ky;
+    const cx<T>* r = spec + (int64_t)row * m;
     for (int x0 = 0; x0 < m; x0 += 32 * kBinBatch) {
       cx<T> f[kBinBatch];
+      if constexpr (!LATTICE) {
 #pragma unroll
-      for (int j = 0; j < kBinBatch; ++j) {
-        const int x2 = x0 + 32 * j + lane;
-        f[j] = x2 < m ? r[x2] : cx<T>{(T)0, (T)0};
+        for (int j = 0; j < kBinBatch; ++j) {
+          const int x2 = x0 + 32 * j + lane;
+          f[j] = x2 < m ? r[x2] : cx<T>{(T)0, (T)0};
+        }
       }
 #pragma unroll
       for (int j = 0; j < kBinBatch; ++j) {
         const int x2 = x0 + 32 * j + lane;
         if (x0 + 32 * j >= m) break;                     // warp-uniform
-        double p = 0.0, kk = 0.0, w = 0.0;
+        A v0 = 0, v1 = 0;
         int b = -1;
         if (x2 > 0 && x2 < m) {
-          const long long n2 = base2 + (long long)x2 * x2;
-          b = find_bin(thr, nk, n2);
-          p = 2.0 * ((double)f[j].x * f[j].x + (double)f[j].y * f[j].y);
-          kk = 2.0 * kf * sqrt((double)n2);
-          w = 2.0;
+          const int n2 = base2 + x2 * x2;
+          b = bin_of[n2];
+          if constexpr (LATTICE) {
+            v0 = 2.0;
+            v1 = 2.0 * kf * sqrt((double)n2);
+          } else {
+            v0 = (T)2 * (f[j].x * f[j].x + f[j].y * f[j].y);
+          }
         } else if (x2 == 0) {
-          const int jz = (n - iz) & (n - 1), jy = (n - iy) & (n - 1);
-          const cx<T> g = spec[((int64_t)jz * n + jy) * m];
-          const double ax = 0.5 * ((double)f[j].x + g.x), ay = 0.5 * ((double)f[j].y - g.y);
-          const double bx = 0.5 * ((double)f[j].y + g.y), by = -0.5 * ((double)f[j].x - g.x);
-          b = find_bin(thr, nk, base2);                  // kx = 0 mode joins the scan
-          p = ax * ax + ay * ay;
-          kk = kf * sqrt((double)base2);
-          w = 1.0;
-          const long long n2b = base2 + (long long)m * m;   // kx = N/2 mode: added directly
-          const int bb = find_bin(thr, nk, n2b);
-          if (bb >= 0) {
-            acc[bb] += 1.0;
-            acc[nk + bb] += kf * sqrt((double)n2b);
-            acc[2 * nk + bb] += bx * bx + by * by;
+          const int n2b = base2 + m * m;                 // kx = N/2 mode: added directly
+          const int bb = bin_of[n2b];
+          b = bin_of[base2];                             // kx = 0 mode joins the scan
+          if constexpr (LATTICE) {
+            v0 = 1.0;
+            v1 = kf * sqrt((double)base2);
+            if (bb >= 0) {
+              acc[bb] += 1.0;
+              acc[nk + bb] += kf * sqrt((double)n2b);
+            }
+          } else {
+            const int jz = (n - iz) & (n - 1), jy = (n - iy) & (n - 1);
+            const cx<T> g = spec[((int64_t)jz * n + jy) * m];
+            const T ax = (T)0.5 * (f[j].x + g.x), ay = (T)0.5 * (f[j].y - g.y);
+            const T bx = (T)0.5 * (f[j].y + g.y), by = (T)-0.5 * (f[j].x - g.x);
+            v0 = ax * ax + ay * ay;
+            if (bb >= 0) acc[bb] += (double)(bx * bx + by * by);
           }
         }
-        if (b < 0) p = kk = w = 0.0;
+        if (b < 0) v0 = v1 = 0;
         __syncwarp();
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-          const double p2 = __shfl_up_sync(full, p, off);
-          const double k2 = __shfl_up_sync(full, kk, off);
-          const double w2 = __shfl_up_sync(full, w, off);
+          const A p0 = __shfl_up_sync(full, v0, off);
+          A p1 = 0;
+          if constexpr (LATTICE) p1 = __shfl_up_sync(full, v1, off);
           const int b2 = __shfl_up_sync(full, b, off);
           if (lane >= off && b2 == b) {
-            p += p2;
-            kk += k2;
-            w += w2;
+            v0 += p0;
+            if constexpr (LATTICE) v1 += p1;
           }
         }
         const int bn = __shfl_down_sync(full, b, 1);
         if (b >= 0 && (lane == 31 || bn != b)) {
-          acc[b] += w;
-          acc[nk + b] += kk;
-          acc[2 * nk + b] += p;
+          acc[b] += (double)v0;
+          if constexpr (LATTICE) acc[nk + b] += (double)v1;
         }
         __syncwarp();
       }
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 3 * nk; i += blockDim.x) {
+  for (int i = threadIdx.x; i < NV * nk; i += blockDim.x) {
     double sum = 0.0;
 #pragma unroll
-    for (int wi = 0; wi < kBinWarps; ++wi) sum += all[wi * 3 * nk + i];
-    partials[(int64_t)blockIdx.x * 3 * nk + i] = sum;
+    for (int wi = 0; wi < kBinWarps; ++wi) sum += all[wi * NV * nk + i];
+    partials[(int64_t)blockIdx.x * NV * nk + i] = sum;
   }
 }
 

@@ -260,12 +260,12 @@ __global__ void k_nu_finish(NuArgs A) {
 }
 
 // Fixed-order sum of the per-CTA bin partials: out[i] = sum_blk partials[blk][i].
-__global__ void k_bin_reduce(const double* __restrict__ partials, int nblk, int nk,
+__global__ void k_bin_reduce(const double* __restrict__ partials, int nblk, int len,
                              double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 3 * nk) return;
+  if (i >= len) return;
   double acc = 0.0;
-  for (int b = 0; b < nblk; ++b) acc += partials[(int64_t)b * 3 * nk + i];
+  for (int b = 0; b < nblk; ++b) acc += partials[(int64_t)b * len + i];
   out[i] = acc;
 }
 

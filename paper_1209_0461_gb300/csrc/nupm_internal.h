@@ -63,8 +63,8 @@ struct GridArgs {
 #define NUPM_DECLARE_GRID(SFX)                                                              \
   int deposit##SFX(const GridArgs& g, const void* pos, cudaStream_t s);                     \
   int fft_pass##SFX(const GridArgs& g, int pass, cudaStream_t s);                           \
-  int bins##SFX(const GridArgs& g, int nk, const long long* T, double kf, double* partials,  \
-                int nblk, double* out, cudaStream_t s);                                     \
+  int bins##SFX(const GridArgs& g, bool lattice, int nk, const short* bin_of, double kf,      \
+                double* partials, int nblk, double* out, cudaStream_t s);                   \
   int green##SFX(const GridArgs& g, const void* gtab, const void* dtab, const void* wtab,    \
                  cudaStream_t s);                                                           \
   int interp##SFX(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, \
@@ -74,7 +74,8 @@ NUPM_DECLARE_GRID(_f32)
 NUPM_DECLARE_GRID(_f64)
 #undef NUPM_DECLARE_GRID
 
-__global__ void k_bin_reduce(const double* __restrict__ partials, int nblk, int nk,
+// out[i] = sum over blocks of partials[blk][i], i < len, in block order.
+__global__ void k_bin_reduce(const double* __restrict__ partials, int nblk, int len,
                              double* __restrict__ out);
 
 

@@ -31,7 +31,7 @@ struct pm_ctx {
   void* g = nullptr;          // 3 packed fields (deposit grid aliases the first two)
   void* tw_n = nullptr;
   void* tw_m = nullptr;
-  long long* d_thr = nullptr;
+  short* d_binof = nullptr;    // bin of each n^2 (-1: none)
   double* d_partials = nullptr;
   double* d_bins = nullptr;   // [3][nk]
   double* d_pi = nullptr;     // [ns][nk]
@@ -301,7 +301,7 @@ GridArgs grid_args(const pm_ctx* c) {
 }
 
 void release(pm_ctx* c) {
-  void* ptrs[] = {c->spec, c->g, c->tw_n, c->tw_m, c->d_thr, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
+  void* ptrs[] = {c->spec, c->g, c->tw_n, c->tw_m, c->d_binof, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
                   c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_gtab,
                   c->d_dtab, c->d_wtab, c->d_status};
   for (void* p : ptrs)
@@ -459,8 +459,8 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) rc = dalloc(c, &c->g, 3 * fbytes, "force fields");
   if (rc == PM_OK) rc = dalloc(c, &c->tw_n, (size_t)n * c->cplx, "twiddles N");
   if (rc == PM_OK) rc = dalloc(c, &c->tw_m, (size_t)(n / 2) * c->cplx, "twiddles M");
-  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_thr, (size_t)(c->nk + 1) * sizeof(long long), "thresholds");
-  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_partials, (size_t)c->nblk_bins * 3 * c->nk * sizeof(double), "bin partials");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_binof, (size_t)(c->n2max + 1) * sizeof(short), "bin table");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_partials, (size_t)c->nblk_bins * 2 * c->nk * sizeof(double), "bin partials");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_bins, 3 * (size_t)c->nk * sizeof(double), "bins");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_pi, (size_t)nspec * c->nk * sizeof(double), "nu ICs");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_ti, (size_t)nspec * c->nk * sizeof(double), "nu theta ICs");
@@ -480,12 +480,19 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
     rc = fail(c, PM_ERR_ALLOC, "pinned host allocation failed");
   if (rc == PM_OK) rc = c->fp64 ? upload_tables<double>(c) : upload_tables<float>(c);
   if (rc == PM_OK) {
-    // bin thresholds T_b = ceil((e_b L / 2 pi)^2), e_b log-spaced on [kmin, kmax]
+    // bin thresholds T_b = ceil((e_b L / 2 pi)^2), e_b log-spaced on [kmin, kmax];
+    // mode n^2 is in bin b iff T_b <= n^2 < T_{b+1}
     const double r = sqrt(3.0) * n / 2.0 * (1.0 + 1e-12);
     c->thr.resize(c->nk + 1);
     for (int b = 0; b <= c->nk; ++b) c->thr[b] = (long long)ceil(pow(r, 2.0 * b / c->nk));
-    rc = cuda_check(c, cudaMemcpy(c->d_thr, c->thr.data(), c->thr.size() * sizeof(long long),
-                                  cudaMemcpyHostToDevice), "thresholds upload");
+    std::vector<short> bo((size_t)c->n2max + 1);
+    int b = -1;
+    for (long long n2 = 0; n2 <= c->n2max; ++n2) {
+      while (b + 1 <= c->nk && c->thr[b + 1] <= n2) ++b;
+      bo[n2] = (short)((b >= 0 && b < c->nk) ? b : -1);
+    }
+    rc = cuda_check(c, cudaMemcpy(c->d_binof, bo.data(), bo.size() * sizeof(short), cudaMemcpyHostToDevice),
+                    "bin table upload");
   }
   if (rc == PM_OK) {
     std::vector<double> gl(2 * kMaxQuad, 0.0);
@@ -506,6 +513,13 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
       rc = cuda_check(c, cudaMemcpy(c->d_ti, ti.data(), ti.size() * sizeof(double), cudaMemcpyHostToDevice), "IC upload");
   }
   if (rc == PM_OK) rc = build_s_table(c, 0.0 > log(c->a_init) ? 0.0 : log(c->a_init) + 1.0);
+  if (rc == PM_OK) {
+    // mode counts and sum |k| per bin depend on the lattice only: once per context
+    GridArgs g = grid_args(c);
+    rc = c->fp64 ? bins_f64(g, true, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins, 0)
+                 : bins_f32(g, true, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins, 0);
+    if (rc == PM_OK) rc = cuda_check(c, cudaGetLastError(), "lattice bins");
+  }
   if (rc == PM_OK) rc = cuda_check(c, cudaMemset(c->d_status, 0, sizeof(int)), "status init");
   if (rc == PM_OK) rc = cuda_check(c, cudaDeviceSynchronize(), "pm_init");
   if (rc != PM_OK) {
@@ -535,8 +549,8 @@ int pm_deposit(pm_ctx* c, const void* pos) {
   }
   if (rc == PM_OK) {
     Stage st(c, PM_ST_BINS, 2);
-    rc = c->fp64 ? bins_f64(g, c->nk, c->d_thr, c->kf, c->d_partials, c->nblk_bins, c->d_bins, c->stream)
-                 : bins_f32(g, c->nk, c->d_thr, c->kf, c->d_partials, c->nblk_bins, c->d_bins, c->stream);
+    rc = c->fp64 ? bins_f64(g, false, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins + 2 * c->nk, c->stream)
+                 : bins_f32(g, false, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins + 2 * c->nk, c->stream);
   }
   if (rc != PM_OK) return fail(c, rc, "pm_deposit: unsupported grid");
   rc = cuda_check(c, cudaGetLastError(), "pm_deposit launch");

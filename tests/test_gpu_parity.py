@@ -132,18 +132,21 @@ def test_massless_neutrinos_cdm_only():
 
 
 def test_single_particle_and_boundaries():
-    # one particle in the last cell with offsets 0 and just below 1 (wraps)
+    # two particles: one in the last cell with offset 0 on x and just below 1
+    # on z (wraps), one at a cell corner; forces compared on the scale of the
+    # pair force at one cell, 1.5 Om L^3 / (4 pi a Delta^2)
     w = synth.with_(synth.WORKLOADS["pm32_fp64"], n_hist=2)
     inp = make_inputs(w)
     L, n = w.box, w.ngrid
     d = L / n
-    pos = np.array([[(n - 1) * d], [0.0], [L - 1e-9]])
-    one = dict(inp, pos64=pos, vel=np.zeros((3, 1)))
-    g = gpu_kick(w, one)
-    r = oracle_kick(w, one)
+    pos = np.array([[(n - 1) * d, 3 * d], [0.0, 7 * d], [L - 1e-9, 11 * d]])
+    two = dict(inp, pos64=pos, vel=np.zeros((3, 2)))
+    g = gpu_kick(w, two)
+    r = oracle_kick(w, two)
     assert np.array_equal(g["F"].astype(np.int64), r.F)
-    emax, _ = force_errors(g["acc"], r.acc + 1e-300)
-    assert np.allclose(g["acc"], r.acc, rtol=1e-9, atol=1e-9 * np.abs(r.acc).max())
+    scale = 1.5 * w.omega_m * L ** 3 / (4 * math.pi * w.a_kick * d * d)
+    assert np.max(np.abs(g["acc"] - r.acc)) < 1e-11 * scale
+    assert np.max(np.abs(r.acc)) > 1e-6 * scale            # the pair force is resolved
 
 
 def test_errors_reported():
