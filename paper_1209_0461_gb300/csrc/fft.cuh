@@ -262,6 +262,109 @@ k_fft_col(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
 }
 
 // ---------------------------------------------------------------------------
+// Inverse z pass with the Green function (a5 + first third of a6).  Columns
+// (x2, ky), transform along kz.  Two transforms per tile from the same input
+// spectrum (the second read hits L2):
+//   out_phi = IFFT_z(G F),   out_dz = IFFT_z(-i D(kz) G F)
+// G = gtab[n^2] (x wtab^3 with deconvolution).  The packed column x2 = 0
+// (A + i B of the kx = 0 / N/2 planes, whose G differ) comes pre-multiplied
+// from plane0[ky][kz] (k_green_plane0).  grid = (M / W, N)
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(ColCfg<T, N>::THREADS, ColCfg<T, N>::MIN_BLOCKS)
+k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, cx<T>* __restrict__ out_dz,
+                  const cx<T>* __restrict__ plane0, const T* __restrict__ gtab, const T* __restrict__ dtab,
+                  const T* __restrict__ wtab, const cx<T>* __restrict__ tw) {
+  using Cfg = ColCfg<T, N>;
+  constexpr int M = N / 2, E = Plan<T, N>::R1, NT = N / E, W = Cfg::W, RL = last_radix<T, N>();
+  constexpr int64_t ES = (int64_t)N * M;   // element stride along z
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = threadIdx.x % W;
+  const int t = threadIdx.x / W;
+  const int x2 = blockIdx.x * W + c;
+  const int iy = blockIdx.y;
+  const int ky = iy < N / 2 ? iy : iy - N;
+  const int base2 = ky * ky + x2 * x2;
+  const int64_t off = (int64_t)iy * M + x2;
+  ColSmem<T, W, Cfg::PAD> sm{reinterpret_cast<cx<T>*>(smem_raw), c};
+  const T wyx = wtab ? wtab[iy] * wtab[x2] : (T)1;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    cx<T> v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int iz = t + NT * i;
+      cx<T> f;
+      if (x2 == 0) {
+        f = plane0[(int64_t)iy * N + iz];
+      } else {
+        const int kz = iz < N / 2 ? iz : iz - N;
+        T g = gtab[base2 + kz * kz];
+        if (wtab) g *= wyx * wtab[iz];
+        f = cscale(spec[off + (int64_t)iz * ES], g);
+      }
+      if (pass == 1) {
+        const T d = dtab[iz];
+        f = {d * f.y, -d * f.x};                 // -i D(kz) f
+      }
+      v[i] = f;
+    }
+    fft_regs<T, N, +1>(v, sm, t, tw);
+    cx<T>* dst = pass == 0 ? out_phi : out_dz;
+#pragma unroll
+    for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+      for (int i = 0; i < RL; ++i) dst[off + (int64_t)(t + NT * b + i * (N / RL)) * ES] = v[b * RL + i];
+    __syncthreads();   // the next transform reuses the shared memory
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse y pass with the y gradient (second third of a6).  Columns (x2, z),
+// transform along ky, three transforms per tile:
+//   g_dy  = IFFT_y(-i D(ky) g_phi)   (reads g_phi)
+//   g_phi = IFFT_y(g_phi)            (re-reads g_phi, L2)
+//   g_dz  = IFFT_y(g_dz)
+// -i D(ky) is linear, so it acts on the packed column x2 = 0 as on the others.
+// grid = (M / W, N)
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(ColCfg<T, N>::THREADS, ColCfg<T, N>::MIN_BLOCKS)
+k_fft_y_inv_grad(cx<T>* __restrict__ g_phi, cx<T>* __restrict__ g_dy, cx<T>* __restrict__ g_dz,
+                 const T* __restrict__ dtab, const cx<T>* __restrict__ tw) {
+  using Cfg = ColCfg<T, N>;
+  constexpr int M = N / 2, E = Plan<T, N>::R1, NT = N / E, W = Cfg::W, RL = last_radix<T, N>();
+  constexpr int64_t ES = M;   // element stride along y
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = threadIdx.x % W;
+  const int t = threadIdx.x / W;
+  const int64_t off = (int64_t)blockIdx.y * N * M + (int64_t)blockIdx.x * W + c;
+  ColSmem<T, W, Cfg::PAD> sm{reinterpret_cast<cx<T>*>(smem_raw), c};
+#pragma unroll 1
+  for (int pass = 0; pass < 3; ++pass) {
+    const cx<T>* src = pass == 2 ? g_dz : g_phi;
+    cx<T>* dst = pass == 0 ? g_dy : (pass == 1 ? g_phi : g_dz);
+    cx<T> v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int iy = t + NT * i;
+      cx<T> f = src[off + (int64_t)iy * ES];
+      if (pass == 0) {
+        const T d = dtab[iy];
+        f = {d * f.y, -d * f.x};
+      }
+      v[i] = f;
+    }
+    fft_regs<T, N, +1>(v, sm, t, tw);
+#pragma unroll
+    for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+      for (int i = 0; i < RL; ++i) dst[off + (int64_t)(t + NT * b + i * (N / RL)) * ES] = v[b * RL + i];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Forward x pass: fixed-point deposit rows -> delta -> packed half spectrum.
 //   z[n] = delta[2n] + i delta[2n+1];  Z = FFT_M(z);
 //   X[k] = (Z[k] + conj Z[M-k]) / 2 - (i/2) W_N^k (Z[k] - conj Z[M-k]),
@@ -329,7 +432,8 @@ k_fft_x_fwd(const unsigned long long* __restrict__ grid, cx<T>* __restrict__ spe
 }
 
 // ---------------------------------------------------------------------------
-// Inverse x pass, in place: packed half-spectrum rows -> N reals (unscaled):
+// Inverse x pass, in place: packed half-spectrum rows -> N reals (unscaled),
+// fields with bit f of grad_mask set are first multiplied by -i D(kx):
 //   Z'[k] = (X[k] + conj X[M-k]) + i W_N^{-k} (X[k] - conj X[M-k]),
 //   Z'[0] = (X0 + XM) + i (X0 - XM) with X0 = Re P0, XM = Im P0;
 //   z = IFFT_M(Z');  x[2n] = Re z[n], x[2n+1] = Im z[n].
@@ -338,7 +442,7 @@ k_fft_x_fwd(const unsigned long long* __restrict__ grid, cx<T>* __restrict__ spe
 template <typename T, int N>
 __global__ void __launch_bounds__(RowCfg<T, N>::THREADS)
 k_fft_x_inv(cx<T>* __restrict__ data, int64_t field_stride, const cx<T>* __restrict__ tw_m,
-            const cx<T>* __restrict__ tw_n) {
+            const cx<T>* __restrict__ tw_n, const T* __restrict__ dtab, int grad_mask) {
   using Cfg = RowCfg<T, N>;
   constexpr int M = N / 2, E = Plan<T, M>::R1, NT = M / E, RL = last_radix<T, M>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -347,8 +451,20 @@ k_fft_x_inv(cx<T>* __restrict__ data, int64_t field_stride, const cx<T>* __restr
   const int64_t row = (int64_t)blockIdx.x * Cfg::ROWS + r;
   RowSmem<T> sm{reinterpret_cast<cx<T>*>(smem_raw) + r * Cfg::ROW_WORDS};
   cx<T>* rowp = data + (int64_t)blockIdx.z * field_stride + row * M;
+  if ((grad_mask >> blockIdx.z) & 1) {
+    // x gradient first: X'[k] = -i D(k) X[k]; D vanishes on kx = 0 and N/2, so the
+    // packed slot 0 (X[0] + i X[N/2]) becomes 0
 #pragma unroll
-  for (int i = 0; i < E; ++i) sm.st(t + NT * i, rowp[t + NT * i]);
+    for (int i = 0; i < E; ++i) {
+      const int k = t + NT * i;
+      const cx<T> x = rowp[k];
+      const T d = k == 0 ? (T)0 : dtab[k];
+      sm.st(k, cx<T>{d * x.y, -d * x.x});
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) sm.st(t + NT * i, rowp[t + NT * i]);
+  }
   __syncthreads();
   cx<T> v[E];
 #pragma unroll

@@ -26,8 +26,9 @@ void ensure_attrs() {
   const int col_smem = (int)((size_t)CC::SMEM_WORDS * sizeof(C));
   cudaFuncSetAttribute(k_fft_x_fwd<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
   cudaFuncSetAttribute(k_fft_col<T, N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
-  cudaFuncSetAttribute(k_fft_col<T, N, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
   cudaFuncSetAttribute(k_fft_x_inv<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
+  cudaFuncSetAttribute(k_fft_z_inv_green<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+  cudaFuncSetAttribute(k_fft_y_inv_grad<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
   done = true;
 }
 
@@ -57,16 +58,25 @@ void fft_pass_n(const GridArgs& g, int pass, cudaStream_t s) {
     case kPassZFwd:
       k_fft_col<T, N, -1><<<dim3(M / CC::W, N, 1), CC::THREADS, col_smem, s>>>(spec, (int64_t)M, (int64_t)N * M, 0, twn);
       break;
-    case kPassZInv:
-      k_fft_col<T, N, +1><<<dim3(M / CC::W, N, 3), CC::THREADS, col_smem, s>>>(f, (int64_t)M, (int64_t)N * M,
-                                                                             g.field_elems, twn);
+    case kPassZInv: {
+      // Green + z: spectrum -> g0 (phi), g2 (d/dz phi)
+      const int64_t fe = g.field_elems;
+      k_fft_z_inv_green<T, N><<<dim3(M / CC::W, N, 1), CC::THREADS, col_smem, s>>>(
+          spec, f, f + 2 * fe, reinterpret_cast<const C*>(g.plane0), reinterpret_cast<const T*>(g.gtab),
+          reinterpret_cast<const T*>(g.dtab), reinterpret_cast<const T*>(g.wtab), twn);
       break;
-    case kPassYInv:
-      k_fft_col<T, N, +1><<<dim3(M / CC::W, N, 3), CC::THREADS, col_smem, s>>>(f, (int64_t)N * M, (int64_t)M,
-                                                                             g.field_elems, twn);
+    }
+    case kPassYInv: {
+      // y with the y gradient: g0 -> g1 (d/dy), g0 -> g0, g2 -> g2
+      const int64_t fe = g.field_elems;
+      k_fft_y_inv_grad<T, N><<<dim3(M / CC::W, N, 1), CC::THREADS, col_smem, s>>>(
+          f, f + fe, f + 2 * fe, reinterpret_cast<const T*>(g.dtab), twn);
       break;
+    }
     case kPassXInv:
-      k_fft_x_inv<T, N><<<dim3((unsigned)(rows / RC::ROWS), 1, 3), RC::THREADS, row_smem, s>>>(f, g.field_elems, twm, twn);
+      // x with the x gradient on field 0 (phi -> d/dx phi); fields 1, 2 as they are
+      k_fft_x_inv<T, N><<<dim3((unsigned)(rows / RC::ROWS), 1, 3), RC::THREADS, row_smem, s>>>(
+          f, g.field_elems, twm, twn, reinterpret_cast<const T*>(g.dtab), 1);
       break;
   }
 }
@@ -128,12 +138,11 @@ int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const short* bin_of, 
   return PM_OK;
 }
 
-int NUPM_FN(green)(const GridArgs& g, const void* gtab, const void* dtab, const void* wtab, cudaStream_t s) {
-  const int64_t total = (int64_t)g.n * g.n * (g.n / 2);
-  k_green<T><<<grid_blocks(total, 256), 256, 0, s>>>(reinterpret_cast<const C*>(g.spec), reinterpret_cast<C*>(g.g),
-                                                    g.field_elems, g.n, reinterpret_cast<const T*>(gtab),
-                                                    reinterpret_cast<const T*>(dtab),
-                                                    reinterpret_cast<const T*>(wtab));
+int NUPM_FN(green)(const GridArgs& g, cudaStream_t s) {
+  const int total = g.n * g.n;
+  k_green_plane0<T><<<grid_blocks(total, 256), 256, 0, s>>>(
+      reinterpret_cast<const C*>(g.spec), reinterpret_cast<C*>(g.plane0), g.n, reinterpret_cast<const T*>(g.gtab),
+      reinterpret_cast<const T*>(g.wtab));
   return PM_OK;
 }
 

@@ -222,58 +222,32 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restri
 }
 
 // ---------------------------------------------------------------------------
-// a5: Green function + gradient.  phi = G(n^2) [D^-4] delta_cdm with the
-// neutrino factor folded into G(n^2) (k_green_table), acc_c = -i D_c(k) phi.
-// grid-stride over all modes of the packed spectrum; writes 3 packed spectra.
+// a5 on the packed column x2 = 0: its slot holds A + i B, the kx = 0 and
+// kx = N/2 plane spectra, whose Green factors differ.  Unpack with the
+// partner at (-ky, -kz), multiply each by its G(n^2) (and deconvolution), and
+// repack P = G_A A + i G_B B into plane0[ky][kz] for k_fft_z_inv_green.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out, int64_t field_stride,
-                        int n, const T* __restrict__ gtab, const T* __restrict__ dtab,
-                        const T* __restrict__ wtab /* 1/sinc^4 per index or nullptr */) {
+__global__ void k_green_plane0(const cx<T>* __restrict__ spec, cx<T>* __restrict__ plane0, int n,
+                               const T* __restrict__ gtab, const T* __restrict__ wtab) {
   const int m = n / 2;
-  const int64_t total = (int64_t)n * n * m;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int x2 = (int)(idx % m);
-    const int64_t row = idx / m;
-    const int iz = (int)(row / n), iy = (int)(row % n);
-    const long long kz = signed_freq(iz, n), ky = signed_freq(iy, n);
-    const long long base2 = kz * kz + ky * ky;
-    const T dy = dtab[iy], dz = dtab[iz];
-    const cx<T> f = spec[idx];
-    cx<T> o0, o1, o2;
-    if (x2 > 0) {
-      T g = gtab[base2 + (long long)x2 * x2];
-      if (wtab) g *= wtab[x2] * wtab[iy] * wtab[iz];
-      const cx<T> phi = cscale(f, g);
-      const T dx = dtab[x2];
-      o0 = {dx * phi.y, -dx * phi.x};
-      o1 = {dy * phi.y, -dy * phi.x};
-      o2 = {dz * phi.y, -dz * phi.x};
-    } else {
-      const int jz = (n - iz) % n, jy = (n - iy) % n;
-      const cx<T> h = spec[((int64_t)jz * n + jy) * m];
-      const cx<T> A = {(T)0.5 * (f.x + h.x), (T)0.5 * (f.y - h.y)};
-      const cx<T> B = {(T)0.5 * (f.y + h.y), (T)-0.5 * (f.x - h.x)};
-      T ga = gtab[base2], gb = gtab[base2 + (long long)m * m];
-      if (wtab) {
-        const T wyz = wtab[iy] * wtab[iz];
-        ga *= wtab[0] * wyz;
-        gb *= wtab[m] * wyz;
-      }
-      const cx<T> pa = cscale(A, ga), pb = cscale(B, gb);
-      const T dxa = dtab[0], dxb = dtab[m];
-      // acc spectra of the kx = 0 (a) and kx = N/2 (b) modes, repacked as a + i b
-      const cx<T> a0 = {dxa * pa.y, -dxa * pa.x}, b0 = {dxb * pb.y, -dxb * pb.x};
-      const cx<T> a1 = {dy * pa.y, -dy * pa.x}, b1 = {dy * pb.y, -dy * pb.x};
-      const cx<T> a2 = {dz * pa.y, -dz * pa.x}, b2 = {dz * pb.y, -dz * pb.x};
-      o0 = {a0.x - b0.y, a0.y + b0.x};
-      o1 = {a1.x - b1.y, a1.y + b1.x};
-      o2 = {a2.x - b2.y, a2.y + b2.x};
+  const int total = n * n;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int iy = idx / n, iz = idx - (idx / n) * n;    // plane0 layout [ky][kz]
+    const int ky = signed_freq(iy, n), kz = signed_freq(iz, n);
+    const int jy = (n - iy) & (n - 1), jz = (n - iz) & (n - 1);
+    const cx<T> f = spec[((int64_t)iz * n + iy) * m];
+    const cx<T> h = spec[((int64_t)jz * n + jy) * m];
+    const cx<T> A = {(T)0.5 * (f.x + h.x), (T)0.5 * (f.y - h.y)};
+    const cx<T> B = {(T)0.5 * (f.y + h.y), (T)-0.5 * (f.x - h.x)};
+    const int n2a = ky * ky + kz * kz;
+    T ga = gtab[n2a], gb = gtab[n2a + m * m];
+    if (wtab) {
+      const T wyz = wtab[iy] * wtab[iz];
+      ga *= wtab[0] * wyz;
+      gb *= wtab[m] * wyz;
     }
-    out[idx] = o0;
-    out[field_stride + idx] = o1;
-    out[2 * field_stride + idx] = o2;
+    plane0[idx] = {ga * A.x - gb * B.y, ga * A.y + gb * B.x};   // G_A A + i G_B B
   }
 }
 

@@ -59,14 +59,17 @@ struct GridArgs {
   const void* tw_n;               // W_N^m, m < N
   const void* tw_m;               // W_M^m, m < M
   int* status;
+  const void* gtab;               // Green table G(n^2), grid precision
+  const void* dtab;               // 4-point gradient multiplier per index
+  const void* wtab;               // 1/sinc^4 per index, or nullptr (no deconvolution)
+  void* plane0;                   // [N][N] complex: Green-multiplied packed column x2 = 0
 };
 #define NUPM_DECLARE_GRID(SFX)                                                              \
   int deposit##SFX(const GridArgs& g, const void* pos, cudaStream_t s);                     \
   int fft_pass##SFX(const GridArgs& g, int pass, cudaStream_t s);                           \
   int bins##SFX(const GridArgs& g, bool lattice, int nk, const short* bin_of, double kf,      \
                 double* partials, int nblk, double* out, cudaStream_t s);                   \
-  int green##SFX(const GridArgs& g, const void* gtab, const void* dtab, const void* wtab,    \
-                 cudaStream_t s);                                                           \
+  int green##SFX(const GridArgs& g, cudaStream_t s);                                        \
   int interp##SFX(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, \
                   cudaStream_t s);                                                          \
   int unpack##SFX(const GridArgs& g, void* dst, cudaStream_t s);

@@ -48,6 +48,7 @@ struct pm_ctx {
   void* d_gtab = nullptr;
   void* d_dtab = nullptr;
   void* d_wtab = nullptr;
+  void* d_plane0 = nullptr;   // [N][N] complex, Green-multiplied packed column
   int* d_status = nullptr;
   // pinned host staging
   double* h_hist_u = nullptr;
@@ -297,13 +298,17 @@ GridArgs grid_args(const pm_ctx* c) {
   g.tw_n = c->tw_n;
   g.tw_m = c->tw_m;
   g.status = c->d_status;
+  g.gtab = c->d_gtab;
+  g.dtab = c->d_dtab;
+  g.wtab = (c->p.flags & PM_DECONV_CIC) ? c->d_wtab : nullptr;
+  g.plane0 = c->d_plane0;
   return g;
 }
 
 void release(pm_ctx* c) {
   void* ptrs[] = {c->spec, c->g, c->tw_n, c->tw_m, c->d_binof, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
                   c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_gtab,
-                  c->d_dtab, c->d_wtab, c->d_status};
+                  c->d_dtab, c->d_wtab, c->d_plane0, c->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_hist_u) cudaFreeHost(c->h_hist_u);
@@ -473,6 +478,7 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) rc = dalloc(c, &c->d_gtab, (size_t)(c->n2max + 1) * real, "Green table");
   if (rc == PM_OK) rc = dalloc(c, &c->d_dtab, (size_t)n * real, "gradient table");
   if (rc == PM_OK) rc = dalloc(c, &c->d_wtab, (size_t)n * real, "deconvolution table");
+  if (rc == PM_OK) rc = dalloc(c, &c->d_plane0, (size_t)n * n * c->cplx, "Green plane x2=0");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_status, sizeof(int), "status");
   if (rc == PM_OK && cudaMallocHost((void**)&c->h_hist_u, (size_t)(p.n_hist_max + 1) * sizeof(double)) != cudaSuccess)
     rc = fail(c, PM_ERR_ALLOC, "pinned host allocation failed");
@@ -664,11 +670,10 @@ int pm_kick(pm_ctx* c, const void* pos, void* vel, double a, double kick_factor,
   if (a != c->a_response) return fail(c, PM_ERR_ORDER, "pm_kick at a different a than pm_nu_response");
   if (!isfinite(kick_factor)) return fail(c, PM_ERR_INVALID, "kick_factor must be finite");
   GridArgs g = grid_args(c);
-  const void* wt = (c->p.flags & PM_DECONV_CIC) ? c->d_wtab : nullptr;
   int rc = PM_OK;
   {
     Stage st(c, PM_ST_GREEN, 1);
-    rc = c->fp64 ? green_f64(g, c->d_gtab, c->d_dtab, wt, c->stream) : green_f32(g, c->d_gtab, c->d_dtab, wt, c->stream);
+    rc = c->fp64 ? green_f64(g, c->stream) : green_f32(g, c->stream);
   }
   c->deposit_grid_valid = false;
   const int inv[3] = {kPassZInv, kPassYInv, kPassXInv};
