@@ -218,6 +218,31 @@ NUPM_API int pm_timing(pm_ctx* ctx, int32_t enable);
  * calls[PM_NSTAGES] (times the stage ran); any pointer may be NULL. */
 NUPM_API int pm_get_timing(pm_ctx* ctx, double* ms, int64_t* launches, int64_t* calls);
 
+/*
+ * Binned power spectrum of a caller-owned half spectrum, allocating no device
+ * memory.  The paper has no counterpart: this is a service for callers that
+ * cannot call cudaMalloc -- codes that reserve all device memory for their
+ * own pool at start-up, or that must not allocate inside their time-step loop
+ * (an allocation can synchronise the device or fail mid-run) -- but still
+ * want the P(k) diagnostic.  Its scratch (per-block partial sums) is a
+ * fixed file-scope device array of 1.8 MB, held by every device that loads
+ * the library until the process exits.
+ *   spec        DEVICE complex [N][N][N/2+1] (numpy rfftn layout; double2 for
+ *               PM_FP64, float2 for PM_FP32), e.g. pm_copy_field(PM_FIELD_DELTA_K)
+ *   ngrid       N, a power of two in [16, 1024]
+ *   n_kbins     1..256 (more is rejected with PM_ERR_RANGE)
+ *   count, ksum, psum   DEVICE double[n_kbins] or NULL: sum w, sum w |k|,
+ *               sum w |delta_k|^2 with the bins and weights of pm_get_bins
+ *   cuda_stream stream to issue the work on
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Calls share the scratch: each call rewrites all
+ * of it that it reads, but calls that overlap on the GPU race.
+ */
+NUPM_API int pm_bin_power_static(const void* spec, int32_t ngrid, double box, int32_t n_kbins,
+                                 int32_t precision, double* count, double* ksum, double* psum,
+                                 void* cuda_stream);
+
 /* Bytes of device memory the context holds. */
 NUPM_API int64_t pm_device_bytes(const pm_ctx* ctx);
 

@@ -71,6 +71,7 @@ def lib():
         "pm_device_bytes": (i64, [vp]),
         "pm_timing": (C.c_int, [vp, i32]),
         "pm_get_timing": (C.c_int, [vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "pm_bin_power_static": (C.c_int, [vp, i32, d, i32, i32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -92,6 +93,26 @@ def _dptr(arr):
 
 def _tptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def bin_power_static(spec, ngrid, box, n_kbins, count=None, ksum=None, psum=None, stream=None):
+    """pm_bin_power_static: bins of a CUDA rfftn-layout spectrum (complex128 or
+    complex64 [N, N, N/2+1]) into caller-given CUDA float64 [n_kbins] tensors,
+    without any device allocation inside the library."""
+    import torch
+    if spec.dtype not in (torch.complex128, torch.complex64) or not spec.is_cuda or not spec.is_contiguous():
+        raise ValueError("spec must be a contiguous CUDA complex tensor [N, N, N/2+1]")
+    if tuple(spec.shape) != (ngrid, ngrid, ngrid // 2 + 1):
+        raise ValueError("spec shape must be [N, N, N/2+1]")
+    for t in (count, ksum, psum):
+        if t is not None and (t.dtype != torch.float64 or not t.is_cuda or t.numel() < n_kbins):
+            raise ValueError("outputs must be CUDA float64 [n_kbins]")
+    prec = PM_FP64 if spec.dtype == torch.complex128 else PM_FP32
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().pm_bin_power_static(_tptr(spec), int(ngrid), float(box), int(n_kbins), prec, _tptr(count),
+                                   _tptr(ksum), _tptr(psum), C.c_void_p(st.cuda_stream))
+    if rc != PM_OK:
+        raise PMError(rc, "pm_bin_power_static failed")
 
 
 class PM:
