@@ -120,9 +120,9 @@ def stage_bytes(w, stage):
         "fft_y_fwd": 2 * c * Mc,
         "fft_z_fwd": 2 * c * Mc,
         "bins": c * Mc,
-        "green": c * Mc + 3 * c * Mc,
-        "fft_z_inv": 3 * 2 * c * Mc,
-        "fft_y_inv": 3 * 2 * c * Mc,
+        "green": 3 * c * n * n,                           # packed kx=0 plane: 2 reads + 1 write
+        "fft_z_inv": c * Mc + 2 * c * Mc,                 # spectrum -> phi, d/dz phi
+        "fft_y_inv": 2 * c * Mc + 3 * c * Mc,             # 2 fields -> 3 fields
         "fft_x_inv": 3 * (c * Mc + r * M),
         "interp": p * Np + min(3 * r * M, 24 * r * Np) + 2 * 3 * v * Np,
     }.get(stage)

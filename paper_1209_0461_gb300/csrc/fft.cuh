@@ -21,6 +21,8 @@
 
 namespace nupm {
 
+constexpr int kFacTableDev = 2048;   // must equal kFacTable (nupm_internal.h)
+
 template <typename T>
 struct alignas(2 * sizeof(T)) cx {
   T x, y;
@@ -274,13 +276,20 @@ template <typename T, int N>
 __global__ void __launch_bounds__(ColCfg<T, N>::THREADS, ColCfg<T, N>::MIN_BLOCKS)
 k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, cx<T>* __restrict__ out_dz,
                   const cx<T>* __restrict__ plane0, const T* __restrict__ gtab, const T* __restrict__ dtab,
-                  const T* __restrict__ wtab, const cx<T>* __restrict__ tw) {
+                  const T* __restrict__ wtab, const cx<T>* __restrict__ tw, const float* __restrict__ fac,
+                  float fac_inv_du, float coeff) {
   using Cfg = ColCfg<T, N>;
   constexpr int M = N / 2, E = Plan<T, N>::R1, NT = N / E, W = Cfg::W, RL = last_radix<T, N>();
   constexpr int64_t ES = (int64_t)N * M;   // element stride along z
+  constexpr bool kFac = sizeof(T) == 4;    // FP32: G from the fac table, no n^2 gathers
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x % W;
   const int t = threadIdx.x / W;
+  float* fac_s = reinterpret_cast<float*>(smem_raw + (size_t)Cfg::SMEM_WORDS * sizeof(cx<T>));
+  if constexpr (kFac) {
+    for (int j = threadIdx.x; j < kFacTableDev; j += blockDim.x) fac_s[j] = fac[j];
+    __syncthreads();
+  }
   const int x2 = blockIdx.x * W + c;
   const int iy = blockIdx.y;
   const int ky = iy < N / 2 ? iy : iy - N;
@@ -299,7 +308,18 @@ k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, c
         f = plane0[(int64_t)iy * N + iz];
       } else {
         const int kz = iz < N / 2 ? iz : iz - N;
-        T g = gtab[base2 + kz * kz];
+        const int n2 = base2 + kz * kz;                // >= 1 since x2 >= 1
+        T g;
+        if constexpr (kFac) {
+          // G = coeff fac(u) / n^2, u = ln sqrt(n^2), fac linear in u on the table
+          const float tt = 0.5f * __logf((float)n2) * fac_inv_du;
+          const int j = min((int)tt, kFacTableDev - 2);
+          const float fr = tt - (float)j;
+          const float fv = fac_s[j] + fr * (fac_s[j + 1] - fac_s[j]);
+          g = (T)(coeff * fv / (float)n2);
+        } else {
+          g = gtab[n2];
+        }
         if (wtab) g *= wyx * wtab[iz];
         f = cscale(spec[off + (int64_t)iz * ES], g);
       }

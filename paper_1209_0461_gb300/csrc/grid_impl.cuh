@@ -27,7 +27,8 @@ void ensure_attrs() {
   cudaFuncSetAttribute(k_fft_x_fwd<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
   cudaFuncSetAttribute(k_fft_col<T, N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
   cudaFuncSetAttribute(k_fft_x_inv<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
-  cudaFuncSetAttribute(k_fft_z_inv_green<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+  cudaFuncSetAttribute(k_fft_z_inv_green<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       col_smem + kFacTable * (int)sizeof(float));
   cudaFuncSetAttribute(k_fft_y_inv_grad<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
   done = true;
 }
@@ -61,9 +62,10 @@ void fft_pass_n(const GridArgs& g, int pass, cudaStream_t s) {
     case kPassZInv: {
       // Green + z: spectrum -> g0 (phi), g2 (d/dz phi)
       const int64_t fe = g.field_elems;
-      k_fft_z_inv_green<T, N><<<dim3(M / CC::W, N, 1), CC::THREADS, col_smem, s>>>(
+      k_fft_z_inv_green<T, N><<<dim3(M / CC::W, N, 1), CC::THREADS, col_smem + kFacTable * sizeof(float), s>>>(
           spec, f, f + 2 * fe, reinterpret_cast<const C*>(g.plane0), reinterpret_cast<const T*>(g.gtab),
-          reinterpret_cast<const T*>(g.dtab), reinterpret_cast<const T*>(g.wtab), twn);
+          reinterpret_cast<const T*>(g.dtab), reinterpret_cast<const T*>(g.wtab), twn, g.fac, g.fac_inv_du,
+          g.green_coeff);
       break;
     }
     case kPassYInv: {

@@ -26,19 +26,27 @@ __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(st
 // Periodic wrap onto [0, n), n a power of two (two's complement mask).
 __device__ __forceinline__ int wrap_index(long long c, int n) { return (int)(c & (long long)(n - 1)); }
 
-// Quantised particle: cell (wrapped) and 16-bit weight per axis.  Returns
-// false (and records PM_ERR_RANGE) for an invalid particle.
+// Quantised particle: cell (wrapped) and 16-bit weight per axis.  load()
+// fetches the raw position words, get() turns them into (cell, weight) and
+// returns false (recording PM_ERR_RANGE) for an invalid particle.  Keeping
+// the two apart lets a thread put several particles' loads in flight at once.
 template <typename T>
 struct Quant;
 
 template <>
 struct Quant<double> {   // FP64 comoving positions, double[3][np]
-  __device__ static __forceinline__ bool get(const void* pos, int64_t np, int64_t p, int n,
-                                             double delta, int (&c)[3], int (&w)[3], int* status) {
+  struct Raw {
+    double x[3];
+  };
+  __device__ static __forceinline__ Raw load(const void* pos, int64_t np, int64_t p) {
     const double* x = reinterpret_cast<const double*>(pos);
+    return Raw{{x[p], x[np + p], x[2 * np + p]}};
+  }
+  __device__ static __forceinline__ bool get(const Raw& r, int n, double delta, int (&c)[3], int (&w)[3],
+                                             int* status) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const double u = x[d * np + p] / delta;          // same IEEE division as the definition
+      const double u = r.x[d] / delta;                 // same IEEE division as the definition
       if (!(fabs(u) < 4503599627370496.0)) {           // non-finite or |u| >= 2^52
         set_status(status, PM_ERR_RANGE);
         return false;
@@ -54,22 +62,34 @@ struct Quant<double> {   // FP64 comoving positions, double[3][np]
 
 template <>
 struct Quant<float> {    // int32 words [6][np]: cells rows 0-2, FP32 offsets rows 3-5
-  __device__ static __forceinline__ bool get(const void* pos, int64_t np, int64_t p, int n,
-                                             double, int (&c)[3], int (&w)[3], int* status) {
+  struct Raw {
+    int32_t q[6];
+  };
+  __device__ static __forceinline__ Raw load(const void* pos, int64_t np, int64_t p) {
     const int32_t* q = reinterpret_cast<const int32_t*>(pos);
+    Raw r;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) r.q[d] = q[d * np + p];
+    return r;
+  }
+  __device__ static __forceinline__ bool get(const Raw& r, int n, double, int (&c)[3], int (&w)[3],
+                                             int* status) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const float o = __int_as_float(q[(3 + d) * np + p]);
+      const float o = __int_as_float(r.q[3 + d]);
       if (!(o >= 0.0f && o < 1.0f)) {
         set_status(status, PM_ERR_RANGE);
         return false;
       }
       w[d] = (int)floorf(o * (float)kWeightOne);       // exact scaling by 2^16
-      c[d] = wrap_index((long long)q[d * np + p], n);
+      c[d] = wrap_index((long long)r.q[d], n);
     }
     return true;
   }
 };
+
+constexpr int kDepositBatch = 4;   // particles per thread per iteration
+constexpr int kInterpBatch = 2;
 
 // ---------------------------------------------------------------------------
 // a1: CIC deposit.  Corner (dx,dy,dz) of cell c gets prod_d (dx ? w_d : 2^16 - w_d).
@@ -78,29 +98,39 @@ struct Quant<float> {    // int32 words [6][np]: cells rows 0-2, FP32 offsets ro
 template <typename T>
 __global__ void k_deposit(const void* __restrict__ pos, int64_t np, int n, double delta,
                           unsigned long long* __restrict__ grid, int* status) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    int c[3], w[3];
-    if (!Quant<T>::get(pos, np, p, n, delta, c, w, status)) continue;
-    const unsigned long long wx[2] = {(unsigned long long)(kWeightOne - w[0]), (unsigned long long)w[0]};
-    const unsigned long long wy[2] = {(unsigned long long)(kWeightOne - w[1]), (unsigned long long)w[1]};
-    const unsigned long long wz[2] = {(unsigned long long)(kWeightOne - w[2]), (unsigned long long)w[2]};
-    const int x1 = c[0] + 1 == n ? 0 : c[0] + 1;
-    const int y1 = c[1] + 1 == n ? 0 : c[1] + 1;
-    const int z1 = c[2] + 1 == n ? 0 : c[2] + 1;
-    const int xs[2] = {c[0], x1}, ys[2] = {c[1], y1}, zs[2] = {c[2], z1};
+  constexpr int U = kDepositBatch;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < np; p0 += stride * U) {
+    typename Quant<T>::Raw raw[U];
 #pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = p0 + u * stride;
+      if (p < np) raw[u] = Quant<T>::load(pos, np, p);
+    }
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
-        const unsigned long long wzy = wz[dz] * wy[dy];
-        const int64_t rowi = ((int64_t)zs[dz] * n + ys[dy]) * n;
+    for (int u = 0; u < U; ++u) {
+      int c[3], w[3];
+      if (p0 + u * stride >= np || !Quant<T>::get(raw[u], n, delta, c, w, status)) continue;
+      const unsigned long long wx[2] = {(unsigned long long)(kWeightOne - w[0]), (unsigned long long)w[0]};
+      const unsigned long long wy[2] = {(unsigned long long)(kWeightOne - w[1]), (unsigned long long)w[1]};
+      const unsigned long long wz[2] = {(unsigned long long)(kWeightOne - w[2]), (unsigned long long)w[2]};
+      const int x1 = c[0] + 1 == n ? 0 : c[0] + 1;
+      const int y1 = c[1] + 1 == n ? 0 : c[1] + 1;
+      const int z1 = c[2] + 1 == n ? 0 : c[2] + 1;
+      const int xs[2] = {c[0], x1}, ys[2] = {c[1], y1}, zs[2] = {c[2], z1};
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-          const unsigned long long wt = wzy * wx[dx];
-          if (wt) atomicAdd(grid + rowi + xs[dx], wt);
+      for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const unsigned long long wzy = wz[dz] * wy[dy];
+          const int64_t rowi = ((int64_t)zs[dz] * n + ys[dy]) * n;
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const unsigned long long wt = wzy * wx[dx];
+            if (wt) atomicAdd(grid + rowi + xs[dx], wt);
+          }
         }
-      }
+    }
   }
 }
 
@@ -259,28 +289,60 @@ template <typename T>
 __global__ void k_interp_kick(const void* __restrict__ pos, int64_t np, int n, double delta,
                               const T* __restrict__ grids, int64_t field_stride, T* __restrict__ vel,
                               T kick, T* __restrict__ acc_out, int* status) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    int c[3], w[3];
-    if (!Quant<T>::get(pos, np, p, n, delta, c, w, status)) continue;
-    const T inv = (T)1.0 / (T)kWeightOne;
-    const T fx1 = (T)w[0] * inv, fy1 = (T)w[1] * inv, fz1 = (T)w[2] * inv;
-    const T fx0 = (T)1 - fx1, fy0 = (T)1 - fy1, fz0 = (T)1 - fz1;
-    const int x1 = c[0] + 1 == n ? 0 : c[0] + 1;
-    const int y1 = c[1] + 1 == n ? 0 : c[1] + 1;
-    const int z1 = c[2] + 1 == n ? 0 : c[2] + 1;
-    const int64_t r00 = ((int64_t)c[2] * n + c[1]) * n, r01 = ((int64_t)c[2] * n + y1) * n;
-    const int64_t r10 = ((int64_t)z1 * n + c[1]) * n, r11 = ((int64_t)z1 * n + y1) * n;
+  constexpr int U = kInterpBatch;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < np; p0 += stride * U) {
+    typename Quant<T>::Raw raw[U];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const T* g = grids + d * field_stride;
-      const T v00 = fx0 * g[r00 + c[0]] + fx1 * g[r00 + x1];
-      const T v01 = fx0 * g[r01 + c[0]] + fx1 * g[r01 + x1];
-      const T v10 = fx0 * g[r10 + c[0]] + fx1 * g[r10 + x1];
-      const T v11 = fx0 * g[r11 + c[0]] + fx1 * g[r11 + x1];
-      const T a = fz0 * (fy0 * v00 + fy1 * v01) + fz1 * (fy0 * v10 + fy1 * v11);
-      vel[d * np + p] += a * kick;
-      if (acc_out) acc_out[d * np + p] = a;
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = p0 + u * stride;
+      if (p < np) raw[u] = Quant<T>::load(pos, np, p);
+    }
+    // gather all corners of all U particles before the arithmetic
+    T g[U][3][8];
+    T f[U][6];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int c[3], w[3];
+      ok[u] = p0 + u * stride < np && Quant<T>::get(raw[u], n, delta, c, w, status);
+      if (!ok[u]) continue;
+      const T inv = (T)1.0 / (T)kWeightOne;
+      f[u][1] = (T)w[0] * inv;
+      f[u][3] = (T)w[1] * inv;
+      f[u][5] = (T)w[2] * inv;
+      f[u][0] = (T)1 - f[u][1];
+      f[u][2] = (T)1 - f[u][3];
+      f[u][4] = (T)1 - f[u][5];
+      const int x1 = c[0] + 1 == n ? 0 : c[0] + 1;
+      const int y1 = c[1] + 1 == n ? 0 : c[1] + 1;
+      const int z1 = c[2] + 1 == n ? 0 : c[2] + 1;
+      const int64_t r[4] = {((int64_t)c[2] * n + c[1]) * n, ((int64_t)c[2] * n + y1) * n,
+                            ((int64_t)z1 * n + c[1]) * n, ((int64_t)z1 * n + y1) * n};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T* gd = grids + d * field_stride;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          g[u][d][2 * q] = gd[r[q] + c[0]];
+          g[u][d][2 * q + 1] = gd[r[q] + x1];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!ok[u]) continue;
+      const int64_t p = p0 + u * stride;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T v00 = f[u][0] * g[u][d][0] + f[u][1] * g[u][d][1];   // (y0, z0)
+        const T v01 = f[u][0] * g[u][d][2] + f[u][1] * g[u][d][3];   // (y1, z0)
+        const T v10 = f[u][0] * g[u][d][4] + f[u][1] * g[u][d][5];   // (y0, z1)
+        const T v11 = f[u][0] * g[u][d][6] + f[u][1] * g[u][d][7];   // (y1, z1)
+        const T a = f[u][4] * (f[u][2] * v00 + f[u][3] * v01) + f[u][5] * (f[u][2] * v10 + f[u][3] * v11);
+        vel[d * np + p] += a * kick;
+        if (acc_out) acc_out[d * np + p] = a;
+      }
     }
   }
 }

@@ -324,6 +324,54 @@ __global__ void k_green_table(T* __restrict__ gtab, long long n2max, double kf, 
   }
 }
 
+// fac table for the FP32 Green function: the same ln-k interpolation of R as
+// k_green_table, sampled on a uniform grid of u = ln(k / kf).
+__global__ void k_fac_table(float* __restrict__ fac, double umax, double kf, double f_nu,
+                            const double* __restrict__ R, const double* __restrict__ bins, int nk) {
+  extern __shared__ double sh[];
+  double* lk = sh;
+  double* rv = sh + nk;
+  __shared__ int nne;
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int b = 0; b < nk; ++b)
+      if (bins[b] > 0.0) {
+        lk[c] = log(bins[nk + b] / bins[b]);
+        rv[c] = R[b];
+        ++c;
+      }
+    nne = c;
+  }
+  __syncthreads();
+  const int cnum = nne;
+  const double lkf = log(kf);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < kFacTable; j += gridDim.x * blockDim.x) {
+    double r = 0.0;
+    if (f_nu > 0.0 && cnum > 0) {
+      const double l = lkf + umax * (double)j / (double)(kFacTable - 1);
+      if (l <= lk[0]) {
+        r = rv[0];
+      } else if (l >= lk[cnum - 1]) {
+        r = rv[cnum - 1];
+      } else {
+        int lo = 0, hi = cnum - 1;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (lk[mid] <= l) lo = mid; else hi = mid;
+        }
+        r = rv[lo] + (rv[hi] - rv[lo]) * (l - lk[lo]) / (lk[hi] - lk[lo]);
+      }
+    }
+    fac[j] = (float)((1.0 - f_nu) + f_nu * r);
+  }
+}
+
+void launch_fac_table(float* fac, double umax, double kf, double f_nu, const double* R, const double* bins,
+                      int nk, cudaStream_t s) {
+  k_fac_table<<<(kFacTable + 255) / 256, 256, 2 * (size_t)nk * sizeof(double), s>>>(fac, umax, kf, f_nu, R,
+                                                                                     bins, nk);
+}
+
 void launch_green_table(bool fp64, void* gtab, long long n2max, double kf, double coeff,
                         double f_nu, const double* R, const double* bins, int nk, cudaStream_t s) {
   const int threads = 256;

@@ -41,6 +41,11 @@ struct NuArgs {
 };
 
 void launch_nu_response(const NuArgs& a, cudaStream_t s);
+// fac(u) = (1 - f) + f R(k), ln k = ln kf + u, on kFacTable points of u in [0, umax]
+// (u = ln sqrt(n^2)); the FP32 inverse z pass interpolates it linearly in u.
+constexpr int kFacTable = 2048;
+void launch_fac_table(float* fac, double umax, double kf, double f_nu, const double* R, const double* bins,
+                      int nk, cudaStream_t s);
 // Green table G(n^2), n^2 = 0..n2max, precision T; coeff = -1.5 Om / (a kf^2 N^3)
 void launch_green_table(bool fp64, void* gtab, long long n2max, double kf, double coeff,
                         double f_nu, const double* R, const double* bins, int nk, cudaStream_t s);
@@ -63,6 +68,9 @@ struct GridArgs {
   const void* dtab;               // 4-point gradient multiplier per index
   const void* wtab;               // 1/sinc^4 per index, or nullptr (no deconvolution)
   void* plane0;                   // [N][N] complex: Green-multiplied packed column x2 = 0
+  const float* fac;               // FP32 path: fac table (kFacTable points)
+  float fac_inv_du;               // 1 / table spacing in u = ln sqrt(n^2)
+  float green_coeff;              // -1.5 Omega_M / (a kf^2 N^3)
 };
 #define NUPM_DECLARE_GRID(SFX)                                                              \
   int deposit##SFX(const GridArgs& g, const void* pos, cudaStream_t s);                     \

@@ -49,6 +49,8 @@ struct pm_ctx {
   void* d_dtab = nullptr;
   void* d_wtab = nullptr;
   void* d_plane0 = nullptr;   // [N][N] complex, Green-multiplied packed column
+  float* d_fac = nullptr;     // fac table of the FP32 Green function
+  double green_coeff = 0;     // -1.5 Omega_M / (a kf^2 N^3) of the last response
   int* d_status = nullptr;
   // pinned host staging
   double* h_hist_u = nullptr;
@@ -302,13 +304,16 @@ GridArgs grid_args(const pm_ctx* c) {
   g.dtab = c->d_dtab;
   g.wtab = (c->p.flags & PM_DECONV_CIC) ? c->d_wtab : nullptr;
   g.plane0 = c->d_plane0;
+  g.fac = c->d_fac;
+  g.fac_inv_du = (float)((kFacTable - 1) / (0.5 * log((double)c->n2max)));
+  g.green_coeff = (float)c->green_coeff;
   return g;
 }
 
 void release(pm_ctx* c) {
   void* ptrs[] = {c->spec, c->g, c->tw_n, c->tw_m, c->d_binof, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
                   c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_gtab,
-                  c->d_dtab, c->d_wtab, c->d_plane0, c->d_status};
+                  c->d_dtab, c->d_wtab, c->d_plane0, c->d_fac, c->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_hist_u) cudaFreeHost(c->h_hist_u);
@@ -479,6 +484,7 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) rc = dalloc(c, &c->d_dtab, (size_t)n * real, "gradient table");
   if (rc == PM_OK) rc = dalloc(c, &c->d_wtab, (size_t)n * real, "deconvolution table");
   if (rc == PM_OK) rc = dalloc(c, &c->d_plane0, (size_t)n * n * c->cplx, "Green plane x2=0");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_fac, kFacTable * sizeof(float), "fac table");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_status, sizeof(int), "status");
   if (rc == PM_OK && cudaMallocHost((void**)&c->h_hist_u, (size_t)(p.n_hist_max + 1) * sizeof(double)) != cudaSuccess)
     rc = fail(c, PM_ERR_ALLOC, "pinned host allocation failed");
@@ -592,7 +598,7 @@ int pm_nu_response(pm_ctx* c, double a, const double* a_hist, const double* sqrt
                                                  cudaMemcpyHostToDevice, c->stream), "history upload");
     if (rc != PM_OK) return rc;
   }
-  Stage stage(c, PM_ST_RESPONSE, (c->ns > 0 && c->f_nu > 0) ? 3 : 2);
+  Stage stage(c, PM_ST_RESPONSE, ((c->ns > 0 && c->f_nu > 0) ? 3 : 2) + (c->fp64 ? 0 : 1));
   if (c->ns > 0 && c->f_nu > 0) {
     NuArgs A{};
     A.nk = c->nk;
@@ -656,6 +662,9 @@ int pm_nu_response(pm_ctx* c, double a, const double* a_hist, const double* sqrt
   }
   const double coeff = -1.5 * c->omega_m / (a * c->kf * c->kf * (double)c->n * c->n * c->n);
   launch_green_table(c->fp64, c->d_gtab, c->n2max, c->kf, coeff, c->f_nu, c->d_R, c->d_bins, c->nk, c->stream);
+  if (!c->fp64)
+    launch_fac_table(c->d_fac, 0.5 * log((double)c->n2max), c->kf, c->f_nu, c->d_R, c->d_bins, c->nk, c->stream);
+  c->green_coeff = coeff;
   const int rc = cuda_check(c, cudaGetLastError(), "pm_nu_response launch");
   if (rc != PM_OK) return rc;
   c->have_response = true;
