@@ -115,8 +115,8 @@ def stage_bytes(w, stage):
     v = r
     Np = w.npart
     return {
-        "deposit": p * Np + 8 * M,                       # (one scatter launch)
-        "fft_x_fwd": 8 * M + c * Mc,
+        "deposit": 12 * Np,                              # row sort: keys in, permutation out
+        "fft_x_fwd": (p + 4) * Np + c * Mc,              # fused deposit + x: particles, perm, spectrum
         "fft_y_fwd": 2 * c * Mc,
         "fft_z_fwd": 2 * c * Mc,
         "bins": c * Mc,

@@ -66,6 +66,8 @@ extern "C" {
 /* ---- flags ---- */
 #define PM_I_FIT       0x1u  /* use the App. C fitting formula (Eq. fit) for I(x) */
 #define PM_DECONV_CIC  0x2u  /* divide the Green function by prod sinc^4 (CIC windows) */
+#define PM_KEEP_DEPOSIT 0x4u /* also write the fixed-point deposit grid (PM_FIELD_DEPOSIT) */
+#define PM_UNFUSED_DEPOSIT 0x8u /* global-atomic deposit + separate x pass (no particle sort) */
 
 /*
  * Problem statement (Sec. 4.3-4.4, Table 1).  Omega_M = omega_cdm + omega_nu
@@ -184,7 +186,8 @@ NUPM_API int pm_get_thresholds(const pm_ctx* ctx, int64_t* thresholds);
 
 /* Copy an internal field to DEVICE memory `dst` (stream-ordered):
  *   PM_FIELD_DEPOSIT   uint64[N][N][N] fixed-point deposit (valid after pm_deposit,
- *                      until pm_kick overwrites it)
+ *                      until pm_kick overwrites it; needs PM_KEEP_DEPOSIT or
+ *                      PM_UNFUSED_DEPOSIT)
  *   PM_FIELD_DELTA_K   the forward spectrum, complex[N][N][N/2+1] unpacked
  *                      (numpy rfftn layout), valid after pm_deposit
  *   PM_FIELD_ACC_X/Y/Z the real acceleration grids [N][N][N], valid after pm_kick
@@ -198,8 +201,8 @@ NUPM_API int pm_copy_field(pm_ctx* ctx, int32_t which, void* dst);
 
 /* ---- per-stage timing (CUDA events on the context's stream) ----
  * Stages of one kick, in launch order. */
-#define PM_ST_DEPOSIT    0   /* memset + CIC scatter */
-#define PM_ST_FFT_X_FWD  1
+#define PM_ST_DEPOSIT    0   /* particle row sort (or, unfused, memset + CIC scatter) */
+#define PM_ST_FFT_X_FWD  1   /* CIC deposit into row tiles + forward x transform */
 #define PM_ST_FFT_Y_FWD  2
 #define PM_ST_FFT_Z_FWD  3
 #define PM_ST_BINS       4   /* P_cdm bins + fixed-order reduction */

@@ -297,34 +297,43 @@ k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, c
   const int64_t off = (int64_t)iy * M + x2;
   ColSmem<T, W, Cfg::PAD> sm{reinterpret_cast<cx<T>*>(smem_raw), c};
   const T wyx = wtab ? wtab[iy] * wtab[x2] : (T)1;
+  // Green factors of this thread's elements, once per tile, into its own
+  // shared-memory slots (layout [i][thread]): keeps them out of registers
+  T* gs = reinterpret_cast<T*>(fac_s + (kFac ? kFacTableDev : 0));
+  const bool col0 = x2 == 0;
+#pragma unroll 1
+  for (int i = 0; i < E; ++i) {
+    const int iz = t + NT * i;
+    const int kz = iz < N / 2 ? iz : iz - N;
+    const int n2 = max(base2 + kz * kz, 1);            // >= 1 unless col0
+    T g;
+    if constexpr (kFac) {
+      // G = coeff fac(u) / n^2, u = ln sqrt(n^2), fac linear in u on the table
+      const float tt = 0.5f * __logf((float)n2) * fac_inv_du;
+      const int j = min((int)tt, kFacTableDev - 2);
+      const float fr = tt - (float)j;
+      const float fv = fac_s[j] + fr * (fac_s[j + 1] - fac_s[j]);
+      g = (T)(coeff * fv / (float)n2);
+    } else {
+      g = gtab[n2];
+    }
+    if (wtab) g *= wyx * wtab[iz];
+    gs[i * Cfg::THREADS + threadIdx.x] = col0 ? (T)1 : g;
+  }
+  // branch-free loads: the packed column x2 = 0 reads its pre-multiplied
+  // plane0 values (element stride 1), every other column the spectrum
+  const cx<T>* src = col0 ? plane0 + (int64_t)iy * N : spec + off;
+  const int64_t sstride = col0 ? 1 : ES;
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
     cx<T> v[E];
 #pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = src[(int64_t)(t + NT * i) * sstride];
+#pragma unroll
     for (int i = 0; i < E; ++i) {
-      const int iz = t + NT * i;
-      cx<T> f;
-      if (x2 == 0) {
-        f = plane0[(int64_t)iy * N + iz];
-      } else {
-        const int kz = iz < N / 2 ? iz : iz - N;
-        const int n2 = base2 + kz * kz;                // >= 1 since x2 >= 1
-        T g;
-        if constexpr (kFac) {
-          // G = coeff fac(u) / n^2, u = ln sqrt(n^2), fac linear in u on the table
-          const float tt = 0.5f * __logf((float)n2) * fac_inv_du;
-          const int j = min((int)tt, kFacTableDev - 2);
-          const float fr = tt - (float)j;
-          const float fv = fac_s[j] + fr * (fac_s[j + 1] - fac_s[j]);
-          g = (T)(coeff * fv / (float)n2);
-        } else {
-          g = gtab[n2];
-        }
-        if (wtab) g *= wyx * wtab[iz];
-        f = cscale(spec[off + (int64_t)iz * ES], g);
-      }
+      cx<T> f = cscale(v[i], gs[i * Cfg::THREADS + threadIdx.x]);
       if (pass == 1) {
-        const T d = dtab[iz];
+        const T d = dtab[t + NT * i];
         f = {d * f.y, -d * f.x};                 // -i D(kz) f
       }
       v[i] = f;
@@ -446,6 +455,150 @@ k_fft_x_fwd(const unsigned long long* __restrict__ grid, cx<T>* __restrict__ spe
       const cx<T> w = twid_table<-1>(tw_n, k);
       const cx<T> wo = cmul(w, od);
       out = {ev.x + wo.y, ev.y - wo.x};                     // ev - i * wo
+    }
+    dst[k] = out;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused a1 + forward x pass.  A CTA owns TZ x TY grid rows (z, y): it
+// deposits every particle of the (TZ+1) x (TY+1) source rows that touch them
+// (rows sorted by k_row_scatter) into a shared-memory int64 tile with 64-bit
+// shared atomics, then transforms those rows exactly as k_fft_x_fwd.  No
+// global deposit grid, no memset, no atomics to DRAM.  With `keep` set the
+// tile is also written out (inspection).  grid = (N / TY, N / TZ).
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+struct FusedCfg {
+  static constexpr int TZ = 2, TY = 4;
+  static constexpr int ROWS = TZ * TY;
+  static constexpr int M = N / 2;
+  static constexpr int NT = M / Plan<T, M>::R1;
+  static constexpr int THREADS = ROWS * NT;
+  static constexpr int SRC = (TZ + 1) * (TY + 1);
+  static constexpr size_t ACC_BYTES = (size_t)ROWS * N * 8;
+  static constexpr size_t XCH_BYTES = (size_t)ROWS * RowSmem<T>::words(M) * sizeof(cx<T>);
+  static constexpr size_t SMEM = (ACC_BYTES > XCH_BYTES ? ACC_BYTES : XCH_BYTES);
+};
+
+template <typename T, int N, class Q>
+__global__ void __launch_bounds__(FusedCfg<T, N>::THREADS)
+k_deposit_fft_x(const void* __restrict__ pos, int64_t np, double delta, const int* __restrict__ row_start,
+                const int* __restrict__ perm, cx<T>* __restrict__ spec, double scale, const cx<T>* __restrict__ tw_m,
+                const cx<T>* __restrict__ tw_n, unsigned long long* __restrict__ keep, int* status) {
+  using Cfg = FusedCfg<T, N>;
+  constexpr int TZ = Cfg::TZ, TY = Cfg::TY, ROWS = Cfg::ROWS, M = N / 2, E = Plan<T, M>::R1, NT = Cfg::NT;
+  constexpr int RL = last_radix<T, M>(), SRC = Cfg::SRC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);   // [ROWS][N]
+  __shared__ int pre[SRC + 1], beg[SRC];
+  const int ty0 = blockIdx.x * TY, tz0 = blockIdx.y * TZ;
+  for (int i = threadIdx.x; i < ROWS * N / 2; i += blockDim.x)
+    reinterpret_cast<ulonglong2*>(acc)[i] = ulonglong2{0ull, 0ull};
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int sidx = 0; sidx < SRC; ++sidx) {
+      const int sz = (tz0 - 1 + sidx / (TY + 1)) & (N - 1), sy = (ty0 - 1 + sidx % (TY + 1)) & (N - 1);
+      const int r = sz * N + sy;
+      const int b0 = row_start[r], b1 = row_start[r + 1];
+      beg[sidx] = b0;
+      pre[sidx] = run;
+      run += b1 - b0;
+    }
+    pre[SRC] = run;
+  }
+  __syncthreads();
+  const int total = pre[SRC];
+  constexpr int U = 4;
+  for (int j0 = threadIdx.x; j0 < total; j0 += blockDim.x * U) {
+    typename Q::Raw raw[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u * blockDim.x;
+      if (j < total) {
+        int sidx = 0;
+#pragma unroll 1
+        while (pre[sidx + 1] <= j) ++sidx;
+        raw[u] = Q::load(pos, np, perm[beg[sidx] + (j - pre[sidx])]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int c[3], w[3];
+      if (j0 + u * (int)blockDim.x >= total || !Q::get(raw[u], N, delta, c, w, status)) continue;
+      const int x1 = (c[0] + 1) & (N - 1);
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz) {
+        const int zl = (c[2] + dz - tz0) & (N - 1);
+        if (zl >= TZ) continue;
+        const unsigned long long wz = dz ? (unsigned long long)w[2] : (unsigned long long)(65536 - w[2]);
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const int yl = (c[1] + dy - ty0) & (N - 1);
+          if (yl >= TY) continue;
+          const unsigned long long wzy = wz * (dy ? (unsigned long long)w[1] : (unsigned long long)(65536 - w[1]));
+          unsigned long long* rowp = acc + (zl * TY + yl) * N;
+          const unsigned long long w0 = wzy * (unsigned long long)(65536 - w[0]);
+          const unsigned long long w1 = wzy * (unsigned long long)w[0];
+          if (w0) atomicAdd(rowp + c[0], w0);
+          if (w1) atomicAdd(rowp + x1, w1);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // forward x transform of the tile's rows (as k_fft_x_fwd)
+  const int t = threadIdx.x % NT;
+  const int r = threadIdx.x / NT;
+  const int gz = tz0 + r / TY, gy = ty0 + r % TY;
+  const int64_t grow = (int64_t)gz * N + gy;
+  const ulonglong2* src = reinterpret_cast<const ulonglong2*>(acc + r * N);
+  cx<T> v[E];
+  if (keep) {
+    ulonglong2* kd = reinterpret_cast<ulonglong2*>(keep + grow * N);
+#pragma unroll
+    for (int i = 0; i < E; ++i) kd[t + NT * i] = src[t + NT * i];
+  }
+  if constexpr (sizeof(T) == 4) {
+    const float hs = (float)(scale * 4294967296.0), ls = (float)scale;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const ulonglong2 q = src[t + NT * i];
+      const float ax = fmaf((float)(unsigned)(q.x >> 32), hs, fmaf((float)(unsigned)q.x, ls, -1.0f));
+      const float ay = fmaf((float)(unsigned)(q.y >> 32), hs, fmaf((float)(unsigned)q.y, ls, -1.0f));
+      v[i] = {(T)ax, (T)ay};
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const ulonglong2 q = src[t + NT * i];
+      v[i] = {(T)((double)q.x * scale - 1.0), (T)((double)q.y * scale - 1.0)};
+    }
+  }
+  __syncthreads();   // the tile is consumed; its memory now serves the exchange buffers
+  RowSmem<T> sm{reinterpret_cast<cx<T>*>(smem_raw) + r * RowSmem<T>::words(M)};
+  fft_regs<T, M, -1>(v, sm, t, tw_m);
+  if constexpr (Plan<T, M>::R2 > 1) __syncthreads();
+#pragma unroll
+  for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+    for (int i = 0; i < RL; ++i) sm.st(t + NT * b + i * (M / RL), v[b * RL + i]);
+  __syncthreads();
+  cx<T>* dst = spec + grow * M;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int k = t + NT * i;
+    const cx<T> zk = sm.ld(k);
+    cx<T> out;
+    if (k == 0) {
+      out = {zk.x + zk.y, zk.x - zk.y};
+    } else {
+      const cx<T> zm = cconj(sm.ld(M - k));
+      const cx<T> ev = cscale(zk + zm, (T)0.5);
+      const cx<T> od = cscale(zk - zm, (T)0.5);
+      const cx<T> wv = twid_table<-1>(tw_n, k);
+      const cx<T> wo = cmul(wv, od);
+      out = {ev.x + wo.y, ev.y - wo.x};
     }
     dst[k] = out;
   }

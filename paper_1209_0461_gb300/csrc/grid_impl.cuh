@@ -6,6 +6,7 @@
 #include "fft.cuh"
 #include "grid_kernels.cuh"
 #include "nupm_internal.h"
+#include "sort.cuh"
 
 namespace nupm {
 namespace {
@@ -13,6 +14,15 @@ namespace {
 using T = NUPM_T;
 using C = cx<T>;
 constexpr int kSMs = 152;
+
+// Shared memory of the Green z pass: exchange buffer, fac table (FP32) and
+// the per-thread Green factors.
+template <int N>
+constexpr size_t green_smem() {
+  using CC = ColCfg<T, N>;
+  return (size_t)CC::SMEM_WORDS * sizeof(C) + (sizeof(T) == 4 ? kFacTable * sizeof(float) : 0) +
+         (size_t)Plan<T, N>::R1 * CC::THREADS * sizeof(T);
+}
 
 // Opt the FFT kernels of size N into their dynamic shared memory (once per
 // process; every kernel of this size gets its attribute on first use).
@@ -28,7 +38,7 @@ void ensure_attrs() {
   cudaFuncSetAttribute(k_fft_col<T, N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
   cudaFuncSetAttribute(k_fft_x_inv<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
   cudaFuncSetAttribute(k_fft_z_inv_green<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       col_smem + kFacTable * (int)sizeof(float));
+                       (int)green_smem<N>());
   cudaFuncSetAttribute(k_fft_y_inv_grad<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
   done = true;
 }
@@ -62,7 +72,7 @@ void fft_pass_n(const GridArgs& g, int pass, cudaStream_t s) {
     case kPassZInv: {
       // Green + z: spectrum -> g0 (phi), g2 (d/dz phi)
       const int64_t fe = g.field_elems;
-      k_fft_z_inv_green<T, N><<<dim3(M / CC::W, N, 1), CC::THREADS, col_smem + kFacTable * sizeof(float), s>>>(
+      k_fft_z_inv_green<T, N><<<dim3(M / CC::W, N, 1), CC::THREADS, green_smem<N>(), s>>>(
           spec, f, f + 2 * fe, reinterpret_cast<const C*>(g.plane0), reinterpret_cast<const T*>(g.gtab),
           reinterpret_cast<const T*>(g.dtab), reinterpret_cast<const T*>(g.wtab), twn, g.fac, g.fac_inv_du,
           g.green_coeff);
@@ -81,6 +91,22 @@ void fft_pass_n(const GridArgs& g, int pass, cudaStream_t s) {
           f, g.field_elems, twm, twn, reinterpret_cast<const T*>(g.dtab), 1);
       break;
   }
+}
+
+// Fused deposit + forward x pass of size N (rows sorted beforehand).
+template <int N>
+void deposit_fft_x_n(const GridArgs& g, const void* pos, bool keep, cudaStream_t s) {
+  using F = FusedCfg<T, N>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_deposit_fft_x<T, N, Quant<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)F::SMEM);
+    attr = true;
+  }
+  k_deposit_fft_x<T, N, Quant<T>><<<dim3(N / F::TY, N / F::TZ), F::THREADS, F::SMEM, s>>>(
+      pos, g.np, g.delta, g.row_start, g.perm, reinterpret_cast<C*>(g.spec), g.scale,
+      reinterpret_cast<const C*>(g.tw_m), reinterpret_cast<const C*>(g.tw_n),
+      keep ? reinterpret_cast<unsigned long long*>(g.g) : nullptr, g.status);
 }
 
 #define NUPM_DISPATCH(fn)                                  \
@@ -114,6 +140,34 @@ int NUPM_FN(deposit)(const GridArgs& g, const void* pos, cudaStream_t s) {
   if (g.np > 0)
     k_deposit<T><<<grid_blocks(g.np, 256), 256, 0, s>>>(pos, g.np, g.n, g.delta,
                                                        reinterpret_cast<unsigned long long*>(g.g), g.status);
+  return PM_OK;
+}
+
+int NUPM_FN(row_sort)(const GridArgs& g, const void* pos, cudaStream_t s) {
+  const int rows = g.n * g.n;
+  cudaMemsetAsync(g.row_count, 0, (size_t)(rows + 1) * sizeof(int), s);
+  const int blocks = grid_blocks(g.np, 256);
+  if (g.np > 0) k_row_count<T><<<blocks, 256, 0, s>>>(pos, g.np, g.n, g.delta, g.row_count, g.status);
+  const int len = rows + 1;
+  const int nb = (len + 2 * kScanBlock - 1) / (2 * kScanBlock);
+  k_scan_blocks<<<nb, kScanBlock, 0, s>>>(g.row_count, g.row_start, g.scan_tot, len);
+  k_scan_totals<<<1, kScanBlock, 0, s>>>(g.scan_tot, nb);
+  k_scan_add<<<(len + 255) / 256, 256, 0, s>>>(g.row_start, g.scan_tot, len, g.row_cursor);
+  if (g.np > 0) k_row_scatter<T><<<blocks, 256, 0, s>>>(pos, g.np, g.n, g.delta, g.row_cursor, g.perm);
+  return PM_OK;
+}
+
+int NUPM_FN(deposit_fft_x)(const GridArgs& g, const void* pos, bool keep, cudaStream_t s) {
+  switch (g.n) {
+    case 16: deposit_fft_x_n<16>(g, pos, keep, s); break;
+    case 32: deposit_fft_x_n<32>(g, pos, keep, s); break;
+    case 64: deposit_fft_x_n<64>(g, pos, keep, s); break;
+    case 128: deposit_fft_x_n<128>(g, pos, keep, s); break;
+    case 256: deposit_fft_x_n<256>(g, pos, keep, s); break;
+    case 512: deposit_fft_x_n<512>(g, pos, keep, s); break;
+    case 1024: deposit_fft_x_n<1024>(g, pos, keep, s); break;
+    default: return PM_ERR_UNSUPPORTED;
+  }
   return PM_OK;
 }
 

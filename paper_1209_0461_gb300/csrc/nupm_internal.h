@@ -68,12 +68,19 @@ struct GridArgs {
   const void* dtab;               // 4-point gradient multiplier per index
   const void* wtab;               // 1/sinc^4 per index, or nullptr (no deconvolution)
   void* plane0;                   // [N][N] complex: Green-multiplied packed column x2 = 0
+  int* row_count;                  // [N^2 + 1] particles per row (sort)
+  int* row_start;                  // [N^2 + 1] exclusive prefix of row_count
+  int* row_cursor;                 // [N^2 + 1]
+  int* scan_tot;                   // [2 * 1024] block totals of the scan
+  int* perm;                       // [npart] particle indices sorted by row
   const float* fac;               // FP32 path: fac table (kFacTable points)
   float fac_inv_du;               // 1 / table spacing in u = ln sqrt(n^2)
   float green_coeff;              // -1.5 Omega_M / (a kf^2 N^3)
 };
 #define NUPM_DECLARE_GRID(SFX)                                                              \
   int deposit##SFX(const GridArgs& g, const void* pos, cudaStream_t s);                     \
+  int row_sort##SFX(const GridArgs& g, const void* pos, cudaStream_t s);                    \
+  int deposit_fft_x##SFX(const GridArgs& g, const void* pos, bool keep, cudaStream_t s);    \
   int fft_pass##SFX(const GridArgs& g, int pass, cudaStream_t s);                           \
   int bins##SFX(const GridArgs& g, bool lattice, int nk, const short* bin_of, double kf,      \
                 double* partials, int nblk, double* out, cudaStream_t s);                   \

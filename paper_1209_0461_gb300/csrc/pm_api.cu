@@ -50,6 +50,11 @@ struct pm_ctx {
   void* d_wtab = nullptr;
   void* d_plane0 = nullptr;   // [N][N] complex, Green-multiplied packed column
   float* d_fac = nullptr;     // fac table of the FP32 Green function
+  int* d_rowc = nullptr;      // particle row sort: counts, starts, cursors, scan totals, perm
+  int* d_rows = nullptr;
+  int* d_rowcur = nullptr;
+  int* d_scantot = nullptr;
+  int* d_perm = nullptr;
   double green_coeff = 0;     // -1.5 Omega_M / (a kf^2 N^3) of the last response
   int* d_status = nullptr;
   // pinned host staging
@@ -304,6 +309,11 @@ GridArgs grid_args(const pm_ctx* c) {
   g.dtab = c->d_dtab;
   g.wtab = (c->p.flags & PM_DECONV_CIC) ? c->d_wtab : nullptr;
   g.plane0 = c->d_plane0;
+  g.row_count = c->d_rowc;
+  g.row_start = c->d_rows;
+  g.row_cursor = c->d_rowcur;
+  g.scan_tot = c->d_scantot;
+  g.perm = c->d_perm;
   g.fac = c->d_fac;
   g.fac_inv_du = (float)((kFacTable - 1) / (0.5 * log((double)c->n2max)));
   g.green_coeff = (float)c->green_coeff;
@@ -313,7 +323,8 @@ GridArgs grid_args(const pm_ctx* c) {
 void release(pm_ctx* c) {
   void* ptrs[] = {c->spec, c->g, c->tw_n, c->tw_m, c->d_binof, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
                   c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_gtab,
-                  c->d_dtab, c->d_wtab, c->d_plane0, c->d_fac, c->d_status};
+                  c->d_dtab, c->d_wtab, c->d_plane0, c->d_fac, c->d_rowc, c->d_rows, c->d_rowcur,
+                  c->d_scantot, c->d_perm, c->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_hist_u) cudaFreeHost(c->h_hist_u);
@@ -378,7 +389,8 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   else if (p.precision != PM_FP64 && p.precision != PM_FP32) bad(PM_ERR_INVALID, "precision must be PM_FP64 or PM_FP32");
   else if (p.iters < 1 || p.iters > 16) bad(PM_ERR_INVALID, "iters must be 1..16");
   else if (p.quad_nodes < 2 || p.quad_nodes > kMaxQuad) bad(PM_ERR_INVALID, "quad_nodes must be 2..16");
-  else if (p.flags & ~(PM_I_FIT | PM_DECONV_CIC)) bad(PM_ERR_INVALID, "unknown flag bits");
+  else if (p.flags & ~(PM_I_FIT | PM_DECONV_CIC | PM_KEEP_DEPOSIT | PM_UNFUSED_DEPOSIT))
+    bad(PM_ERR_INVALID, "unknown flag bits");
   if (rc != PM_OK) {
     // report through a context so pm_last_error works; caller still gets NULL
     fprintf(stderr, "pm_init: %s\n", c->err.c_str());
@@ -485,6 +497,12 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) rc = dalloc(c, &c->d_wtab, (size_t)n * real, "deconvolution table");
   if (rc == PM_OK) rc = dalloc(c, &c->d_plane0, (size_t)n * n * c->cplx, "Green plane x2=0");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_fac, kFacTable * sizeof(float), "fac table");
+  const size_t nrow1 = (size_t)n * n + 1;
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rowc, nrow1 * sizeof(int), "row counts");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rows, nrow1 * sizeof(int), "row starts");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rowcur, nrow1 * sizeof(int), "row cursors");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_scantot, 2048 * sizeof(int), "scan totals");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_perm, (size_t)c->np * sizeof(int), "row permutation");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_status, sizeof(int), "status");
   if (rc == PM_OK && cudaMallocHost((void**)&c->h_hist_u, (size_t)(p.n_hist_max + 1) * sizeof(double)) != cudaSuccess)
     rc = fail(c, PM_ERR_ALLOC, "pinned host allocation failed");
@@ -549,13 +567,30 @@ int pm_deposit(pm_ctx* c, const void* pos) {
   if (!pos) return fail(c, PM_ERR_INVALID, "pm_deposit: pos is NULL");
   GridArgs g = grid_args(c);
   int rc = PM_OK;
-  {
-    Stage st(c, PM_ST_DEPOSIT, 1);
-    rc = c->fp64 ? deposit_f64(g, pos, c->stream) : deposit_f32(g, pos, c->stream);
+  const bool unfused = (c->p.flags & PM_UNFUSED_DEPOSIT) != 0;
+  const bool keep = (c->p.flags & PM_KEEP_DEPOSIT) != 0;
+  if (unfused) {
+    {
+      Stage st(c, PM_ST_DEPOSIT, 1);
+      rc = c->fp64 ? deposit_f64(g, pos, c->stream) : deposit_f32(g, pos, c->stream);
+    }
+    if (rc == PM_OK) {
+      Stage st(c, PM_ST_FFT_X_FWD, 1);
+      rc = c->fp64 ? fft_pass_f64(g, kPassXFwd, c->stream) : fft_pass_f32(g, kPassXFwd, c->stream);
+    }
+  } else {
+    {
+      Stage st(c, PM_ST_DEPOSIT, 5);
+      rc = c->fp64 ? row_sort_f64(g, pos, c->stream) : row_sort_f32(g, pos, c->stream);
+    }
+    if (rc == PM_OK) {
+      Stage st(c, PM_ST_FFT_X_FWD, 1);
+      rc = c->fp64 ? deposit_fft_x_f64(g, pos, keep, c->stream) : deposit_fft_x_f32(g, pos, keep, c->stream);
+    }
   }
-  const int fwd[3] = {kPassXFwd, kPassYFwd, kPassZFwd};
-  const int fst[3] = {PM_ST_FFT_X_FWD, PM_ST_FFT_Y_FWD, PM_ST_FFT_Z_FWD};
-  for (int i = 0; i < 3 && rc == PM_OK; ++i) {
+  const int fwd[2] = {kPassYFwd, kPassZFwd};
+  const int fst[2] = {PM_ST_FFT_Y_FWD, PM_ST_FFT_Z_FWD};
+  for (int i = 0; i < 2 && rc == PM_OK; ++i) {
     Stage st(c, fst[i], 1);
     rc = c->fp64 ? fft_pass_f64(g, fwd[i], c->stream) : fft_pass_f32(g, fwd[i], c->stream);
   }
@@ -568,7 +603,7 @@ int pm_deposit(pm_ctx* c, const void* pos) {
   rc = cuda_check(c, cudaGetLastError(), "pm_deposit launch");
   if (rc != PM_OK) return rc;
   c->deposited = true;
-  c->deposit_grid_valid = true;    // the fixed-point grid stays intact until pm_kick
+  c->deposit_grid_valid = unfused || keep;   // the fixed-point grid stays intact until pm_kick
   c->have_response = false;
   c->have_kick = false;
   return PM_OK;
@@ -771,7 +806,9 @@ int pm_copy_field(pm_ctx* c, int32_t which, void* dst) {
   cudaError_t e = cudaSuccess;
   switch (which) {
     case PM_FIELD_DEPOSIT:
-      if (!c->deposit_grid_valid) return fail(c, PM_ERR_ORDER, "deposit grid not valid (no deposit, or a kick overwrote it)");
+      if (!c->deposit_grid_valid)
+        return fail(c, PM_ERR_ORDER, "deposit grid not kept (needs PM_KEEP_DEPOSIT or PM_UNFUSED_DEPOSIT, "
+                                     "after pm_deposit and before pm_kick)");
       e = cudaMemcpyAsync(dst, c->g, (size_t)n3 * 8, cudaMemcpyDeviceToDevice, c->stream);
       break;
     case PM_FIELD_DELTA_K: {

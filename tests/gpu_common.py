@@ -29,7 +29,11 @@ def make_inputs(w, npart=None, seed_shift=0):
     return dict(pos64=pos64, vel=vel, a_hist=a_hist, hist=hist, pi=pi, ti=ti)
 
 
-def gpu_kick(w, inp, K=0.01, iters=1, flags=0, n_hist=None, prev=None, quad=8, keep_fields=False):
+KEEP_DEPOSIT = 0x4
+UNFUSED_DEPOSIT = 0x8
+
+
+def gpu_kick(w, inp, K=0.01, iters=1, flags=KEEP_DEPOSIT, n_hist=None, prev=None, quad=8, keep_fields=False):
     """Deposit, response and kick through the C ABI.  Returns numpy results."""
     import torch
     dev = torch.device("cuda")

@@ -13,7 +13,8 @@ from paper_1209_0461_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
-from gpu_common import build_lib, force_errors, gpu_kick, make_inputs, oracle_kick  # noqa: E402
+from gpu_common import (KEEP_DEPOSIT, UNFUSED_DEPOSIT, build_lib, force_errors, gpu_kick,  # noqa: E402
+                        make_inputs, oracle_kick)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -113,8 +114,8 @@ def test_options_iters_fit_deconv_nohist_prev():
     inp = make_inputs(w)
     prev = np.abs(inp["pi"][0]) * 1.7
     for kw, okw in ((dict(iters=2), dict(iters=2)),
-                    (dict(flags=0x1), dict(I_func=O.nu_I_fit)),
-                    (dict(flags=0x2), dict(deconvolve=True)),
+                    (dict(flags=0x1 | KEEP_DEPOSIT), dict(I_func=O.nu_I_fit)),
+                    (dict(flags=0x2 | KEEP_DEPOSIT), dict(deconvolve=True)),
                     (dict(n_hist=0), dict(n_hist=0)),
                     (dict(prev=prev), dict(prev=prev))):
         g = gpu_kick(w, inp, **kw)
@@ -206,3 +207,21 @@ def test_deposit_deterministic_under_shuffle():
     g3 = gpu_kick(w, inp)
     assert np.array_equal(g1["F"], g2["F"]) and np.array_equal(g1["F"], g3["F"])
     assert np.allclose(g1["acc"][:, perm], g2["acc"], rtol=0, atol=1e-12 * np.abs(g1["acc"]).max())
+
+
+@pytest.mark.parametrize("prec,n", [("fp64", 32), ("fp32", 64), ("fp32", 256), ("fp64", 128)])
+def test_fused_deposit_equals_unfused(prec, n):
+    # the row-sorted shared-memory deposit fused with the x transform gives the
+    # same integer grid and the same spectrum as the global-atomic path, for
+    # lattice-ordered and shuffled particles
+    w = synth.Workload(f"fuse{n}", n, n // 2 if n > 64 else n, 2.0 * n, 0.06, 3, 4, 16, prec)
+    inp = make_inputs(w)
+    perm = np.random.default_rng(11).permutation(inp["pos64"].shape[1])
+    shuf = dict(inp, pos64=inp["pos64"][:, perm].copy(), vel=inp["vel"][:, perm].copy())
+    a = gpu_kick(w, inp, flags=UNFUSED_DEPOSIT)
+    b = gpu_kick(w, inp, flags=KEEP_DEPOSIT)
+    c = gpu_kick(w, shuf, flags=KEEP_DEPOSIT)
+    assert np.array_equal(a["F"], b["F"]) and np.array_equal(a["F"], c["F"])
+    assert np.array_equal(a["spec"], b["spec"]) and np.array_equal(a["spec"], c["spec"])
+    assert np.array_equal(a["acc"], b["acc"])
+    assert np.array_equal(a["acc"][:, perm], c["acc"])

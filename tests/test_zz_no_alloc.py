@@ -24,7 +24,7 @@ def test_static_bins_match_context_bins(prec, n, nk):
     parts = synth.particles(w)
     dev = torch.device("cuda")
     pm = nupm.PM(w.ngrid, w.npart, w.box, w.omega_cdm, w.omega_nu, w.h, w.m_nu_total, 3,
-                 n_kbins=nk, precision=prec)
+                 n_kbins=nk, precision=prec)   # deposit path as in production (fused)
     if prec == "fp64":
         pos = torch.from_numpy(parts["pos64"]).to(dev).contiguous()
     else:
