@@ -481,6 +481,17 @@ struct FusedCfg {
   static constexpr size_t SMEM = (ACC_BYTES > XCH_BYTES ? ACC_BYTES : XCH_BYTES);
 };
 
+// Exact 64-bit add on shared memory from two native 32-bit atomics: the low
+// word's returned old value gives the carry into the high word.  Integer
+// addition stays associative, so the sum is bit-exact in any order.
+__device__ __forceinline__ void add_u64_shared(unsigned long long* p, unsigned long long v) {
+  unsigned int* w = reinterpret_cast<unsigned int*>(p);   // little endian: w[0] low, w[1] high
+  const unsigned int lo = (unsigned int)v, hi = (unsigned int)(v >> 32);
+  const unsigned int old = atomicAdd(w, lo);
+  const unsigned int carry = (old + lo < old) ? 1u : 0u;
+  if (hi + carry) atomicAdd(w + 1, hi + carry);
+}
+
 template <typename T, int N, class Q>
 __global__ void __launch_bounds__(FusedCfg<T, N>::THREADS)
 k_deposit_fft_x(const void* __restrict__ pos, int64_t np, double delta, const int* __restrict__ row_start,
@@ -540,8 +551,8 @@ k_deposit_fft_x(const void* __restrict__ pos, int64_t np, double delta, const in
           unsigned long long* rowp = acc + (zl * TY + yl) * N;
           const unsigned long long w0 = wzy * (unsigned long long)(65536 - w[0]);
           const unsigned long long w1 = wzy * (unsigned long long)w[0];
-          if (w0) atomicAdd(rowp + c[0], w0);
-          if (w1) atomicAdd(rowp + x1, w1);
+          if (w0) add_u64_shared(rowp + c[0], w0);
+          if (w1) add_u64_shared(rowp + x1, w1);
         }
       }
     }

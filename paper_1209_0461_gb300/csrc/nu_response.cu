@@ -106,14 +106,16 @@ struct Panel {
   int seg;   // history interval: -1 before node 0, j in [0, n-1) between nodes, n-1 the last
 };
 
-// One warp per (bin, species): IC, J_hist, W_cur.
+// One warp per (bin, species, chunk of 32 panels): partial IC, J_hist, W_cur.
 __global__ void k_nu_panels(NuArgs A) {
   __shared__ Panel panels[4][kMaxPanels];
   __shared__ int npan[4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * 4 + warp;
-  if (item >= A.nk * A.ns) return;
-  const int b = item % A.nk, s = item / A.nk;
+  if (item >= A.nk * A.ns * kNuChunks) return;
+  const int chunk = item % kNuChunks;
+  const int bs = item / kNuChunks;
+  const int b = bs % A.nk, s = bs / A.nk;
   double* out = A.parts + (int64_t)item * 3;
   const double cnt = A.bins[b];
   if (cnt <= 0.0) {
@@ -161,7 +163,7 @@ __global__ void k_nu_panels(NuArgs A) {
   const int np = npan[warp];
   const int Q = A.quad;
   double jh = 0.0, wc = 0.0;
-  for (int pi = lane; pi < np; pi += 32) {
+  for (int pi = chunk * 32 + lane; pi < np; pi += 32 * kNuChunks) {
     const Panel pn = P[pi];
     if (!(pn.hi > pn.lo)) continue;
     const double half = 0.5 * (pn.hi - pn.lo);
@@ -215,10 +217,12 @@ __global__ void k_nu_panels(NuArgs A) {
     wc += __shfl_down_sync(0xffffffffu, wc, off);
   }
   if (lane == 0) {
-    const double xi = kappa * s_end;
-    const double Ii = A.use_fit ? nu_I_fit(xi) : nu_I_exact(xi);
-    const double ic = Ii * A.pnu_init[(int64_t)s * A.nk + b] *
-                      (1.0 - s_end * A.a_init * A.theta_init[(int64_t)s * A.nk + b]);
+    double ic = 0.0;
+    if (chunk == 0) {
+      const double xi = kappa * s_end;
+      const double Ii = A.use_fit ? nu_I_fit(xi) : nu_I_exact(xi);
+      ic = Ii * A.pnu_init[(int64_t)s * A.nk + b] * (1.0 - s_end * A.a_init * A.theta_init[(int64_t)s * A.nk + b]);
+    }
     const double c = 1.5 * A.omega_m;
     out[0] = ic;
     out[1] = c * jh;
@@ -238,10 +242,16 @@ __global__ void k_nu_finish(NuArgs A) {
     const double pcdm = sqrt(A.bins[2 * A.nk + b] / cnt * L3 / (n3 * n3));
     double ic = 0.0, jh = 0.0, wc = 0.0, guess = 0.0;
     for (int s = 0; s < A.ns; ++s) {
-      const double* q = A.parts + ((int64_t)s * A.nk + b) * 3;
-      ic += A.w_species[s] * q[0];
-      jh += A.w_species[s] * q[1];
-      wc += A.w_species[s] * q[2];
+      double qi = 0.0, qj = 0.0, qw = 0.0;
+      for (int ch = 0; ch < kNuChunks; ++ch) {   // fixed chunk order
+        const double* q = A.parts + (((int64_t)s * A.nk + b) * kNuChunks + ch) * 3;
+        qi += q[0];
+        qj += q[1];
+        qw += q[2];
+      }
+      ic += A.w_species[s] * qi;
+      jh += A.w_species[s] * qj;
+      wc += A.w_species[s] * qw;
       guess += A.w_species[s] * A.pnu_init[(int64_t)s * A.nk + b];
     }
     if (A.prev) guess = A.prev[b];
@@ -269,10 +279,32 @@ __global__ void k_bin_reduce(const double* __restrict__ partials, int nblk, int 
   out[i] = acc;
 }
 
+// Compacted (ln k_b, R_b) of the non-empty bins, in bin order, for the Green
+// and fac tables: rlist[0..c) = ln k_b, rlist[nk..nk+c) = R_b, rlist[2 nk] = c.
+// One block of nk <= 1024 threads.
+__global__ void k_nu_rlist(const double* __restrict__ bins, const double* __restrict__ R, int nk,
+                           double* __restrict__ rlist) {
+  __shared__ int warp_cnt[32];
+  const int b = threadIdx.x, lane = b & 31, warp = b >> 5;
+  const bool ne = b < nk && bins[b] > 0.0;
+  const unsigned m = __ballot_sync(0xffffffffu, ne);
+  if (lane == 0) warp_cnt[warp] = __popc(m);
+  __syncthreads();
+  int base = 0;
+  for (int w = 0; w < warp; ++w) base += warp_cnt[w];
+  const int pos = base + __popc(m & ((1u << lane) - 1));
+  if (ne) {
+    rlist[pos] = log(bins[nk + b] / bins[b]);
+    rlist[nk + pos] = R[b];
+  }
+  if (b == blockDim.x - 1) rlist[2 * nk] = (double)(base + __popc(m));
+}
+
 void launch_nu_response(const NuArgs& a, cudaStream_t s) {
-  const int items = a.nk * a.ns;
+  const int items = a.nk * a.ns * kNuChunks;
   if (items > 0) k_nu_panels<<<(items + 3) / 4, 128, 0, s>>>(a);
   k_nu_finish<<<(a.nk + 127) / 128, 128, 0, s>>>(a);
+  k_nu_rlist<<<1, ((a.nk + 31) / 32) * 32, 0, s>>>(a.bins, a.R, a.nk, a.rlist);
 }
 
 // ---------------------------------------------------------------- Green table
@@ -280,24 +312,16 @@ void launch_nu_response(const NuArgs& a, cudaStream_t s) {
 // between non-empty bins (k_b = ksum/count), constant beyond the end bins.
 template <typename T>
 __global__ void k_green_table(T* __restrict__ gtab, long long n2max, double kf, double coeff,
-                              double f_nu, const double* __restrict__ R,
-                              const double* __restrict__ bins, int nk) {
+                              double f_nu, const double* __restrict__ rlist, int nk) {
   extern __shared__ double sh[];
   double* lk = sh;          // ln k of non-empty bins
   double* rv = sh + nk;     // their R
-  __shared__ int nne;
-  if (threadIdx.x == 0) {
-    int c = 0;
-    for (int b = 0; b < nk; ++b)
-      if (bins[b] > 0.0) {
-        lk[c] = log(bins[nk + b] / bins[b]);
-        rv[c] = R[b];
-        ++c;
-      }
-    nne = c;
+  const int cnum = (int)rlist[2 * nk];
+  for (int i = threadIdx.x; i < cnum; i += blockDim.x) {
+    lk[i] = rlist[i];
+    rv[i] = rlist[nk + i];
   }
   __syncthreads();
-  const int cnum = nne;
   for (long long n2 = (long long)blockIdx.x * blockDim.x + threadIdx.x; n2 <= n2max;
        n2 += (long long)gridDim.x * blockDim.x) {
     if (n2 == 0) {
@@ -327,23 +351,16 @@ __global__ void k_green_table(T* __restrict__ gtab, long long n2max, double kf, 
 // fac table for the FP32 Green function: the same ln-k interpolation of R as
 // k_green_table, sampled on a uniform grid of u = ln(k / kf).
 __global__ void k_fac_table(float* __restrict__ fac, double umax, double kf, double f_nu,
-                            const double* __restrict__ R, const double* __restrict__ bins, int nk) {
+                            const double* __restrict__ rlist, int nk) {
   extern __shared__ double sh[];
   double* lk = sh;
   double* rv = sh + nk;
-  __shared__ int nne;
-  if (threadIdx.x == 0) {
-    int c = 0;
-    for (int b = 0; b < nk; ++b)
-      if (bins[b] > 0.0) {
-        lk[c] = log(bins[nk + b] / bins[b]);
-        rv[c] = R[b];
-        ++c;
-      }
-    nne = c;
+  const int cnum = (int)rlist[2 * nk];
+  for (int i = threadIdx.x; i < cnum; i += blockDim.x) {
+    lk[i] = rlist[i];
+    rv[i] = rlist[nk + i];
   }
   __syncthreads();
-  const int cnum = nne;
   const double lkf = log(kf);
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < kFacTable; j += gridDim.x * blockDim.x) {
     double r = 0.0;
@@ -366,24 +383,21 @@ __global__ void k_fac_table(float* __restrict__ fac, double umax, double kf, dou
   }
 }
 
-void launch_fac_table(float* fac, double umax, double kf, double f_nu, const double* R, const double* bins,
-                      int nk, cudaStream_t s) {
-  k_fac_table<<<(kFacTable + 255) / 256, 256, 2 * (size_t)nk * sizeof(double), s>>>(fac, umax, kf, f_nu, R,
-                                                                                     bins, nk);
+void launch_fac_table(float* fac, double umax, double kf, double f_nu, const double* rlist, int nk,
+                      cudaStream_t s) {
+  k_fac_table<<<(kFacTable + 255) / 256, 256, 2 * (size_t)nk * sizeof(double), s>>>(fac, umax, kf, f_nu, rlist, nk);
 }
 
 void launch_green_table(bool fp64, void* gtab, long long n2max, double kf, double coeff,
-                        double f_nu, const double* R, const double* bins, int nk, cudaStream_t s) {
+                        double f_nu, const double* rlist, int nk, cudaStream_t s) {
   const int threads = 256;
   long long blocks = (n2max + 1 + threads - 1) / threads;
   if (blocks > 1216) blocks = 1216;
   const size_t sh = 2 * (size_t)nk * sizeof(double);
   if (fp64)
-    k_green_table<double><<<(int)blocks, threads, sh, s>>>((double*)gtab, n2max, kf, coeff, f_nu, R,
-                                                           bins, nk);
+    k_green_table<double><<<(int)blocks, threads, sh, s>>>((double*)gtab, n2max, kf, coeff, f_nu, rlist, nk);
   else
-    k_green_table<float><<<(int)blocks, threads, sh, s>>>((float*)gtab, n2max, kf, coeff, f_nu, R,
-                                                          bins, nk);
+    k_green_table<float><<<(int)blocks, threads, sh, s>>>((float*)gtab, n2max, kf, coeff, f_nu, rlist, nk);
 }
 
 }  // namespace nupm

@@ -13,6 +13,7 @@ constexpr double kTnu0eV = 1.68e-4;       // T_nu,0 [eV], Sec. 2.1 (value as pri
 constexpr double kOmegaNuEv = 93.14;      // Omega_nu h^2 = sum m / 93.14 eV, Sec. 2.1
 constexpr int kMaxQuad = 16;
 constexpr int kMaxPanels = 320;           // history nodes + graded points + ends
+constexpr int kNuChunks = 10;             // warps per (bin, species), 32 panels each
 
 // Device inputs of the response kernels (one struct, passed by value).
 struct NuArgs {
@@ -31,7 +32,8 @@ struct NuArgs {
   int n_stab;
   double stab_u0, stab_inv_h, stab_h;
   const double* gl;               // [2][quad] nodes, weights on [-1, 1]
-  double* parts;                  // [ns][nk][3] IC, J_hist, W_cur
+  double* parts;                  // [ns][nk][kNuChunks][3] IC, J_hist, W_cur per panel chunk
+  double* rlist;                  // [2 nk + 1]: ln k_b and R_b of the non-empty bins, then their count
   double* R;                      // [nk]
   double* pnu;                    // [nk]
   double* pm;                     // [nk]
@@ -44,11 +46,12 @@ void launch_nu_response(const NuArgs& a, cudaStream_t s);
 // fac(u) = (1 - f) + f R(k), ln k = ln kf + u, on kFacTable points of u in [0, umax]
 // (u = ln sqrt(n^2)); the FP32 inverse z pass interpolates it linearly in u.
 constexpr int kFacTable = 2048;
-void launch_fac_table(float* fac, double umax, double kf, double f_nu, const double* R, const double* bins,
-                      int nk, cudaStream_t s);
-// Green table G(n^2), n^2 = 0..n2max, precision T; coeff = -1.5 Om / (a kf^2 N^3)
+void launch_fac_table(float* fac, double umax, double kf, double f_nu, const double* rlist, int nk,
+                      cudaStream_t s);
+// Green table G(n^2), n^2 = 0..n2max, precision T; coeff = -1.5 Om / (a kf^2 N^3);
+// rlist from the response (compacted non-empty bins)
 void launch_green_table(bool fp64, void* gtab, long long n2max, double kf, double coeff,
-                        double f_nu, const double* R, const double* bins, int nk, cudaStream_t s);
+                        double f_nu, const double* rlist, int nk, cudaStream_t s);
 
 // FFT passes in launch order of one kick
 constexpr int kPassXFwd = 0, kPassYFwd = 1, kPassZFwd = 2, kPassZInv = 3, kPassYInv = 4, kPassXInv = 5;

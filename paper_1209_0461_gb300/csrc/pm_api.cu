@@ -45,6 +45,7 @@ struct pm_ctx {
   double* d_R = nullptr;
   double* d_pnu = nullptr;
   double* d_pm = nullptr;
+  double* d_rlist = nullptr;  // [2 nk + 1] compacted non-empty (ln k_b, R_b)
   void* d_gtab = nullptr;
   void* d_dtab = nullptr;
   void* d_wtab = nullptr;
@@ -322,7 +323,7 @@ GridArgs grid_args(const pm_ctx* c) {
 
 void release(pm_ctx* c) {
   void* ptrs[] = {c->spec, c->g, c->tw_n, c->tw_m, c->d_binof, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
-                  c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_gtab,
+                  c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_rlist, c->d_gtab,
                   c->d_dtab, c->d_wtab, c->d_plane0, c->d_fac, c->d_rowc, c->d_rows, c->d_rowcur,
                   c->d_scantot, c->d_perm, c->d_status};
   for (void* p : ptrs)
@@ -488,7 +489,8 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_ti, (size_t)nspec * c->nk * sizeof(double), "nu theta ICs");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_hist_u, (size_t)(p.n_hist_max + 1) * sizeof(double), "history ln a");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_gl, 2 * kMaxQuad * sizeof(double), "quadrature");
-  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_parts, (size_t)nspec * c->nk * 3 * sizeof(double), "response parts");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_parts, (size_t)nspec * c->nk * kNuChunks * 3 * sizeof(double), "response parts");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rlist, (2 * (size_t)c->nk + 1) * sizeof(double), "ratio list");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_R, (size_t)c->nk * sizeof(double), "ratio");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_pnu, (size_t)c->nk * sizeof(double), "P_nu");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_pm, (size_t)c->nk * sizeof(double), "P_M");
@@ -633,7 +635,7 @@ int pm_nu_response(pm_ctx* c, double a, const double* a_hist, const double* sqrt
                                                  cudaMemcpyHostToDevice, c->stream), "history upload");
     if (rc != PM_OK) return rc;
   }
-  Stage stage(c, PM_ST_RESPONSE, ((c->ns > 0 && c->f_nu > 0) ? 3 : 2) + (c->fp64 ? 0 : 1));
+  Stage stage(c, PM_ST_RESPONSE, ((c->ns > 0 && c->f_nu > 0) ? 4 : 3) + (c->fp64 ? 0 : 1));
   if (c->ns > 0 && c->f_nu > 0) {
     NuArgs A{};
     A.nk = c->nk;
@@ -668,6 +670,7 @@ int pm_nu_response(pm_ctx* c, double a, const double* a_hist, const double* sqrt
     A.stab_inv_h = 1.0 / c->stab_h;
     A.gl = c->d_gl;
     A.parts = c->d_parts;
+    A.rlist = c->d_rlist;
     A.R = c->d_R;
     A.pnu = c->d_pnu;
     A.pm = c->d_pm;
@@ -681,11 +684,12 @@ int pm_nu_response(pm_ctx* c, double a, const double* a_hist, const double* sqrt
     A.nk = c->nk;
     A.ns = 0;
     A.iters = 1;
-    A.f_nu = 0;
+    A.f_nu = c->f_nu;   // (1 - f_nu) P_cdm^{1/2} for the total-matter spectrum
     A.ngrid = c->n;
     A.box = c->box;
     A.bins = c->d_bins;
     A.parts = c->d_parts;
+    A.rlist = c->d_rlist;
     A.pnu_init = c->d_pi;
     A.R = c->d_R;
     A.pnu = c->d_pnu;
@@ -696,9 +700,9 @@ int pm_nu_response(pm_ctx* c, double a, const double* a_hist, const double* sqrt
     launch_nu_response(A, c->stream);   // zero items in the panel kernel; finish sets outputs
   }
   const double coeff = -1.5 * c->omega_m / (a * c->kf * c->kf * (double)c->n * c->n * c->n);
-  launch_green_table(c->fp64, c->d_gtab, c->n2max, c->kf, coeff, c->f_nu, c->d_R, c->d_bins, c->nk, c->stream);
+  launch_green_table(c->fp64, c->d_gtab, c->n2max, c->kf, coeff, c->f_nu, c->d_rlist, c->nk, c->stream);
   if (!c->fp64)
-    launch_fac_table(c->d_fac, 0.5 * log((double)c->n2max), c->kf, c->f_nu, c->d_R, c->d_bins, c->nk, c->stream);
+    launch_fac_table(c->d_fac, 0.5 * log((double)c->n2max), c->kf, c->f_nu, c->d_rlist, c->nk, c->stream);
   c->green_coeff = coeff;
   const int rc = cuda_check(c, cudaGetLastError(), "pm_nu_response launch");
   if (rc != PM_OK) return rc;
