@@ -68,6 +68,8 @@ extern "C" {
 #define PM_DECONV_CIC  0x2u  /* divide the Green function by prod sinc^4 (CIC windows) */
 #define PM_KEEP_DEPOSIT 0x4u /* also write the fixed-point deposit grid (PM_FIELD_DEPOSIT) */
 #define PM_UNFUSED_DEPOSIT 0x8u /* global-atomic deposit + separate x pass (no particle sort) */
+#define PM_TMA_COLUMNS 0x10u /* column FFT passes as persistent TMA-pipelined kernels (comparison;
+                                 1 CTA/SM: slower than the default on a 1024^3 grid) */
 
 /*
  * Problem statement (Sec. 4.3-4.4, Table 1).  Omega_M = omega_cdm + omega_nu

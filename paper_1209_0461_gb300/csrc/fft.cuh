@@ -467,6 +467,7 @@ k_fft_x_fwd(const unsigned long long* __restrict__ grid, cx<T>* __restrict__ spe
 // shared atomics, then transforms those rows exactly as k_fft_x_fwd.  No
 // global deposit grid, no memset, no atomics to DRAM.  With `keep` set the
 // tile is also written out (inspection).  grid = (N / TY, N / TZ).
+// Accumulation uses three 32-bit planes of 16-bit weight slices (add_sliced).
 // ---------------------------------------------------------------------------
 template <typename T, int N>
 struct FusedCfg {
@@ -476,20 +477,25 @@ struct FusedCfg {
   static constexpr int NT = M / Plan<T, M>::R1;
   static constexpr int THREADS = ROWS * NT;
   static constexpr int SRC = (TZ + 1) * (TY + 1);
-  static constexpr size_t ACC_BYTES = (size_t)ROWS * N * 8;
+  static constexpr size_t ACC_BYTES = (size_t)3 * ROWS * N * 4;   // three 16-bit-slice planes
   static constexpr size_t XCH_BYTES = (size_t)ROWS * RowSmem<T>::words(M) * sizeof(cx<T>);
   static constexpr size_t SMEM = (ACC_BYTES > XCH_BYTES ? ACC_BYTES : XCH_BYTES);
 };
 
-// Exact 64-bit add on shared memory from two native 32-bit atomics: the low
-// word's returned old value gives the carry into the high word.  Integer
-// addition stays associative, so the sum is bit-exact in any order.
-__device__ __forceinline__ void add_u64_shared(unsigned long long* p, unsigned long long v) {
-  unsigned int* w = reinterpret_cast<unsigned int*>(p);   // little endian: w[0] low, w[1] high
-  const unsigned int lo = (unsigned int)v, hi = (unsigned int)(v >> 32);
-  const unsigned int old = atomicAdd(w, lo);
-  const unsigned int carry = (old + lo < old) ? 1u : 0u;
-  if (hi + carry) atomicAdd(w + 1, hi + carry);
+// Exact deposit sums without 64-bit shared atomics: a weight w < 2^48 + 1 is
+// split into 16-bit slices w = a 2^32 + b 2^16 + c and each slice is added
+// to its own 32-bit plane with a native, result-free shared atomic.  A plane
+// counter overflows only after 65536 additions to one node (the same bound
+// as the 64-bit grid); F = A 2^32 + B 2^16 + C is exact and order-independent.
+__device__ __forceinline__ void add_sliced(unsigned int* plane0, int plane_stride, int idx, unsigned long long w) {
+  atomicAdd(plane0 + idx, (unsigned int)(w & 0xffffu));
+  atomicAdd(plane0 + plane_stride + idx, (unsigned int)((w >> 16) & 0xffffu));
+  atomicAdd(plane0 + 2 * plane_stride + idx, (unsigned int)(w >> 32));
+}
+
+__device__ __forceinline__ unsigned long long sliced_value(const unsigned int* plane0, int plane_stride, int idx) {
+  return ((unsigned long long)plane0[2 * plane_stride + idx] << 32) +
+         ((unsigned long long)plane0[plane_stride + idx] << 16) + (unsigned long long)plane0[idx];
 }
 
 template <typename T, int N, class Q>
@@ -501,11 +507,11 @@ k_deposit_fft_x(const void* __restrict__ pos, int64_t np, double delta, const in
   constexpr int TZ = Cfg::TZ, TY = Cfg::TY, ROWS = Cfg::ROWS, M = N / 2, E = Plan<T, M>::R1, NT = Cfg::NT;
   constexpr int RL = last_radix<T, M>(), SRC = Cfg::SRC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);   // [ROWS][N]
+  unsigned int* acc = reinterpret_cast<unsigned int*>(smem_raw);   // [3][ROWS][N] slice planes
+  constexpr int PS = ROWS * N;                                      // plane stride
   __shared__ int pre[SRC + 1], beg[SRC];
   const int ty0 = blockIdx.x * TY, tz0 = blockIdx.y * TZ;
-  for (int i = threadIdx.x; i < ROWS * N / 2; i += blockDim.x)
-    reinterpret_cast<ulonglong2*>(acc)[i] = ulonglong2{0ull, 0ull};
+  for (int i = threadIdx.x; i < 3 * PS / 4; i += blockDim.x) reinterpret_cast<uint4*>(acc)[i] = uint4{0u, 0u, 0u, 0u};
   if (threadIdx.x == 0) {
     int run = 0;
     for (int sidx = 0; sidx < SRC; ++sidx) {
@@ -548,11 +554,11 @@ k_deposit_fft_x(const void* __restrict__ pos, int64_t np, double delta, const in
           const int yl = (c[1] + dy - ty0) & (N - 1);
           if (yl >= TY) continue;
           const unsigned long long wzy = wz * (dy ? (unsigned long long)w[1] : (unsigned long long)(65536 - w[1]));
-          unsigned long long* rowp = acc + (zl * TY + yl) * N;
+          const int rb = (zl * TY + yl) * N;
           const unsigned long long w0 = wzy * (unsigned long long)(65536 - w[0]);
           const unsigned long long w1 = wzy * (unsigned long long)w[0];
-          if (w0) add_u64_shared(rowp + c[0], w0);
-          if (w1) add_u64_shared(rowp + x1, w1);
+          if (w0) add_sliced(acc, PS, rb + c[0], w0);
+          if (w1) add_sliced(acc, PS, rb + x1, w1);
         }
       }
     }
@@ -563,27 +569,32 @@ k_deposit_fft_x(const void* __restrict__ pos, int64_t np, double delta, const in
   const int r = threadIdx.x / NT;
   const int gz = tz0 + r / TY, gy = ty0 + r % TY;
   const int64_t grow = (int64_t)gz * N + gy;
-  const ulonglong2* src = reinterpret_cast<const ulonglong2*>(acc + r * N);
+  const int rb = r * N;
   cx<T> v[E];
   if (keep) {
     ulonglong2* kd = reinterpret_cast<ulonglong2*>(keep + grow * N);
 #pragma unroll
-    for (int i = 0; i < E; ++i) kd[t + NT * i] = src[t + NT * i];
+    for (int i = 0; i < E; ++i) {
+      const int x = 2 * (t + NT * i);
+      kd[t + NT * i] = ulonglong2{sliced_value(acc, PS, rb + x), sliced_value(acc, PS, rb + x + 1)};
+    }
   }
   if constexpr (sizeof(T) == 4) {
-    const float hs = (float)(scale * 4294967296.0), ls = (float)scale;
+    // delta = (A 2^32 + B 2^16 + C) s - 1 in FP32 FMAs (no FP64 arithmetic)
+    const float s2 = (float)(scale * 4294967296.0), s1 = (float)(scale * 65536.0), s0 = (float)scale;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-      const ulonglong2 q = src[t + NT * i];
-      const float ax = fmaf((float)(unsigned)(q.x >> 32), hs, fmaf((float)(unsigned)q.x, ls, -1.0f));
-      const float ay = fmaf((float)(unsigned)(q.y >> 32), hs, fmaf((float)(unsigned)q.y, ls, -1.0f));
+      const int x = rb + 2 * (t + NT * i);
+      const float ax = fmaf((float)acc[2 * PS + x], s2, fmaf((float)acc[PS + x], s1, fmaf((float)acc[x], s0, -1.0f)));
+      const float ay = fmaf((float)acc[2 * PS + x + 1], s2,
+                            fmaf((float)acc[PS + x + 1], s1, fmaf((float)acc[x + 1], s0, -1.0f)));
       v[i] = {(T)ax, (T)ay};
     }
   } else {
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-      const ulonglong2 q = src[t + NT * i];
-      v[i] = {(T)((double)q.x * scale - 1.0), (T)((double)q.y * scale - 1.0)};
+      const int x = rb + 2 * (t + NT * i);
+      v[i] = {(T)((double)sliced_value(acc, PS, x) * scale - 1.0), (T)((double)sliced_value(acc, PS, x + 1) * scale - 1.0)};
     }
   }
   __syncthreads();   // the tile is consumed; its memory now serves the exchange buffers

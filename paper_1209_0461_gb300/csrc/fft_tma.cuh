@@ -1,0 +1,255 @@
+// TMA-pipelined column passes (y and z) of the 3-D FFT, persistent CTAs.
+//
+// Each work item is one W x N column tile of a field.  Thread 0 loads tiles
+// with cp.async.bulk.tensor (4-D tensor map: x2, y, z, field) into one of
+// two shared buffers; completion is tracked by an mbarrier per buffer.  While
+// the CTA transforms item k (registers + padded exchange buffer) and stores
+// it, the copy of item k+2 is already in flight, so the HBM stream does not
+// stop for the arithmetic.  Items that need two transforms of the same input
+// (Green z pass, y-gradient pass) read the staged tile twice from shared
+// memory instead of re-reading global memory.
+//
+// Every wait is bounded: on timeout the kernel records PM_ERR_TIMEOUT, waits
+// (bounded) for its own outstanding copies and returns.
+#pragma once
+#include <cuda.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+
+namespace nupm {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false after kSpinLimit tries.
+constexpr uint32_t kSpinLimit = 1u << 24;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+enum ColMode { kColFwdY = 0, kColFwdZ = 1, kColInvZGreen = 2, kColInvYGrad = 3 };
+
+template <typename T>
+struct ColTmaArgs {
+  cx<T>* spec;            // packed spectrum (forward passes in place; Green pass input)
+  cx<T>* g;               // 3 packed fields
+  int64_t field_elems;
+  const cx<T>* tw;        // W_N^m
+  const cx<T>* plane0;    // Green pass: pre-multiplied packed column x2 = 0, [ky][kz]
+  const T* dtab;          // 4-point gradient multiplier per index
+  const T* wtab;          // deconvolution (or nullptr)
+  const T* gtab;          // FP64 Green table
+  const float* fac;       // FP32 fac table
+  float fac_inv_du, coeff;
+  int* status;
+};
+
+template <typename T, int N>
+struct ColTmaCfg {
+  static constexpr int M = N / 2;
+  static constexpr int E = Plan<T, N>::R1;
+  static constexpr int NT = N / E;
+  static constexpr int W = sizeof(T) == 4 ? 8 : 4;          // 64-byte row segments
+  static constexpr int THREADS = W * NT;
+  static constexpr int PAD = ColCfg<T, N>::PAD;
+  static constexpr int BOX = N < 256 ? N : 256;             // TMA box extent along the transform
+  static constexpr int NBOX = N / BOX;
+  static constexpr size_t TILE_BYTES = (size_t)N * W * sizeof(cx<T>);
+  static constexpr size_t XCH_BYTES = (size_t)ColSmem<T, W, PAD>::words(N) * sizeof(cx<T>);
+  static constexpr size_t FAC_BYTES = sizeof(T) == 4 ? 2048 * sizeof(float) : 0;
+  static constexpr size_t SMEM = 2 * TILE_BYTES + XCH_BYTES + FAC_BYTES + 64;
+  static constexpr int TILES_PER_ROW = M / W;
+};
+
+// Work item -> (field, x2 tile, other index, second transform flag).
+template <int MODE>
+__device__ __forceinline__ void col_item(int item, int tiles, int tpr, int& field, int& xt, int& other) {
+  int k = item;
+  field = 0;
+  if (MODE == kColInvYGrad && k >= tiles) {   // second half: the d/dz field
+    k -= tiles;
+    field = 2;
+  }
+  xt = k % tpr;
+  other = k / tpr;
+}
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(ColTmaCfg<T, N>::THREADS, 1)
+k_col_tma(const __grid_constant__ CUtensorMap map, ColTmaArgs<T> A) {
+  using Cfg = ColTmaCfg<T, N>;
+  constexpr int M = N / 2, E = Cfg::E, NT = Cfg::NT, W = Cfg::W, RL = last_radix<T, N>();
+  constexpr bool AXIS_Z = (MODE == kColFwdZ || MODE == kColInvZGreen);
+  constexpr int64_t ES = AXIS_Z ? (int64_t)N * M : (int64_t)M;     // element stride
+  constexpr int64_t OS = AXIS_Z ? (int64_t)M : (int64_t)N * M;     // stride of the other index
+  constexpr int DIR = (MODE == kColFwdY || MODE == kColFwdZ) ? -1 : +1;
+  constexpr bool kFac = sizeof(T) == 4;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cx<T>* tile[2] = {reinterpret_cast<cx<T>*>(smem_raw),
+                    reinterpret_cast<cx<T>*>(smem_raw + Cfg::TILE_BYTES)};
+  cx<T>* xch = reinterpret_cast<cx<T>*>(smem_raw + 2 * Cfg::TILE_BYTES);
+  float* fac_s = reinterpret_cast<float*>(smem_raw + 2 * Cfg::TILE_BYTES + Cfg::XCH_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * Cfg::TILE_BYTES + Cfg::XCH_BYTES + Cfg::FAC_BYTES);
+
+  const int tiles = Cfg::TILES_PER_ROW * N;
+  const int items = MODE == kColInvYGrad ? 2 * tiles : tiles;
+  const int c = threadIdx.x % W;
+  const int t = threadIdx.x / W;
+  ColSmem<T, W, Cfg::PAD> sm{xch, c};
+
+  auto issue = [&](int item, int buf) {
+    int field, xt, other;
+    col_item<MODE>(item, tiles, Cfg::TILES_PER_ROW, field, xt, other);
+    const int xcoord = xt * W * (sizeof(T) == 4 ? 1 : 2);
+    mbar_expect_tx(&bar[buf], (uint32_t)Cfg::TILE_BYTES);
+#pragma unroll
+    for (int bx = 0; bx < Cfg::NBOX; ++bx) {
+      cx<T>* dst = tile[buf] + (size_t)bx * Cfg::BOX * W;
+      if (AXIS_Z) tma_load_4d(dst, &map, &bar[buf], xcoord, other, bx * Cfg::BOX, field);
+      else tma_load_4d(dst, &map, &bar[buf], xcoord, bx * Cfg::BOX, other, field);
+    }
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  if constexpr (MODE == kColInvZGreen && kFac)
+    for (int j = threadIdx.x; j < 2048; j += blockDim.x) fac_s[j] = A.fac[j];
+  __syncthreads();
+  const int first = blockIdx.x, step = gridDim.x;
+  if (threadIdx.x == 0) {
+    if (first < items) issue(first, 0);
+    if (first + step < items) issue(first + step, 1);
+  }
+  int k = 0;
+  for (int item = first; item < items; item += step, ++k) {
+    const int buf = k & 1;
+    const bool ok = mbar_wait_bounded(&bar[buf], (uint32_t)((k >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicCAS(A.status, 0, PM_ERR_TIMEOUT);
+        // let this CTA's own copies finish (bounded) before returning
+        mbar_wait_bounded(&bar[buf], (uint32_t)((k >> 1) & 1));
+        if (item + step < items) mbar_wait_bounded(&bar[buf ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
+      }
+      return;
+    }
+    int field, xt, other;
+    col_item<MODE>(item, tiles, Cfg::TILES_PER_ROW, field, xt, other);
+    const int x2 = xt * W + c;
+    const cx<T>* st = tile[buf];
+    const int ntr = (MODE == kColInvZGreen || (MODE == kColInvYGrad && field == 0)) ? 2 : 1;
+    for (int tr = 0; tr < ntr; ++tr) {
+      cx<T> v[E];
+#pragma unroll
+      for (int i = 0; i < E; ++i) v[i] = st[(t + NT * i) * W + c];
+      if constexpr (MODE == kColInvZGreen) {
+        // G delta (tr = 0) and -i D(kz) G delta (tr = 1); packed column x2 = 0
+        // takes its pre-multiplied plane0 values instead
+        const int iy = other;
+        const int ky = iy < N / 2 ? iy : iy - N;
+        const int base2 = ky * ky + x2 * x2;
+        const T wyx = A.wtab ? A.wtab[iy] * A.wtab[x2] : (T)1;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int iz = t + NT * i;
+          cx<T> f;
+          if (x2 == 0) {
+            f = A.plane0[(int64_t)iy * N + iz];
+          } else {
+            const int kz = iz < N / 2 ? iz : iz - N;
+            const int n2 = base2 + kz * kz;
+            T gval;
+            if constexpr (kFac) {
+              const float tt = 0.5f * __logf((float)n2) * A.fac_inv_du;
+              const int j = min((int)tt, 2048 - 2);
+              const float fr = tt - (float)j;
+              gval = (T)(A.coeff * (fac_s[j] + fr * (fac_s[j + 1] - fac_s[j])) / (float)n2);
+            } else {
+              gval = A.gtab[n2];
+            }
+            if (A.wtab) gval *= wyx * A.wtab[iz];
+            f = cscale(v[i], gval);
+          }
+          if (tr == 1) {
+            const T d = A.dtab[iz];
+            f = {d * f.y, -d * f.x};
+          }
+          v[i] = f;
+        }
+      }
+      if constexpr (MODE == kColInvYGrad) {
+        if (field == 0 && tr == 0) {   // -i D(ky) phi
+#pragma unroll
+          for (int i = 0; i < E; ++i) {
+            const T d = A.dtab[t + NT * i];
+            v[i] = {d * v[i].y, -d * v[i].x};
+          }
+        }
+      }
+      // all reads of the staged tile done (last transform: the buffer may be
+      // refilled) and the previous transform's exchange reads finished
+      __syncthreads();
+      if (tr == ntr - 1 && threadIdx.x == 0 && item + 2 * step < items) issue(item + 2 * step, buf);
+      fft_regs<T, N, DIR>(v, sm, t, A.tw);
+      // destination
+      cx<T>* dst;
+      if constexpr (MODE == kColFwdY || MODE == kColFwdZ) {
+        dst = A.spec;
+      } else if constexpr (MODE == kColInvZGreen) {
+        dst = A.g + (tr == 0 ? 0 : 2 * A.field_elems);
+      } else {
+        dst = A.g + (field == 2 ? 2 * A.field_elems : (tr == 0 ? A.field_elems : 0));
+      }
+      dst += (int64_t)other * OS + x2;
+#pragma unroll
+      for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+        for (int i = 0; i < RL; ++i) dst[(int64_t)(t + NT * b + i * (N / RL)) * ES] = v[b * RL + i];
+    }
+  }
+}
+
+}  // namespace nupm

@@ -7,6 +7,7 @@
 #include "grid_kernels.cuh"
 #include "nupm_internal.h"
 #include "sort.cuh"
+#include "fft_tma.cuh"
 
 namespace nupm {
 namespace {
@@ -43,9 +44,46 @@ void ensure_attrs() {
   done = true;
 }
 
+// TMA-pipelined column pass of size N.
+template <int N, int MODE>
+void col_tma_n(const GridArgs& g, const CUtensorMap* map, cudaStream_t s) {
+  using Cfg = ColTmaCfg<T, N>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_col_tma<T, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    attr = true;
+  }
+  ColTmaArgs<T> a;
+  a.spec = reinterpret_cast<C*>(g.spec);
+  a.g = reinterpret_cast<C*>(g.g);
+  a.field_elems = g.field_elems;
+  a.tw = reinterpret_cast<const C*>(g.tw_n);
+  a.plane0 = reinterpret_cast<const C*>(g.plane0);
+  a.dtab = reinterpret_cast<const T*>(g.dtab);
+  a.wtab = reinterpret_cast<const T*>(g.wtab);
+  a.gtab = reinterpret_cast<const T*>(g.gtab);
+  a.fac = g.fac;
+  a.fac_inv_du = g.fac_inv_du;
+  a.coeff = g.green_coeff;
+  a.status = g.status;
+  const int tiles = Cfg::TILES_PER_ROW * N;
+  const int items = MODE == kColInvYGrad ? 2 * tiles : tiles;
+  const int grid = items < g.sm_count ? items : g.sm_count;
+  k_col_tma<T, N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*map, a);
+}
+
 // One FFT pass of size N (pass: kPassXFwd .. kPassXInv, see nupm_internal.h).
 template <int N>
 void fft_pass_n(const GridArgs& g, int pass, cudaStream_t s) {
+  if (g.tmap_spec_y) {
+    switch (pass) {
+      case kPassYFwd: col_tma_n<N, kColFwdY>(g, g.tmap_spec_y, s); return;
+      case kPassZFwd: col_tma_n<N, kColFwdZ>(g, g.tmap_spec_z, s); return;
+      case kPassZInv: col_tma_n<N, kColInvZGreen>(g, g.tmap_spec_z, s); return;
+      case kPassYInv: col_tma_n<N, kColInvYGrad>(g, g.tmap_g_y, s); return;
+      default: break;
+    }
+  }
   constexpr int M = N / 2;
   using RC = RowCfg<T, N>;
   using CC = ColCfg<T, N>;

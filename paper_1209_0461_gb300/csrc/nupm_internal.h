@@ -1,6 +1,7 @@
 // Internal declarations shared by the host API and the kernel translation
 // units of libnupm.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -76,6 +77,10 @@ struct GridArgs {
   int* row_cursor;                 // [N^2 + 1]
   int* scan_tot;                   // [2 * 1024] block totals of the scan
   int* perm;                       // [npart] particle indices sorted by row
+  const CUtensorMap* tmap_spec_y;  // TMA maps of the column passes (nullptr: plain kernels)
+  const CUtensorMap* tmap_spec_z;
+  const CUtensorMap* tmap_g_y;
+  int sm_count;
   const float* fac;               // FP32 path: fac table (kFacTable points)
   float fac_inv_du;               // 1 / table spacing in u = ln sqrt(n^2)
   float green_coeff;              // -1.5 Omega_M / (a kf^2 N^3)

@@ -8,6 +8,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cudaTypedefs.h>
+
 #include <string>
 #include <vector>
 
@@ -56,6 +58,10 @@ struct pm_ctx {
   int* d_rowcur = nullptr;
   int* d_scantot = nullptr;
   int* d_perm = nullptr;
+  // TMA tensor maps of the column passes (spectrum along y / z, fields along y)
+  bool tma = false;
+  alignas(64) CUtensorMap tm_spec_y, tm_spec_z, tm_g_y;
+  int sm_count = 152;
   double green_coeff = 0;     // -1.5 Omega_M / (a kf^2 N^3) of the last response
   int* d_status = nullptr;
   // pinned host staging
@@ -293,6 +299,38 @@ void drain_timing(pm_ctx* c) {
   cudaGetLastError();
 }
 
+// Encode a 4-D tensor map over a packed complex field array [F][N][N][M]
+// (x2 fastest) with a box of W x2-columns by `box` elements along y or z.
+int encode_col_map(pm_ctx* c, CUtensorMap* map, void* base, int fields, bool along_z) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return fail(c, PM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int n = c->n, m = c->m;
+  const bool f64 = c->fp64;
+  const int w = f64 ? 4 : 8;                       // column tile width (64-byte segments)
+  const int box = n < 256 ? n : 256;
+  const cuuint64_t e0 = f64 ? 2 * (cuuint64_t)m : (cuuint64_t)m;   // elements of 8 bytes
+  cuuint64_t dims[4] = {e0, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)fields};
+  cuuint64_t strides[3] = {e0 * 8, e0 * 8 * n, e0 * 8 * n * n};
+  cuuint32_t boxd[4] = {(cuuint32_t)(f64 ? 2 * w : w), along_z ? 1u : (cuuint32_t)box,
+                        along_z ? (cuuint32_t)box : 1u, 1u};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = encode(map, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, base,
+                            dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(c, PM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return PM_OK;
+}
+
 GridArgs grid_args(const pm_ctx* c) {
   GridArgs g;
   g.n = c->n;
@@ -315,6 +353,10 @@ GridArgs grid_args(const pm_ctx* c) {
   g.row_cursor = c->d_rowcur;
   g.scan_tot = c->d_scantot;
   g.perm = c->d_perm;
+  g.tmap_spec_y = c->tma ? &c->tm_spec_y : nullptr;
+  g.tmap_spec_z = c->tma ? &c->tm_spec_z : nullptr;
+  g.tmap_g_y = c->tma ? &c->tm_g_y : nullptr;
+  g.sm_count = c->sm_count;
   g.fac = c->d_fac;
   g.fac_inv_du = (float)((kFacTable - 1) / (0.5 * log((double)c->n2max)));
   g.green_coeff = (float)c->green_coeff;
@@ -390,7 +432,7 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   else if (p.precision != PM_FP64 && p.precision != PM_FP32) bad(PM_ERR_INVALID, "precision must be PM_FP64 or PM_FP32");
   else if (p.iters < 1 || p.iters > 16) bad(PM_ERR_INVALID, "iters must be 1..16");
   else if (p.quad_nodes < 2 || p.quad_nodes > kMaxQuad) bad(PM_ERR_INVALID, "quad_nodes must be 2..16");
-  else if (p.flags & ~(PM_I_FIT | PM_DECONV_CIC | PM_KEEP_DEPOSIT | PM_UNFUSED_DEPOSIT))
+  else if (p.flags & ~(PM_I_FIT | PM_DECONV_CIC | PM_KEEP_DEPOSIT | PM_UNFUSED_DEPOSIT | PM_TMA_COLUMNS))
     bad(PM_ERR_INVALID, "unknown flag bits");
   if (rc != PM_OK) {
     // report through a context so pm_last_error works; caller still gets NULL
@@ -545,6 +587,17 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
       rc = cuda_check(c, cudaMemcpy(c->d_ti, ti.data(), ti.size() * sizeof(double), cudaMemcpyHostToDevice), "IC upload");
   }
   if (rc == PM_OK) rc = build_s_table(c, 0.0 > log(c->a_init) ? 0.0 : log(c->a_init) + 1.0);
+  if (rc == PM_OK) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (p.flags & PM_TMA_COLUMNS) {
+      rc = encode_col_map(c, &c->tm_spec_y, c->spec, 1, false);
+      if (rc == PM_OK) rc = encode_col_map(c, &c->tm_spec_z, c->spec, 1, true);
+      if (rc == PM_OK) rc = encode_col_map(c, &c->tm_g_y, c->g, 3, false);
+      c->tma = rc == PM_OK;
+    }
+  }
   if (rc == PM_OK) {
     // mode counts and sum |k| per bin depend on the lattice only: once per context
     GridArgs g = grid_args(c);

@@ -225,3 +225,15 @@ def test_fused_deposit_equals_unfused(prec, n):
     assert np.array_equal(a["spec"], b["spec"]) and np.array_equal(a["spec"], c["spec"])
     assert np.array_equal(a["acc"], b["acc"])
     assert np.array_equal(a["acc"][:, perm], c["acc"])
+
+
+@pytest.mark.parametrize("prec,n", [("fp64", 32), ("fp32", 64), ("fp32", 128), ("fp64", 64)])
+def test_tma_column_passes_equal_plain(prec, n):
+    # the TMA-pipelined column passes do the same arithmetic in the same order
+    # as the plain column kernels: identical spectra and forces
+    w = synth.Workload(f"tma{n}", n, n, 2.0 * n, 0.15, 3, 4, 16, prec)
+    inp = make_inputs(w)
+    a = gpu_kick(w, inp, flags=KEEP_DEPOSIT | 0x10)     # PM_TMA_COLUMNS
+    b = gpu_kick(w, inp, flags=KEEP_DEPOSIT)
+    assert np.array_equal(a["spec"], b["spec"])
+    assert np.array_equal(a["acc"], b["acc"])
