@@ -103,9 +103,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def stage_bytes(w, stage):
+def stage_bytes(w, stage, fused_interp=True):
     """Algorithmic (compulsory) HBM bytes of ONE launch of a stage: each pass
-    reads its inputs and writes its outputs once at stored precision."""
+    reads its inputs and writes its outputs once at stored precision.  With
+    the fused interpolation the inverse x stage reads the three fields and
+    the particles (positions, row permutation) and updates the velocities."""
     n = w.ngrid
     M = n ** 3
     Mc = n * n * (n // 2)                 # packed complex elements per field
@@ -115,7 +117,7 @@ def stage_bytes(w, stage):
     v = r
     Np = w.npart
     return {
-        "deposit": 12 * Np,                              # row sort: keys in, permutation out
+        "deposit": 20 * Np,                              # row sort: y, z words in, permutation out
         "fft_x_fwd": (p + 4) * Np + c * Mc,              # fused deposit + x: particles, perm, spectrum
         "fft_y_fwd": 2 * c * Mc,
         "fft_z_fwd": 2 * c * Mc,
@@ -123,7 +125,7 @@ def stage_bytes(w, stage):
         "green": 3 * c * n * n,                           # packed kx=0 plane: 2 reads + 1 write
         "fft_z_inv": c * Mc + 2 * c * Mc,                 # spectrum -> phi, d/dz phi
         "fft_y_inv": 2 * c * Mc + 3 * c * Mc,             # 2 fields -> 3 fields
-        "fft_x_inv": 3 * (c * Mc + r * M),
+        "fft_x_inv": (3 * c * Mc + (p + 4 + 2 * 3 * v) * Np) if fused_interp else 3 * (c * Mc + r * M),
         "interp": p * Np + min(3 * r * M, 24 * r * Np) + 2 * 3 * v * Np,
     }.get(stage)
 
@@ -282,14 +284,15 @@ def run_gpu(args, w, rank, world):
     per_launch_ms = tot_ms / max(launches, 1)
     if dom in ("deposit", "bins"):
         per_launch_ms = tot_ms / max(calls, 1)     # memset/reduce ride along in the stage
-    alg = stage_bytes(wr, dom)
+    fused = stages["interp"][1] == 0
+    alg = stage_bytes(wr, dom, fused)
     achieved = alg / (per_launch_ms / 1e3) / 1e9
     roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
             "traffic": traffic_from_profiles(dom, wr.name), "alg_bytes_per_launch": int(alg),
             "ms_per_launch": round(per_launch_ms, 4)}
     total_launch = sum(v[1] for v in stages.values())
-    step_alg = sum(stage_bytes(wr, k) * (v[2] if k in ("deposit", "bins") else v[1])
+    step_alg = sum(stage_bytes(wr, k, fused) * (v[2] if k in ("deposit", "bins") else v[1])
                    for k, v in stages.items() if k != "response") / args.steps
     res = dict(value=world * wr.npart / (ms / 1e3), ms_per_step=ms, e2e=e2e, roofline=roof,
                stages={k: {"ms_per_step": round(v[0] / args.steps, 4), "launches_per_step": v[1] // args.steps}

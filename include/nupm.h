@@ -68,6 +68,9 @@ extern "C" {
 #define PM_DECONV_CIC  0x2u  /* divide the Green function by prod sinc^4 (CIC windows) */
 #define PM_KEEP_DEPOSIT 0x4u /* also write the fixed-point deposit grid (PM_FIELD_DEPOSIT) */
 #define PM_UNFUSED_DEPOSIT 0x8u /* global-atomic deposit + separate x pass (no particle sort) */
+#define PM_FUSED_GATHER 0x20u /* inverse x transform fused with the CIC gather + kick in a
+                                 sliding window (no force grids; comparison: one CTA/SM on a
+                                 1024^3 grid, slower than the separate pass + gather) */
 #define PM_TMA_COLUMNS 0x10u /* column FFT passes as persistent TMA-pipelined kernels (comparison;
                                  1 CTA/SM: slower than the default on a 1024^3 grid) */
 
@@ -193,6 +196,7 @@ NUPM_API int pm_get_thresholds(const pm_ctx* ctx, int64_t* thresholds);
  *   PM_FIELD_DELTA_K   the forward spectrum, complex[N][N][N/2+1] unpacked
  *                      (numpy rfftn layout), valid after pm_deposit
  *   PM_FIELD_ACC_X/Y/Z the real acceleration grids [N][N][N], valid after pm_kick
+ *                      without PM_FUSED_GATHER
  * Element type is the precision's float type (complex = 2 of them). */
 #define PM_FIELD_DEPOSIT 0
 #define PM_FIELD_DELTA_K 1
@@ -212,8 +216,8 @@ NUPM_API int pm_copy_field(pm_ctx* ctx, int32_t which, void* dst);
 #define PM_ST_GREEN      6
 #define PM_ST_FFT_Z_INV  7
 #define PM_ST_FFT_Y_INV  8
-#define PM_ST_FFT_X_INV  9
-#define PM_ST_INTERP    10   /* CIC gather + kick */
+#define PM_ST_FFT_X_INV  9   /* inverse x transform (+ CIC gather + kick with PM_FUSED_GATHER) */
+#define PM_ST_INTERP    10   /* CIC gather + kick (not launched with PM_FUSED_GATHER) */
 #define PM_NSTAGES      11
 /* enable != 0: record an event pair around every stage from now on and
  * clear the totals; 0: stop recording. */

@@ -467,7 +467,6 @@ k_fft_x_fwd(const unsigned long long* __restrict__ grid, cx<T>* __restrict__ spe
 // shared atomics, then transforms those rows exactly as k_fft_x_fwd.  No
 // global deposit grid, no memset, no atomics to DRAM.  With `keep` set the
 // tile is also written out (inspection).  grid = (N / TY, N / TZ).
-// Accumulation uses three 32-bit planes of 16-bit weight slices (add_sliced).
 // ---------------------------------------------------------------------------
 template <typename T, int N>
 struct FusedCfg {
@@ -477,25 +476,20 @@ struct FusedCfg {
   static constexpr int NT = M / Plan<T, M>::R1;
   static constexpr int THREADS = ROWS * NT;
   static constexpr int SRC = (TZ + 1) * (TY + 1);
-  static constexpr size_t ACC_BYTES = (size_t)3 * ROWS * N * 4;   // three 16-bit-slice planes
+  static constexpr size_t ACC_BYTES = (size_t)ROWS * N * 8;
   static constexpr size_t XCH_BYTES = (size_t)ROWS * RowSmem<T>::words(M) * sizeof(cx<T>);
   static constexpr size_t SMEM = (ACC_BYTES > XCH_BYTES ? ACC_BYTES : XCH_BYTES);
 };
 
-// Exact deposit sums without 64-bit shared atomics: a weight w < 2^48 + 1 is
-// split into 16-bit slices w = a 2^32 + b 2^16 + c and each slice is added
-// to its own 32-bit plane with a native, result-free shared atomic.  A plane
-// counter overflows only after 65536 additions to one node (the same bound
-// as the 64-bit grid); F = A 2^32 + B 2^16 + C is exact and order-independent.
-__device__ __forceinline__ void add_sliced(unsigned int* plane0, int plane_stride, int idx, unsigned long long w) {
-  atomicAdd(plane0 + idx, (unsigned int)(w & 0xffffu));
-  atomicAdd(plane0 + plane_stride + idx, (unsigned int)((w >> 16) & 0xffffu));
-  atomicAdd(plane0 + 2 * plane_stride + idx, (unsigned int)(w >> 32));
-}
-
-__device__ __forceinline__ unsigned long long sliced_value(const unsigned int* plane0, int plane_stride, int idx) {
-  return ((unsigned long long)plane0[2 * plane_stride + idx] << 32) +
-         ((unsigned long long)plane0[plane_stride + idx] << 16) + (unsigned long long)plane0[idx];
+// Exact 64-bit add on shared memory from two native 32-bit atomics: the low
+// word's returned old value gives the carry into the high word.  Integer
+// addition stays associative, so the sum is bit-exact in any order.
+__device__ __forceinline__ void add_u64_shared(unsigned long long* p, unsigned long long v) {
+  unsigned int* w = reinterpret_cast<unsigned int*>(p);   // little endian: w[0] low, w[1] high
+  const unsigned int lo = (unsigned int)v, hi = (unsigned int)(v >> 32);
+  const unsigned int old = atomicAdd(w, lo);
+  const unsigned int carry = (old + lo < old) ? 1u : 0u;
+  if (hi + carry) atomicAdd(w + 1, hi + carry);
 }
 
 template <typename T, int N, class Q>
@@ -507,11 +501,11 @@ k_deposit_fft_x(const void* __restrict__ pos, int64_t np, double delta, const in
   constexpr int TZ = Cfg::TZ, TY = Cfg::TY, ROWS = Cfg::ROWS, M = N / 2, E = Plan<T, M>::R1, NT = Cfg::NT;
   constexpr int RL = last_radix<T, M>(), SRC = Cfg::SRC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned int* acc = reinterpret_cast<unsigned int*>(smem_raw);   // [3][ROWS][N] slice planes
-  constexpr int PS = ROWS * N;                                      // plane stride
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);   // [ROWS][N]
   __shared__ int pre[SRC + 1], beg[SRC];
   const int ty0 = blockIdx.x * TY, tz0 = blockIdx.y * TZ;
-  for (int i = threadIdx.x; i < 3 * PS / 4; i += blockDim.x) reinterpret_cast<uint4*>(acc)[i] = uint4{0u, 0u, 0u, 0u};
+  for (int i = threadIdx.x; i < ROWS * N / 2; i += blockDim.x)
+    reinterpret_cast<ulonglong2*>(acc)[i] = ulonglong2{0ull, 0ull};
   if (threadIdx.x == 0) {
     int run = 0;
     for (int sidx = 0; sidx < SRC; ++sidx) {
@@ -554,11 +548,11 @@ k_deposit_fft_x(const void* __restrict__ pos, int64_t np, double delta, const in
           const int yl = (c[1] + dy - ty0) & (N - 1);
           if (yl >= TY) continue;
           const unsigned long long wzy = wz * (dy ? (unsigned long long)w[1] : (unsigned long long)(65536 - w[1]));
-          const int rb = (zl * TY + yl) * N;
+          unsigned long long* rowp = acc + (zl * TY + yl) * N;
           const unsigned long long w0 = wzy * (unsigned long long)(65536 - w[0]);
           const unsigned long long w1 = wzy * (unsigned long long)w[0];
-          if (w0) add_sliced(acc, PS, rb + c[0], w0);
-          if (w1) add_sliced(acc, PS, rb + x1, w1);
+          if (w0) add_u64_shared(rowp + c[0], w0);
+          if (w1) add_u64_shared(rowp + x1, w1);
         }
       }
     }
@@ -569,32 +563,28 @@ k_deposit_fft_x(const void* __restrict__ pos, int64_t np, double delta, const in
   const int r = threadIdx.x / NT;
   const int gz = tz0 + r / TY, gy = ty0 + r % TY;
   const int64_t grow = (int64_t)gz * N + gy;
-  const int rb = r * N;
+  const ulonglong2* src = reinterpret_cast<const ulonglong2*>(acc + r * N);
   cx<T> v[E];
   if (keep) {
     ulonglong2* kd = reinterpret_cast<ulonglong2*>(keep + grow * N);
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
-      const int x = 2 * (t + NT * i);
-      kd[t + NT * i] = ulonglong2{sliced_value(acc, PS, rb + x), sliced_value(acc, PS, rb + x + 1)};
-    }
+    for (int i = 0; i < E; ++i) kd[t + NT * i] = src[t + NT * i];
   }
   if constexpr (sizeof(T) == 4) {
-    // delta = (A 2^32 + B 2^16 + C) s - 1 in FP32 FMAs (no FP64 arithmetic)
-    const float s2 = (float)(scale * 4294967296.0), s1 = (float)(scale * 65536.0), s0 = (float)scale;
+    // F = hi 2^32 + lo: delta = hi (s 2^32) + (lo s - 1) in FP32 FMAs
+    const float hs = (float)(scale * 4294967296.0), ls = (float)scale;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-      const int x = rb + 2 * (t + NT * i);
-      const float ax = fmaf((float)acc[2 * PS + x], s2, fmaf((float)acc[PS + x], s1, fmaf((float)acc[x], s0, -1.0f)));
-      const float ay = fmaf((float)acc[2 * PS + x + 1], s2,
-                            fmaf((float)acc[PS + x + 1], s1, fmaf((float)acc[x + 1], s0, -1.0f)));
+      const ulonglong2 q = src[t + NT * i];
+      const float ax = fmaf((float)(unsigned)(q.x >> 32), hs, fmaf((float)(unsigned)q.x, ls, -1.0f));
+      const float ay = fmaf((float)(unsigned)(q.y >> 32), hs, fmaf((float)(unsigned)q.y, ls, -1.0f));
       v[i] = {(T)ax, (T)ay};
     }
   } else {
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-      const int x = rb + 2 * (t + NT * i);
-      v[i] = {(T)((double)sliced_value(acc, PS, x) * scale - 1.0), (T)((double)sliced_value(acc, PS, x + 1) * scale - 1.0)};
+      const ulonglong2 q = src[t + NT * i];
+      v[i] = {(T)((double)q.x * scale - 1.0), (T)((double)q.y * scale - 1.0)};
     }
   }
   __syncthreads();   // the tile is consumed; its memory now serves the exchange buffers
@@ -685,6 +675,142 @@ k_fft_x_inv(cx<T>* __restrict__ data, int64_t field_stride, const cx<T>* __restr
       const int n = t + NT * b + i * (M / RL);
       reinterpret_cast<cx<T>*>(out)[n] = v[b * RL + i];    // (x[2n], x[2n+1])
     }
+}
+
+// ---------------------------------------------------------------------------
+// Fused inverse x pass + CIC interpolation + kick (a6 last third + a7).
+// Work item = (z slab of TZ particle rows, y segment of LY particle rows).  The
+// CTA walks y: at step j it inverse-transforms the x rows (z0 .. z0+TZ, y0+j)
+// of the three fields (phi gets -i D(kx) first) into a shared slice, then
+// interpolates the particles of rows (z0 .. z0+TZ-1, y0+j-1) from slices j-1
+// and j (their 2 x 2 corner rows) and kicks them.  Every particle is handled
+// by exactly one CTA, without atomics; the force grids never reach HBM.
+// Persistent grid; particle rows from the deposit's row sort.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+struct XiCfg {
+  static constexpr int TZ = 4;
+  static constexpr int SLAB = TZ + 1;              // field rows per slice and component
+  static constexpr int USED = 3 * SLAB;            // 15 rows per step
+  static constexpr int ROWS = 16;
+  static constexpr int M = N / 2;
+  static constexpr int NT = M / Plan<T, M>::R1;
+  static constexpr int THREADS = ROWS * NT;
+  static constexpr int LY = N >= 64 ? 32 : N / 2;
+  static constexpr size_t XCH = (size_t)ROWS * RowSmem<T>::words(M) * sizeof(cx<T>);
+  static constexpr size_t SLICE = (size_t)USED * N * sizeof(T);
+  static constexpr size_t SMEM = XCH + 2 * SLICE;
+};
+
+template <typename T, int N, class Q>
+__global__ void __launch_bounds__(XiCfg<T, N>::THREADS, 1)
+k_xinv_interp(const cx<T>* __restrict__ g, int64_t field_elems, const cx<T>* __restrict__ tw_m,
+              const cx<T>* __restrict__ tw_n, const T* __restrict__ dtab, const void* __restrict__ pos, int64_t np,
+              double delta, const int* __restrict__ row_start, const int* __restrict__ perm, T* __restrict__ vel,
+              T kick, T* __restrict__ acc_out, int* status) {
+  using Cfg = XiCfg<T, N>;
+  constexpr int M = N / 2, E = Plan<T, M>::R1, NT = Cfg::NT, RL = last_radix<T, M>();
+  constexpr int TZ = Cfg::TZ, SLAB = Cfg::SLAB, USED = Cfg::USED, LY = Cfg::LY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* slices = reinterpret_cast<T*>(smem_raw + Cfg::XCH);      // [2][USED][N]
+  __shared__ int pre[TZ + 1], beg[TZ];
+  const int t = threadIdx.x % NT;
+  const int r = threadIdx.x / NT;                              // row group (r == USED: idle duplicate)
+  const int comp = (r < USED ? r : 0) / SLAB, zz = (r < USED ? r : 0) % SLAB;
+  RowSmem<T> sm{reinterpret_cast<cx<T>*>(smem_raw) + r * RowSmem<T>::words(M)};
+  const int ysegs = N / LY;
+  const int items = (N / TZ) * ysegs;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int z0 = (item / ysegs) * TZ, y0 = (item % ysegs) * LY;
+    for (int j = 0; j <= LY; ++j) {
+      const int cur = j & 1;
+      const int y = (y0 + j) & (N - 1);
+      // ---- inverse x transform of row (z0 + zz, y) of field comp into slice cur
+      const cx<T>* rowp = g + (int64_t)comp * field_elems + ((int64_t)((z0 + zz) & (N - 1)) * N + y) * M;
+      if (comp == 0) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int k = t + NT * i;
+          const cx<T> x = rowp[k];
+          const T d = k == 0 ? (T)0 : dtab[k];
+          sm.st(k, cx<T>{d * x.y, -d * x.x});
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) sm.st(t + NT * i, rowp[t + NT * i]);
+      }
+      __syncthreads();
+      cx<T> v[E];
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int k = t + NT * i;
+        const cx<T> xk = sm.ld(k);
+        if (k == 0) {
+          v[i] = {xk.x + xk.y, xk.x - xk.y};
+        } else {
+          const cx<T> xm = cconj(sm.ld(M - k));
+          const cx<T> sp = xk + xm;
+          const cx<T> dd = cmul(twid_table<+1>(tw_n, k), xk - xm);
+          v[i] = {sp.x - dd.y, sp.y + dd.x};
+        }
+      }
+      __syncthreads();
+      fft_regs<T, M, +1>(v, sm, t, tw_m);
+      if (r < USED) {
+        cx<T>* out = reinterpret_cast<cx<T>*>(slices + ((size_t)cur * USED + r) * N);
+#pragma unroll
+        for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+          for (int i = 0; i < RL; ++i) out[t + NT * b + i * (M / RL)] = v[b * RL + i];
+      }
+      if (threadIdx.x == 0 && j >= 1) {
+        int run = 0;
+        const int py = (y0 + j - 1) & (N - 1);
+        for (int q = 0; q < TZ; ++q) {
+          const int rr = ((z0 + q) & (N - 1)) * N + py;
+          beg[q] = row_start[rr];
+          pre[q] = run;
+          run += row_start[rr + 1] - row_start[rr];
+        }
+        pre[TZ] = run;
+      }
+      __syncthreads();
+      // ---- particles of rows (z0 .. z0+TZ-1, y - 1): slices cur^1 (dy = 0) and cur (dy = 1)
+      if (j >= 1) {
+        const T* s0 = slices + (size_t)(cur ^ 1) * USED * N;
+        const T* s1 = slices + (size_t)cur * USED * N;
+        const int total = pre[TZ];
+        for (int jj = threadIdx.x; jj < total; jj += blockDim.x) {
+          int q = 0;
+          while (pre[q + 1] <= jj) ++q;
+          const int64_t p = perm[beg[q] + (jj - pre[q])];
+          int c[3], w[3];
+          const typename Q::Raw raw = Q::load(pos, np, p);
+          if (!Q::get(raw, N, delta, c, w, status)) continue;
+          const T inv = (T)1.0 / (T)65536;
+          const T fx1 = (T)w[0] * inv, fy1 = (T)w[1] * inv, fz1 = (T)w[2] * inv;
+          const T fx0 = (T)1 - fx1, fy0 = (T)1 - fy1, fz0 = (T)1 - fz1;
+          const int zl = (c[2] - z0) & (N - 1);             // 0 .. TZ-1
+          const int x0 = c[0], x1 = (c[0] + 1) & (N - 1);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const T* a0 = s0 + (size_t)(d * SLAB + zl) * N;  // (z, y)
+            const T* a1 = a0 + N;                             // (z + 1, y)
+            const T* b0 = s1 + (size_t)(d * SLAB + zl) * N;  // (z, y + 1)
+            const T* b1 = b0 + N;                             // (z + 1, y + 1)
+            const T v00 = fx0 * a0[x0] + fx1 * a0[x1];
+            const T v01 = fx0 * b0[x0] + fx1 * b0[x1];
+            const T v10 = fx0 * a1[x0] + fx1 * a1[x1];
+            const T v11 = fx0 * b1[x0] + fx1 * b1[x1];
+            const T acc = fz0 * (fy0 * v00 + fy1 * v01) + fz1 * (fy0 * v10 + fy1 * v11);
+            vel[d * np + p] += acc * kick;
+            if (acc_out) acc_out[d * np + p] = acc;
+          }
+        }
+      }
+      __syncthreads();   // slice cur^1 is refilled at the next step
+    }
+  }
 }
 
 }  // namespace nupm

@@ -147,6 +147,23 @@ void deposit_fft_x_n(const GridArgs& g, const void* pos, bool keep, cudaStream_t
       keep ? reinterpret_cast<unsigned long long*>(g.g) : nullptr, g.status);
 }
 
+// Fused inverse x + interpolation + kick of size N (persistent grid).
+template <int N>
+void xinv_interp_n(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, cudaStream_t s) {
+  using X = XiCfg<T, N>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_xinv_interp<T, N, Quant<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::SMEM);
+    attr = true;
+  }
+  const int items = (N / X::TZ) * (N / X::LY);
+  const int grid = items < g.sm_count ? items : g.sm_count;
+  k_xinv_interp<T, N, Quant<T>><<<grid, X::THREADS, X::SMEM, s>>>(
+      reinterpret_cast<const C*>(g.g), g.field_elems, reinterpret_cast<const C*>(g.tw_m),
+      reinterpret_cast<const C*>(g.tw_n), reinterpret_cast<const T*>(g.dtab), pos, g.np, g.delta, g.row_start,
+      g.perm, reinterpret_cast<T*>(vel), (T)kick, reinterpret_cast<T*>(acc_out), g.status);
+}
+
 #define NUPM_DISPATCH(fn)                                  \
   switch (g.n) {                                           \
     case 16: fn<16>(g, pass, s); break;                    \
@@ -245,6 +262,21 @@ int NUPM_FN(interp)(const GridArgs& g, const void* pos, void* vel, double kick, 
     k_interp_kick<T><<<grid_blocks(g.np, 256), 256, 0, s>>>(pos, g.np, g.n, g.delta, reinterpret_cast<const T*>(g.g),
                                                            2 * g.field_elems, reinterpret_cast<T*>(vel), (T)kick,
                                                            reinterpret_cast<T*>(acc_out), g.status);
+  return PM_OK;
+}
+
+int NUPM_FN(xinv_interp)(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out,
+                         cudaStream_t s) {
+  switch (g.n) {
+    case 16: xinv_interp_n<16>(g, pos, vel, kick, acc_out, s); break;
+    case 32: xinv_interp_n<32>(g, pos, vel, kick, acc_out, s); break;
+    case 64: xinv_interp_n<64>(g, pos, vel, kick, acc_out, s); break;
+    case 128: xinv_interp_n<128>(g, pos, vel, kick, acc_out, s); break;
+    case 256: xinv_interp_n<256>(g, pos, vel, kick, acc_out, s); break;
+    case 512: xinv_interp_n<512>(g, pos, vel, kick, acc_out, s); break;
+    case 1024: xinv_interp_n<1024>(g, pos, vel, kick, acc_out, s); break;
+    default: return PM_ERR_UNSUPPORTED;
+  }
   return PM_OK;
 }
 

@@ -95,6 +95,8 @@ struct GridArgs {
   int green##SFX(const GridArgs& g, cudaStream_t s);                                        \
   int interp##SFX(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, \
                   cudaStream_t s);                                                          \
+  int xinv_interp##SFX(const GridArgs& g, const void* pos, void* vel, double kick,          \
+                       void* acc_out, cudaStream_t s);                                      \
   int unpack##SFX(const GridArgs& g, void* dst, cudaStream_t s);
 NUPM_DECLARE_GRID(_f32)
 NUPM_DECLARE_GRID(_f64)

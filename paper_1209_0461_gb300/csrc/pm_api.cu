@@ -432,7 +432,7 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   else if (p.precision != PM_FP64 && p.precision != PM_FP32) bad(PM_ERR_INVALID, "precision must be PM_FP64 or PM_FP32");
   else if (p.iters < 1 || p.iters > 16) bad(PM_ERR_INVALID, "iters must be 1..16");
   else if (p.quad_nodes < 2 || p.quad_nodes > kMaxQuad) bad(PM_ERR_INVALID, "quad_nodes must be 2..16");
-  else if (p.flags & ~(PM_I_FIT | PM_DECONV_CIC | PM_KEEP_DEPOSIT | PM_UNFUSED_DEPOSIT | PM_TMA_COLUMNS))
+  else if (p.flags & ~(PM_I_FIT | PM_DECONV_CIC | PM_KEEP_DEPOSIT | PM_UNFUSED_DEPOSIT | PM_TMA_COLUMNS | PM_FUSED_GATHER))
     bad(PM_ERR_INVALID, "unknown flag bits");
   if (rc != PM_OK) {
     // report through a context so pm_last_error works; caller still gets NULL
@@ -777,20 +777,33 @@ int pm_kick(pm_ctx* c, const void* pos, void* vel, double a, double kick_factor,
     rc = c->fp64 ? green_f64(g, c->stream) : green_f32(g, c->stream);
   }
   c->deposit_grid_valid = false;
+  // the fused gather walks the row sort of pm_deposit, absent on the unfused path
+  const bool separate = !(c->p.flags & PM_FUSED_GATHER) || (c->p.flags & PM_UNFUSED_DEPOSIT);
   const int inv[3] = {kPassZInv, kPassYInv, kPassXInv};
   const int ist[3] = {PM_ST_FFT_Z_INV, PM_ST_FFT_Y_INV, PM_ST_FFT_X_INV};
-  for (int i = 0; i < 3 && rc == PM_OK; ++i) {
+  for (int i = 0; i < 2 && rc == PM_OK; ++i) {
     Stage st(c, ist[i], 1);
     rc = c->fp64 ? fft_pass_f64(g, inv[i], c->stream) : fft_pass_f32(g, inv[i], c->stream);
   }
-  if (rc == PM_OK) {
-    Stage st(c, PM_ST_INTERP, 1);
-    rc = c->fp64 ? interp_f64(g, pos, vel, kick_factor, acc_out, c->stream)
-                 : interp_f32(g, pos, vel, kick_factor, acc_out, c->stream);
+  if (separate) {
+    if (rc == PM_OK) {
+      Stage st(c, ist[2], 1);
+      rc = c->fp64 ? fft_pass_f64(g, inv[2], c->stream) : fft_pass_f32(g, inv[2], c->stream);
+    }
+    if (rc == PM_OK) {
+      Stage st(c, PM_ST_INTERP, 1);
+      rc = c->fp64 ? interp_f64(g, pos, vel, kick_factor, acc_out, c->stream)
+                   : interp_f32(g, pos, vel, kick_factor, acc_out, c->stream);
+    }
+  } else if (rc == PM_OK) {
+    // the row sort of pm_deposit lists the particles of each row (same positions)
+    Stage st(c, PM_ST_FFT_X_INV, 1);
+    rc = c->fp64 ? xinv_interp_f64(g, pos, vel, kick_factor, acc_out, c->stream)
+                 : xinv_interp_f32(g, pos, vel, kick_factor, acc_out, c->stream);
   }
   if (rc != PM_OK) return fail(c, rc, "pm_kick: unsupported grid");
   rc = cuda_check(c, cudaGetLastError(), "pm_kick launch");
-  if (rc == PM_OK) c->have_kick = true;
+  if (rc == PM_OK) c->have_kick = separate;   // force grids exist only on the separate path
   return rc;
 }
 
@@ -879,7 +892,8 @@ int pm_copy_field(pm_ctx* c, int32_t which, void* dst) {
     case PM_FIELD_ACC_X:
     case PM_FIELD_ACC_Y:
     case PM_FIELD_ACC_Z: {
-      if (!c->have_kick) return fail(c, PM_ERR_ORDER, "no force grids before pm_kick");
+      if (!c->have_kick)
+        return fail(c, PM_ERR_ORDER, "no force grids (pm_kick ran with PM_FUSED_GATHER)");
       const int comp = which - PM_FIELD_ACC_X;
       const char* src = reinterpret_cast<const char*>(c->g) + (size_t)comp * c->field_elems * c->cplx;
       e = cudaMemcpyAsync(dst, src, (size_t)n3 * real, cudaMemcpyDeviceToDevice, c->stream);

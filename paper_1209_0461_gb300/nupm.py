@@ -21,7 +21,8 @@ PM_OK = 0
 ERRORS = {-1: "PM_ERR_INVALID", -2: "PM_ERR_RANGE", -3: "PM_ERR_OVERFLOW", -4: "PM_ERR_CUDA",
           -5: "PM_ERR_ALLOC", -6: "PM_ERR_TIMEOUT", -7: "PM_ERR_ORDER", -8: "PM_ERR_UNSUPPORTED"}
 PM_FP64, PM_FP32 = 0, 1
-PM_I_FIT, PM_DECONV_CIC, PM_KEEP_DEPOSIT, PM_UNFUSED_DEPOSIT, PM_TMA_COLUMNS = 0x1, 0x2, 0x4, 0x8, 0x10
+PM_I_FIT, PM_DECONV_CIC, PM_KEEP_DEPOSIT, PM_UNFUSED_DEPOSIT = 0x1, 0x2, 0x4, 0x8
+PM_TMA_COLUMNS, PM_FUSED_GATHER = 0x10, 0x20
 FIELD_DEPOSIT, FIELD_DELTA_K, FIELD_ACC_X, FIELD_ACC_Y, FIELD_ACC_Z = range(5)
 STAGES = ["deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_fwd", "bins", "response", "green",
           "fft_z_inv", "fft_y_inv", "fft_x_inv", "interp"]

@@ -31,6 +31,7 @@ def make_inputs(w, npart=None, seed_shift=0):
 
 KEEP_DEPOSIT = 0x4
 UNFUSED_DEPOSIT = 0x8
+FUSED_GATHER = 0x20
 
 
 def gpu_kick(w, inp, K=0.01, iters=1, flags=KEEP_DEPOSIT, n_hist=None, prev=None, quad=8, keep_fields=False):
