@@ -117,8 +117,8 @@ def stage_bytes(w, stage, fused_interp=True):
     v = r
     Np = w.npart
     return {
-        "deposit": 20 * Np,                              # row sort: y, z words in, permutation out
-        "fft_x_fwd": (p + 4) * Np + c * Mc,              # fused deposit + x: particles, perm, spectrum
+        "deposit": (p + 8) * Np,                         # row sort: positions in, 8-byte records out
+        "fft_x_fwd": 8 * Np + c * Mc,                    # fused deposit + x: records in, spectrum out
         "fft_y_fwd": 2 * c * Mc,
         "fft_z_fwd": 2 * c * Mc,
         "bins": c * Mc,

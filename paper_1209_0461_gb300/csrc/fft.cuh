@@ -167,10 +167,10 @@ __device__ __forceinline__ void stockham_stage(cx<T> (&v)[E], const SM& sm, int 
 // Full transform of length L held as E = R1 registers per thread.  On entry v
 // holds in[t + NT i] (i < E); on exit v[b R_last + i] holds
 // out[(t + NT b) + i (L / R_last)].
-template <typename T, int L, int DIR, class SM>
-__device__ __forceinline__ void fft_regs(cx<T> (&v)[Plan<T, L>::R1], const SM& sm, int t,
+template <typename T, int L, int DIR, class SM, class P = Plan<T, L>>
+__device__ __forceinline__ void fft_regs(cx<T> (&v)[P::R1], const SM& sm, int t,
                                          const cx<T>* __restrict__ tw) {
-  constexpr int R1 = Plan<T, L>::R1, R2 = Plan<T, L>::R2, R3 = Plan<T, L>::R3;
+  constexpr int R1 = P::R1, R2 = P::R2, R3 = P::R3;
   constexpr int E = R1, NT = L / R1;
   if constexpr (R2 == 1) {
     stockham_stage<T, L, E, NT, R1, 1, DIR, true, true>(v, sm, t, tw);
@@ -184,10 +184,24 @@ __device__ __forceinline__ void fft_regs(cx<T> (&v)[Plan<T, L>::R1], const SM& s
   }
 }
 
-template <typename T, int L>
+template <typename T, int L, class P = Plan<T, L>>
 __host__ __device__ constexpr int last_radix() {
-  return Plan<T, L>::R3 > 1 ? Plan<T, L>::R3 : (Plan<T, L>::R2 > 1 ? Plan<T, L>::R2 : Plan<T, L>::R1);
+  return P::R3 > 1 ? P::R3 : (P::R2 > 1 ? P::R2 : P::R1);
 }
+
+// Plans with fewer elements per thread for the fused deposit/x kernel: more
+// threads per tile for the particle phase and fewer registers, so that the
+// shared-memory tile, not the register file, sets the CTAs per SM.
+template <typename T, int L>
+struct FusedPlan : Plan<T, L> {};
+template <>
+struct FusedPlan<float, 512> {
+  static constexpr int R1 = 16, R2 = 8, R3 = 4;
+};
+template <>
+struct FusedPlan<float, 256> {
+  static constexpr int R1 = 8, R2 = 8, R3 = 4;
+};
 
 // Shared-memory view of one column of a W-column tile: element e of column c
 // at e*W + c + (e >> 5) * PAD (PAD breaks bank conflicts of the stage writes).
@@ -473,88 +487,148 @@ struct FusedCfg {
   static constexpr int TZ = 2, TY = 4;
   static constexpr int ROWS = TZ * TY;
   static constexpr int M = N / 2;
-  static constexpr int NT = M / Plan<T, M>::R1;
+  using P = FusedPlan<T, M>;
+  static constexpr int E = P::R1;
+  static constexpr int NT = M / E;
   static constexpr int THREADS = ROWS * NT;
   static constexpr int SRC = (TZ + 1) * (TY + 1);
   static constexpr size_t ACC_BYTES = (size_t)ROWS * N * 8;
   static constexpr size_t XCH_BYTES = (size_t)ROWS * RowSmem<T>::words(M) * sizeof(cx<T>);
   static constexpr size_t SMEM = (ACC_BYTES > XCH_BYTES ? ACC_BYTES : XCH_BYTES);
+  // CTAs per SM that the shared-memory tile allows (227 KB), at most 4 (FP32)
+  // or 2 (FP64, whose transform needs twice the registers)
+  static constexpr int BY_SMEM = (int)((227u * 1024u) / (SMEM + 1024u));
+  static constexpr int CAP = sizeof(T) == 4 ? 4 : 2;
+  static constexpr int MIN_BLOCKS = BY_SMEM < 1 ? 1 : (BY_SMEM > CAP ? CAP : BY_SMEM);
 };
 
-// Exact 64-bit add on shared memory from two native 32-bit atomics: the low
+// Exact 64-bit sums on shared memory from native 32-bit atomics: the low
 // word's returned old value gives the carry into the high word.  Integer
-// addition stays associative, so the sum is bit-exact in any order.
-__device__ __forceinline__ void add_u64_shared(unsigned long long* p, unsigned long long v) {
-  unsigned int* w = reinterpret_cast<unsigned int*>(p);   // little endian: w[0] low, w[1] high
-  const unsigned int lo = (unsigned int)v, hi = (unsigned int)(v >> 32);
-  const unsigned int old = atomicAdd(w, lo);
-  const unsigned int carry = (old + lo < old) ? 1u : 0u;
-  if (hi + carry) atomicAdd(w + 1, hi + carry);
+// addition stays associative, so the sum is bit-exact in any order, and the
+// high-word adds may trail the low-word adds of other corners.
+__device__ __forceinline__ unsigned int carry_of(unsigned int old, unsigned int lo) {
+  return (old + lo < old) ? 1u : 0u;
 }
 
-template <typename T, int N, class Q>
-__global__ void __launch_bounds__(FusedCfg<T, N>::THREADS)
-k_deposit_fft_x(const void* __restrict__ pos, int64_t np, double delta, const int* __restrict__ row_start,
-                const int* __restrict__ perm, cx<T>* __restrict__ spec, double scale, const cx<T>* __restrict__ tw_m,
-                const cx<T>* __restrict__ tw_n, unsigned long long* __restrict__ keep, int* status) {
+template <typename T, int N>
+__global__ void __launch_bounds__(FusedCfg<T, N>::THREADS, FusedCfg<T, N>::MIN_BLOCKS)
+k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restrict__ row_start,
+                cx<T>* __restrict__ spec, double scale, const cx<T>* __restrict__ tw_m, const cx<T>* __restrict__ tw_n,
+                unsigned long long* __restrict__ keep) {
   using Cfg = FusedCfg<T, N>;
-  constexpr int TZ = Cfg::TZ, TY = Cfg::TY, ROWS = Cfg::ROWS, M = N / 2, E = Plan<T, M>::R1, NT = Cfg::NT;
-  constexpr int RL = last_radix<T, M>(), SRC = Cfg::SRC;
+  using P = typename Cfg::P;
+  constexpr int TZ = Cfg::TZ, TY = Cfg::TY, ROWS = Cfg::ROWS, M = N / 2, E = Cfg::E, NT = Cfg::NT;
+  constexpr int RL = last_radix<T, M, P>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);   // [ROWS][N]
-  __shared__ int pre[SRC + 1], beg[SRC];
+  // The source rows (tz0-1 .. tz0+TZ-1) x (ty0-1 .. ty0+TY-1) are, per z, one
+  // contiguous run of the row-sorted permutation, plus the wrapped row y = N-1
+  // when ty0 = 0: NSEG segments, concatenated in a virtual index j.
+  constexpr int NSEG = 2 * (TZ + 1);
+  __shared__ int seg_pre[NSEG + 1], seg_beg[NSEG];
   const int ty0 = blockIdx.x * TY, tz0 = blockIdx.y * TZ;
   for (int i = threadIdx.x; i < ROWS * N / 2; i += blockDim.x)
     reinterpret_cast<ulonglong2*>(acc)[i] = ulonglong2{0ull, 0ull};
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int sidx = 0; sidx < SRC; ++sidx) {
-      const int sz = (tz0 - 1 + sidx / (TY + 1)) & (N - 1), sy = (ty0 - 1 + sidx % (TY + 1)) & (N - 1);
-      const int r = sz * N + sy;
-      const int b0 = row_start[r], b1 = row_start[r + 1];
-      beg[sidx] = b0;
-      pre[sidx] = run;
-      run += b1 - b0;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int len = 0, b0 = 0;
+    if (lane < NSEG) {
+      const int sz = (tz0 - 1 + lane / 2) & (N - 1);
+      int r0, r1;
+      if (lane & 1) {            // main run of rows
+        r0 = sz * N + (ty0 ? ty0 - 1 : 0);
+        r1 = sz * N + ty0 + TY;
+      } else {                   // wrapped row N-1 (empty unless ty0 = 0)
+        r0 = sz * N + N - 1;
+        r1 = ty0 ? r0 : r0 + 1;
+      }
+      b0 = row_start[r0];
+      len = row_start[r1] - b0;
     }
-    pre[SRC] = run;
+    int incl = len;
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += o;
+    }
+    if (lane < NSEG) {
+      seg_beg[lane] = b0;
+      seg_pre[lane + 1] = incl;
+    }
+    if (lane == 0) seg_pre[0] = 0;
   }
   __syncthreads();
-  const int total = pre[SRC];
+  const int total = seg_pre[NSEG];
+  int bound[NSEG], off[NSEG];   // j >= bound[s] -> record index j + off[s]
+#pragma unroll
+  for (int k = 0; k < NSEG; ++k) {
+    bound[k] = seg_pre[k];
+    off[k] = seg_beg[k] - seg_pre[k];
+  }
+  unsigned int* accw = reinterpret_cast<unsigned int*>(acc);   // little endian: [2i] low, [2i+1] high
+  // window rows: z planes tz0-1 .. tz0+TZ-1 (segment / 2), y rows ws .. ws+TY
+  // (identified by the record's y cell mod 32; N >= 32 or the mask below)
+  constexpr int YM = (N < 32 ? N : 32) - 1;
+  const int ws = (ty0 - 1) & (N - 1);
   constexpr int U = 4;
   for (int j0 = threadIdx.x; j0 < total; j0 += blockDim.x * U) {
-    typename Q::Raw raw[U];
+    unsigned long long rr[U];
+    int zp[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = j0 + u * blockDim.x;
-      if (j < total) {
-        int sidx = 0;
-#pragma unroll 1
-        while (pre[sidx + 1] <= j) ++sidx;
-        raw[u] = Q::load(pos, np, perm[beg[sidx] + (j - pre[sidx])]);
-      }
+      int o = off[0], z = 0;
+#pragma unroll
+      for (int k = 1; k < NSEG; ++k)
+        if (j >= bound[k]) {
+          o = off[k];
+          z = k >> 1;
+        }
+      zp[u] = z;
+      rr[u] = j < total ? rec[j + o] : 0ull;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      int c[3], w[3];
-      if (j0 + u * (int)blockDim.x >= total || !Q::get(raw[u], N, delta, c, w, status)) continue;
-      const int x1 = (c[0] + 1) & (N - 1);
+      if (j0 + u * (int)blockDim.x >= total) continue;
+      const unsigned long long r = rr[u];
+      const unsigned wx = (unsigned)r & 0xffffu, wy = (unsigned)(r >> 16) & 0xffffu;
+      const unsigned wzz = (unsigned)(r >> 32) & 0xffffu;
+      const int cx = (int)(r >> 48) & 0x7ff;
+      const int yo = ((int)(r >> 59) - ws) & YM;      // 0 .. TY: row of the window
+      const int x1 = (cx + 1) & (N - 1);
+      // the particle's (up to) 8 corners in this tile: all low-word adds in
+      // flight before any carry is needed
+      int slot[8];
+      unsigned int lo[8], hi[8], old[8];
 #pragma unroll
       for (int dz = 0; dz < 2; ++dz) {
-        const int zl = (c[2] + dz - tz0) & (N - 1);
-        if (zl >= TZ) continue;
-        const unsigned long long wz = dz ? (unsigned long long)w[2] : (unsigned long long)(65536 - w[2]);
+        const int zl = zp[u] - 1 + dz;
+        const unsigned long long wz = dz ? (unsigned long long)wzz : (unsigned long long)(65536u - wzz);
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
-          const int yl = (c[1] + dy - ty0) & (N - 1);
-          if (yl >= TY) continue;
-          const unsigned long long wzy = wz * (dy ? (unsigned long long)w[1] : (unsigned long long)(65536 - w[1]));
-          unsigned long long* rowp = acc + (zl * TY + yl) * N;
-          const unsigned long long w0 = wzy * (unsigned long long)(65536 - w[0]);
-          const unsigned long long w1 = wzy * (unsigned long long)w[0];
-          if (w0) add_u64_shared(rowp + c[0], w0);
-          if (w1) add_u64_shared(rowp + x1, w1);
+          const int yl = yo - 1 + dy;
+          const bool in = zl >= 0 && zl < TZ && yl >= 0 && yl < TY;
+          const unsigned long long wzy = wz * (dy ? (unsigned long long)wy : (unsigned long long)(65536u - wy));
+          const int rb = (zl * TY + yl) * N;
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const int k = dz * 4 + dy * 2 + dx;
+            const unsigned long long v = in ? wzy * (unsigned long long)(dx ? wx : 65536u - wx) : 0ull;
+            slot[k] = 2 * (rb + (dx ? x1 : cx));
+            lo[k] = (unsigned int)v;
+            hi[k] = (unsigned int)(v >> 32);
+          }
         }
       }
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (lo[k] | hi[k]) old[k] = atomicAdd(accw + slot[k], lo[k]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (lo[k] | hi[k]) {
+          const unsigned int h = hi[k] + carry_of(old[k], lo[k]);
+          if (h) atomicAdd(accw + slot[k] + 1, h);
+        }
     }
   }
   __syncthreads();
@@ -589,8 +663,8 @@ k_deposit_fft_x(const void* __restrict__ pos, int64_t np, double delta, const in
   }
   __syncthreads();   // the tile is consumed; its memory now serves the exchange buffers
   RowSmem<T> sm{reinterpret_cast<cx<T>*>(smem_raw) + r * RowSmem<T>::words(M)};
-  fft_regs<T, M, -1>(v, sm, t, tw_m);
-  if constexpr (Plan<T, M>::R2 > 1) __syncthreads();
+  fft_regs<T, M, -1, RowSmem<T>, P>(v, sm, t, tw_m);
+  if constexpr (P::R2 > 1) __syncthreads();
 #pragma unroll
   for (int b = 0; b < E / RL; ++b)
 #pragma unroll

@@ -137,14 +137,12 @@ void deposit_fft_x_n(const GridArgs& g, const void* pos, bool keep, cudaStream_t
   using F = FusedCfg<T, N>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_deposit_fft_x<T, N, Quant<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)F::SMEM);
+    cudaFuncSetAttribute(k_deposit_fft_x<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
     attr = true;
   }
-  k_deposit_fft_x<T, N, Quant<T>><<<dim3(N / F::TY, N / F::TZ), F::THREADS, F::SMEM, s>>>(
-      pos, g.np, g.delta, g.row_start, g.perm, reinterpret_cast<C*>(g.spec), g.scale,
-      reinterpret_cast<const C*>(g.tw_m), reinterpret_cast<const C*>(g.tw_n),
-      keep ? reinterpret_cast<unsigned long long*>(g.g) : nullptr, g.status);
+  k_deposit_fft_x<T, N><<<dim3(N / F::TY, N / F::TZ), F::THREADS, F::SMEM, s>>>(
+      g.rec, g.row_start, reinterpret_cast<C*>(g.spec), g.scale, reinterpret_cast<const C*>(g.tw_m),
+      reinterpret_cast<const C*>(g.tw_n), keep ? reinterpret_cast<unsigned long long*>(g.g) : nullptr);
 }
 
 // Fused inverse x + interpolation + kick of size N (persistent grid).
@@ -208,7 +206,7 @@ int NUPM_FN(row_sort)(const GridArgs& g, const void* pos, cudaStream_t s) {
   k_scan_blocks<<<nb, kScanBlock, 0, s>>>(g.row_count, g.row_start, g.scan_tot, len);
   k_scan_totals<<<1, kScanBlock, 0, s>>>(g.scan_tot, nb);
   k_scan_add<<<(len + 255) / 256, 256, 0, s>>>(g.row_start, g.scan_tot, len, g.row_cursor);
-  if (g.np > 0) k_row_scatter<T><<<blocks, 256, 0, s>>>(pos, g.np, g.n, g.delta, g.row_cursor, g.perm);
+  if (g.np > 0) k_row_scatter<T><<<blocks, 256, 0, s>>>(pos, g.np, g.n, g.delta, g.row_cursor, g.perm, g.rec);
   return PM_OK;
 }
 
@@ -234,7 +232,7 @@ int NUPM_FN(fft_pass)(const GridArgs& g, int pass, cudaStream_t s) {
 int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const short* bin_of, double kf, double* partials,
                   int nblk, double* out, cudaStream_t s) {
   const int nv = lattice ? 2 : 1;
-  const size_t sh = kBinWarps * (size_t)nv * nk * sizeof(double);
+  const size_t sh = kBinWarps * (size_t)nv * nk * sizeof(double) + (lattice ? 0 : kBinWarps * (size_t)nk * sizeof(float));
   static size_t attr_l = 48 * 1024, attr_p = 48 * 1024;
   size_t& attr = lattice ? attr_l : attr_p;
   if (sh > attr) {

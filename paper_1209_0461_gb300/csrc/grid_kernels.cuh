@@ -42,21 +42,23 @@ struct Quant<double> {   // FP64 comoving positions, double[3][np]
     const double* x = reinterpret_cast<const double*>(pos);
     return Raw{{x[p], x[np + p], x[2 * np + p]}};
   }
-  __device__ static __forceinline__ bool get(const Raw& r, int n, double delta, int (&c)[3], int (&w)[3],
-                                             int* status) {
+  __device__ static __forceinline__ bool cells(const Raw& r, int n, double delta, int (&c)[3], int (&w)[3]) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double u = r.x[d] / delta;                 // same IEEE division as the definition
-      if (!(fabs(u) < 4503599627370496.0)) {           // non-finite or |u| >= 2^52
-        set_status(status, PM_ERR_RANGE);
-        return false;
-      }
+      if (!(fabs(u) < 4503599627370496.0)) return false;   // non-finite or |u| >= 2^52
       const double cf = floor(u);
       const double o = u - cf;                         // exact
       w[d] = (int)floor(o * (double)kWeightOne);
       c[d] = wrap_index((long long)cf, n);
     }
     return true;
+  }
+  __device__ static __forceinline__ bool get(const Raw& r, int n, double delta, int (&c)[3], int (&w)[3],
+                                             int* status) {
+    if (cells(r, n, delta, c, w)) return true;
+    set_status(status, PM_ERR_RANGE);
+    return false;
   }
 };
 
@@ -72,19 +74,21 @@ struct Quant<float> {    // int32 words [6][np]: cells rows 0-2, FP32 offsets ro
     for (int d = 0; d < 6; ++d) r.q[d] = q[d * np + p];
     return r;
   }
-  __device__ static __forceinline__ bool get(const Raw& r, int n, double, int (&c)[3], int (&w)[3],
-                                             int* status) {
+  __device__ static __forceinline__ bool cells(const Raw& r, int n, double, int (&c)[3], int (&w)[3]) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const float o = __int_as_float(r.q[3 + d]);
-      if (!(o >= 0.0f && o < 1.0f)) {
-        set_status(status, PM_ERR_RANGE);
-        return false;
-      }
+      if (!(o >= 0.0f && o < 1.0f)) return false;
       w[d] = (int)floorf(o * (float)kWeightOne);       // exact scaling by 2^16
       c[d] = wrap_index((long long)r.q[d], n);
     }
     return true;
+  }
+  __device__ static __forceinline__ bool get(const Raw& r, int n, double delta, int (&c)[3], int (&w)[3],
+                                             int* status) {
+    if (cells(r, n, delta, c, w)) return true;
+    set_status(status, PM_ERR_RANGE);
+    return false;
   }
 };
 
@@ -162,11 +166,17 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restri
             double kf, double* __restrict__ partials) {
   constexpr int NV = LATTICE ? 2 : 1;
   using A = typename std::conditional<LATTICE, double, T>::type;   // scan type
+  // FP32 power: per-row sums in FP32 (at most M modes a bin), added to the
+  // warp's FP64 sums once per row (GB300's FP64 pipe is narrow)
+  constexpr bool ROWF = !LATTICE && sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* all = reinterpret_cast<double*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* acc = all + warp * NV * nk;
+  float* racc = reinterpret_cast<float*>(all + kBinWarps * NV * nk) + warp * nk;
   for (int i = threadIdx.x; i < kBinWarps * NV * nk; i += blockDim.x) all[i] = 0.0;
+  if constexpr (ROWF)
+    for (int i = threadIdx.x; i < kBinWarps * nk; i += blockDim.x) racc[i - warp * nk] = 0.0f;
   __syncthreads();
   const unsigned full = 0xffffffffu;
   const int m = n / 2;
@@ -217,7 +227,10 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restri
             const T ax = (T)0.5 * (f[j].x + g.x), ay = (T)0.5 * (f[j].y - g.y);
             const T bx = (T)0.5 * (f[j].y + g.y), by = (T)-0.5 * (f[j].x - g.x);
             v0 = ax * ax + ay * ay;
-            if (bb >= 0) acc[bb] += (double)(bx * bx + by * by);
+            if (bb >= 0) {
+              if constexpr (ROWF) racc[bb] += (float)(bx * bx + by * by);
+              else acc[bb] += (double)(bx * bx + by * by);
+            }
           }
         }
         if (b < 0) v0 = v1 = 0;
@@ -235,11 +248,27 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restri
         }
         const int bn = __shfl_down_sync(full, b, 1);
         if (b >= 0 && (lane == 31 || bn != b)) {
-          acc[b] += (double)v0;
-          if constexpr (LATTICE) acc[nk + b] += (double)v1;
+          if constexpr (ROWF) {
+            racc[b] += (float)v0;
+          } else {
+            acc[b] += (double)v0;
+            if constexpr (LATTICE) acc[nk + b] += (double)v1;
+          }
         }
         __syncwarp();
       }
+    }
+    if constexpr (ROWF) {
+      // the row's modes have n^2 in [base2, base2 + m^2]: bins b_lo .. b_hi
+      // (bin_of is non-decreasing where it is >= 0; -1 ends fall back to all bins)
+      int b_lo = bin_of[base2 == 0 ? 1 : base2], b_hi = bin_of[base2 + m * m];
+      if (b_lo < 0) b_lo = 0;
+      if (b_hi < 0) b_hi = nk - 1;
+      for (int b = b_lo + lane; b <= b_hi; b += 32) {
+        acc[b] += (double)racc[b];
+        racc[b] = 0.0f;
+      }
+      __syncwarp();
     }
   }
   __syncthreads();

@@ -76,7 +76,8 @@ struct GridArgs {
   int* row_start;                  // [N^2 + 1] exclusive prefix of row_count
   int* row_cursor;                 // [N^2 + 1]
   int* scan_tot;                   // [2 * 1024] block totals of the scan
-  int* perm;                       // [npart] particle indices sorted by row
+  int* perm;                       // [npart] particle indices sorted by row (fused gather only, else null)
+  unsigned long long* rec;         // [npart] packed particle records sorted by row
   const CUtensorMap* tmap_spec_y;  // TMA maps of the column passes (nullptr: plain kernels)
   const CUtensorMap* tmap_spec_z;
   const CUtensorMap* tmap_g_y;

@@ -58,6 +58,7 @@ struct pm_ctx {
   int* d_rowcur = nullptr;
   int* d_scantot = nullptr;
   int* d_perm = nullptr;
+  unsigned long long* d_rec = nullptr;
   // TMA tensor maps of the column passes (spectrum along y / z, fields along y)
   bool tma = false;
   alignas(64) CUtensorMap tm_spec_y, tm_spec_z, tm_g_y;
@@ -353,6 +354,7 @@ GridArgs grid_args(const pm_ctx* c) {
   g.row_cursor = c->d_rowcur;
   g.scan_tot = c->d_scantot;
   g.perm = c->d_perm;
+  g.rec = c->d_rec;
   g.tmap_spec_y = c->tma ? &c->tm_spec_y : nullptr;
   g.tmap_spec_z = c->tma ? &c->tm_spec_z : nullptr;
   g.tmap_g_y = c->tma ? &c->tm_g_y : nullptr;
@@ -367,7 +369,7 @@ void release(pm_ctx* c) {
   void* ptrs[] = {c->spec, c->g, c->tw_n, c->tw_m, c->d_binof, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
                   c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_rlist, c->d_gtab,
                   c->d_dtab, c->d_wtab, c->d_plane0, c->d_fac, c->d_rowc, c->d_rows, c->d_rowcur,
-                  c->d_scantot, c->d_perm, c->d_status};
+                  c->d_scantot, c->d_perm, c->d_rec, c->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_hist_u) cudaFreeHost(c->h_hist_u);
@@ -546,7 +548,9 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rows, nrow1 * sizeof(int), "row starts");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rowcur, nrow1 * sizeof(int), "row cursors");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_scantot, 2048 * sizeof(int), "scan totals");
-  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_perm, (size_t)c->np * sizeof(int), "row permutation");
+  if (rc == PM_OK && (p.flags & PM_FUSED_GATHER))
+    rc = dalloc(c, (void**)&c->d_perm, (size_t)c->np * sizeof(int), "row permutation");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rec, (size_t)c->np * sizeof(unsigned long long), "sorted records");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_status, sizeof(int), "status");
   if (rc == PM_OK && cudaMallocHost((void**)&c->h_hist_u, (size_t)(p.n_hist_max + 1) * sizeof(double)) != cudaSuccess)
     rc = fail(c, PM_ERR_ALLOC, "pinned host allocation failed");

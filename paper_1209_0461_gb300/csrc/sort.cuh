@@ -1,12 +1,12 @@
 // Counting sort of the particles by grid row (cz, cy): row key r = cz N + cy.
 // The fused deposit/x-transform kernel reads, for its tile of rows, exactly
-// the particles that touch it.  Only the permutation is stored (perm[i] =
-// particle index); the order inside a row follows atomic arrival and does
-// not affect any result (integer deposit sums, per-particle interpolation).
+// the particles that touch it, as packed 8-byte records (cells and weights,
+// quantised once here).  The order inside a row follows atomic arrival and
+// does not affect any result (integer deposit sums, per-particle gathers).
 //
 //   k_row_count   warp-aggregated histogram of the keys
 //   k_scan_*      exclusive scan of the N^2 counts -> row_start
-//   k_row_scatter warp-aggregated cursors -> perm
+//   k_row_scatter warp-aggregated cursors -> records (and the permutation)
 #pragma once
 #include <stdint.h>
 
@@ -14,7 +14,8 @@
 
 namespace nupm {
 
-// Row key of particle p (-1 for an invalid particle; recorded by the deposit).
+// Row key of particle p (-1 for an invalid particle; recorded by the count).
+// Valid exactly when Quant<T>::cells accepts the particle, with the same cells.
 template <typename T>
 struct RowKey;
 
@@ -23,8 +24,9 @@ struct RowKey<float> {
   __device__ static __forceinline__ int get(const void* pos, int64_t np, int64_t p, int n, double) {
     const int32_t* q = reinterpret_cast<const int32_t*>(pos);
     const int cy = q[np + p] & (n - 1), cz = q[2 * np + p] & (n - 1);
+    const float ox = __int_as_float(q[3 * np + p]);
     const float oy = __int_as_float(q[4 * np + p]), oz = __int_as_float(q[5 * np + p]);
-    if (!(oy >= 0.0f && oy < 1.0f && oz >= 0.0f && oz < 1.0f)) return -1;
+    if (!(ox >= 0.0f && ox < 1.0f && oy >= 0.0f && oy < 1.0f && oz >= 0.0f && oz < 1.0f)) return -1;
     return cz * n + cy;
   }
 };
@@ -33,12 +35,22 @@ template <>
 struct RowKey<double> {
   __device__ static __forceinline__ int get(const void* pos, int64_t np, int64_t p, int n, double delta) {
     const double* x = reinterpret_cast<const double*>(pos);
-    const double uy = x[np + p] / delta, uz = x[2 * np + p] / delta;
-    if (!(fabs(uy) < 4503599627370496.0 && fabs(uz) < 4503599627370496.0)) return -1;
+    const double ux = x[p] / delta, uy = x[np + p] / delta, uz = x[2 * np + p] / delta;
+    if (!(fabs(ux) < 4503599627370496.0 && fabs(uy) < 4503599627370496.0 && fabs(uz) < 4503599627370496.0))
+      return -1;
     const int cy = wrap_index((long long)floor(uy), n), cz = wrap_index((long long)floor(uz), n);
     return cz * n + cy;
   }
 };
+
+// Sorted particle record, 8 bytes: bits 0-47 the 16-bit CIC weights of x, y
+// and z, bits 48-58 the x cell (N <= 2048), bits 59-63 the y cell mod 32.
+// The z cell and the rest of the y cell follow from the record's row.
+__device__ __forceinline__ unsigned long long pack_record(const int (&c)[3], const int (&w)[3]) {
+  return (unsigned long long)(unsigned)w[0] | ((unsigned long long)(unsigned)w[1] << 16) |
+         ((unsigned long long)(unsigned)w[2] << 32) | ((unsigned long long)(unsigned)c[0] << 48) |
+         ((unsigned long long)(unsigned)(c[1] & 31) << 59);
+}
 
 template <typename T>
 __global__ void k_row_count(const void* __restrict__ pos, int64_t np, int n, double delta,
@@ -57,21 +69,33 @@ __global__ void k_row_count(const void* __restrict__ pos, int64_t np, int n, dou
   }
 }
 
+// Place each valid particle at its row's cursor: the packed record (and, when
+// perm is given, the particle index) at the same sorted slot.
 template <typename T>
 __global__ void k_row_scatter(const void* __restrict__ pos, int64_t np, int n, double delta,
-                              int* __restrict__ cursor, int* __restrict__ perm) {
+                              int* __restrict__ cursor, int* __restrict__ perm,
+                              unsigned long long* __restrict__ rec) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
     const int64_t p = base + lane;
-    const int key = p < np ? RowKey<T>::get(pos, np, p, n, delta) : -2;
+    int c[3] = {0, 0, 0}, w[3] = {0, 0, 0};
+    int key = -2;
+    if (p < np) {
+      const typename Quant<T>::Raw raw = Quant<T>::load(pos, np, p);
+      key = Quant<T>::cells(raw, n, delta, c, w) ? c[2] * n + c[1] : -1;
+    }
     const unsigned peers = __match_any_sync(full, key);
     const int leader = __ffs(peers) - 1;
     int start = 0;
     if (key >= 0 && lane == leader) start = atomicAdd(cursor + key, __popc(peers));
     start = __shfl_sync(full, start, leader);
-    if (key >= 0) perm[start + __popc(peers & ((1u << lane) - 1))] = (int)p;
+    if (key >= 0) {
+      const int slot = start + __popc(peers & ((1u << lane) - 1));
+      rec[slot] = pack_record(c, w);
+      if (perm) perm[slot] = (int)p;
+    }
   }
 }
 
