@@ -224,20 +224,30 @@ struct RowSmem {
 };
 
 // Column tile width (consecutive x2 columns per CTA) and pad per plan.
-template <typename T, int N>
-struct ColCfg {
+template <typename T, int N, int WREQ, class PL = Plan<T, N>>
+struct ColCfgW {
+  using P = PL;
   static constexpr int M = N / 2;
-  static constexpr int W0 = sizeof(T) == 4 ? 8 : 4;     // >= 64 B per row segment
-  static constexpr int NT = N / Plan<T, N>::R1;
+  static constexpr int E = P::R1;
+  static constexpr int NT = N / E;
   // widen small transforms so a CTA has >= 128 threads, never past M columns
-  static constexpr int Wt = (W0 * NT < 128) ? (128 / NT) : W0;
+  static constexpr int Wt = (WREQ * NT < 128) ? (128 / NT) : WREQ;
   static constexpr int W = Wt > M ? M : Wt;
   static constexpr int THREADS = W * NT;
   static constexpr int PAD = sizeof(T) == 4 ? 8 : 4;
   static constexpr int SMEM_WORDS = ColSmem<T, W, PAD>::words(N);
-  // at least two resident CTAs per SM so one CTA's loads overlap another's math
-  static constexpr int MIN_BLOCKS = 2;
+  // two resident CTAs per SM where the exchange buffer allows it, so one
+  // CTA's loads overlap another's math
+  static constexpr int MIN_BLOCKS = (size_t)SMEM_WORDS * sizeof(cx<T>) <= 100 * 1024 ? 2 : 1;
 };
+// y passes: 64-byte row segments (>= 8 FP32 / 4 FP64 columns per tile)
+template <typename T, int N>
+struct ColCfg : ColCfgW<T, N, sizeof(T) == 4 ? 8 : 4> {};
+// z passes: a z step is an N*M-element stride, and 64-byte segments there
+// halve the achieved read bandwidth (measured on GB300); 128-byte segments
+// from N >= 256 on.
+template <typename T, int N>
+struct ColCfgZ : ColCfgW<T, N, (N >= 256 ? 2 : 1) * (sizeof(T) == 4 ? 8 : 4)> {};
 
 // Rows per CTA of the x pass.
 template <typename T, int N>
@@ -254,12 +264,12 @@ struct RowCfg {
 //   data + field * field_stride + blockIdx.y * other_stride + x2 + e * elem_stride
 // grid = (M / W, N, nfields)
 // ---------------------------------------------------------------------------
-template <typename T, int N, int DIR>
-__global__ void __launch_bounds__(ColCfg<T, N>::THREADS, ColCfg<T, N>::MIN_BLOCKS)
+template <typename T, int N, int DIR, class Cfg = ColCfg<T, N>>
+__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MIN_BLOCKS)
 k_fft_col(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
           int64_t field_stride, const cx<T>* __restrict__ tw) {
-  using Cfg = ColCfg<T, N>;
-  constexpr int E = Plan<T, N>::R1, NT = N / E, W = Cfg::W, RL = last_radix<T, N>();
+  using P = typename Cfg::P;
+  constexpr int E = Cfg::E, NT = Cfg::NT, W = Cfg::W, RL = last_radix<T, N, P>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x % W;
   const int t = threadIdx.x / W;
@@ -269,7 +279,7 @@ k_fft_col(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
   cx<T> v[E];
 #pragma unroll
   for (int i = 0; i < E; ++i) v[i] = col[(int64_t)(t + NT * i) * elem_stride];
-  fft_regs<T, N, DIR>(v, sm, t, tw);
+  fft_regs<T, N, DIR, ColSmem<T, W, Cfg::PAD>, P>(v, sm, t, tw);
 #pragma unroll
   for (int b = 0; b < E / RL; ++b)
 #pragma unroll
@@ -286,14 +296,14 @@ k_fft_col(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
 // (A + i B of the kx = 0 / N/2 planes, whose G differ) comes pre-multiplied
 // from plane0[ky][kz] (k_green_plane0).  grid = (M / W, N)
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(ColCfg<T, N>::THREADS, ColCfg<T, N>::MIN_BLOCKS)
+template <typename T, int N, class Cfg = ColCfgZ<T, N>>
+__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MIN_BLOCKS)
 k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, cx<T>* __restrict__ out_dz,
                   const cx<T>* __restrict__ plane0, const T* __restrict__ gtab, const T* __restrict__ dtab,
                   const T* __restrict__ wtab, const cx<T>* __restrict__ tw, const float* __restrict__ fac,
                   float fac_inv_du, float coeff) {
-  using Cfg = ColCfg<T, N>;
-  constexpr int M = N / 2, E = Plan<T, N>::R1, NT = N / E, W = Cfg::W, RL = last_radix<T, N>();
+  using P = typename Cfg::P;
+  constexpr int M = N / 2, E = Cfg::E, NT = Cfg::NT, W = Cfg::W, RL = last_radix<T, N, P>();
   constexpr int64_t ES = (int64_t)N * M;   // element stride along z
   constexpr bool kFac = sizeof(T) == 4;    // FP32: G from the fac table, no n^2 gathers
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -352,7 +362,7 @@ k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, c
       }
       v[i] = f;
     }
-    fft_regs<T, N, +1>(v, sm, t, tw);
+    fft_regs<T, N, +1, ColSmem<T, W, Cfg::PAD>, P>(v, sm, t, tw);
     cx<T>* dst = pass == 0 ? out_phi : out_dz;
 #pragma unroll
     for (int b = 0; b < E / RL; ++b)

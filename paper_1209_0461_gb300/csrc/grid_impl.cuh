@@ -20,9 +20,9 @@ constexpr int kSMs = 152;
 // the per-thread Green factors.
 template <int N>
 constexpr size_t green_smem() {
-  using CC = ColCfg<T, N>;
+  using CC = ColCfgZ<T, N>;
   return (size_t)CC::SMEM_WORDS * sizeof(C) + (sizeof(T) == 4 ? kFacTable * sizeof(float) : 0) +
-         (size_t)Plan<T, N>::R1 * CC::THREADS * sizeof(T);
+         (size_t)CC::E * CC::THREADS * sizeof(T);
 }
 
 // Opt the FFT kernels of size N into their dynamic shared memory (once per
@@ -37,6 +37,8 @@ void ensure_attrs() {
   const int col_smem = (int)((size_t)CC::SMEM_WORDS * sizeof(C));
   cudaFuncSetAttribute(k_fft_x_fwd<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
   cudaFuncSetAttribute(k_fft_col<T, N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+  cudaFuncSetAttribute(k_fft_col<T, N, -1, ColCfgZ<T, N>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)((size_t)ColCfgZ<T, N>::SMEM_WORDS * sizeof(C)));
   cudaFuncSetAttribute(k_fft_x_inv<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
   cudaFuncSetAttribute(k_fft_z_inv_green<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)green_smem<N>());
@@ -104,13 +106,16 @@ void fft_pass_n(const GridArgs& g, int pass, cudaStream_t s) {
     case kPassYFwd:
       k_fft_col<T, N, -1><<<dim3(M / CC::W, N, 1), CC::THREADS, col_smem, s>>>(spec, (int64_t)N * M, (int64_t)M, 0, twn);
       break;
-    case kPassZFwd:
-      k_fft_col<T, N, -1><<<dim3(M / CC::W, N, 1), CC::THREADS, col_smem, s>>>(spec, (int64_t)M, (int64_t)N * M, 0, twn);
+    case kPassZFwd: {
+      using CZ = ColCfgZ<T, N>;
+      k_fft_col<T, N, -1, CZ><<<dim3(M / CZ::W, N, 1), CZ::THREADS, (size_t)CZ::SMEM_WORDS * sizeof(C), s>>>(
+          spec, (int64_t)M, (int64_t)N * M, 0, twn);
       break;
+    }
     case kPassZInv: {
       // Green + z: spectrum -> g0 (phi), g2 (d/dz phi)
       const int64_t fe = g.field_elems;
-      k_fft_z_inv_green<T, N><<<dim3(M / CC::W, N, 1), CC::THREADS, green_smem<N>(), s>>>(
+      k_fft_z_inv_green<T, N><<<dim3(M / ColCfgZ<T, N>::W, N, 1), ColCfgZ<T, N>::THREADS, green_smem<N>(), s>>>(
           spec, f, f + 2 * fe, reinterpret_cast<const C*>(g.plane0), reinterpret_cast<const T*>(g.gtab),
           reinterpret_cast<const T*>(g.dtab), reinterpret_cast<const T*>(g.wtab), twn, g.fac, g.fac_inv_du,
           g.green_coeff);
@@ -229,10 +234,11 @@ int NUPM_FN(fft_pass)(const GridArgs& g, int pass, cudaStream_t s) {
   return PM_OK;
 }
 
-int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const short* bin_of, double kf, double* partials,
-                  int nblk, double* out, cudaStream_t s) {
+int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const short* bin_of, const int* thr, float bin_c,
+                  double kf, double* partials, int nblk, double* out, cudaStream_t s) {
   const int nv = lattice ? 2 : 1;
-  const size_t sh = kBinWarps * (size_t)nv * nk * sizeof(double) + (lattice ? 0 : kBinWarps * (size_t)nk * sizeof(float));
+  const size_t sh = kBinWarps * (size_t)nv * nk * sizeof(double) +
+                    (lattice ? 0 : kBinWarps * (size_t)nk * sizeof(float) + (size_t)(nk + 1) * sizeof(int));
   static size_t attr_l = 48 * 1024, attr_p = 48 * 1024;
   size_t& attr = lattice ? attr_l : attr_p;
   if (sh > attr) {
@@ -241,8 +247,8 @@ int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const short* bin_of, 
     attr = sh;
   }
   const C* spec = reinterpret_cast<const C*>(g.spec);
-  if (lattice) k_bin_power<T, true><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, bin_of, kf, partials);
-  else k_bin_power<T, false><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, bin_of, kf, partials);
+  if (lattice) k_bin_power<T, true><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, bin_of, thr, bin_c, kf, partials);
+  else k_bin_power<T, false><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, bin_of, thr, bin_c, kf, partials);
   k_bin_reduce<<<(nv * nk + 127) / 128, 128, 0, s>>>(partials, nblk, nv * nk, out);
   return PM_OK;
 }

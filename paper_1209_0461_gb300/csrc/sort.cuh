@@ -52,20 +52,31 @@ __device__ __forceinline__ unsigned long long pack_record(const int (&c)[3], con
          ((unsigned long long)(unsigned)(c[1] & 31) << 59);
 }
 
+// Each warp takes kSortBatch x 32 consecutive particles per step (all their
+// loads in flight first); the match below sees every lane of the warp.
+constexpr int kSortBatch = 4;
+
 template <typename T>
 __global__ void k_row_count(const void* __restrict__ pos, int64_t np, int n, double delta,
                             int* __restrict__ count, int* status) {
+  constexpr int U = kSortBatch;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  // whole warps iterate together so the match below sees every lane
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
-    const int64_t p = base + lane;
-    const int key = p < np ? RowKey<T>::get(pos, np, p, n, delta) : -2;
-    const unsigned peers = __match_any_sync(full, key);
-    const int leader = __ffs(peers) - 1;
-    if (key >= 0 && lane == leader) atomicAdd(count + key, __popc(peers));
-    if (key == -1) set_status(status, PM_ERR_RANGE);   // skipped by every later stage
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * U;
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U; base < np; base += stride) {
+    int key[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = base + u * 32 + lane;
+      key[u] = p < np ? RowKey<T>::get(pos, np, p, n, delta) : -2;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const unsigned peers = __match_any_sync(full, key[u]);
+      const int leader = __ffs(peers) - 1;
+      if (key[u] >= 0 && lane == leader) atomicAdd(count + key[u], __popc(peers));
+      if (key[u] == -1) set_status(status, PM_ERR_RANGE);   // skipped by every later stage
+    }
   }
 }
 
@@ -75,26 +86,33 @@ template <typename T>
 __global__ void k_row_scatter(const void* __restrict__ pos, int64_t np, int n, double delta,
                               int* __restrict__ cursor, int* __restrict__ perm,
                               unsigned long long* __restrict__ rec) {
+  constexpr int U = kSortBatch;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
-    const int64_t p = base + lane;
-    int c[3] = {0, 0, 0}, w[3] = {0, 0, 0};
-    int key = -2;
-    if (p < np) {
-      const typename Quant<T>::Raw raw = Quant<T>::load(pos, np, p);
-      key = Quant<T>::cells(raw, n, delta, c, w) ? c[2] * n + c[1] : -1;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * U;
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U; base < np; base += stride) {
+    typename Quant<T>::Raw raw[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = base + u * 32 + lane;
+      if (p < np) raw[u] = Quant<T>::load(pos, np, p);
     }
-    const unsigned peers = __match_any_sync(full, key);
-    const int leader = __ffs(peers) - 1;
-    int start = 0;
-    if (key >= 0 && lane == leader) start = atomicAdd(cursor + key, __popc(peers));
-    start = __shfl_sync(full, start, leader);
-    if (key >= 0) {
-      const int slot = start + __popc(peers & ((1u << lane) - 1));
-      rec[slot] = pack_record(c, w);
-      if (perm) perm[slot] = (int)p;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = base + u * 32 + lane;
+      int c[3] = {0, 0, 0}, w[3] = {0, 0, 0};
+      int key = -2;
+      if (p < np) key = Quant<T>::cells(raw[u], n, delta, c, w) ? c[2] * n + c[1] : -1;
+      const unsigned peers = __match_any_sync(full, key);
+      const int leader = __ffs(peers) - 1;
+      int start = 0;
+      if (key >= 0 && lane == leader) start = atomicAdd(cursor + key, __popc(peers));
+      start = __shfl_sync(full, start, leader);
+      if (key >= 0) {
+        const int slot = start + __popc(peers & ((1u << lane) - 1));
+        rec[slot] = pack_record(c, w);
+        if (perm) perm[slot] = (int)p;
+      }
     }
   }
 }
