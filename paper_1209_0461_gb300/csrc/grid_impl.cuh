@@ -234,11 +234,10 @@ int NUPM_FN(fft_pass)(const GridArgs& g, int pass, cudaStream_t s) {
   return PM_OK;
 }
 
-int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const short* bin_of, const int* thr, float bin_c,
-                  double kf, double* partials, int nblk, double* out, cudaStream_t s) {
+int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const short* bin_of, double kf, double* partials,
+                  int nblk, double* out, cudaStream_t s) {
   const int nv = lattice ? 2 : 1;
-  const size_t sh = kBinWarps * (size_t)nv * nk * sizeof(double) +
-                    (lattice ? 0 : kBinWarps * (size_t)nk * sizeof(float) + (size_t)(nk + 1) * sizeof(int));
+  const size_t sh = kBinWarps * (size_t)nv * nk * sizeof(double) + (lattice ? 0 : kBinWarps * (size_t)nk * sizeof(float));
   static size_t attr_l = 48 * 1024, attr_p = 48 * 1024;
   size_t& attr = lattice ? attr_l : attr_p;
   if (sh > attr) {
@@ -247,8 +246,8 @@ int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const short* bin_of, 
     attr = sh;
   }
   const C* spec = reinterpret_cast<const C*>(g.spec);
-  if (lattice) k_bin_power<T, true><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, bin_of, thr, bin_c, kf, partials);
-  else k_bin_power<T, false><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, bin_of, thr, bin_c, kf, partials);
+  if (lattice) k_bin_power<T, true><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, bin_of, kf, partials);
+  else k_bin_power<T, false><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, bin_of, kf, partials);
   k_bin_reduce<<<(nv * nk + 127) / 128, 128, 0, s>>>(partials, nblk, nv * nk, out);
   return PM_OK;
 }

@@ -148,36 +148,22 @@ __device__ __forceinline__ int signed_freq(int i, int n) { return i < n / 2 ? i 
 // segmented shuffle scan sums each segment and its last lane adds the sum to
 // the warp's private accumulator (one writer per bin, no atomics).  Warps and
 // CTAs are then summed in a fixed order (k_bin_reduce).  The bin of each n^2
-// comes from a lookup table (bin_of[n2], -1 outside the bins) for the
-// lattice sums; the power sums compute it from the thresholds T_b in shared
-// memory (a log estimate, corrected by exact integer comparisons), which
-// spares the L2 the table's scattered lines.
+// comes from a lookup table (bin_of[n2], -1 outside the bins).
 //   LATTICE = true : accumulate the mode count sum w and sum w |k| (depends on
 //                    the lattice only; run once per context)
 //   LATTICE = false: accumulate sum w |delta_k|^2; per-mode arithmetic in the
 //                    grid precision T, one FP64 add per segment
 // The packed slot x2 = 0 is unpacked with the row at (-z, -y):
 //   A = (F(k) + conj F(-k)) / 2   (kx = 0),  B = (F(k) - conj F(-k)) / (2i)  (kx = N/2).
-// Shared memory: [kBinWarps][NV][nk] doubles (NV = 2 lattice sums or 1),
-// then (power) [kBinWarps][nk] FP32 row sums and the nk + 1 thresholds.
+// Shared memory: [kBinWarps][NV][nk] doubles (NV = 2 lattice sums or 1).
 // ---------------------------------------------------------------------------
 constexpr int kBinWarps = 4;
-
-// Bin b with T_b <= n2 < T_{b+1} (-1 outside [T_0, T_nk)).  T_b = ceil(r^(2b/nk))
-// gives b ~ c ln n2 with c = nk / (2 ln r); the loops fix the estimate exactly.
-__device__ __forceinline__ int bin_from_thresholds(int n2, const int* thr, int nk, float c) {
-  int b = (int)(__logf((float)max(n2, 1)) * c);
-  b = min(max(b, 0), nk - 1);
-  while (b > 0 && n2 < thr[b]) --b;
-  while (b < nk - 1 && n2 >= thr[b + 1]) ++b;
-  return (n2 >= thr[0] && n2 < thr[nk]) ? b : -1;
-}
 constexpr int kBinBatch = 8;   // chunks loaded per batch (bytes in flight)
 
 template <typename T, bool LATTICE>
 __global__ void __launch_bounds__(kBinWarps * 32)
 k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restrict__ bin_of,
-            const int* __restrict__ thr, float bin_c, double kf, double* __restrict__ partials) {
+            double kf, double* __restrict__ partials) {
   constexpr int NV = LATTICE ? 2 : 1;
   using A = typename std::conditional<LATTICE, double, T>::type;   // scan type
   // FP32 power: per-row sums in FP32 (at most M modes a bin), added to the
@@ -188,17 +174,10 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restri
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* acc = all + warp * NV * nk;
   float* racc = reinterpret_cast<float*>(all + kBinWarps * NV * nk) + warp * nk;
-  int* thr_s = reinterpret_cast<int*>(reinterpret_cast<float*>(all + kBinWarps * NV * nk) + kBinWarps * nk);
   for (int i = threadIdx.x; i < kBinWarps * NV * nk; i += blockDim.x) all[i] = 0.0;
-  if constexpr (!LATTICE) {
+  if constexpr (ROWF)
     for (int i = threadIdx.x; i < kBinWarps * nk; i += blockDim.x) racc[i - warp * nk] = 0.0f;
-    for (int i = threadIdx.x; i <= nk; i += blockDim.x) thr_s[i] = thr[i];
-  }
   __syncthreads();
-  auto bin_of_n2 = [&](int n2) -> int {
-    if constexpr (LATTICE) return bin_of[n2];
-    else return bin_from_thresholds(n2, thr_s, nk, bin_c);
-  };
   const unsigned full = 0xffffffffu;
   const int m = n / 2;
   const int rows = n * n;
@@ -224,7 +203,7 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restri
         int b = -1;
         if (x2 > 0 && x2 < m) {
           const int n2 = base2 + x2 * x2;
-          b = bin_of_n2(n2);
+          b = bin_of[n2];
           if constexpr (LATTICE) {
             v0 = 2.0;
             v1 = 2.0 * kf * sqrt((double)n2);
@@ -233,8 +212,8 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restri
           }
         } else if (x2 == 0) {
           const int n2b = base2 + m * m;                 // kx = N/2 mode: added directly
-          const int bb = bin_of_n2(n2b);
-          b = bin_of_n2(base2);                          // kx = 0 mode joins the scan
+          const int bb = bin_of[n2b];
+          b = bin_of[base2];                             // kx = 0 mode joins the scan
           if constexpr (LATTICE) {
             v0 = 1.0;
             v1 = kf * sqrt((double)base2);
@@ -282,7 +261,7 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restri
     if constexpr (ROWF) {
       // the row's modes have n^2 in [base2, base2 + m^2]: bins b_lo .. b_hi
       // (bin_of is non-decreasing where it is >= 0; -1 ends fall back to all bins)
-      int b_lo = bin_of_n2(base2 == 0 ? 1 : base2), b_hi = bin_of_n2(base2 + m * m);
+      int b_lo = bin_of[base2 == 0 ? 1 : base2], b_hi = bin_of[base2 + m * m];
       if (b_lo < 0) b_lo = 0;
       if (b_hi < 0) b_hi = nk - 1;
       for (int b = b_lo + lane; b <= b_hi; b += 32) {

@@ -91,9 +91,8 @@ struct GridArgs {
   int row_sort##SFX(const GridArgs& g, const void* pos, cudaStream_t s);                    \
   int deposit_fft_x##SFX(const GridArgs& g, const void* pos, bool keep, cudaStream_t s);    \
   int fft_pass##SFX(const GridArgs& g, int pass, cudaStream_t s);                           \
-  int bins##SFX(const GridArgs& g, bool lattice, int nk, const short* bin_of, const int* thr, \
-                float bin_c, double kf, double* partials, int nblk, double* out,            \
-                cudaStream_t s);                                                            \
+  int bins##SFX(const GridArgs& g, bool lattice, int nk, const short* bin_of, double kf,      \
+                double* partials, int nblk, double* out, cudaStream_t s);                   \
   int green##SFX(const GridArgs& g, cudaStream_t s);                                        \
   int interp##SFX(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, \
                   cudaStream_t s);                                                          \

@@ -73,8 +73,6 @@ struct pm_ctx {
   double a_response = 0;
   int64_t bytes = 0;
   std::vector<long long> thr;
-  int* d_thr = nullptr;       // [nk + 1] thresholds T_b as int (power bins)
-  float bin_c = 0.0f;         // nk / (2 ln r): bin estimate from ln n^2
   std::string err;
   // per-stage timing: pending (stage, start, stop) event triples
   bool timing = false;
@@ -371,7 +369,7 @@ void release(pm_ctx* c) {
   void* ptrs[] = {c->spec, c->g, c->tw_n, c->tw_m, c->d_binof, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
                   c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_rlist, c->d_gtab,
                   c->d_dtab, c->d_wtab, c->d_plane0, c->d_fac, c->d_rowc, c->d_rows, c->d_rowcur,
-                  c->d_scantot, c->d_perm, c->d_rec, c->d_thr, c->d_status};
+                  c->d_scantot, c->d_perm, c->d_rec, c->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_hist_u) cudaFreeHost(c->h_hist_u);
@@ -529,7 +527,6 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) rc = dalloc(c, &c->tw_n, (size_t)n * c->cplx, "twiddles N");
   if (rc == PM_OK) rc = dalloc(c, &c->tw_m, (size_t)(n / 2) * c->cplx, "twiddles M");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_binof, (size_t)(c->n2max + 1) * sizeof(short), "bin table");
-  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_thr, (size_t)(c->nk + 1) * sizeof(int), "bin thresholds");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_partials, (size_t)c->nblk_bins * 2 * c->nk * sizeof(double), "bin partials");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_bins, 3 * (size_t)c->nk * sizeof(double), "bins");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_pi, (size_t)nspec * c->nk * sizeof(double), "nu ICs");
@@ -574,11 +571,6 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
     }
     rc = cuda_check(c, cudaMemcpy(c->d_binof, bo.data(), bo.size() * sizeof(short), cudaMemcpyHostToDevice),
                     "bin table upload");
-    std::vector<int> ti(c->thr.begin(), c->thr.end());
-    c->bin_c = (float)(c->nk / (2.0 * log(r)));
-    if (rc == PM_OK)
-      rc = cuda_check(c, cudaMemcpy(c->d_thr, ti.data(), ti.size() * sizeof(int), cudaMemcpyHostToDevice),
-                      "threshold upload");
   }
   if (rc == PM_OK) {
     std::vector<double> gl(2 * kMaxQuad, 0.0);
@@ -613,10 +605,8 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) {
     // mode counts and sum |k| per bin depend on the lattice only: once per context
     GridArgs g = grid_args(c);
-    rc = c->fp64 ? bins_f64(g, true, c->nk, c->d_binof, c->d_thr, c->bin_c, c->kf, c->d_partials, c->nblk_bins,
-                            c->d_bins, 0)
-                 : bins_f32(g, true, c->nk, c->d_binof, c->d_thr, c->bin_c, c->kf, c->d_partials, c->nblk_bins,
-                            c->d_bins, 0);
+    rc = c->fp64 ? bins_f64(g, true, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins, 0)
+                 : bins_f32(g, true, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins, 0);
     if (rc == PM_OK) rc = cuda_check(c, cudaGetLastError(), "lattice bins");
   }
   if (rc == PM_OK) rc = cuda_check(c, cudaMemset(c->d_status, 0, sizeof(int)), "status init");
@@ -665,10 +655,10 @@ int pm_deposit(pm_ctx* c, const void* pos) {
   }
   if (rc == PM_OK) {
     Stage st(c, PM_ST_BINS, 2);
-    rc = c->fp64 ? bins_f64(g, false, c->nk, c->d_binof, c->d_thr, c->bin_c, c->kf, c->d_partials, c->nblk_bins,
-                            c->d_bins + 2 * c->nk, c->stream)
-                 : bins_f32(g, false, c->nk, c->d_binof, c->d_thr, c->bin_c, c->kf, c->d_partials, c->nblk_bins,
-                            c->d_bins + 2 * c->nk, c->stream);
+    rc = c->fp64 ? bins_f64(g, false, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins + 2 * c->nk,
+                            c->stream)
+                 : bins_f32(g, false, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins + 2 * c->nk,
+                            c->stream);
   }
   if (rc != PM_OK) return fail(c, rc, "pm_deposit: unsupported grid");
   rc = cuda_check(c, cudaGetLastError(), "pm_deposit launch");
