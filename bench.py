@@ -305,6 +305,115 @@ def run_gpu(args, w, rank, world):
     return res
 
 
+# ------------------------------------------------------------------ other forms
+def _kick_form(w, pos64, vel64, precision, steps, warmup, mlp=None, keep_acc=True):
+    """Time `steps` kicks of workload w (inputs resident) in the given
+    precision, exact or surrogate response.  Returns (ms per kick, response
+    ms per kick, acc [3, Np] on the device or None)."""
+    import torch
+    from paper_1209_0461_gb300 import nupm
+    dev = torch.device("cuda")
+    a_hist, hist = synth.history(w)
+    pi, ti = synth.nu_initial(w)
+    if precision == "fp32":
+        pos = torch.from_numpy(synth.to_cell_offset(pos64, w.box, w.ngrid)).to(dev)
+        vel = torch.from_numpy(vel64.astype(np.float32)).to(dev)
+    else:
+        pos = torch.from_numpy(pos64).to(dev)
+        vel = torch.from_numpy(vel64).to(dev)
+    hist_d = torch.from_numpy(np.ascontiguousarray(hist)).to(dev)
+    pm = nupm.PM(w.ngrid, w.npart, w.box, w.omega_cdm, w.omega_nu, w.h, w.m_nu_total, w.n_species,
+                 a_init=w.a_init, n_kbins=w.n_kbins, n_hist_max=w.n_hist, precision=precision,
+                 sqrtPnu_init=pi, theta_over_delta_init=ti)
+    a = w.a_kick
+    K = pm.kick_factor(a, a * 1.01)
+    acc = torch.empty_like(vel) if keep_acc else None
+
+    def step(out=None):
+        pm.deposit(pos)
+        if mlp is None:
+            pm.nu_response(a, a_hist, hist_d)
+        else:
+            pm.nu_response_mlp(mlp, a, a_hist, hist_d)
+        pm.kick(pos, vel, a, K, acc_out=out)
+
+    for _ in range(warmup):
+        step(acc)
+    torch.cuda.synchronize()
+    pm.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    st = pm.get_timing()
+    pm.timing(False)
+    pm.check()
+    ms = e0.elapsed_time(e1) / steps
+    pm.close()
+    del pos, vel, hist_d
+    return ms, st["response"][0] / steps, acc
+
+
+def _rms_rel(acc, ref):
+    """RMS over particles of |a - a_ref| / RMS |a_ref| (measurement only)."""
+    d = (acc.double() - ref.double()).pow(2).sum(0).mean().sqrt()
+    return float((d / ref.double().pow(2).sum(0).mean().sqrt()).item())
+
+
+def run_forms(steps=3, warmup=1):
+    """The FP64 kick against the FP32 (precision) form on the 1024^3 workload,
+    and the surrogate form on 512^3 particles / 512^3 grid, each with its force
+    accuracy against the plain FP64 GPU kick on the same particles."""
+    import torch
+    from paper_1209_0461_gb300 import nupm, surrogate
+    out = {}
+    # precision form vs plain FP64
+    w = synth.WORKLOADS["pm1024_p512_fp32"]
+    parts = synth.particles(w)
+    ms64, r64, acc64 = _kick_form(synth.with_(w, precision="fp64"), parts["pos64"], parts["vel"], "fp64",
+                                  steps, warmup)
+    ms32, r32, acc32 = _kick_form(w, parts["pos64"], parts["vel"], "fp32", steps, warmup)
+    out["fp64_vs_fp32"] = {"workload": w.name, "fp64_ms_per_kick": round(ms64, 3),
+                           "fp32_ms_per_kick": round(ms32, 3), "speedup": round(ms64 / ms32, 2),
+                           "fp32_force_rms_rel_vs_fp64": _rms_rel(acc32, acc64)}
+    del acc64, acc32, parts
+    torch.cuda.empty_cache()
+    # surrogate form
+    w = synth.WORKLOADS["pm512_p512_fp32"]
+    t0 = time.time()
+    X, y, _, _ = surrogate.build_set(64, 64, seed0=0, n_kbins=256, n_hist_max=128)
+    Xv, yv, _, fv = surrogate.build_set(8, 16, seed0=5000, n_kbins=256, n_hist_max=128)
+    t_gen = time.time() - t0
+    mlp = nupm.MLP()
+    mlp.set_params(surrogate.init_params(0))
+    surrogate.fit_norm(mlp, X, y)
+    t0 = time.time()
+    hist = surrogate.train(mlp, X, y, epochs=30, batch=4096, lr0=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    rel, force = surrogate.errors(mlp, Xv, yv, fv)
+    parts = synth.particles(w)
+    ms64, _, acc64 = _kick_form(synth.with_(w, precision="fp64"), parts["pos64"], parts["vel"], "fp64",
+                                steps, warmup)
+    msx, rx, accx = _kick_form(w, parts["pos64"], parts["vel"], "fp32", steps, warmup)
+    msm, rm, accm = _kick_form(w, parts["pos64"], parts["vel"], "fp32", steps, warmup, mlp=mlp)
+    out["surrogate"] = {
+        "workload": w.name, "train_samples": int(X.shape[0]), "gen_s": round(t_gen, 1),
+        "train_s": round(t_train, 1), "epochs": len(hist), "final_loss": hist[-1],
+        "val_rel_R_median": float(np.median(rel)), "val_rel_R_p99": float(np.percentile(rel, 99)),
+        "val_force_bound_max": float(np.max(force)),
+        "fp64_exact_ms_per_kick": round(ms64, 3), "fp32_exact_ms_per_kick": round(msx, 3),
+        "fp32_surrogate_ms_per_kick": round(msm, 3),
+        "response_ms_exact": round(rx, 4), "response_ms_surrogate": round(rm, 4),
+        "force_rms_rel_surrogate_vs_fp64": _rms_rel(accm, acc64),
+        "force_rms_rel_exact_fp32_vs_fp64": _rms_rel(accx, acc64),
+        "force_rms_rel_surrogate_vs_exact_fp32": _rms_rel(accm, accx)}
+    mlp.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -315,6 +424,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP64 / surrogate comparisons")
     args = ap.parse_args()
     w = synth.WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -366,10 +476,13 @@ def main():
         cpu = {"value": npart / t, "unit": "particle-kicks/s", "cores": 1, "kind": "oracle",
                "sample": f"one oracle kick on a {s.ngrid}^3 grid with {s.npart_side}^3 particles "
                          f"(box {s.box:g} Mpc/h, same cell size, bins and history), {t:.1f} s"}
+    forms = None
+    if world == 1 and not args.no_forms and args.workload == "pm1024_p512_fp32":
+        forms = run_forms()
     line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"], e2e=res["e2e"],
                 roofline=res["roofline"], cpu_baseline=cpu, gpu_launches=res["gpu_launches"],
                 clocks=res["clocks"], step_model_gb=res["step_alg_gb"], step_hbm_frac=res["step_frac"],
-                stages_ms=res["stages"])
+                stages_ms=res["stages"], forms=forms)
     print(json.dumps(line))
     if world > 1:
         import torch

@@ -255,6 +255,74 @@ NUPM_API int pm_bin_power_static(const void* spec, int32_t ngrid, double box, in
 /* Bytes of device memory the context holds. */
 NUPM_API int64_t pm_device_bytes(const pm_ctx* ctx);
 
+/* ---- learned response surrogate ----
+ * The paper has no learned part; this stands in for the response integral of
+ * pm_nu_response (Eq. P-final with Eq. deltaI-nu), which stays the fallback
+ * and the judge of its error.  A 3-layer perceptron
+ *   h1 = tanh(W1 xh + b1), h2 = tanh(W2 h1 + b2), out = w3 . h2 + b3,
+ *   xh = (x - mu) / sigma,  ln R = y_mu + y_sigma out,
+ * width 128, BF16 weight matrices (W1, W2, w3), FP32 biases, FP32 accumulation,
+ * maps the PM_MLP_FEATURES features of one k bin
+ *   x = (ln k_b [h/Mpc], ln a, M_nu [eV], Omega_nu, c_0 .. c_7)
+ * to ln R_b, R_b = P_nu^{1/2}(k_b, a) / P_cdm^{1/2}(k_b, a).  c_j (j < 8) are the
+ * Chebyshev coefficients, c_j = (2/8) sum_m g(u_m) cos(j pi (m + 1/2) / 8), of
+ *   g(u) = ln( P_M^{1/2}(k_b, a'(u)) / P_cdm^{1/2}(k_b, a) ),
+ *   u_m = ln a_i + (t_m + 1)/2 (ln a - ln a_i), t_m = cos(pi (m + 1/2) / 8),
+ * with P_M^{1/2} linear in ln a' between the stored history nodes, closed by
+ * the node (a, P_cdm^{1/2}(k_b, a)) and constant back to a_i.
+ * Flat FP32 parameter layout (pm_mlp_param_count values):
+ *   W1 [128][n_in], b1 [128], W2 [128][128], b2 [128], w3 [128], b3 [1].
+ * Arrays marked DEVICE are device pointers; the work is ordered on the stream
+ * given at creation.  Errors: PM_ERR_INVALID (bad sizes, NULL pointers),
+ * PM_ERR_ALLOC, PM_ERR_CUDA. */
+#define PM_MLP_FEATURES 12
+#define PM_MLP_WIDTH 128
+typedef struct pm_mlp pm_mlp;
+/* n_in in 1..16, width must be PM_MLP_WIDTH.  Parameters start at zero (set
+ * them with pm_mlp_set_params); normalisation starts at mu = 0, sigma = 1. */
+NUPM_API int pm_mlp_create(int32_t n_in, int32_t width, void* cuda_stream, pm_mlp** out);
+NUPM_API void pm_mlp_free(pm_mlp* mlp);
+NUPM_API int64_t pm_mlp_param_count(const pm_mlp* mlp);
+/* HOST float[pm_mlp_param_count]: the FP32 master copy (BF16 weight copies are
+ * rounded from it to nearest even); resets the Adam moments and step count.
+ * Synchronises the stream. */
+NUPM_API int pm_mlp_set_params(pm_mlp* mlp, const float* host_params);
+NUPM_API int pm_mlp_get_params(const pm_mlp* mlp, float* host_params);
+/* HOST mu[n_in], sigma[n_in] (> 0) and the output scale (y_sigma > 0). */
+NUPM_API int pm_mlp_set_norm(pm_mlp* mlp, const float* mu, const float* sigma, float y_mu, float y_sigma);
+/* DEVICE X float[n][n_in] raw features -> DEVICE y float[n] = ln R. */
+NUPM_API int pm_mlp_forward(pm_mlp* mlp, const float* X, int64_t n, float* y);
+/* Gradient of L = (1/n) sum_i (out_i - (y_i - y_mu)/y_sigma)^2 with respect to
+ * the parameters (the forward pass uses the BF16 weights), summed over CTAs
+ * in a fixed order.  DEVICE grad float[param_count] and loss float[1], either
+ * may be NULL. */
+NUPM_API int pm_mlp_grad(pm_mlp* mlp, const float* X, const float* y, int64_t n, float* grad, float* loss);
+/* pm_mlp_grad, then one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning
+ * rate lr > 0) on the FP32 master copy and the BF16 copies.  DEVICE loss may
+ * be NULL (the loss before the step). */
+NUPM_API int pm_mlp_train_step(pm_mlp* mlp, const float* X, const float* y, int64_t n, float lr, float* loss);
+/* The surrogate's features of every bin of the context's current P_cdm bins
+ * (after pm_deposit or pm_set_power) at scale factor a with the stored history
+ * (same arguments and checks as pm_nu_response): DEVICE X float[n_kbins][12];
+ * rows of empty bins are zero. */
+NUPM_API int pm_response_features(pm_ctx* ctx, double a, const double* a_hist, const double* sqrtPM_hist,
+                                  int32_t n_hist, float* X);
+/* pm_nu_response with the surrogate in place of the integral: R_b = exp(ln R_b)
+ * for non-empty bins (0 for empty ones), P_nu^{1/2} = R_b P_cdm^{1/2},
+ * P_M^{1/2} = (1 - f_nu) P_cdm^{1/2} + f_nu P_nu^{1/2}; prepares pm_kick exactly
+ * as pm_nu_response does.  Outputs as pm_nu_response (DEVICE, may be NULL).
+ * Without massive neutrinos it behaves as pm_nu_response (R = 0). */
+NUPM_API int pm_nu_response_mlp(pm_ctx* ctx, pm_mlp* mlp, double a, const double* a_hist,
+                                const double* sqrtPM_hist, int32_t n_hist, double* ratio_out,
+                                double* sqrtPnu_out, double* sqrtPM_out);
+/* Replace the context's P_cdm bins with caller values (HOST double[n_kbins]:
+ * count, ksum = count k_b [h/Mpc], psum in the units of pm_get_bins) so that
+ * pm_nu_response / pm_response_features can run on chosen spectra (e.g. to
+ * generate the surrogate's training set from the exact integral).  pm_kick
+ * then needs a new pm_deposit (PM_ERR_ORDER otherwise).  The paper has no
+ * counterpart. */
+NUPM_API int pm_set_power(pm_ctx* ctx, const double* count, const double* ksum, const double* psum);
+
 #ifdef __cplusplus
 }
 #endif

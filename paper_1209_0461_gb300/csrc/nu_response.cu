@@ -307,6 +307,87 @@ void launch_nu_response(const NuArgs& a, cudaStream_t s) {
   k_nu_rlist<<<1, ((a.nk + 31) / 32) * 32, 0, s>>>(a.bins, a.R, a.nk, a.rlist);
 }
 
+// ---------------------------------------------------------------- surrogate
+// Features of bin b for the learned response (FP64, one thread per bin):
+//   (ln k_b, ln a, M_nu, Omega_nu, c_0 .. c_7), c_j the Chebyshev coefficients
+// on 8 points of g(u) = ln(P_M^{1/2}(u) / P_cdm^{1/2}(a)), u = ln a' in
+// [ln a_i, ln a]; P_M^{1/2} linear in u between the nodes (hist_u[j], hist[j][b])
+// closed by (ln a, P_cdm^{1/2}), constant before the first node.
+__global__ void k_nu_features(NuArgs A, double m_nu, double omega_nu, float* __restrict__ X) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= A.nk) return;
+  float* row = X + (int64_t)b * 12;
+  const double cnt = A.bins[b];
+  if (!(cnt > 0.0)) {
+    for (int i = 0; i < 12; ++i) row[i] = 0.0f;
+    return;
+  }
+  const double L3 = A.box * A.box * A.box;
+  const double n3 = (double)A.ngrid * A.ngrid * A.ngrid;
+  const double pcdm = sqrt(A.bins[2 * A.nk + b] / cnt * L3 / (n3 * n3));
+  const double kb = A.bins[A.nk + b] / cnt;
+  double g[8];
+  for (int m = 0; m < 8; ++m) {
+    const double t = cospi((m + 0.5) / 8.0);
+    const double u = A.ui + 0.5 * (t + 1.0) * (A.ue - A.ui);
+    double h = pcdm;
+    if (A.n_hist > 0) {
+      if (u <= A.hist_u[0]) {
+        h = A.hist[b];
+      } else {
+        int j = 0;
+        while (j + 1 < A.n_hist && A.hist_u[j + 1] < u) ++j;
+        const double u0 = A.hist_u[j], h0 = A.hist[(int64_t)j * A.nk + b];
+        const double u1 = j + 1 < A.n_hist ? A.hist_u[j + 1] : A.ue;
+        const double h1 = j + 1 < A.n_hist ? A.hist[(int64_t)(j + 1) * A.nk + b] : pcdm;
+        h = h0 + (h1 - h0) * (u - u0) / (u1 - u0);
+      }
+    }
+    g[m] = (h > 0.0 && pcdm > 0.0) ? log(h / pcdm) : 0.0;
+  }
+  row[0] = (float)log(kb);
+  row[1] = (float)A.ue;
+  row[2] = (float)m_nu;
+  row[3] = (float)omega_nu;
+  for (int jc = 0; jc < 8; ++jc) {
+    double c = 0.0;
+    for (int m = 0; m < 8; ++m) c += g[m] * cospi(jc * (m + 0.5) / 8.0);
+    row[4 + jc] = (float)(0.25 * c);
+  }
+}
+
+// R_b = exp(ln R_b) from the surrogate, then P_nu^{1/2} and P_M^{1/2} as the
+// exact finish does (empty bins: 0).
+__global__ void k_nu_from_lnR(NuArgs A, const float* __restrict__ lnR) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= A.nk) return;
+  const double cnt = A.bins[b];
+  double R = 0.0, pnu = 0.0, pm = 0.0;
+  if (cnt > 0.0) {
+    const double L3 = A.box * A.box * A.box;
+    const double n3 = (double)A.ngrid * A.ngrid * A.ngrid;
+    const double pcdm = sqrt(A.bins[2 * A.nk + b] / cnt * L3 / (n3 * n3));
+    R = exp((double)lnR[b]);
+    pnu = R * pcdm;
+    pm = (1.0 - A.f_nu) * pcdm + A.f_nu * pnu;
+  }
+  A.R[b] = R;
+  A.pnu[b] = pnu;
+  A.pm[b] = pm;
+  if (A.R_user) A.R_user[b] = R;
+  if (A.pnu_user) A.pnu_user[b] = pnu;
+  if (A.pm_user) A.pm_user[b] = pm;
+}
+
+void launch_nu_features(const NuArgs& a, double m_nu, double omega_nu, float* X, cudaStream_t s) {
+  k_nu_features<<<(a.nk + 127) / 128, 128, 0, s>>>(a, m_nu, omega_nu, X);
+}
+
+void launch_nu_from_lnR(const NuArgs& a, const float* lnR, cudaStream_t s) {
+  k_nu_from_lnR<<<(a.nk + 127) / 128, 128, 0, s>>>(a, lnR);
+  k_nu_rlist<<<1, ((a.nk + 31) / 32) * 32, 0, s>>>(a.bins, a.R, a.nk, a.rlist);
+}
+
 // ---------------------------------------------------------------- Green table
 // G(n^2) = coeff [(1 - f) + f R(k)] / n^2, k = kf sqrt(n^2); R linear in ln k
 // between non-empty bins (k_b = ksum/count), constant beyond the end bins.

@@ -44,6 +44,13 @@ struct NuArgs {
 };
 
 void launch_nu_response(const NuArgs& a, cudaStream_t s);
+// Surrogate: features [nk][12] of the bins and history in a (FP64 -> float),
+// and the finish from the surrogate's ln R (R, P_nu, P_M, rlist).
+void launch_nu_features(const NuArgs& a, double m_nu, double omega_nu, float* X, cudaStream_t s);
+void launch_nu_from_lnR(const NuArgs& a, const float* lnR, cudaStream_t s);
+// Surrogate network (mlp.cu): input count, and the forward pass on a given stream.
+int mlp_inputs(const pm_mlp* m);
+int mlp_forward_on(pm_mlp* m, const float* X, int64_t n, float* y, cudaStream_t s);
 // fac(u) = (1 - f) + f R(k), ln k = ln kf + u, on kFacTable points of u in [0, umax]
 // (u = ln sqrt(n^2)); the FP32 inverse z pass interpolates it linearly in u.
 constexpr int kFacTable = 2048;

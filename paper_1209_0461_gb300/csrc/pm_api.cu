@@ -70,6 +70,10 @@ struct pm_ctx {
   int* h_status = nullptr;
   // state
   bool deposited = false, deposit_grid_valid = false, have_response = false, have_kick = false;
+  bool power_set = false;         // bins replaced by pm_set_power (no spectrum behind them)
+  double* d_bins_lattice = nullptr;   // [2][nk] lattice count / ksum, restored after pm_set_power
+  float* d_X = nullptr;           // [nk][12] surrogate features
+  float* d_lnR = nullptr;         // [nk] surrogate output
   double a_response = 0;
   int64_t bytes = 0;
   std::vector<long long> thr;
@@ -366,7 +370,8 @@ GridArgs grid_args(const pm_ctx* c) {
 }
 
 void release(pm_ctx* c) {
-  void* ptrs[] = {c->spec, c->g, c->tw_n, c->tw_m, c->d_binof, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
+  void* ptrs[] = {c->d_bins_lattice, c->d_X, c->d_lnR,
+                  c->spec, c->g, c->tw_n, c->tw_m, c->d_binof, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
                   c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_rlist, c->d_gtab,
                   c->d_dtab, c->d_wtab, c->d_plane0, c->d_fac, c->d_rowc, c->d_rows, c->d_rowcur,
                   c->d_scantot, c->d_perm, c->d_rec, c->d_status};
@@ -529,6 +534,9 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_binof, (size_t)(c->n2max + 1) * sizeof(short), "bin table");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_partials, (size_t)c->nblk_bins * 2 * c->nk * sizeof(double), "bin partials");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_bins, 3 * (size_t)c->nk * sizeof(double), "bins");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_bins_lattice, 2 * (size_t)c->nk * sizeof(double), "lattice bins");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_X, 12 * (size_t)c->nk * sizeof(float), "surrogate features");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_lnR, (size_t)c->nk * sizeof(float), "surrogate output");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_pi, (size_t)nspec * c->nk * sizeof(double), "nu ICs");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_ti, (size_t)nspec * c->nk * sizeof(double), "nu theta ICs");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_hist_u, (size_t)(p.n_hist_max + 1) * sizeof(double), "history ln a");
@@ -608,6 +616,9 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
     rc = c->fp64 ? bins_f64(g, true, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins, 0)
                  : bins_f32(g, true, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins, 0);
     if (rc == PM_OK) rc = cuda_check(c, cudaGetLastError(), "lattice bins");
+    if (rc == PM_OK)
+      rc = cuda_check(c, cudaMemcpy(c->d_bins_lattice, c->d_bins, 2 * (size_t)c->nk * sizeof(double),
+                                    cudaMemcpyDeviceToDevice), "lattice bins copy");
   }
   if (rc == PM_OK) rc = cuda_check(c, cudaMemset(c->d_status, 0, sizeof(int)), "status init");
   if (rc == PM_OK) rc = cuda_check(c, cudaDeviceSynchronize(), "pm_init");
@@ -626,6 +637,12 @@ int pm_deposit(pm_ctx* c, const void* pos) {
   if (!pos) return fail(c, PM_ERR_INVALID, "pm_deposit: pos is NULL");
   GridArgs g = grid_args(c);
   int rc = PM_OK;
+  if (c->power_set) {
+    rc = cuda_check(c, cudaMemcpyAsync(c->d_bins, c->d_bins_lattice, 2 * (size_t)c->nk * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, c->stream), "lattice bins restore");
+    if (rc != PM_OK) return rc;
+    c->power_set = false;
+  }
   const bool unfused = (c->p.flags & PM_UNFUSED_DEPOSIT) != 0;
   const bool keep = (c->p.flags & PM_KEEP_DEPOSIT) != 0;
   if (unfused) {
@@ -670,9 +687,13 @@ int pm_deposit(pm_ctx* c, const void* pos) {
   return PM_OK;
 }
 
-int pm_nu_response(pm_ctx* c, double a, const double* a_hist, const double* sqrtPM_hist, int32_t n_hist,
-                   const double* sqrtPnu_prev, double* ratio_out, double* sqrtPnu_out, double* sqrtPM_out) {
-  if (!c) return PM_ERR_INVALID;
+}  // extern "C"
+
+namespace {
+
+// Checks of a response call's arguments, history upload (ln a_j) and the s(a)
+// table extension, shared by the exact and the surrogate response.
+int response_prepare(pm_ctx* c, double a, const double* a_hist, const double* sqrtPM_hist, int32_t n_hist) {
   if (!c->deposited) return fail(c, PM_ERR_ORDER, "pm_nu_response before pm_deposit");
   if (!(isfinite(a) && a >= c->a_init)) return fail(c, PM_ERR_RANGE, "a must be finite and >= a_init");
   if (n_hist < 0 || n_hist > c->p.n_hist_max) return fail(c, PM_ERR_INVALID, "n_hist outside 0..n_hist_max");
@@ -689,11 +710,64 @@ int pm_nu_response(pm_ctx* c, double a, const double* a_hist, const double* sqrt
     if (rc != PM_OK) return rc;
   }
   for (int j = 0; j < n_hist; ++j) c->h_hist_u[j] = log(a_hist[j]);
-  if (n_hist > 0) {
-    const int rc = cuda_check(c, cudaMemcpyAsync(c->d_hist_u, c->h_hist_u, n_hist * sizeof(double),
-                                                 cudaMemcpyHostToDevice, c->stream), "history upload");
+  if (n_hist > 0)
+    return cuda_check(c, cudaMemcpyAsync(c->d_hist_u, c->h_hist_u, n_hist * sizeof(double), cudaMemcpyHostToDevice,
+                                         c->stream), "history upload");
+  return PM_OK;
+}
+
+// NuArgs of the surrogate kernels (bins, history, outputs).
+NuArgs surrogate_args(pm_ctx* c, double a, const double* sqrtPM_hist, int32_t n_hist, double* ratio_out,
+                      double* sqrtPnu_out, double* sqrtPM_out) {
+  NuArgs A{};
+  A.nk = c->nk;
+  A.ns = c->ns;
+  A.n_hist = n_hist;
+  A.ngrid = c->n;
+  A.a = a;
+  A.ue = log(a);
+  A.ui = log(c->a_init);
+  A.f_nu = c->f_nu;
+  A.box = c->box;
+  A.bins = c->d_bins;
+  A.hist_u = c->d_hist_u;
+  A.hist = sqrtPM_hist;
+  A.rlist = c->d_rlist;
+  A.R = c->d_R;
+  A.pnu = c->d_pnu;
+  A.pm = c->d_pm;
+  A.R_user = ratio_out;
+  A.pnu_user = sqrtPnu_out;
+  A.pm_user = sqrtPM_out;
+  return A;
+}
+
+// Green and fac tables from the response's rlist (both response forms).
+int response_tables(pm_ctx* c, double a) {
+  const double coeff = -1.5 * c->omega_m / (a * c->kf * c->kf * (double)c->n * c->n * c->n);
+  launch_green_table(c->fp64, c->d_gtab, c->n2max, c->kf, coeff, c->f_nu, c->d_rlist, c->nk, c->stream);
+  if (!c->fp64)
+    launch_fac_table(c->d_fac, 0.5 * log((double)c->n2max), c->kf, c->f_nu, c->d_rlist, c->nk, c->stream);
+  c->green_coeff = coeff;
+  const int rc = cuda_check(c, cudaGetLastError(), "pm_nu_response launch");
+  if (rc != PM_OK) return rc;
+  c->have_response = true;
+  c->a_response = a;
+  return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pm_nu_response(pm_ctx* c, double a, const double* a_hist, const double* sqrtPM_hist, int32_t n_hist,
+                   const double* sqrtPnu_prev, double* ratio_out, double* sqrtPnu_out, double* sqrtPM_out) {
+  if (!c) return PM_ERR_INVALID;
+  {
+    const int rc = response_prepare(c, a, a_hist, sqrtPM_hist, n_hist);
     if (rc != PM_OK) return rc;
   }
+  const double ue = log(a);
   Stage stage(c, PM_ST_RESPONSE, ((c->ns > 0 && c->f_nu > 0) ? 4 : 3) + (c->fp64 ? 0 : 1));
   if (c->ns > 0 && c->f_nu > 0) {
     NuArgs A{};
@@ -758,15 +832,64 @@ int pm_nu_response(pm_ctx* c, double a, const double* a_hist, const double* sqrt
     A.pm_user = sqrtPM_out;
     launch_nu_response(A, c->stream);   // zero items in the panel kernel; finish sets outputs
   }
-  const double coeff = -1.5 * c->omega_m / (a * c->kf * c->kf * (double)c->n * c->n * c->n);
-  launch_green_table(c->fp64, c->d_gtab, c->n2max, c->kf, coeff, c->f_nu, c->d_rlist, c->nk, c->stream);
-  if (!c->fp64)
-    launch_fac_table(c->d_fac, 0.5 * log((double)c->n2max), c->kf, c->f_nu, c->d_rlist, c->nk, c->stream);
-  c->green_coeff = coeff;
-  const int rc = cuda_check(c, cudaGetLastError(), "pm_nu_response launch");
+  return response_tables(c, a);
+}
+
+int pm_response_features(pm_ctx* c, double a, const double* a_hist, const double* sqrtPM_hist, int32_t n_hist,
+                         float* X) {
+  if (!c) return PM_ERR_INVALID;
+  if (!X) return fail(c, PM_ERR_INVALID, "pm_response_features: X is NULL");
+  int rc = response_prepare(c, a, a_hist, sqrtPM_hist, n_hist);
   if (rc != PM_OK) return rc;
-  c->have_response = true;
-  c->a_response = a;
+  NuArgs A = surrogate_args(c, a, sqrtPM_hist, n_hist, nullptr, nullptr, nullptr);
+  launch_nu_features(A, c->p.m_nu_total_eV, c->omega_nu, X, c->stream);
+  return cuda_check(c, cudaGetLastError(), "pm_response_features launch");
+}
+
+int pm_nu_response_mlp(pm_ctx* c, pm_mlp* mlp, double a, const double* a_hist, const double* sqrtPM_hist,
+                       int32_t n_hist, double* ratio_out, double* sqrtPnu_out, double* sqrtPM_out) {
+  if (!c) return PM_ERR_INVALID;
+  if (!mlp) return fail(c, PM_ERR_INVALID, "pm_nu_response_mlp: mlp is NULL");
+  if (mlp_inputs(mlp) != PM_MLP_FEATURES) return fail(c, PM_ERR_INVALID, "surrogate needs 12 input features");
+  int rc = response_prepare(c, a, a_hist, sqrtPM_hist, n_hist);
+  if (rc != PM_OK) return rc;
+  NuArgs A = surrogate_args(c, a, sqrtPM_hist, n_hist, ratio_out, sqrtPnu_out, sqrtPM_out);
+  Stage stage(c, PM_ST_RESPONSE, (c->ns > 0 && c->f_nu > 0) ? 4 : 2);
+  if (c->ns > 0 && c->f_nu > 0) {
+    launch_nu_features(A, c->p.m_nu_total_eV, c->omega_nu, c->d_X, c->stream);
+    rc = mlp_forward_on(mlp, c->d_X, c->nk, c->d_lnR, c->stream);
+    if (rc != PM_OK) return fail(c, rc, "surrogate forward launch failed");
+    launch_nu_from_lnR(A, c->d_lnR, c->stream);
+  } else {
+    A.ns = 0;
+    A.iters = 1;
+    A.parts = c->d_parts;
+    A.pnu_init = c->d_pi;
+    launch_nu_response(A, c->stream);   // R = 0 as the exact path
+  }
+  return response_tables(c, a);
+}
+
+int pm_set_power(pm_ctx* c, const double* count, const double* ksum, const double* psum) {
+  if (!c) return PM_ERR_INVALID;
+  if (!count || !ksum || !psum) return fail(c, PM_ERR_INVALID, "pm_set_power: NULL array");
+  const int nk = c->nk;
+  std::vector<double> h(3 * (size_t)nk);
+  for (int b = 0; b < nk; ++b) {
+    if (!(count[b] >= 0.0 && isfinite(count[b]) && isfinite(ksum[b]) && isfinite(psum[b]) && psum[b] >= 0.0) ||
+        (count[b] > 0.0 && !(ksum[b] > 0.0)))
+      return fail(c, PM_ERR_RANGE, "pm_set_power: counts, ksum and psum must be finite, >= 0 (ksum > 0 if count > 0)");
+    h[b] = count[b];
+    h[nk + b] = ksum[b];
+    h[2 * nk + b] = psum[b];
+  }
+  int rc = cuda_check(c, cudaMemcpyAsync(c->d_bins, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                         c->stream), "pm_set_power upload");
+  if (rc == PM_OK) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "pm_set_power sync");
+  if (rc != PM_OK) return rc;
+  c->deposited = true;
+  c->power_set = true;
+  c->have_response = false;
   return PM_OK;
 }
 
@@ -774,6 +897,7 @@ int pm_kick(pm_ctx* c, const void* pos, void* vel, double a, double kick_factor,
   if (!c) return PM_ERR_INVALID;
   if (!pos || !vel) return fail(c, PM_ERR_INVALID, "pm_kick: pos/vel is NULL");
   if (!c->deposited || !c->have_response) return fail(c, PM_ERR_ORDER, "pm_kick needs pm_deposit and pm_nu_response first");
+  if (c->power_set) return fail(c, PM_ERR_ORDER, "pm_kick after pm_set_power needs a new pm_deposit");
   if (a != c->a_response) return fail(c, PM_ERR_ORDER, "pm_kick at a different a than pm_nu_response");
   if (!isfinite(kick_factor)) return fail(c, PM_ERR_INVALID, "kick_factor must be finite");
   GridArgs g = grid_args(c);

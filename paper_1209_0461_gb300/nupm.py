@@ -24,6 +24,7 @@ PM_FP64, PM_FP32 = 0, 1
 PM_I_FIT, PM_DECONV_CIC, PM_KEEP_DEPOSIT, PM_UNFUSED_DEPOSIT = 0x1, 0x2, 0x4, 0x8
 PM_TMA_COLUMNS, PM_FUSED_GATHER = 0x10, 0x20
 FIELD_DEPOSIT, FIELD_DELTA_K, FIELD_ACC_X, FIELD_ACC_Y, FIELD_ACC_Z = range(5)
+MLP_FEATURES, MLP_WIDTH = 12, 128
 STAGES = ["deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_fwd", "bins", "response", "green",
           "fft_z_inv", "fft_y_inv", "fft_x_inv", "interp"]
 
@@ -73,6 +74,18 @@ def lib():
         "pm_timing": (C.c_int, [vp, i32]),
         "pm_get_timing": (C.c_int, [vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "pm_bin_power_static": (C.c_int, [vp, i32, d, i32, i32, vp, vp, vp, vp]),
+        "pm_mlp_create": (C.c_int, [i32, i32, vp, C.POINTER(vp)]),
+        "pm_mlp_free": (None, [vp]),
+        "pm_mlp_param_count": (i64, [vp]),
+        "pm_mlp_set_params": (C.c_int, [vp, C.POINTER(C.c_float)]),
+        "pm_mlp_get_params": (C.c_int, [vp, C.POINTER(C.c_float)]),
+        "pm_mlp_set_norm": (C.c_int, [vp, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_float, C.c_float]),
+        "pm_mlp_forward": (C.c_int, [vp, vp, i64, vp]),
+        "pm_mlp_grad": (C.c_int, [vp, vp, vp, i64, vp, vp]),
+        "pm_mlp_train_step": (C.c_int, [vp, vp, vp, i64, C.c_float, vp]),
+        "pm_response_features": (C.c_int, [vp, d, dp, vp, i32, vp]),
+        "pm_nu_response_mlp": (C.c_int, [vp, vp, d, dp, vp, i32, vp, vp, vp]),
+        "pm_set_power": (C.c_int, [vp, dp, dp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -209,6 +222,47 @@ class PM:
     def check(self):
         self._ok(lib().pm_check(self.ctx), "pm_check")
 
+    def _history(self, a_hist, sqrtPM_hist):
+        import torch
+        ah = np.ascontiguousarray(a_hist if a_hist is not None else [], dtype=np.float64)
+        n = int(ah.size)
+        if n and (sqrtPM_hist is None or sqrtPM_hist.dtype != torch.float64 or not sqrtPM_hist.is_cuda
+                  or sqrtPM_hist.numel() < n * self.nk or not sqrtPM_hist.is_contiguous()):
+            raise ValueError("sqrtPM_hist must be a contiguous CUDA float64 [n_hist, n_kbins]")
+        return ah, n
+
+    # -- the learned response
+    def response_features(self, a, a_hist, sqrtPM_hist, X=None):
+        """pm_response_features -> CUDA float32 [n_kbins, 12]."""
+        import torch
+        ah, n = self._history(a_hist, sqrtPM_hist)
+        if X is None:
+            X = torch.empty((self.nk, MLP_FEATURES), dtype=torch.float32, device="cuda")
+        elif X.dtype != torch.float32 or not X.is_cuda or X.numel() < self.nk * MLP_FEATURES:
+            raise ValueError("X must be CUDA float32 [n_kbins, 12]")
+        self._ok(lib().pm_response_features(self.ctx, float(a), _dptr(ah) if n else None,
+                                            _tptr(sqrtPM_hist) if n else None, n, _tptr(X)),
+                 "pm_response_features")
+        return X
+
+    def nu_response_mlp(self, mlp, a, a_hist, sqrtPM_hist, ratio=None, sqrtPnu=None, sqrtPM=None):
+        """pm_nu_response_mlp: the surrogate in place of the response integral."""
+        import torch
+        ah, n = self._history(a_hist, sqrtPM_hist)
+        for t in (ratio, sqrtPnu, sqrtPM):
+            if t is not None and (t.dtype != torch.float64 or not t.is_cuda or t.numel() < self.nk):
+                raise ValueError("per-bin vectors must be CUDA float64 [n_kbins]")
+        self._ok(lib().pm_nu_response_mlp(self.ctx, mlp.handle, float(a), _dptr(ah) if n else None,
+                                          _tptr(sqrtPM_hist) if n else None, n, _tptr(ratio), _tptr(sqrtPnu),
+                                          _tptr(sqrtPM)), "pm_nu_response_mlp")
+
+    def set_power(self, count, ksum, psum):
+        """pm_set_power: host float64 [n_kbins] bins (units of bins())."""
+        arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (count, ksum, psum)]
+        if any(x.size != self.nk for x in arrs):
+            raise ValueError("count, ksum, psum must hold n_kbins values")
+        self._ok(lib().pm_set_power(self.ctx, *(_dptr(x) for x in arrs)), "pm_set_power")
+
     # -- background
     def kick_factor(self, a0, a1):
         return lib().pm_kick_factor(self.ctx, float(a0), float(a1))
@@ -261,6 +315,87 @@ class PM:
         if getattr(self, "ctx", None):
             lib().pm_free(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The surrogate network (pm_mlp_*): 12 -> 128 -> 128 -> 1, tanh, BF16 weights."""
+
+    def __init__(self, n_in=MLP_FEATURES, width=MLP_WIDTH, stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        rc = lib().pm_mlp_create(int(n_in), int(width), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc != PM_OK:
+            raise PMError(rc, "pm_mlp_create failed")
+        self.handle = h
+        self.n_in = int(n_in)
+        self.P = int(lib().pm_mlp_param_count(h))
+
+    def _ok(self, rc, what):
+        if rc != PM_OK:
+            raise PMError(rc, what)
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        if th.size != self.P:
+            raise ValueError(f"expected {self.P} parameters")
+        self._ok(lib().pm_mlp_set_params(self.handle, th.ctypes.data_as(C.POINTER(C.c_float))), "pm_mlp_set_params")
+
+    def get_params(self):
+        th = np.zeros(self.P, dtype=np.float32)
+        self._ok(lib().pm_mlp_get_params(self.handle, th.ctypes.data_as(C.POINTER(C.c_float))), "pm_mlp_get_params")
+        return th
+
+    def set_norm(self, mu, sigma, y_mu, y_sigma):
+        m = np.ascontiguousarray(mu, dtype=np.float32)
+        s = np.ascontiguousarray(sigma, dtype=np.float32)
+        if m.size != self.n_in or s.size != self.n_in:
+            raise ValueError("mu and sigma need n_in values")
+        self._ok(lib().pm_mlp_set_norm(self.handle, m.ctypes.data_as(C.POINTER(C.c_float)),
+                                       s.ctypes.data_as(C.POINTER(C.c_float)), float(y_mu), float(y_sigma)),
+                 "pm_mlp_set_norm")
+        self.norm = (m.astype(np.float64), s.astype(np.float64), float(np.float32(y_mu)), float(np.float32(y_sigma)))
+
+    def _xy(self, X, y=None):
+        import torch
+        if X.dtype != torch.float32 or not X.is_cuda or not X.is_contiguous() or X.dim() != 2 or X.shape[1] != self.n_in:
+            raise ValueError("X must be a contiguous CUDA float32 [n, n_in]")
+        if y is not None and (y.dtype != torch.float32 or not y.is_cuda or y.numel() != X.shape[0]):
+            raise ValueError("y must be CUDA float32 [n]")
+        return int(X.shape[0])
+
+    def forward(self, X, out=None):
+        import torch
+        n = self._xy(X)
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device="cuda")
+        self._ok(lib().pm_mlp_forward(self.handle, _tptr(X), n, _tptr(out)), "pm_mlp_forward")
+        return out
+
+    def grad(self, X, y):
+        """(grad CUDA float32 [P], loss CUDA float32 [1])."""
+        import torch
+        n = self._xy(X, y)
+        g = torch.empty(self.P, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        self._ok(lib().pm_mlp_grad(self.handle, _tptr(X), _tptr(y), n, _tptr(g), _tptr(loss)), "pm_mlp_grad")
+        return g, loss
+
+    def train_step(self, X, y, lr, loss=None):
+        n = self._xy(X, y)
+        self._ok(lib().pm_mlp_train_step(self.handle, _tptr(X), _tptr(y), n, float(lr), _tptr(loss)),
+                 "pm_mlp_train_step")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pm_mlp_free(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

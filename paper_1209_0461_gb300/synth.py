@@ -85,6 +85,8 @@ WORKLOADS = {
     # smaller analogue of the precision form (same cell size and particle:grid
     # ratio; every grid still larger than L2) for detailed profiling
     "pm512_p256_fp32": Workload("pm512_p256_fp32", 512, 256, 500.0, 0.06, 3, 128, 256, "fp32"),
+    # surrogate form: 512^3 particles on a 512^3 grid (M_nu inside the surrogate's range)
+    "pm512_p512_fp32": Workload("pm512_p512_fp32", 512, 512, 500.0, 0.3, 3, 128, 256, "fp32"),
 }
 
 
@@ -228,18 +230,66 @@ def history(w: Workload):
 
 def nu_initial(w: Workload):
     """sqrtPnu_init [n_species, n_kbins], theta_over_delta_init [n_species, n_kbins]."""
-    kc = bin_log_centres(w)
+    return nu_initial_at(bin_log_centres(w), w)
+
+
+def nu_initial_at(kc, w: Workload):
+    """The neutrino initial conditions of ``nu_initial`` at wavenumbers kc."""
+    kc = np.asarray(kc, dtype=np.float64)
     ai = w.a_init
     D, f = growth(ai, w.omega_m)
     H = float(hubble(ai, w.omega_m))
     om_a = w.omega_m / ai ** 3 / H ** 2
     p = np.sqrt(linear_power(kc, w)) * D
     ns = len(w.masses)
-    P = np.zeros((max(ns, 1), w.n_kbins))
-    T = np.zeros((max(ns, 1), w.n_kbins))
+    P = np.zeros((max(ns, 1), kc.size))
+    T = np.zeros((max(ns, 1), kc.size))
     for s, m in enumerate(w.masses):
         v2 = 2 * math.log(2) / (3 * ZETA3) * (m * ai / T_NU0_EV) ** 2
         kfs = math.sqrt(1.5 * om_a * v2) * ai * H / C_OVER_H0
         P[s] = p / (1.0 + kc / kfs) ** 2
         T[s] = -ai * H * f
     return P, T
+
+
+# ---------------------------------------------------------------- surrogate training scenarios
+SURROGATE_K = (0.002, 20.0)          # h/Mpc range of the training bins
+SURROGATE_M_NU = (0.04, 0.65)        # eV, a little beyond the surrogate's [0.05, 0.6]
+SURROGATE_A = (0.04, 1.0)
+
+
+def surrogate_kbins(n_kbins: int = 256):
+    """Log-spaced wavenumbers of the training bins [h/Mpc]."""
+    lo, hi = SURROGATE_K
+    return lo * (hi / lo) ** ((np.arange(n_kbins) + 0.5) / n_kbins)
+
+
+def surrogate_group(seed: int, n_scen: int, n_kbins: int = 256, n_hist_max: int = 128):
+    """One neutrino mass and n_scen seeded scenarios of (a, stored history,
+    current CDM amplitude) on the surrogate's k bins.  Histories follow
+    sqrt(P_lin(k)) D(a') times a smooth perturbation 1 + eps(k) sin(pi v),
+    v = (ln a' - ln a_i)/(ln a - ln a_i) in [0, 1) (vanishing at a_i), eps(k) =
+    e0 + e1 tanh(ln(k / 0.1 h/Mpc)), e0, e1 uniform in [-0.08, 0.08]; node counts
+    from {4, 8, 16, 32, 64, 128} (<= n_hist_max), log-spaced on [a_i, a); the
+    current amplitude is sqrt(P_lin) D(a) (1 + 0.02 N(0, 1)).
+    Returns (workload carrying M_nu, kb, list of scenario dicts)."""
+    rng = np.random.default_rng(10_000 + seed)
+    m_nu = float(rng.uniform(*SURROGATE_M_NU))
+    w = Workload(f"sur{seed}", 32, 32, 1000.0, m_nu, 3, 16, n_kbins, "fp64")
+    kb = surrogate_kbins(n_kbins)
+    p = np.sqrt(linear_power(kb, w))
+    scen = []
+    choices = [n for n in (4, 8, 16, 32, 64, 128) if n <= n_hist_max]
+    for _ in range(n_scen):
+        a = float(math.exp(rng.uniform(math.log(SURROGATE_A[0]), math.log(SURROGATE_A[1]))))
+        nh = int(rng.choice(choices))
+        j = np.arange(nh, dtype=np.float64)
+        a_hist = w.a_init * (a / w.a_init) ** (j / nh)
+        v = (np.log(a_hist) - math.log(w.a_init)) / (math.log(a) - math.log(w.a_init))
+        e0, e1 = rng.uniform(-0.08, 0.08, size=2)
+        eps = e0 + e1 * np.tanh(np.log(kb / 0.1))
+        D = np.array([growth(x, w.omega_m)[0] for x in a_hist])
+        hist = D[:, None] * p[None, :] * (1.0 + eps[None, :] * np.sin(np.pi * v)[:, None])
+        cur = p * growth(a, w.omega_m)[0] * (1.0 + 0.02 * rng.normal(size=n_kbins))
+        scen.append(dict(a=a, a_hist=a_hist, hist=hist, sqrtPcdm=cur))
+    return w, kb, scen

@@ -50,3 +50,17 @@ def test_null_arguments(L):
     assert L.pm_get_timing(None, None, None, None) == -1
     L.pm_free(None)
     assert L.pm_last_error(None) == b"null context"
+
+
+def test_surrogate_entry_points_validate_without_gpu(L):
+    h = C.c_void_p()
+    assert L.pm_mlp_create(0, 128, None, C.byref(h)) == -1
+    assert L.pm_mlp_create(12, 64, None, C.byref(h)) == -1
+    assert L.pm_mlp_create(17, 128, None, C.byref(h)) == -1
+    assert not h.value
+    assert L.pm_mlp_param_count(None) == 0
+    assert L.pm_mlp_forward(None, None, 4, None) == -1
+    assert L.pm_mlp_train_step(None, None, None, 4, 0.1, None) == -1
+    assert L.pm_set_power(None, None, None, None) == -1
+    assert L.pm_response_features(None, 0.1, None, None, 0, None) == -1
+    assert L.pm_nu_response_mlp(None, None, 0.1, None, None, 0, None, None, None) == -1
