@@ -362,13 +362,70 @@ def _rms_rel(acc, ref):
     return float((d / ref.double().pow(2).sum(0).mean().sqrt()).item())
 
 
+def run_batched(steps=10, warmup=3):
+    """The batched form: 32 boxes (64^3 / 128^3 / 192^3, one particle per cell,
+    seeds 0-31, M_nu in {0, 0.06, 0.15, 0.3, 0.6} eV) stepped by one CUDA-graph
+    launch after autotuning, against the same 32 kicks launched one after
+    another on one stream in FP32 and in FP64; force accuracy per box as the
+    RMS of the velocity change against the FP64 kick."""
+    import torch
+    from paper_1209_0461_gb300 import batch
+    boxes = synth.batched_boxes(32)
+
+    def timed(fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    out = {"boxes": len(boxes), "particles": int(sum(w.npart for w in boxes))}
+    dv = {}
+    for name, prec, streams, tune, graph in (("fp64_sequential", "fp64", 1, False, False),
+                                             ("fp32_sequential", "fp32", 1, False, False),
+                                             ("fp32_graph", "fp32", 8, True, True)):
+        b = batch.Batch(boxes, n_streams=streams, autotune=tune, precision=prec)
+        if graph:
+            b.capture()
+            step = b.step
+            out["graph_nodes"] = b.graph.nodes()
+            out["tuning"] = {str(k): list(v) for k, v in b.tuning.items()}
+        else:
+            step = b.eager_step
+        b.reset_velocities()
+        step()
+        b.check()
+        torch.cuda.synchronize()
+        dv[name] = [(it["vel"] - it["vel0"]).double() for it in b.items]
+        for _ in range(warmup):
+            step()
+        ms = timed(step, steps)
+        b.check()
+        out[name] = {"ms_per_step": round(ms, 3), "kicks_per_s": b.npart / (ms / 1e3)}
+        b.close()
+        torch.cuda.empty_cache()
+    for name in ("fp32_sequential", "fp32_graph"):
+        errs = [float(((x - r).pow(2).sum(0).mean().sqrt() / r.pow(2).sum(0).mean().sqrt()).item())
+                for x, r in zip(dv[name], dv["fp64_sequential"])]
+        out[name]["force_rms_rel_vs_fp64_max"] = max(errs)
+    out["graph_speedup_vs_fp32_sequential"] = round(out["fp32_sequential"]["ms_per_step"] /
+                                                     out["fp32_graph"]["ms_per_step"], 2)
+    out["graph_speedup_vs_fp64_sequential"] = round(out["fp64_sequential"]["ms_per_step"] /
+                                                     out["fp32_graph"]["ms_per_step"], 2)
+    return out
+
+
 def run_forms(steps=3, warmup=1):
     """The FP64 kick against the FP32 (precision) form on the 1024^3 workload,
     and the surrogate form on 512^3 particles / 512^3 grid, each with its force
     accuracy against the plain FP64 GPU kick on the same particles."""
     import torch
     from paper_1209_0461_gb300 import nupm, surrogate
-    out = {}
+    out = {"batched": run_batched()}
+    torch.cuda.empty_cache()
     # precision form vs plain FP64
     w = synth.WORKLOADS["pm1024_p512_fp32"]
     parts = synth.particles(w)
@@ -390,7 +447,7 @@ def run_forms(steps=3, warmup=1):
     mlp.set_params(surrogate.init_params(0))
     surrogate.fit_norm(mlp, X, y)
     t0 = time.time()
-    hist = surrogate.train(mlp, X, y, epochs=30, batch=4096, lr0=2e-3)
+    hist = surrogate.train(mlp, X, y, epochs=80, batch=4096, lr0=2e-3)
     torch.cuda.synchronize()
     t_train = time.time() - t0
     rel, force = surrogate.errors(mlp, Xv, yv, fv)

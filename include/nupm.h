@@ -88,7 +88,8 @@ extern "C" {
  *   quad_nodes         Gauss-Legendre nodes per panel of the response integral (4..16)
  */
 typedef struct {
-  int32_t ngrid;          /* N: grid points per side (16..1024, power of two) */
+  int32_t ngrid;          /* N: grid points per side: a power of two in 16..1024, or 192
+                             (radix-3 transforms; not with PM_TMA_COLUMNS / PM_FUSED_GATHER) */
   int64_t npart;          /* number of CDM particles */
   double box;             /* L [Mpc/h] */
   double particle_mass;
@@ -254,6 +255,41 @@ NUPM_API int pm_bin_power_static(const void* spec, int32_t ngrid, double box, in
 
 /* Bytes of device memory the context holds. */
 NUPM_API int64_t pm_device_bytes(const pm_ctx* ctx);
+
+/* ---- autotuner ----
+ * Times, on `reps` kicks of this context with the given particles (kick
+ * factor 0, so velocities are unchanged), each candidate of
+ *   wide_y / wide_z   column tiles of the y / z FFT passes: 0 = 64-byte row
+ *                     segments (8 FP32 columns), 1 = 128-byte segments
+ *   ctas_per_sm       CTAs per SM of the particle kernels (row sort, CIC
+ *                     gather): 4, 8, 16, 32
+ * one knob at a time, keeps the fastest and writes HOST tuned[3] = {wide_y,
+ * wide_z, ctas_per_sm} (may be NULL).  a, a_hist, sqrtPM_hist, n_hist: as
+ * pm_nu_response (the tuning kicks need a response).  Results are bit-identical
+ * across choices except for the order of atomic arrival, which no output
+ * depends on.  The paper has no counterpart (it is a property of this GPU). */
+NUPM_API int pm_autotune(pm_ctx* ctx, const void* pos, void* vel, double a, const double* a_hist,
+                         const double* sqrtPM_hist, int32_t n_hist, int32_t reps, int32_t* tuned);
+/* Set the three knobs directly (-1 = built-in choice for wide_y / wide_z). */
+NUPM_API int pm_set_tuning(pm_ctx* ctx, const int32_t* tuned);
+
+/* ---- CUDA graphs of whole kicks (batched form) ----
+ * pm_graph_begin starts capturing `stream` (thread-local capture mode);
+ * pm_deposit, pm_nu_response, pm_nu_response_mlp and pm_kick calls of
+ * contexts whose stream is `stream` -- or a stream joined to the capture by
+ * an event recorded on it -- are recorded instead of run; pm_graph_end ends
+ * the capture and instantiates the graph.  Each pm_graph_launch then replays
+ * every recorded kick (velocities updated in place each time).  Capture
+ * rules: run each recorded call once uncaptured first (kernel attributes and
+ * tables are set up then), keep pm_timing off, do not call pm_check or
+ * pm_get_* inside the capture, and keep the history pointers and values alive
+ * and unchanged while the graph is used.  The paper has no counterpart. */
+typedef struct pm_graph pm_graph;
+NUPM_API int pm_graph_begin(void* cuda_stream);
+NUPM_API int pm_graph_end(void* cuda_stream, pm_graph** out);
+NUPM_API int pm_graph_launch(pm_graph* graph, void* cuda_stream);
+NUPM_API int64_t pm_graph_nodes(const pm_graph* graph);
+NUPM_API void pm_graph_free(pm_graph* graph);
 
 /* ---- learned response surrogate ----
  * The paper has no learned part; this stands in for the response integral of

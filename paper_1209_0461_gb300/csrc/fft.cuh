@@ -41,23 +41,44 @@ __device__ __forceinline__ cx<T> cconj(cx<T> a) { return {a.x, -a.y}; }
 template <typename T>
 __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return {a.x * s, a.y * s}; }
 
-// a * exp(DIR * 2 pi i k / R) with a compile-time R and (after unrolling) k.
+// a * exp(DIR * 2 pi i k / R) with a compile-time R and (after unrolling) k;
+// R divides 64 or 192.
 template <int R, int DIR, typename T>
 __device__ __forceinline__ cx<T> twid_const(cx<T> a, int k) {
+  static_assert(64 % R == 0 || 192 % R == 0, "radix must divide 64 or 192");
   if (k == 0) return a;
   if (4 * k == R) return DIR < 0 ? cx<T>{a.y, -a.x} : cx<T>{-a.y, a.x};
-  const int j = k * (64 / R);
-  const T c = (T)cos64(j);
-  const T s = (T)DIR * (T)cos64(j + 48);   // sin(t) = cos(t + 3 pi / 2)
+  T c, s;
+  if constexpr (64 % R == 0) {
+    const int j = k * (64 / R);
+    c = (T)cos64(j);
+    s = (T)DIR * (T)cos64(j + 48);   // sin(t) = cos(t + 3 pi / 2)
+  } else {
+    const int j = k * (192 / R);
+    c = (T)cos192(j);
+    s = (T)DIR * (T)cos192(j + 144);
+  }
   return {a.x * c - a.y * s, a.x * s + a.y * c};
 }
 
-// In-register DFT of length R (power of two <= 64), recursive radix-2
-// decimation in time.  DIR = -1 forward (exp(-i...)), +1 inverse; unscaled.
+// In-register DFT of length R (2^k or 3 * 2^k, dividing 64 or 192), recursive
+// radix-2 decimation in time down to a radix-3 or radix-2 butterfly.
+// DIR = -1 forward (exp(-i...)), +1 inverse; unscaled.
 template <int R, int DIR, typename T>
 __device__ __forceinline__ void dft(cx<T>* v) {
   if constexpr (R == 1) {
     return;
+  } else if constexpr (R == 3) {
+    // w = exp(DIR 2 pi i / 3): X0 = a + b + c, X1 = a + b w + c w^2,
+    // X2 = a + b w^2 + c w^4 = a - (b + c)/2 -/+ DIR i (sqrt 3 / 2)(b - c)
+    const cx<T> a = v[0], b = v[1], c = v[2];
+    const cx<T> s = b + c, d = b - c;
+    const T h = (T)0.86602540378443864676;          // sqrt(3) / 2
+    const cx<T> m = {a.x - (T)0.5 * s.x, a.y - (T)0.5 * s.y};
+    const cx<T> r = {(T)(-DIR) * h * d.y, (T)DIR * h * d.x};   // DIR i h d
+    v[0] = a + s;
+    v[1] = m + r;
+    v[2] = m - r;
   } else if constexpr (R == 2) {
     const cx<T> a = v[0], b = v[1];
     v[0] = a + b;
@@ -114,6 +135,8 @@ NUPM_PLAN(float, 128, 16, 8, 1)
 NUPM_PLAN(float, 256, 16, 16, 1)
 NUPM_PLAN(float, 512, 32, 16, 1)
 NUPM_PLAN(float, 1024, 32, 32, 1)
+NUPM_PLAN(float, 96, 12, 4, 2)
+NUPM_PLAN(float, 192, 12, 4, 4)
 NUPM_PLAN(double, 8, 8, 1, 1)
 NUPM_PLAN(double, 16, 4, 4, 1)
 NUPM_PLAN(double, 32, 8, 4, 1)
@@ -122,6 +145,8 @@ NUPM_PLAN(double, 128, 16, 8, 1)
 NUPM_PLAN(double, 256, 16, 16, 1)
 NUPM_PLAN(double, 512, 16, 8, 4)
 NUPM_PLAN(double, 1024, 16, 16, 4)
+NUPM_PLAN(double, 96, 12, 4, 2)
+NUPM_PLAN(double, 192, 12, 4, 4)
 #undef NUPM_PLAN
 
 // ---------------------------------------------------------------------------
@@ -148,7 +173,7 @@ __device__ __forceinline__ void stockham_stage(cx<T> (&v)[E], const SM& sm, int 
 #pragma unroll
   for (int b = 0; b < E / R; ++b) {
     const int j = t + NT * b;
-    const int k = j & (NS - 1);
+    const int k = j % NS;
     if constexpr (NS > 1) {
 #pragma unroll
       for (int i = 1; i < R; ++i)
@@ -240,14 +265,17 @@ struct ColCfgW {
   // CTA's loads overlap another's math
   static constexpr int MIN_BLOCKS = (size_t)SMEM_WORDS * sizeof(cx<T>) <= 100 * 1024 ? 2 : 1;
 };
-// y passes: 64-byte row segments (>= 8 FP32 / 4 FP64 columns per tile)
+// Narrow tiles: 64-byte row segments (8 FP32 / 4 FP64 columns); wide tiles:
+// 128-byte segments.  Along z a step is an N*M-element stride, and 64-byte
+// segments there halve the achieved read bandwidth (measured on GB300), so
+// the z passes default to wide tiles from N >= 256 on, the y passes to narrow
+// ones; pm_autotune may pick either per pass.
 template <typename T, int N>
-struct ColCfg : ColCfgW<T, N, sizeof(T) == 4 ? 8 : 4> {};
-// z passes: a z step is an N*M-element stride, and 64-byte segments there
-// halve the achieved read bandwidth (measured on GB300); 128-byte segments
-// from N >= 256 on.
+struct ColNarrow : ColCfgW<T, N, sizeof(T) == 4 ? 8 : 4> {};
 template <typename T, int N>
-struct ColCfgZ : ColCfgW<T, N, (N >= 256 ? 2 : 1) * (sizeof(T) == 4 ? 8 : 4)> {};
+struct ColWide : ColCfgW<T, N, sizeof(T) == 4 ? 16 : 8> {};
+template <typename T, int N>
+struct ColCfg : ColNarrow<T, N> {};
 
 // Rows per CTA of the x pass.
 template <typename T, int N>
@@ -296,7 +324,7 @@ k_fft_col(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
 // (A + i B of the kx = 0 / N/2 planes, whose G differ) comes pre-multiplied
 // from plane0[ky][kz] (k_green_plane0).  grid = (M / W, N)
 // ---------------------------------------------------------------------------
-template <typename T, int N, class Cfg = ColCfgZ<T, N>>
+template <typename T, int N, class Cfg = ColWide<T, N>>
 __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MIN_BLOCKS)
 k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, cx<T>* __restrict__ out_dz,
                   const cx<T>* __restrict__ plane0, const T* __restrict__ gtab, const T* __restrict__ dtab,
@@ -381,12 +409,12 @@ k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, c
 // -i D(ky) is linear, so it acts on the packed column x2 = 0 as on the others.
 // grid = (M / W, N)
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(ColCfg<T, N>::THREADS, ColCfg<T, N>::MIN_BLOCKS)
+template <typename T, int N, class Cfg = ColCfg<T, N>>
+__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MIN_BLOCKS)
 k_fft_y_inv_grad(cx<T>* __restrict__ g_phi, cx<T>* __restrict__ g_dy, cx<T>* __restrict__ g_dz,
                  const T* __restrict__ dtab, const cx<T>* __restrict__ tw) {
-  using Cfg = ColCfg<T, N>;
-  constexpr int M = N / 2, E = Plan<T, N>::R1, NT = N / E, W = Cfg::W, RL = last_radix<T, N>();
+  using P = typename Cfg::P;
+  constexpr int M = N / 2, E = Cfg::E, NT = Cfg::NT, W = Cfg::W, RL = last_radix<T, N, P>();
   constexpr int64_t ES = M;   // element stride along y
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x % W;
@@ -408,7 +436,7 @@ k_fft_y_inv_grad(cx<T>* __restrict__ g_phi, cx<T>* __restrict__ g_dy, cx<T>* __r
       }
       v[i] = f;
     }
-    fft_regs<T, N, +1>(v, sm, t, tw);
+    fft_regs<T, N, +1, ColSmem<T, W, Cfg::PAD>, P>(v, sm, t, tw);
 #pragma unroll
     for (int b = 0; b < E / RL; ++b)
 #pragma unroll
@@ -543,7 +571,7 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
     const int lane = threadIdx.x;
     int len = 0, b0 = 0;
     if (lane < NSEG) {
-      const int sz = (tz0 - 1 + lane / 2) & (N - 1);
+      const int sz = (tz0 - 1 + lane / 2 + N) % N;
       int r0, r1;
       if (lane & 1) {            // main run of rows
         r0 = sz * N + (ty0 ? ty0 - 1 : 0);
@@ -578,8 +606,9 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
   unsigned int* accw = reinterpret_cast<unsigned int*>(acc);   // little endian: [2i] low, [2i+1] high
   // window rows: z planes tz0-1 .. tz0+TZ-1 (segment / 2), y rows ws .. ws+TY
   // (identified by the record's y cell mod 32; N >= 32 or the mask below)
+  static_assert(N < 32 || N % 32 == 0, "the y window is identified mod 32");
   constexpr int YM = (N < 32 ? N : 32) - 1;
-  const int ws = (ty0 - 1) & (N - 1);
+  const int ws = (ty0 - 1 + N) % N;
   constexpr int U = 4;
   for (int j0 = threadIdx.x; j0 < total; j0 += blockDim.x * U) {
     unsigned long long rr[U];
@@ -605,7 +634,7 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
       const unsigned wzz = (unsigned)(r >> 32) & 0xffffu;
       const int cx = (int)(r >> 48) & 0x7ff;
       const int yo = ((int)(r >> 59) - ws) & YM;      // 0 .. TY: row of the window
-      const int x1 = (cx + 1) & (N - 1);
+      const int x1 = cx + 1 == N ? 0 : cx + 1;
       // the particle's (up to) 8 corners in this tile: all low-word adds in
       // flight before any carry is needed
       int slot[8];
@@ -792,6 +821,7 @@ k_xinv_interp(const cx<T>* __restrict__ g, int64_t field_elems, const cx<T>* __r
               const cx<T>* __restrict__ tw_n, const T* __restrict__ dtab, const void* __restrict__ pos, int64_t np,
               double delta, const int* __restrict__ row_start, const int* __restrict__ perm, T* __restrict__ vel,
               T kick, T* __restrict__ acc_out, int* status) {
+  static_assert((N & (N - 1)) == 0, "the sliding-window gather needs a power-of-two grid");
   using Cfg = XiCfg<T, N>;
   constexpr int M = N / 2, E = Plan<T, M>::R1, NT = Cfg::NT, RL = last_radix<T, M>();
   constexpr int TZ = Cfg::TZ, SLAB = Cfg::SLAB, USED = Cfg::USED, LY = Cfg::LY;

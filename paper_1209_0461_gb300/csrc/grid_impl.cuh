@@ -18,32 +18,66 @@ constexpr int kSMs = 152;
 
 // Shared memory of the Green z pass: exchange buffer, fac table (FP32) and
 // the per-thread Green factors.
-template <int N>
+template <int N, class CC>
 constexpr size_t green_smem() {
-  using CC = ColCfgZ<T, N>;
   return (size_t)CC::SMEM_WORDS * sizeof(C) + (sizeof(T) == 4 ? kFacTable * sizeof(float) : 0) +
          (size_t)CC::E * CC::THREADS * sizeof(T);
+}
+template <class CC>
+constexpr size_t col_smem() {
+  return (size_t)CC::SMEM_WORDS * sizeof(C);
 }
 
 // Opt the FFT kernels of size N into their dynamic shared memory (once per
 // process; every kernel of this size gets its attribute on first use).
+template <int N, class CC>
+void col_attrs() {
+  cudaFuncSetAttribute(k_fft_col<T, N, -1, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem<CC>());
+  cudaFuncSetAttribute(k_fft_z_inv_green<T, N, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)green_smem<N, CC>());
+  cudaFuncSetAttribute(k_fft_y_inv_grad<T, N, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)col_smem<CC>());
+}
 template <int N>
 void ensure_attrs() {
   using RC = RowCfg<T, N>;
-  using CC = ColCfg<T, N>;
   static bool done = false;
   if (done) return;
   const int row_smem = (int)((size_t)RC::ROWS * RC::ROW_WORDS * sizeof(C));
-  const int col_smem = (int)((size_t)CC::SMEM_WORDS * sizeof(C));
   cudaFuncSetAttribute(k_fft_x_fwd<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
-  cudaFuncSetAttribute(k_fft_col<T, N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
-  cudaFuncSetAttribute(k_fft_col<T, N, -1, ColCfgZ<T, N>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)((size_t)ColCfgZ<T, N>::SMEM_WORDS * sizeof(C)));
   cudaFuncSetAttribute(k_fft_x_inv<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
-  cudaFuncSetAttribute(k_fft_z_inv_green<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)green_smem<N>());
-  cudaFuncSetAttribute(k_fft_y_inv_grad<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+  col_attrs<N, ColNarrow<T, N>>();
+  col_attrs<N, ColWide<T, N>>();
   done = true;
+}
+
+// Column passes with tile config CC: forward y / z, Green z, gradient y.
+template <int N, class CC>
+void col_pass(const GridArgs& g, int pass, cudaStream_t s) {
+  constexpr int M = N / 2;
+  const dim3 grid(M / CC::W, N, 1);
+  const C* twn = reinterpret_cast<const C*>(g.tw_n);
+  C* spec = reinterpret_cast<C*>(g.spec);
+  C* f = reinterpret_cast<C*>(g.g);
+  const int64_t fe = g.field_elems;
+  switch (pass) {
+    case kPassYFwd:
+      k_fft_col<T, N, -1, CC><<<grid, CC::THREADS, col_smem<CC>(), s>>>(spec, (int64_t)N * M, (int64_t)M, 0, twn);
+      break;
+    case kPassZFwd:
+      k_fft_col<T, N, -1, CC><<<grid, CC::THREADS, col_smem<CC>(), s>>>(spec, (int64_t)M, (int64_t)N * M, 0, twn);
+      break;
+    case kPassZInv:   // Green + z: spectrum -> g0 (phi), g2 (d/dz phi)
+      k_fft_z_inv_green<T, N, CC><<<grid, CC::THREADS, green_smem<N, CC>(), s>>>(
+          spec, f, f + 2 * fe, reinterpret_cast<const C*>(g.plane0), reinterpret_cast<const T*>(g.gtab),
+          reinterpret_cast<const T*>(g.dtab), reinterpret_cast<const T*>(g.wtab), twn, g.fac, g.fac_inv_du,
+          g.green_coeff);
+      break;
+    case kPassYInv:   // y with the y gradient: g0 -> g1 (d/dy), g0 -> g0, g2 -> g2
+      k_fft_y_inv_grad<T, N, CC><<<grid, CC::THREADS, col_smem<CC>(), s>>>(
+          f, f + fe, f + 2 * fe, reinterpret_cast<const T*>(g.dtab), twn);
+      break;
+  }
 }
 
 // TMA-pipelined column pass of size N.
@@ -77,6 +111,7 @@ void col_tma_n(const GridArgs& g, const CUtensorMap* map, cudaStream_t s) {
 // One FFT pass of size N (pass: kPassXFwd .. kPassXInv, see nupm_internal.h).
 template <int N>
 void fft_pass_n(const GridArgs& g, int pass, cudaStream_t s) {
+  if constexpr ((N & (N - 1)) == 0) {   // TMA column passes: power-of-two grids
   if (g.tmap_spec_y) {
     switch (pass) {
       case kPassYFwd: col_tma_n<N, kColFwdY>(g, g.tmap_spec_y, s); return;
@@ -86,53 +121,33 @@ void fft_pass_n(const GridArgs& g, int pass, cudaStream_t s) {
       default: break;
     }
   }
+  }
   constexpr int M = N / 2;
   using RC = RowCfg<T, N>;
-  using CC = ColCfg<T, N>;
   const size_t row_smem = (size_t)RC::ROWS * RC::ROW_WORDS * sizeof(C);
-  const size_t col_smem = (size_t)CC::SMEM_WORDS * sizeof(C);
   ensure_attrs<N>();
   const int64_t rows = (int64_t)N * N;
   const C* twn = reinterpret_cast<const C*>(g.tw_n);
   const C* twm = reinterpret_cast<const C*>(g.tw_m);
-  C* spec = reinterpret_cast<C*>(g.spec);
-  C* f = reinterpret_cast<C*>(g.g);
-  // y pass: columns (x2, z), element stride M; z pass: columns (x2, y), stride N M
+  (void)M;
   switch (pass) {
     case kPassXFwd:
       k_fft_x_fwd<T, N><<<(unsigned)(rows / RC::ROWS), RC::THREADS, row_smem, s>>>(
-          reinterpret_cast<const unsigned long long*>(g.g), spec, g.scale, twm, twn);
+          reinterpret_cast<const unsigned long long*>(g.g), reinterpret_cast<C*>(g.spec), g.scale, twm, twn);
       break;
-    case kPassYFwd:
-      k_fft_col<T, N, -1><<<dim3(M / CC::W, N, 1), CC::THREADS, col_smem, s>>>(spec, (int64_t)N * M, (int64_t)M, 0, twn);
-      break;
-    case kPassZFwd: {
-      using CZ = ColCfgZ<T, N>;
-      k_fft_col<T, N, -1, CZ><<<dim3(M / CZ::W, N, 1), CZ::THREADS, (size_t)CZ::SMEM_WORDS * sizeof(C), s>>>(
-          spec, (int64_t)M, (int64_t)N * M, 0, twn);
-      break;
-    }
-    case kPassZInv: {
-      // Green + z: spectrum -> g0 (phi), g2 (d/dz phi)
-      const int64_t fe = g.field_elems;
-      k_fft_z_inv_green<T, N><<<dim3(M / ColCfgZ<T, N>::W, N, 1), ColCfgZ<T, N>::THREADS, green_smem<N>(), s>>>(
-          spec, f, f + 2 * fe, reinterpret_cast<const C*>(g.plane0), reinterpret_cast<const T*>(g.gtab),
-          reinterpret_cast<const T*>(g.dtab), reinterpret_cast<const T*>(g.wtab), twn, g.fac, g.fac_inv_du,
-          g.green_coeff);
-      break;
-    }
-    case kPassYInv: {
-      // y with the y gradient: g0 -> g1 (d/dy), g0 -> g0, g2 -> g2
-      const int64_t fe = g.field_elems;
-      k_fft_y_inv_grad<T, N><<<dim3(M / CC::W, N, 1), CC::THREADS, col_smem, s>>>(
-          f, f + fe, f + 2 * fe, reinterpret_cast<const T*>(g.dtab), twn);
-      break;
-    }
     case kPassXInv:
       // x with the x gradient on field 0 (phi -> d/dx phi); fields 1, 2 as they are
       k_fft_x_inv<T, N><<<dim3((unsigned)(rows / RC::ROWS), 1, 3), RC::THREADS, row_smem, s>>>(
-          f, g.field_elems, twm, twn, reinterpret_cast<const T*>(g.dtab), 1);
+          reinterpret_cast<C*>(g.g), g.field_elems, twm, twn, reinterpret_cast<const T*>(g.dtab), 1);
       break;
+    default: {
+      // y passes narrow, z passes wide from N >= 256 on, unless tuned
+      const bool zpass = pass == kPassZFwd || pass == kPassZInv;
+      const int tuned = zpass ? g.wide_z : g.wide_y;
+      const bool wide = tuned >= 0 ? tuned == 1 : (zpass && N >= 256);
+      if (wide) col_pass<N, ColWide<T, N>>(g, pass, s);
+      else col_pass<N, ColNarrow<T, N>>(g, pass, s);
+    }
   }
 }
 
@@ -176,12 +191,13 @@ void xinv_interp_n(const GridArgs& g, const void* pos, void* vel, double kick, v
     case 256: fn<256>(g, pass, s); break;                  \
     case 512: fn<512>(g, pass, s); break;                  \
     case 1024: fn<1024>(g, pass, s); break;                \
+    case 192: fn<192>(g, pass, s); break;                  \
     default: return PM_ERR_UNSUPPORTED;                    \
   }
 
-int grid_blocks(int64_t work, int threads) {
+int grid_blocks(int64_t work, int threads, int ctas_per_sm = 16) {
   int64_t b = (work + threads - 1) / threads;
-  const int64_t cap = (int64_t)kSMs * 16;
+  const int64_t cap = (int64_t)kSMs * ctas_per_sm;
   if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (int)b;
@@ -204,7 +220,7 @@ int NUPM_FN(deposit)(const GridArgs& g, const void* pos, cudaStream_t s) {
 int NUPM_FN(row_sort)(const GridArgs& g, const void* pos, cudaStream_t s) {
   const int rows = g.n * g.n;
   cudaMemsetAsync(g.row_count, 0, (size_t)(rows + 1) * sizeof(int), s);
-  const int blocks = grid_blocks(g.np, 256);
+  const int blocks = grid_blocks(g.np, 256, g.part_ctas_per_sm);
   if (g.np > 0) k_row_count<T><<<blocks, 256, 0, s>>>(pos, g.np, g.n, g.delta, g.row_count, g.status);
   const int len = rows + 1;
   const int nb = (len + 2 * kScanBlock - 1) / (2 * kScanBlock);
@@ -224,6 +240,7 @@ int NUPM_FN(deposit_fft_x)(const GridArgs& g, const void* pos, bool keep, cudaSt
     case 256: deposit_fft_x_n<256>(g, pos, keep, s); break;
     case 512: deposit_fft_x_n<512>(g, pos, keep, s); break;
     case 1024: deposit_fft_x_n<1024>(g, pos, keep, s); break;
+    case 192: deposit_fft_x_n<192>(g, pos, keep, s); break;
     default: return PM_ERR_UNSUPPORTED;
   }
   return PM_OK;
@@ -262,7 +279,7 @@ int NUPM_FN(green)(const GridArgs& g, cudaStream_t s) {
 
 int NUPM_FN(interp)(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, cudaStream_t s) {
   if (g.np > 0)
-    k_interp_kick<T><<<grid_blocks(g.np, 256), 256, 0, s>>>(pos, g.np, g.n, g.delta, reinterpret_cast<const T*>(g.g),
+    k_interp_kick<T><<<grid_blocks(g.np, 256, g.part_ctas_per_sm), 256, 0, s>>>(pos, g.np, g.n, g.delta, reinterpret_cast<const T*>(g.g),
                                                            2 * g.field_elems, reinterpret_cast<T*>(vel), (T)kick,
                                                            reinterpret_cast<T*>(acc_out), g.status);
   return PM_OK;

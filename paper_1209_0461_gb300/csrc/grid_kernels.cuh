@@ -23,8 +23,14 @@ constexpr int kWeightOne = 1 << kWeightBits;
 // Record the first device-side error (status 0 -> code).
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
-// Periodic wrap onto [0, n), n a power of two (two's complement mask).
-__device__ __forceinline__ int wrap_index(long long c, int n) { return (int)(c & (long long)(n - 1)); }
+// Periodic wrap onto [0, n): a mask for powers of two, else the floored remainder.
+__device__ __forceinline__ int wrap_index(long long c, int n) {
+  if ((n & (n - 1)) == 0) return (int)(c & (long long)(n - 1));
+  const long long r = c % n;
+  return (int)(r < 0 ? r + n : r);
+}
+// (n - i) mod n for i in [0, n): the index of the Hermitian partner.
+__device__ __forceinline__ int partner_index(int i, int n) { return i == 0 ? 0 : n - i; }
 
 // Quantised particle: cell (wrapped) and 16-bit weight per axis.  load()
 // fetches the raw position words, get() turns them into (cell, weight) and
@@ -222,7 +228,7 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restri
               acc[nk + bb] += kf * sqrt((double)n2b);
             }
           } else {
-            const int jz = (n - iz) & (n - 1), jy = (n - iy) & (n - 1);
+            const int jz = partner_index(iz, n), jy = partner_index(iy, n);
             const cx<T> g = spec[((int64_t)jz * n + jy) * m];
             const T ax = (T)0.5 * (f[j].x + g.x), ay = (T)0.5 * (f[j].y - g.y);
             const T bx = (T)0.5 * (f[j].y + g.y), by = (T)-0.5 * (f[j].x - g.x);
@@ -294,7 +300,7 @@ __global__ void k_green_plane0(const cx<T>* __restrict__ spec, cx<T>* __restrict
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
     const int iy = idx / n, iz = idx - (idx / n) * n;    // plane0 layout [ky][kz]
     const int ky = signed_freq(iy, n), kz = signed_freq(iz, n);
-    const int jy = (n - iy) & (n - 1), jz = (n - iz) & (n - 1);
+    const int jy = partner_index(iy, n), jz = partner_index(iz, n);
     const cx<T> f = spec[((int64_t)iz * n + iy) * m];
     const cx<T> h = spec[((int64_t)jz * n + jy) * m];
     const cx<T> A = {(T)0.5 * (f.x + h.x), (T)0.5 * (f.y - h.y)};

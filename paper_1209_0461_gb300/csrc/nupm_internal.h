@@ -92,6 +92,10 @@ struct GridArgs {
   const float* fac;               // FP32 path: fac table (kFacTable points)
   float fac_inv_du;               // 1 / table spacing in u = ln sqrt(n^2)
   float green_coeff;              // -1.5 Omega_M / (a kf^2 N^3)
+  // tuning (pm_autotune): wide (1) or narrow (0) column tiles of the y and z
+  // passes, -1 = the built-in choice; CTAs per SM of the particle kernels
+  int wide_y = -1, wide_z = -1;
+  int part_ctas_per_sm = 16;
 };
 #define NUPM_DECLARE_GRID(SFX)                                                              \
   int deposit##SFX(const GridArgs& g, const void* pos, cudaStream_t s);                     \

@@ -10,6 +10,8 @@
 
 #include <cudaTypedefs.h>
 
+#include <initializer_list>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -71,6 +73,7 @@ struct pm_ctx {
   // state
   bool deposited = false, deposit_grid_valid = false, have_response = false, have_kick = false;
   bool power_set = false;         // bins replaced by pm_set_power (no spectrum behind them)
+  int wide_y = -1, wide_z = -1, part_cps = 16;   // tuning (pm_autotune)
   double* d_bins_lattice = nullptr;   // [2][nk] lattice count / ksum, restored after pm_set_power
   float* d_X = nullptr;           // [nk][12] surrogate features
   float* d_lnR = nullptr;         // [nk] surrogate output
@@ -338,6 +341,9 @@ int encode_col_map(pm_ctx* c, CUtensorMap* map, void* base, int fields, bool alo
 
 GridArgs grid_args(const pm_ctx* c) {
   GridArgs g;
+  g.wide_y = c->wide_y;
+  g.wide_z = c->wide_z;
+  g.part_ctas_per_sm = c->part_cps;
   g.n = c->n;
   g.np = c->np;
   g.box = c->box;
@@ -424,7 +430,10 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
     rc = code;
   };
   const int n = p.ngrid;
-  if (!(n >= 16 && n <= 1024 && (n & (n - 1)) == 0)) bad(PM_ERR_UNSUPPORTED, "ngrid must be a power of two in [16, 1024]");
+  const bool pow2 = n >= 16 && n <= 1024 && (n & (n - 1)) == 0;
+  if (!pow2 && n != 192) bad(PM_ERR_UNSUPPORTED, "ngrid must be a power of two in [16, 1024] or 192");
+  else if (!pow2 && (p.flags & (PM_TMA_COLUMNS | PM_FUSED_GATHER)))
+    bad(PM_ERR_UNSUPPORTED, "PM_TMA_COLUMNS / PM_FUSED_GATHER need a power-of-two grid");
   else if (p.npart < 1) bad(PM_ERR_INVALID, "npart must be >= 1");
   else if (p.npart > 0x7fffffffLL) bad(PM_ERR_INVALID, "npart must be < 2^31");
   else if (!finite_pos(p.box)) bad(PM_ERR_INVALID, "box must be finite and > 0");
@@ -1063,5 +1072,135 @@ int pm_get_timing(pm_ctx* c, double* ms, int64_t* launches, int64_t* calls) {
 }
 
 int64_t pm_device_bytes(const pm_ctx* c) { return c ? c->bytes : 0; }
+
+int pm_autotune(pm_ctx* c, const void* pos, void* vel, double a, const double* a_hist, const double* sqrtPM_hist,
+                int32_t n_hist, int32_t reps, int32_t* tuned) {
+  if (!c) return PM_ERR_INVALID;
+  if (!pos || !vel) return fail(c, PM_ERR_INVALID, "pm_autotune: pos/vel is NULL");
+  if (reps < 1) return fail(c, PM_ERR_INVALID, "pm_autotune: reps must be >= 1");
+  const bool was_timing = c->timing;
+  // total ms of the given stages over `reps` kicks (kick factor 0: velocities unchanged)
+  auto measure = [&](std::initializer_list<int> stages, double* out) -> int {
+    int rc = pm_timing(c, 1);
+    for (int r = 0; r < reps && rc == PM_OK; ++r) {
+      rc = pm_deposit(c, pos);
+      if (rc == PM_OK) rc = pm_nu_response(c, a, a_hist, sqrtPM_hist, n_hist, nullptr, nullptr, nullptr, nullptr);
+      if (rc == PM_OK) rc = pm_kick(c, pos, vel, a, 0.0, nullptr);
+    }
+    if (rc != PM_OK) return rc;
+    double ms[PM_NSTAGES];
+    rc = pm_get_timing(c, ms, nullptr, nullptr);
+    double t = 0.0;
+    for (int s : stages) t += ms[s];
+    *out = t;
+    return rc;
+  };
+  int rc = PM_OK;
+  double t0 = 0.0, t1 = 0.0;
+  rc = measure({PM_ST_FFT_Y_FWD}, &t0);   // warm-up: attributes, tables
+  // column tiles of the y passes, then of the z passes
+  for (int pass = 0; pass < 2 && rc == PM_OK; ++pass) {
+    int& knob = pass == 0 ? c->wide_y : c->wide_z;
+    const std::initializer_list<int> st = pass == 0 ? std::initializer_list<int>{PM_ST_FFT_Y_FWD, PM_ST_FFT_Y_INV}
+                                                    : std::initializer_list<int>{PM_ST_FFT_Z_FWD, PM_ST_FFT_Z_INV};
+    knob = 0;
+    rc = measure(st, &t0);
+    if (rc != PM_OK) break;
+    knob = 1;
+    rc = measure(st, &t1);
+    if (rc != PM_OK) break;
+    knob = t1 < t0 ? 1 : 0;
+  }
+  // CTAs per SM of the particle kernels (row sort, gather + kick)
+  if (rc == PM_OK) {
+    const int cand[4] = {4, 8, 16, 32};
+    double best = 1e300;
+    int best_c = 16;
+    for (int i = 0; i < 4 && rc == PM_OK; ++i) {
+      c->part_cps = cand[i];
+      double t = 0.0;
+      rc = measure({PM_ST_DEPOSIT, PM_ST_INTERP}, &t);
+      if (t < best) {
+        best = t;
+        best_c = cand[i];
+      }
+    }
+    c->part_cps = best_c;
+  }
+  const int rc2 = pm_timing(c, was_timing ? 1 : 0);
+  if (rc != PM_OK) return rc;
+  if (rc2 != PM_OK) return rc2;
+  c->have_response = false;   // the tuning kicks used a response the caller did not ask for
+  if (tuned) {
+    tuned[0] = c->wide_y;
+    tuned[1] = c->wide_z;
+    tuned[2] = c->part_cps;
+  }
+  return PM_OK;
+}
+
+int pm_set_tuning(pm_ctx* c, const int32_t* tuned) {
+  if (!c || !tuned) return PM_ERR_INVALID;
+  if (tuned[0] < -1 || tuned[0] > 1 || tuned[1] < -1 || tuned[1] > 1 || tuned[2] < 1 || tuned[2] > 64)
+    return fail(c, PM_ERR_INVALID, "pm_set_tuning: wide_y, wide_z in -1..1, ctas_per_sm in 1..64");
+  c->wide_y = tuned[0];
+  c->wide_z = tuned[1];
+  c->part_cps = tuned[2];
+  return PM_OK;
+}
+
+// ---- CUDA graphs of whole kicks ----
+struct GraphHolder {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+int pm_graph_begin(void* stream) {
+  const cudaError_t e = cudaStreamBeginCapture(static_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal);
+  return e == cudaSuccess ? PM_OK : PM_ERR_CUDA;
+}
+
+int pm_graph_end(void* stream, pm_graph** out) {
+  if (!out) return PM_ERR_INVALID;
+  *out = nullptr;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(static_cast<cudaStream_t>(stream), &g) != cudaSuccess || !g) return PM_ERR_CUDA;
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return PM_ERR_CUDA;
+  }
+  GraphHolder* h = new (std::nothrow) GraphHolder;
+  if (!h) {
+    cudaGraphExecDestroy(ex);
+    cudaGraphDestroy(g);
+    return PM_ERR_ALLOC;
+  }
+  h->graph = g;
+  h->exec = ex;
+  *out = reinterpret_cast<pm_graph*>(h);
+  return PM_OK;
+}
+
+int pm_graph_launch(pm_graph* g, void* stream) {
+  if (!g) return PM_ERR_INVALID;
+  GraphHolder* h = reinterpret_cast<GraphHolder*>(g);
+  return cudaGraphLaunch(h->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? PM_OK : PM_ERR_CUDA;
+}
+
+int64_t pm_graph_nodes(const pm_graph* g) {
+  if (!g) return 0;
+  size_t n = 0;
+  cudaGraphGetNodes(reinterpret_cast<const GraphHolder*>(g)->graph, nullptr, &n);
+  return (int64_t)n;
+}
+
+void pm_graph_free(pm_graph* g) {
+  if (!g) return;
+  GraphHolder* h = reinterpret_cast<GraphHolder*>(g);
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  delete h;
+}
 
 }  // extern "C"

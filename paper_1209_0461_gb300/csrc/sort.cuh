@@ -23,7 +23,7 @@ template <>
 struct RowKey<float> {
   __device__ static __forceinline__ int get(const void* pos, int64_t np, int64_t p, int n, double) {
     const int32_t* q = reinterpret_cast<const int32_t*>(pos);
-    const int cy = q[np + p] & (n - 1), cz = q[2 * np + p] & (n - 1);
+    const int cy = wrap_index(q[np + p], n), cz = wrap_index(q[2 * np + p], n);
     const float ox = __int_as_float(q[3 * np + p]);
     const float oy = __int_as_float(q[4 * np + p]), oz = __int_as_float(q[5 * np + p]);
     if (!(ox >= 0.0f && ox < 1.0f && oy >= 0.0f && oy < 1.0f && oz >= 0.0f && oz < 1.0f)) return -1;

@@ -86,6 +86,13 @@ def lib():
         "pm_response_features": (C.c_int, [vp, d, dp, vp, i32, vp]),
         "pm_nu_response_mlp": (C.c_int, [vp, vp, d, dp, vp, i32, vp, vp, vp]),
         "pm_set_power": (C.c_int, [vp, dp, dp, dp]),
+        "pm_autotune": (C.c_int, [vp, vp, vp, d, dp, vp, i32, i32, C.POINTER(C.c_int32)]),
+        "pm_set_tuning": (C.c_int, [vp, C.POINTER(C.c_int32)]),
+        "pm_graph_begin": (C.c_int, [vp]),
+        "pm_graph_end": (C.c_int, [vp, C.POINTER(vp)]),
+        "pm_graph_launch": (C.c_int, [vp, vp]),
+        "pm_graph_nodes": (i64, [vp]),
+        "pm_graph_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -263,6 +270,20 @@ class PM:
             raise ValueError("count, ksum, psum must hold n_kbins values")
         self._ok(lib().pm_set_power(self.ctx, *(_dptr(x) for x in arrs)), "pm_set_power")
 
+    # -- tuning
+    def autotune(self, pos, vel, a, a_hist, sqrtPM_hist, reps=2):
+        """pm_autotune: returns (wide_y, wide_z, ctas_per_sm)."""
+        self._check_pos(pos)
+        ah, n = self._history(a_hist, sqrtPM_hist)
+        t = (C.c_int32 * 3)()
+        self._ok(lib().pm_autotune(self.ctx, _tptr(pos), _tptr(vel), float(a), _dptr(ah) if n else None,
+                                   _tptr(sqrtPM_hist) if n else None, n, int(reps), t), "pm_autotune")
+        return tuple(int(x) for x in t)
+
+    def set_tuning(self, wide_y=-1, wide_z=-1, ctas_per_sm=16):
+        t = (C.c_int32 * 3)(int(wide_y), int(wide_z), int(ctas_per_sm))
+        self._ok(lib().pm_set_tuning(self.ctx, t), "pm_set_tuning")
+
     # -- background
     def kick_factor(self, a0, a1):
         return lib().pm_kick_factor(self.ctx, float(a0), float(a1))
@@ -395,6 +416,48 @@ class MLP:
     def close(self):
         if getattr(self, "handle", None):
             lib().pm_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """A captured CUDA graph of pm_* calls (pm_graph_begin .. pm_graph_end)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    @staticmethod
+    def capture(stream, fn):
+        """Capture everything fn() issues on `stream` (and streams joined to it)."""
+        L = lib()
+        rc = L.pm_graph_begin(C.c_void_p(stream.cuda_stream))
+        if rc != PM_OK:
+            raise PMError(rc, "pm_graph_begin")
+        try:
+            fn()
+        finally:
+            h = C.c_void_p()
+            rc = L.pm_graph_end(C.c_void_p(stream.cuda_stream), C.byref(h))
+        if rc != PM_OK:
+            raise PMError(rc, "pm_graph_end")
+        return Graph(h)
+
+    def launch(self, stream):
+        rc = lib().pm_graph_launch(self.handle, C.c_void_p(stream.cuda_stream))
+        if rc != PM_OK:
+            raise PMError(rc, "pm_graph_launch")
+
+    def nodes(self):
+        return int(lib().pm_graph_nodes(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pm_graph_free(self.handle)
             self.handle = None
 
     def __del__(self):
