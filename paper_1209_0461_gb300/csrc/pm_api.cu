@@ -10,7 +10,6 @@
 
 #include <cudaTypedefs.h>
 
-#include <initializer_list>
 #include <new>
 #include <string>
 #include <vector>
@@ -1080,7 +1079,7 @@ int pm_autotune(pm_ctx* c, const void* pos, void* vel, double a, const double* a
   if (reps < 1) return fail(c, PM_ERR_INVALID, "pm_autotune: reps must be >= 1");
   const bool was_timing = c->timing;
   // total ms of the given stages over `reps` kicks (kick factor 0: velocities unchanged)
-  auto measure = [&](std::initializer_list<int> stages, double* out) -> int {
+  auto measure = [&](const int* stages, int n_stages, double* out) -> int {
     int rc = pm_timing(c, 1);
     for (int r = 0; r < reps && rc == PM_OK; ++r) {
       rc = pm_deposit(c, pos);
@@ -1091,23 +1090,25 @@ int pm_autotune(pm_ctx* c, const void* pos, void* vel, double a, const double* a
     double ms[PM_NSTAGES];
     rc = pm_get_timing(c, ms, nullptr, nullptr);
     double t = 0.0;
-    for (int s : stages) t += ms[s];
+    for (int i = 0; i < n_stages; ++i) t += ms[stages[i]];
     *out = t;
     return rc;
   };
+  static const int kStY[2] = {PM_ST_FFT_Y_FWD, PM_ST_FFT_Y_INV};
+  static const int kStZ[2] = {PM_ST_FFT_Z_FWD, PM_ST_FFT_Z_INV};
+  static const int kStP[2] = {PM_ST_DEPOSIT, PM_ST_INTERP};
   int rc = PM_OK;
   double t0 = 0.0, t1 = 0.0;
-  rc = measure({PM_ST_FFT_Y_FWD}, &t0);   // warm-up: attributes, tables
+  rc = measure(kStY, 1, &t0);   // warm-up: attributes, tables
   // column tiles of the y passes, then of the z passes
   for (int pass = 0; pass < 2 && rc == PM_OK; ++pass) {
     int& knob = pass == 0 ? c->wide_y : c->wide_z;
-    const std::initializer_list<int> st = pass == 0 ? std::initializer_list<int>{PM_ST_FFT_Y_FWD, PM_ST_FFT_Y_INV}
-                                                    : std::initializer_list<int>{PM_ST_FFT_Z_FWD, PM_ST_FFT_Z_INV};
+    const int* st = pass == 0 ? kStY : kStZ;
     knob = 0;
-    rc = measure(st, &t0);
+    rc = measure(st, 2, &t0);
     if (rc != PM_OK) break;
     knob = 1;
-    rc = measure(st, &t1);
+    rc = measure(st, 2, &t1);
     if (rc != PM_OK) break;
     knob = t1 < t0 ? 1 : 0;
   }
@@ -1119,7 +1120,7 @@ int pm_autotune(pm_ctx* c, const void* pos, void* vel, double a, const double* a
     for (int i = 0; i < 4 && rc == PM_OK; ++i) {
       c->part_cps = cand[i];
       double t = 0.0;
-      rc = measure({PM_ST_DEPOSIT, PM_ST_INTERP}, &t);
+      rc = measure(kStP, 2, &t);
       if (t < best) {
         best = t;
         best_c = cand[i];
