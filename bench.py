@@ -181,6 +181,27 @@ def run_oracle_kick(s):
 
 
 # ------------------------------------------------------------------ GPU arm
+def replica(w, rank):
+    """The box rank r runs: the same workload with seed + r (replicas only:
+    boxes are independent, no collective on the data path)."""
+    return synth.with_(w, seed=w.seed + rank)
+
+
+def max_over_ranks(x, world, device=None):
+    """The slowest rank's value (the job's time); x itself with one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Units all ranks processed per second, timed by the slowest rank."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def run_gpu(args, w, rank, world):
     import torch
     from paper_1209_0461_gb300 import build as b
@@ -188,7 +209,7 @@ def run_gpu(args, w, rank, world):
     b.build()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    wr = synth.with_(w, seed=w.seed + rank)
+    wr = replica(w, rank)
     t0 = time.time()
     parts = synth.particles(wr)
     a_hist, hist = synth.history(wr)
@@ -242,11 +263,7 @@ def run_gpu(args, w, rank, world):
     stages = pm.get_timing()
     pm.timing(False)
     pm.check()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
     # end to end through the same API with host buffers: H2D positions and
     # velocities, the kick, D2H velocities, every step
     e2e = None
@@ -267,14 +284,10 @@ def run_gpu(args, w, rank, world):
             vel_out.copy_(vel, non_blocking=True)
         e1.record(stream)
         barrier()
-        ems = e0.elapsed_time(e1) / args.steps
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
         bi = pos_h.numel() * pos_h.element_size() + vel_h.numel() * vel_h.element_size()
         bo = vel_out.numel() * vel_out.element_size()
-        e2e = {"value": world * wr.npart / (ems / 1e3), "unit": "particle-kicks/s",
+        e2e = {"value": whole_job_rate(wr.npart, world, ems), "unit": "particle-kicks/s",
                "ms_per_step": ems, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
     # roofline of the dominant kernel (largest total time among the HBM passes)
     hbm, peak_kind = peaks()
@@ -294,7 +307,7 @@ def run_gpu(args, w, rank, world):
     total_launch = sum(v[1] for v in stages.values())
     step_alg = sum(stage_bytes(wr, k, fused) * (v[2] if k in ("deposit", "bins") else v[1])
                    for k, v in stages.items() if k != "response") / args.steps
-    res = dict(value=world * wr.npart / (ms / 1e3), ms_per_step=ms, e2e=e2e, roofline=roof,
+    res = dict(value=whole_job_rate(wr.npart, world, ms), ms_per_step=ms, e2e=e2e, roofline=roof,
                stages={k: {"ms_per_step": round(v[0] / args.steps, 4), "launches_per_step": v[1] // args.steps}
                        for k, v in stages.items()},
                gpu_launches=int(total_launch), clocks=clk.summary(), gen_s=round(gen_s, 1),
