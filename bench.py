@@ -247,6 +247,11 @@ def run_gpu(args, w, rank, world):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    tuning = None
+    if not args.no_autotune:
+        # kick factor 0 inside: velocities unchanged
+        tuning = list(pm.autotune(pos, vel, a, a_hist, hist_d, reps=2))
+
     for _ in range(args.warmup):
         step(pos, vel)
     pm.check()
@@ -310,7 +315,7 @@ def run_gpu(args, w, rank, world):
     res = dict(value=whole_job_rate(wr.npart, world, ms), ms_per_step=ms, e2e=e2e, roofline=roof,
                stages={k: {"ms_per_step": round(v[0] / args.steps, 4), "launches_per_step": v[1] // args.steps}
                        for k, v in stages.items()},
-               gpu_launches=int(total_launch), clocks=clk.summary(), gen_s=round(gen_s, 1),
+               gpu_launches=int(total_launch), clocks=clk.summary(), gen_s=round(gen_s, 1), tuning=tuning,
                step_alg_gb=round(step_alg / 1e9, 2),
                step_frac=round(step_alg / (ms / 1e3) / 1e9 / hbm, 4),
                device_bytes=pm.device_bytes())
@@ -495,6 +500,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64 / surrogate comparisons")
+    ap.add_argument("--no-autotune", action="store_true", help="built-in tile choices instead of pm_autotune")
     args = ap.parse_args()
     w = synth.WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -552,7 +558,7 @@ def main():
     line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"], e2e=res["e2e"],
                 roofline=res["roofline"], cpu_baseline=cpu, gpu_launches=res["gpu_launches"],
                 clocks=res["clocks"], step_model_gb=res["step_alg_gb"], step_hbm_frac=res["step_frac"],
-                stages_ms=res["stages"], forms=forms)
+                stages_ms=res["stages"], tuning=res["tuning"], forms=forms)
     print(json.dumps(line))
     if world > 1:
         import torch

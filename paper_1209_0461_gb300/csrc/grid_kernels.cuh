@@ -23,7 +23,13 @@ constexpr int kWeightOne = 1 << kWeightBits;
 // Record the first device-side error (status 0 -> code).
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
-// Periodic wrap onto [0, n): a mask for powers of two, else the floored remainder.
+// Periodic wrap onto [0, n): a mask for powers of two, else the floored
+// remainder (32-bit for int cells, 64-bit only for FP64 cell numbers).
+__device__ __forceinline__ int wrap_index(int c, int n) {
+  if ((n & (n - 1)) == 0) return c & (n - 1);
+  const int r = c % n;
+  return r < 0 ? r + n : r;
+}
 __device__ __forceinline__ int wrap_index(long long c, int n) {
   if ((n & (n - 1)) == 0) return (int)(c & (long long)(n - 1));
   const long long r = c % n;
@@ -86,7 +92,7 @@ struct Quant<float> {    // int32 words [6][np]: cells rows 0-2, FP32 offsets ro
       const float o = __int_as_float(r.q[3 + d]);
       if (!(o >= 0.0f && o < 1.0f)) return false;
       w[d] = (int)floorf(o * (float)kWeightOne);       // exact scaling by 2^16
-      c[d] = wrap_index((long long)r.q[d], n);
+      c[d] = wrap_index((int)r.q[d], n);
     }
     return true;
   }

@@ -19,23 +19,35 @@ namespace nupm {
 template <typename T>
 struct RowKey;
 
+// load() fetches the words the key needs (all of a batch's loads go out before
+// any key is computed), key() turns them into the row.
 template <>
 struct RowKey<float> {
-  __device__ static __forceinline__ int get(const void* pos, int64_t np, int64_t p, int n, double) {
+  struct Raw {
+    int32_t cy, cz, ox, oy, oz;
+  };
+  __device__ static __forceinline__ Raw load(const void* pos, int64_t np, int64_t p) {
     const int32_t* q = reinterpret_cast<const int32_t*>(pos);
-    const int cy = wrap_index(q[np + p], n), cz = wrap_index(q[2 * np + p], n);
-    const float ox = __int_as_float(q[3 * np + p]);
-    const float oy = __int_as_float(q[4 * np + p]), oz = __int_as_float(q[5 * np + p]);
+    return Raw{q[np + p], q[2 * np + p], q[3 * np + p], q[4 * np + p], q[5 * np + p]};
+  }
+  __device__ static __forceinline__ int key(const Raw& r, int n, double) {
+    const float ox = __int_as_float(r.ox), oy = __int_as_float(r.oy), oz = __int_as_float(r.oz);
     if (!(ox >= 0.0f && ox < 1.0f && oy >= 0.0f && oy < 1.0f && oz >= 0.0f && oz < 1.0f)) return -1;
-    return cz * n + cy;
+    return wrap_index(r.cz, n) * n + wrap_index(r.cy, n);
   }
 };
 
 template <>
 struct RowKey<double> {
-  __device__ static __forceinline__ int get(const void* pos, int64_t np, int64_t p, int n, double delta) {
+  struct Raw {
+    double x, y, z;
+  };
+  __device__ static __forceinline__ Raw load(const void* pos, int64_t np, int64_t p) {
     const double* x = reinterpret_cast<const double*>(pos);
-    const double ux = x[p] / delta, uy = x[np + p] / delta, uz = x[2 * np + p] / delta;
+    return Raw{x[p], x[np + p], x[2 * np + p]};
+  }
+  __device__ static __forceinline__ int key(const Raw& r, int n, double delta) {
+    const double ux = r.x / delta, uy = r.y / delta, uz = r.z / delta;
     if (!(fabs(ux) < 4503599627370496.0 && fabs(uy) < 4503599627370496.0 && fabs(uz) < 4503599627370496.0))
       return -1;
     const int cy = wrap_index((long long)floor(uy), n), cz = wrap_index((long long)floor(uz), n);
@@ -64,11 +76,17 @@ __global__ void k_row_count(const void* __restrict__ pos, int64_t np, int n, dou
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x * U;
   for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U; base < np; base += stride) {
+    typename RowKey<T>::Raw raw[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = base + u * 32 + lane;
+      if (p < np) raw[u] = RowKey<T>::load(pos, np, p);
+    }
     int key[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t p = base + u * 32 + lane;
-      key[u] = p < np ? RowKey<T>::get(pos, np, p, n, delta) : -2;
+      key[u] = p < np ? RowKey<T>::key(raw[u], n, delta) : -2;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
