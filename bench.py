@@ -269,24 +269,45 @@ def run_gpu(args, w, rank, world):
     pm.timing(False)
     pm.check()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
-    # end to end through the same API with host buffers: H2D positions and
-    # velocities, the kick, D2H velocities, every step
+    # end to end through the same API with host buffers: every step copies its
+    # positions and velocities in from pinned host memory, kicks, and copies the
+    # velocities out.  Copies run on their own streams with two device buffer
+    # pairs, so step i+1's inputs travel while step i kicks.
     e2e = None
     if not args.no_e2e:
         vel_out = torch.empty_like(vel_h).pin_memory()
-        for _ in range(1):
-            pos.copy_(pos_h, non_blocking=True)
-            vel.copy_(vel_h, non_blocking=True)
-            step(pos, vel)
-            vel_out.copy_(vel, non_blocking=True)
+        h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+        bufs = [(pos, vel), (torch.empty_like(pos), torch.empty_like(vel))]
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_done = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
+
+        def e2e_steps(n):
+            start = torch.cuda.Event()
+            start.record(stream)                     # no copy starts before this point
+            h2d.wait_event(start)
+            for i in range(n):
+                b = i % 2
+                p_, v_ = bufs[b]
+                h2d.wait_event(ev_out[b])            # buffer b's previous result is out
+                with torch.cuda.stream(h2d):
+                    p_.copy_(pos_h, non_blocking=True)
+                    v_.copy_(vel_h, non_blocking=True)
+                ev_in[b].record(h2d)
+                stream.wait_event(ev_in[b])
+                step(p_, v_)
+                ev_done[b].record(stream)
+                d2h.wait_event(ev_done[b])
+                with torch.cuda.stream(d2h):
+                    vel_out.copy_(v_, non_blocking=True)
+                ev_out[b].record(d2h)
+            stream.wait_event(ev_out[(n - 1) % 2])
+
+        e2e_steps(2)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
-            pos.copy_(pos_h, non_blocking=True)
-            vel.copy_(vel_h, non_blocking=True)
-            step(pos, vel)
-            vel_out.copy_(vel, non_blocking=True)
+        e2e_steps(args.steps)
         e1.record(stream)
         barrier()
         ems = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)

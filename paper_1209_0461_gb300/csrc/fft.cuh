@@ -567,6 +567,9 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
   const int ty0 = blockIdx.x * TY, tz0 = blockIdx.y * TZ;
   for (int i = threadIdx.x; i < ROWS * N / 2; i += blockDim.x)
     reinterpret_cast<ulonglong2*>(acc)[i] = ulonglong2{0ull, 0ull};
+  // lanes of the (first) warp: all 32, or the whole block when it is smaller
+  static_assert(Cfg::THREADS < 32 || Cfg::THREADS % 32 == 0, "whole warps or a single partial warp");
+  const unsigned wm = Cfg::THREADS >= 32 ? 0xffffffffu : ((1u << Cfg::THREADS) - 1u);
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     int len = 0, b0 = 0;
@@ -586,7 +589,7 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
     int incl = len;
 #pragma unroll
     for (int d = 1; d < 8; d <<= 1) {
-      const int o = __shfl_up_sync(0xffffffffu, incl, d);
+      const int o = __shfl_up_sync(wm, incl, d);
       if (lane >= d) incl += o;
     }
     if (lane < NSEG) {
