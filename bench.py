@@ -276,25 +276,30 @@ def run_gpu(args, w, rank, world):
     e2e = None
     if not args.no_e2e:
         vel_out = torch.empty_like(vel_h).pin_memory()
-        h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+        # the inputs travel as 4 pieces on 4 streams (several copy engines)
+        h2d = [torch.cuda.Stream() for _ in range(4)]
+        d2h = torch.cuda.Stream()
         bufs = [(pos, vel), (torch.empty_like(pos), torch.empty_like(vel))]
-        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_in = [[torch.cuda.Event() for _ in h2d] for _ in range(2)]
         ev_done = [torch.cuda.Event() for _ in range(2)]
         ev_out = [torch.cuda.Event() for _ in range(2)]
+        pieces_h = list(pos_h.view(-1).chunk(3)) + [vel_h.view(-1)]
 
         def e2e_steps(n):
             start = torch.cuda.Event()
             start.record(stream)                     # no copy starts before this point
-            h2d.wait_event(start)
+            for hs in h2d:
+                hs.wait_event(start)
             for i in range(n):
                 b = i % 2
                 p_, v_ = bufs[b]
-                h2d.wait_event(ev_out[b])            # buffer b's previous result is out
-                with torch.cuda.stream(h2d):
-                    p_.copy_(pos_h, non_blocking=True)
-                    v_.copy_(vel_h, non_blocking=True)
-                ev_in[b].record(h2d)
-                stream.wait_event(ev_in[b])
+                pieces_d = list(p_.view(-1).chunk(3)) + [v_.view(-1)]
+                for hs, src, dst, ev in zip(h2d, pieces_h, pieces_d, ev_in[b]):
+                    hs.wait_event(ev_out[b])         # buffer b's previous result is out
+                    with torch.cuda.stream(hs):
+                        dst.copy_(src, non_blocking=True)
+                    ev.record(hs)
+                    stream.wait_event(ev)
                 step(p_, v_)
                 ev_done[b].record(stream)
                 d2h.wait_event(ev_done[b])
