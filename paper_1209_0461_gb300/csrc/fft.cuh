@@ -514,9 +514,9 @@ k_fft_x_fwd(const unsigned long long* __restrict__ grid, cx<T>* __restrict__ spe
 
 // ---------------------------------------------------------------------------
 // Fused a1 + forward x pass.  A CTA owns TZ x TY grid rows (z, y): it
-// deposits every particle of the (TZ+1) x (TY+1) source rows that touch them
-// (rows sorted by k_row_scatter) into a shared-memory int64 tile with 64-bit
-// shared atomics, then transforms those rows exactly as k_fft_x_fwd.  No
+// deposits every particle record of the (TZ+1) x (TY+1) source rows that
+// touch them (sorted into rows by k_row_scatter) into a shared-memory tile of
+// exact 64-bit sums, then transforms those rows exactly as k_fft_x_fwd.  No
 // global deposit grid, no memset, no atomics to DRAM.  With `keep` set the
 // tile is also written out (inspection).  grid = (N / TY, N / TZ).
 // ---------------------------------------------------------------------------
@@ -529,7 +529,6 @@ struct FusedCfg {
   static constexpr int E = P::R1;
   static constexpr int NT = M / E;
   static constexpr int THREADS = ROWS * NT;
-  static constexpr int SRC = (TZ + 1) * (TY + 1);
   static constexpr size_t ACC_BYTES = (size_t)ROWS * N * 8;
   static constexpr size_t XCH_BYTES = (size_t)ROWS * RowSmem<T>::words(M) * sizeof(cx<T>);
   static constexpr size_t SMEM = (ACC_BYTES > XCH_BYTES ? ACC_BYTES : XCH_BYTES);

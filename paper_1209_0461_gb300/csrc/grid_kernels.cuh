@@ -247,40 +247,24 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restri
         }
         if (b < 0) v0 = v1 = 0;
         __syncwarp();
-        // a chunk inside one bin (most chunks at high k): one butterfly sum
-        bool one_bin = false;
-        if constexpr (!LATTICE) {
-          const int bf = __shfl_sync(full, b, 0);
-          one_bin = bf >= 0 && __all_sync(full, b == bf);
-          if (one_bin) {
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v0 += __shfl_xor_sync(full, v0, off);
-            if (lane == 0) {
-              if constexpr (ROWF) racc[bf] += (float)v0;
-              else acc[bf] += (double)v0;
-            }
+        for (int off = 1; off < 32; off <<= 1) {
+          const A p0 = __shfl_up_sync(full, v0, off);
+          A p1 = 0;
+          if constexpr (LATTICE) p1 = __shfl_up_sync(full, v1, off);
+          const int b2 = __shfl_up_sync(full, b, off);
+          if (lane >= off && b2 == b) {
+            v0 += p0;
+            if constexpr (LATTICE) v1 += p1;
           }
         }
-        if (!one_bin) {   // warp-uniform
-#pragma unroll
-          for (int off = 1; off < 32; off <<= 1) {
-            const A p0 = __shfl_up_sync(full, v0, off);
-            A p1 = 0;
-            if constexpr (LATTICE) p1 = __shfl_up_sync(full, v1, off);
-            const int b2 = __shfl_up_sync(full, b, off);
-            if (lane >= off && b2 == b) {
-              v0 += p0;
-              if constexpr (LATTICE) v1 += p1;
-            }
-          }
-          const int bn = __shfl_down_sync(full, b, 1);
-          if (b >= 0 && (lane == 31 || bn != b)) {
-            if constexpr (ROWF) {
-              racc[b] += (float)v0;
-            } else {
-              acc[b] += (double)v0;
-              if constexpr (LATTICE) acc[nk + b] += (double)v1;
-            }
+        const int bn = __shfl_down_sync(full, b, 1);
+        if (b >= 0 && (lane == 31 || bn != b)) {
+          if constexpr (ROWF) {
+            racc[b] += (float)v0;
+          } else {
+            acc[b] += (double)v0;
+            if constexpr (LATTICE) acc[nk + b] += (double)v1;
           }
         }
         __syncwarp();
