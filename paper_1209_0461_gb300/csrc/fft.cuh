@@ -557,7 +557,7 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
   constexpr int TZ = Cfg::TZ, TY = Cfg::TY, ROWS = Cfg::ROWS, M = N / 2, E = Cfg::E, NT = Cfg::NT;
   constexpr int RL = last_radix<T, M, P>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);   // [ROWS][N]
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);   // 2 x [ROWS][N] words
   // The source rows (tz0-1 .. tz0+TZ-1) x (ty0-1 .. ty0+TY-1) are, per z, one
   // contiguous run of the row-sorted permutation, plus the wrapped row y = N-1
   // when ty0 = 0: NSEG segments, concatenated in a virtual index j.
@@ -605,7 +605,10 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
     bound[k] = seg_pre[k];
     off[k] = seg_beg[k] - seg_pre[k];
   }
-  unsigned int* accw = reinterpret_cast<unsigned int*>(acc);   // little endian: [2i] low, [2i+1] high
+  // low words of the cell sums in one plane, high words in the next: the
+  // low-word adds of random x cells spread over all 32 banks
+  unsigned int* accw = reinterpret_cast<unsigned int*>(acc);
+  constexpr int PLANE = ROWS * N;
   // window rows: z planes tz0-1 .. tz0+TZ-1 (segment / 2), y rows ws .. ws+TY
   // (identified by the record's y cell mod 32; N >= 32 or the mask below)
   static_assert(N < 32 || N % 32 == 0, "the y window is identified mod 32");
@@ -655,7 +658,7 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
           for (int dx = 0; dx < 2; ++dx) {
             const int k = dz * 4 + dy * 2 + dx;
             const unsigned long long v = in ? wzy * (unsigned long long)(dx ? wx : 65536u - wx) : 0ull;
-            slot[k] = 2 * (rb + (dx ? x1 : cx));
+            slot[k] = rb + (dx ? x1 : cx);
             lo[k] = (unsigned int)v;
             hi[k] = (unsigned int)(v >> 32);
           }
@@ -668,7 +671,7 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
       for (int k = 0; k < 8; ++k)
         if (lo[k] | hi[k]) {
           const unsigned int h = hi[k] + carry_of(old[k], lo[k]);
-          if (h) atomicAdd(accw + slot[k] + 1, h);
+          if (h) atomicAdd(accw + PLANE + slot[k], h);
         }
     }
   }
@@ -678,28 +681,35 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
   const int r = threadIdx.x / NT;
   const int gz = tz0 + r / TY, gy = ty0 + r % TY;
   const int64_t grow = (int64_t)gz * N + gy;
-  const ulonglong2* src = reinterpret_cast<const ulonglong2*>(acc + r * N);
+  const uint2* lo2 = reinterpret_cast<const uint2*>(accw + r * N);           // cells 2e, 2e+1
+  const uint2* hi2 = reinterpret_cast<const uint2*>(accw + PLANE + r * N);
   cx<T> v[E];
   if (keep) {
     ulonglong2* kd = reinterpret_cast<ulonglong2*>(keep + grow * N);
 #pragma unroll
-    for (int i = 0; i < E; ++i) kd[t + NT * i] = src[t + NT * i];
+    for (int i = 0; i < E; ++i) {
+      const uint2 l = lo2[t + NT * i], h = hi2[t + NT * i];
+      kd[t + NT * i] = ulonglong2{(unsigned long long)l.x | ((unsigned long long)h.x << 32),
+                                  (unsigned long long)l.y | ((unsigned long long)h.y << 32)};
+    }
   }
   if constexpr (sizeof(T) == 4) {
     // F = hi 2^32 + lo: delta = hi (s 2^32) + (lo s - 1) in FP32 FMAs
     const float hs = (float)(scale * 4294967296.0), ls = (float)scale;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-      const ulonglong2 q = src[t + NT * i];
-      const float ax = fmaf((float)(unsigned)(q.x >> 32), hs, fmaf((float)(unsigned)q.x, ls, -1.0f));
-      const float ay = fmaf((float)(unsigned)(q.y >> 32), hs, fmaf((float)(unsigned)q.y, ls, -1.0f));
+      const uint2 l = lo2[t + NT * i], h = hi2[t + NT * i];
+      const float ax = fmaf((float)h.x, hs, fmaf((float)l.x, ls, -1.0f));
+      const float ay = fmaf((float)h.y, hs, fmaf((float)l.y, ls, -1.0f));
       v[i] = {(T)ax, (T)ay};
     }
   } else {
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-      const ulonglong2 q = src[t + NT * i];
-      v[i] = {(T)((double)q.x * scale - 1.0), (T)((double)q.y * scale - 1.0)};
+      const uint2 l = lo2[t + NT * i], h = hi2[t + NT * i];
+      const unsigned long long fa = (unsigned long long)l.x | ((unsigned long long)h.x << 32);
+      const unsigned long long fb = (unsigned long long)l.y | ((unsigned long long)h.y << 32);
+      v[i] = {(T)((double)fa * scale - 1.0), (T)((double)fb * scale - 1.0)};
     }
   }
   __syncthreads();   // the tile is consumed; its memory now serves the exchange buffers
