@@ -350,7 +350,7 @@ def run_gpu(args, w, rank, world):
 
 
 # ------------------------------------------------------------------ other forms
-def _kick_form(w, pos64, vel64, precision, steps, warmup, mlp=None, keep_acc=True):
+def _kick_form(w, pos64, vel64, precision, steps, warmup, mlp=None, keep_acc=True, stages_out=None):
     """Time `steps` kicks of workload w (inputs resident) in the given
     precision, exact or surrogate response.  Returns (ms per kick, response
     ms per kick, acc [3, Np] on the device or None)."""
@@ -394,6 +394,8 @@ def _kick_form(w, pos64, vel64, precision, steps, warmup, mlp=None, keep_acc=Tru
     st = pm.get_timing()
     pm.timing(False)
     pm.check()
+    if stages_out is not None:
+        stages_out.update({k: v[0] / steps for k, v in st.items() if v[1] > 0})
     ms = e0.elapsed_time(e1) / steps
     pm.close()
     del pos, vel, hist_d
@@ -480,6 +482,17 @@ def run_forms(steps=3, warmup=1):
                            "fp32_ms_per_kick": round(ms32, 3), "speedup": round(ms64 / ms32, 2),
                            "fp32_force_rms_rel_vs_fp64": _rms_rel(acc32, acc64)}
     del acc64, acc32, parts
+    torch.cuda.empty_cache()
+    # contention variant: the same workload with the particles at their a = 1
+    # Zel'dovich positions (clustered), reported separately
+    wc = synth.with_(w, clustered=True)
+    parts = synth.particles(wc)
+    msc, _, _ = _kick_form(wc, parts["pos64"], parts["vel"], "fp32", steps, warmup, keep_acc=False,
+                           stages_out=(st := {}))
+    out["clustered"] = {"workload": w.name + " (Zel'dovich positions at a = 1)", "ms_per_kick": round(msc, 3),
+                        "kicks_per_s": w.npart / (msc / 1e3),
+                        "stages_ms": {k: round(v, 4) for k, v in st.items()}}
+    del parts
     torch.cuda.empty_cache()
     # surrogate form
     w = synth.WORKLOADS["pm512_p512_fp32"]

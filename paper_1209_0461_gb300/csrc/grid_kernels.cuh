@@ -331,12 +331,15 @@ __global__ void k_interp_kick(const void* __restrict__ pos, int64_t np, int n, d
                               const T* __restrict__ grids, int64_t field_stride, T* __restrict__ vel,
                               T kick, T* __restrict__ acc_out, int* status) {
   constexpr int U = kInterpBatch;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < np; p0 += stride * U) {
+  // a warp takes U x 32 consecutive particles (its U loads per lane 32 apart),
+  // so the force rows one warp gathers stay close together
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * U;
+  for (int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U + (threadIdx.x & 31); p0 < np;
+       p0 += stride) {
     typename Quant<T>::Raw raw[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t p = p0 + u * stride;
+      const int64_t p = p0 + u * 32;
       if (p < np) raw[u] = Quant<T>::load(pos, np, p);
     }
     // gather all corners of all U particles before the arithmetic
@@ -346,7 +349,7 @@ __global__ void k_interp_kick(const void* __restrict__ pos, int64_t np, int n, d
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       int c[3], w[3];
-      ok[u] = p0 + u * stride < np && Quant<T>::get(raw[u], n, delta, c, w, status);
+      ok[u] = p0 + u * 32 < np && Quant<T>::get(raw[u], n, delta, c, w, status);
       if (!ok[u]) continue;
       const T inv = (T)1.0 / (T)kWeightOne;
       f[u][1] = (T)w[0] * inv;
@@ -373,7 +376,7 @@ __global__ void k_interp_kick(const void* __restrict__ pos, int64_t np, int n, d
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (!ok[u]) continue;
-      const int64_t p = p0 + u * stride;
+      const int64_t p = p0 + u * 32;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const T v00 = f[u][0] * g[u][d][0] + f[u][1] * g[u][d][1];   // (y0, z0)

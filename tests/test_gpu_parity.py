@@ -83,6 +83,19 @@ def test_kick_192_mixed_radix(prec):
     _check_common(w, g, r, prec == "fp64")
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_clustered_kick_contention(prec):
+    # Zel'dovich at a = 1 in a 64 Mpc/h box: 57% of the cells empty, up to ~35
+    # particles in one cell -- the shared-memory tile sums see heavy contention
+    # and carries; the deposit must stay bit-exact
+    w = synth.with_(synth.WORKLOADS["pm32_fp64"], name=f"cl64_{prec}", ngrid=64, npart_side=64,
+                    box=64.0, precision=prec, n_hist=8, n_kbins=24, clustered=True)
+    inp = make_inputs(w)
+    g = gpu_kick(w, inp)
+    r = oracle_kick(w, inp)
+    _check_common(w, g, r, prec == "fp64")
+
+
 def test_fp32_kick_ragged_64():
     # 64^3 grid, FP32 form, a particle count that is not a multiple of any block size
     w = synth.with_(synth.WORKLOADS["pm32_fp64"], name="pm64_fp32", ngrid=64, npart_side=64,
