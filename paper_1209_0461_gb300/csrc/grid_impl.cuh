@@ -279,7 +279,10 @@ int NUPM_FN(green)(const GridArgs& g, cudaStream_t s) {
 
 int NUPM_FN(interp)(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, cudaStream_t s) {
   if (g.np > 0)
-    k_interp_kick<T><<<grid_blocks(g.np, 256, g.part_ctas_per_sm), 256, 0, s>>>(pos, g.np, g.n, g.delta, reinterpret_cast<const T*>(g.g),
+    // 128-thread CTAs: the gather's ~96 registers per thread then fit 5 CTAs
+    // (20 warps) per SM instead of 2 x 256 threads
+    k_interp_kick<T><<<grid_blocks(g.np, 128, 2 * g.part_ctas_per_sm), 128, 0, s>>>(pos, g.np, g.n, g.delta,
+                                                           reinterpret_cast<const T*>(g.g),
                                                            2 * g.field_elems, reinterpret_cast<T*>(vel), (T)kick,
                                                            reinterpret_cast<T*>(acc_out), g.status);
   return PM_OK;
