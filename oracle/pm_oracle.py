@@ -241,6 +241,89 @@ def cic_deposit(c: np.ndarray, w: np.ndarray, ngrid: int) -> np.ndarray:
     return grid.reshape(n, n, n)
 
 
+def cic_deposit_cells(c: np.ndarray, w: np.ndarray, ngrid: int, cells: np.ndarray) -> np.ndarray:
+    """The deposit F of ``cic_deposit`` at the flat nodes ``cells`` ((z N + y)
+    N + x) only, without the N^3 grid: F(t) is the sum over particles p and
+    corners d in {0,1}^3 with (c_p + d) mod N = t of wx[dx] wy[dy] wz[dz].
+    Only particles whose base cell is t - d for some d can contribute, so those
+    are picked first (int64 sums, exact).
+
+    Pinned by: equal to cic_deposit at every sampled node (wrapped nodes too).
+    """
+    n = ngrid
+    cells = np.asarray(cells, dtype=np.int64).reshape(-1)
+    tz, ty, tx = cells // (n * n), (cells // n) % n, cells % n
+    base = []
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                base.append((((tz - dz) % n) * n + (ty - dy) % n) * n + (tx - dx) % n)
+    flat = (c[2].astype(np.int64) * n + c[1]) * n + c[0]
+    sel = np.nonzero(np.isin(flat, np.unique(np.concatenate(base)), kind="table"))[0]
+    cs, ws = c[:, sel], w[:, sel]
+    wx, wy, wz = (_corner_weights(ws[0]), _corner_weights(ws[1]), _corner_weights(ws[2]))
+    out = np.zeros(cells.size, dtype=np.int64)
+    for dz in (0, 1):
+        iz = (cs[2] + dz) % n
+        for dy in (0, 1):
+            iy = (cs[1] + dy) % n
+            for dx in (0, 1):
+                ix = (cs[0] + dx) % n
+                node = (iz * n + iy) * n + ix
+                wt = wx[dx] * wy[dy] * wz[dz]
+                for i, t in enumerate(cells):
+                    out[i] += int(wt[node == t].sum())
+    return out
+
+
+def density_modes(c: np.ndarray, w: np.ndarray, ngrid: int, npart: int, kz, ky, kx,
+                  chunk: int = 1 << 22) -> np.ndarray:
+    """delta(k) of ``forward_fft(density_contrast(cic_deposit(c, w)))`` at the
+    given integer modes (kz, ky signed, kx in [0, N/2]) without the grid: by
+    linearity of the DFT,
+      sum_x F(x) e^{-2 pi i k.x / N}
+        = sum_p prod_axes [W0 e^{-2 pi i k_a c_a / N} + W1 e^{-2 pi i k_a (c_a+1) / N}]
+    (the corner weight is the product of the per-axis weights W0 = 2^16 - w,
+    W1 = w), then delta(k) = that sum N^3 / (Np 2^48) - N^3 [k = 0].  The
+    phases come from a table of e^{-2 pi i m / N} at the exact integer index
+    m = (k c) mod N.  The sum over particles runs in chunks as one matrix
+    product per chunk (library step): rows z-factors, columns the (y, x)
+    factor products.  Plain PyTorch CPU ops (threaded) do the chunk arithmetic.
+
+    Pinned by: equal to a brute-force DFT of the deposited density, and to the
+    FFT route, at sampled modes.
+    """
+    import torch
+    n = ngrid
+    kz, ky, kx = (np.asarray(v, dtype=np.int64).reshape(-1) for v in (kz, ky, kx))
+    uz, iz_of = np.unique(kz, return_inverse=True)
+    uy, iy_of = np.unique(ky, return_inverse=True)
+    ux, ix_of = np.unique(kx, return_inverse=True)
+    unit = torch.exp(-2j * math.pi * torch.arange(n, dtype=torch.float64) / n)
+    fr = [torch.from_numpy(u) for u in (ux, uy, uz)]
+    acc = torch.zeros((uz.size, uy.size * ux.size), dtype=torch.complex128)
+
+    def axis_factor(ca, wa, freqs):
+        ph = unit[torch.remainder(ca[:, None] * freqs[None, :], n)]
+        step = unit[torch.remainder(freqs, n)]
+        return ph * ((WEIGHT_ONE - wa).double()[:, None] + wa.double()[:, None] * step[None, :])
+
+    total = c.shape[1]
+    for s0 in range(0, total, chunk):
+        s1 = min(s0 + chunk, total)
+        cc = torch.from_numpy(np.ascontiguousarray(c[:, s0:s1], dtype=np.int64))
+        ww = torch.from_numpy(np.ascontiguousarray(w[:, s0:s1], dtype=np.int64))
+        fx = axis_factor(cc[0], ww[0], fr[0])
+        fy = axis_factor(cc[1], ww[1], fr[1])
+        fz = axis_factor(cc[2], ww[2], fr[2])
+        yx = (fy[:, :, None] * fx[:, None, :]).reshape(fx.shape[0], -1)
+        acc += fz.T @ yx
+    val = acc.numpy()[iz_of, iy_of * ux.size + ix_of]
+    out = val * (float(n) ** 3 / (float(npart) * MASS_ONE))
+    out[(kz == 0) & (ky == 0) & (kx == 0)] -= float(n) ** 3
+    return out
+
+
 def density_contrast(F: np.ndarray, npart: int) -> np.ndarray:
     """delta = F N^3 / (Np 2^48) - 1 in FP64 (mean particle count per node is
     Np / N^3)."""
@@ -293,6 +376,15 @@ def bin_power(spec: np.ndarray, box: float, n_kbins: int):
     """
     n = spec.shape[0]
     iz, iy, ix = mode_indices(n)
+    return bin_power_modes(spec, iz, iy, ix, n, box, n_kbins)
+
+
+def bin_power_modes(spec, iz, iy, ix, ngrid: int, box: float, n_kbins: int):
+    """``bin_power`` over an explicit set of half-spectrum modes (iz, iy, ix
+    broadcastable to spec): the same weights, thresholds and sums.  Over the
+    whole half lattice it is bin_power; over all modes of some bins it gives
+    those bins' entries exactly."""
+    n = ngrid
     n2 = iz * iz + iy * iy + ix * ix
     w = np.where((ix == 0) | (ix == n // 2), 1.0, 2.0) * np.ones_like(n2, dtype=np.float64)
     T = bin_thresholds(n, n_kbins)
@@ -504,8 +596,22 @@ def green_gradient(spec, box, a, cosmo: Cosmo, kb, R, nonempty, deconvolve=False
     point mass against the Ewald-summed periodic 1/r^2 force.
     """
     n = spec.shape[0]
-    kf = 2.0 * math.pi / box
     iz, iy, ix = mode_indices(n)
+    phi = potential_spectrum(spec, box, a, cosmo, kb, R, nonempty, deconvolve)
+    out = []
+    for comp in (ix, iy, iz):
+        out.append(-1j * gradient_operator(comp, n, box) * phi)
+    return out   # [acc_x, acc_y, acc_z] spectra
+
+
+def potential_spectrum(spec, box, a, cosmo: Cosmo, kb, R, nonempty, deconvolve=False, modes=None, ngrid=None):
+    """phi(k) = G(k) delta_M(k) of ``green_gradient`` (Eq. Poisson with the
+    neutrino-corrected delta_M), before the gradient.  By default over the
+    whole half spectrum; with modes = (iz, iy, ix) and ngrid, at those modes
+    (spec holding delta_k there)."""
+    n = spec.shape[0] if modes is None else ngrid
+    kf = 2.0 * math.pi / box
+    iz, iy, ix = mode_indices(n) if modes is None else modes
     n2 = (iz * iz + iy * iy + ix * ix).astype(np.float64)
     kmag = kf * np.sqrt(n2)
     f = cosmo.f_nu
@@ -520,11 +626,7 @@ def green_gradient(spec, box, a, cosmo: Cosmo, kb, R, nonempty, deconvolve=False
             return np.where(i == 0, 1.0, np.sin(t) / np.where(i == 0, 1.0, t))
         W = sinc(iz) * sinc(iy) * sinc(ix)
         G = G / W ** 4
-    phi = G * spec
-    out = []
-    for comp in (ix, iy, iz):
-        out.append(-1j * gradient_operator(comp, n, box) * phi)
-    return out   # [acc_x, acc_y, acc_z] spectra
+    return G * spec
 
 
 def gradient_operator(i, ngrid, box):

@@ -270,3 +270,64 @@ def test_point_mass_against_ewald():
         assert np.max(err) < 0.08
         # attractive: acceleration points back to the mass
         assert np.all((acc * (pts - x0)).sum(0) < 0)
+
+
+def _random_particles(n, npart, seed):
+    rng = np.random.default_rng(seed)
+    c = rng.integers(0, n, size=(3, npart)).astype(np.int64)
+    w = rng.integers(0, 65536, size=(3, npart)).astype(np.int64)
+    return c, w
+
+
+def test_deposit_at_sampled_cells_equals_brute_force():
+    n = 8
+    c, w = _random_particles(n, 300, 5)
+    c[:, :4] = [[0, n - 1, 0, n - 1], [n - 1, 0, n - 1, 0], [n - 1, n - 1, 0, 0]]   # wrap across every face
+    F = _brute_deposit(c, w, n)
+    rng = np.random.default_rng(6)
+    cells = np.concatenate([[0, n ** 3 - 1, (n - 1) * n * n, n - 1], rng.integers(0, n ** 3, 40)])
+    got = O.cic_deposit_cells(c, w, n, cells)
+    assert np.array_equal(got, F.reshape(-1)[cells])
+
+
+def test_density_modes_equal_brute_dft_of_deposit():
+    n, npart = 8, 200
+    c, w = _random_particles(n, npart, 7)
+    F = _brute_deposit(c, w, n).astype(np.float64)
+    delta = F * (n ** 3 / (npart * 2.0 ** 48)) - 1.0
+    x = np.arange(n)
+    modes = [(0, 0, 0), (0, 0, 1), (1, -2, 0), (-3, 2, 4), (-4, -4, 4), (2, 3, 1), (0, -1, 0), (3, 0, 2)]
+    kz, ky, kx = (np.array(v) for v in zip(*modes))
+    got = O.density_modes(c, w, n, npart, kz, ky, kx, chunk=64)
+    for i, (a, b, d) in enumerate(modes):
+        ph = np.exp(-2j * math.pi * (a * x[:, None, None] + b * x[None, :, None] + d * x[None, None, :]) / n)
+        ref = (delta * ph).sum()
+        assert abs(got[i] - ref) < 1e-12 * (1 + abs(ref)), (modes[i], got[i], ref)
+    # and against the oracle's own FFT route
+    spec = O.forward_fft(O.density_contrast(O.cic_deposit(c, w, n), npart))
+    assert np.allclose(got, spec[kz % n, ky % n, kx], rtol=1e-12, atol=1e-10)
+
+
+def test_bin_power_over_complete_bins_equals_full_bins():
+    n, box, nk = 16, 100.0, 12
+    rng = np.random.default_rng(8)
+    delta = rng.normal(size=(n, n, n))
+    spec = O.forward_fft(delta)
+    full = O.bin_power(spec, box, nk)
+    T = full["T"]
+    lim = 13
+    iz, iy, ix = O.mode_indices(n)
+    n2 = iz * iz + iy * iy + ix * ix
+    sel = np.nonzero((n2 < lim) & (n2 > 0))
+    part = O.bin_power_modes(spec[sel], iz[sel[0], 0, 0], iy[0, sel[1], 0], ix[0, 0, sel[2]], n, box, nk)
+    done = T[1:] <= lim                     # bins all of whose modes have n^2 < lim
+    assert done.sum() >= 3
+    for key in ("count", "ksum", "psum", "k", "P"):
+        assert np.allclose(part[key][done], full[key][done], rtol=1e-13, atol=0), key
+    # the potential at a mode subset equals the full spectrum's values there
+    cos = O.Cosmo(0.25, 0.05, 0.7, (0.1, 0.1, 0.1), 0.02)
+    R = np.linspace(0.2, 0.9, nk)
+    phi = O.potential_spectrum(spec, box, 0.1, cos, full["k"], R, full["nonempty"])
+    phis = O.potential_spectrum(spec[sel], box, 0.1, cos, full["k"], R, full["nonempty"],
+                                modes=(iz[sel[0], 0, 0], iy[0, sel[1], 0], ix[0, 0, sel[2]]), ngrid=n)
+    assert np.array_equal(phis, phi[sel])
