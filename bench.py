@@ -103,11 +103,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def stage_bytes(w, stage, fused_interp=True):
+def stage_bytes(w, stage, fused_interp=True, spectral=False):
     """Algorithmic (compulsory) HBM bytes of ONE launch of a stage: each pass
-    reads its inputs and writes its outputs once at stored precision.  With
-    the fused interpolation the inverse x stage reads the three fields and
-    the particles (positions, row permutation) and updates the velocities."""
+    reads its inputs and writes its outputs once at stored precision.  By
+    default the inverse passes carry the potential alone and the gather reads
+    the real potential grid (its 4-point stencil); with the gradient in
+    Fourier space (spectral) they carry three force fields.  With the fused
+    interpolation the inverse x stage reads the three fields and the
+    particles (positions, row permutation) and updates the velocities."""
     n = w.ngrid
     M = n ** 3
     Mc = n * n * (n // 2)                 # packed complex elements per field
@@ -116,6 +119,19 @@ def stage_bytes(w, stage, fused_interp=True):
     p = 24                                 # position bytes per particle (both forms)
     v = r
     Np = w.npart
+    if not (spectral or fused_interp):
+        return {
+            "deposit": (p + 8) * Np,
+            "fft_x_fwd": 8 * Np + c * Mc,
+            "fft_y_fwd": 2 * c * Mc,
+            "fft_z_fwd": 2 * c * Mc,
+            "bins": c * Mc,
+            "green": 3 * c * n * n,
+            "fft_z_inv": 2 * c * Mc,                      # spectrum -> phi
+            "fft_y_inv": 2 * c * Mc,                      # phi in place
+            "fft_x_inv": c * Mc + r * M,                  # packed rows -> real potential
+            "interp": p * Np + min(r * M, 56 * r * Np) + 2 * 3 * v * Np,
+        }.get(stage)
     return {
         "deposit": (p + 8) * Np,                         # row sort: positions in, 8-byte records out
         "fft_x_fwd": 8 * Np + c * Mc,                    # fused deposit + x: records in, spectrum out
@@ -233,7 +249,8 @@ def run_gpu(args, w, rank, world):
     stream = torch.cuda.current_stream()
     pm = nupm.PM(wr.ngrid, wr.npart, wr.box, wr.omega_cdm, wr.omega_nu, wr.h, wr.m_nu_total,
                  wr.n_species, a_init=wr.a_init, n_kbins=nk, n_hist_max=wr.n_hist,
-                 precision=wr.precision, sqrtPnu_init=pi, theta_over_delta_init=ti, stream=stream)
+                 precision=wr.precision, sqrtPnu_init=pi, theta_over_delta_init=ti, stream=stream,
+                 flags=nupm.PM_SPECTRAL_GRADIENT if args.spectral_gradient else 0)
     a = wr.a_kick
     K = pm.kick_factor(a, a * 1.01)
 
@@ -329,14 +346,15 @@ def run_gpu(args, w, rank, world):
     if dom in ("deposit", "bins"):
         per_launch_ms = tot_ms / max(calls, 1)     # memset/reduce ride along in the stage
     fused = stages["interp"][1] == 0
-    alg = stage_bytes(wr, dom, fused)
+    spectral = bool(args.spectral_gradient)
+    alg = stage_bytes(wr, dom, fused, spectral)
     achieved = alg / (per_launch_ms / 1e3) / 1e9
     roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
             "traffic": traffic_from_profiles(dom, wr.name), "alg_bytes_per_launch": int(alg),
             "ms_per_launch": round(per_launch_ms, 4)}
     total_launch = sum(v[1] for v in stages.values())
-    step_alg = sum(stage_bytes(wr, k, fused) * (v[2] if k in ("deposit", "bins") else v[1])
+    step_alg = sum(stage_bytes(wr, k, fused, spectral) * (v[2] if k in ("deposit", "bins") else v[1])
                    for k, v in stages.items() if k != "response") / args.steps
     res = dict(value=whole_job_rate(wr.npart, world, ms), ms_per_step=ms, e2e=e2e, roofline=roof,
                stages={k: {"ms_per_step": round(v[0] / args.steps, 4), "launches_per_step": v[1] // args.steps}
@@ -540,6 +558,8 @@ def main():
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64 / surrogate comparisons")
     ap.add_argument("--no-autotune", action="store_true", help="built-in tile choices instead of pm_autotune")
+    ap.add_argument("--spectral-gradient", action="store_true",
+                    help="gradient as its Fourier multiplier (three force grids) instead of the real-space stencil")
     args = ap.parse_args()
     w = synth.WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -549,7 +569,9 @@ def main():
               "m_nu_ev": w.m_nu_total, "n_species": w.n_species, "n_kbins": w.n_kbins,
               "n_hist": w.n_hist, "a": w.a_kick, "positions": "int32 cell + fp32 offset"
               if w.precision == "fp32" else "fp64", "response": "fp64",
-              "l2": "inputs larger than L2 (each grid >= 4 GB)", "parallelism": f"replicas x{args.gpus}"}
+              "l2": "inputs larger than L2 (each grid >= 4 GB)", "parallelism": f"replicas x{args.gpus}",
+              "gradient": "4-point multiplier -i D(k) in Fourier space" if args.spectral_gradient
+              else "4-point stencil on the real potential grid"}
     base = {"metric": "particle-kicks/s incl. neutrino response", "unit": "particle-kicks/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype,

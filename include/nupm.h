@@ -73,6 +73,13 @@ extern "C" {
                                  1024^3 grid, slower than the separate pass + gather) */
 #define PM_TMA_COLUMNS 0x10u /* column FFT passes as persistent TMA-pipelined kernels (comparison;
                                  1 CTA/SM: slower than the default on a 1024^3 grid) */
+#define PM_SPECTRAL_GRADIENT 0x40u /* apply the 4-point gradient as its Fourier multiplier
+                                 -i D(k): three force spectra, three inverse transforms, the
+                                 gather reads three force grids (comparison).  Default: one
+                                 inverse transform of the potential, and the gather applies
+                                 the same 4-point difference to the real potential grid
+                                 (equal in exact arithmetic).  PM_FUSED_GATHER and
+                                 PM_TMA_COLUMNS imply it. */
 
 /*
  * Problem statement (Sec. 4.3-4.4, Table 1).  Omega_M = omega_cdm + omega_nu
@@ -197,13 +204,18 @@ NUPM_API int pm_get_thresholds(const pm_ctx* ctx, int64_t* thresholds);
  *   PM_FIELD_DELTA_K   the forward spectrum, complex[N][N][N/2+1] unpacked
  *                      (numpy rfftn layout), valid after pm_deposit
  *   PM_FIELD_ACC_X/Y/Z the real acceleration grids [N][N][N], valid after pm_kick
- *                      without PM_FUSED_GATHER
+ *                      without PM_FUSED_GATHER (by default computed on request
+ *                      from the potential with the gather's 4-point stencil)
+ *   PM_FIELD_PHI       the real potential grid [N][N][N] (Eq. Poisson with the
+ *                      neutrino-corrected delta_M), valid after pm_kick with
+ *                      the default real-space gradient
  * Element type is the precision's float type (complex = 2 of them). */
 #define PM_FIELD_DEPOSIT 0
 #define PM_FIELD_DELTA_K 1
 #define PM_FIELD_ACC_X   2
 #define PM_FIELD_ACC_Y   3
 #define PM_FIELD_ACC_Z   4
+#define PM_FIELD_PHI     5
 NUPM_API int pm_copy_field(pm_ctx* ctx, int32_t which, void* dst);
 
 /* ---- per-stage timing (CUDA events on the context's stream) ----
@@ -260,7 +272,11 @@ NUPM_API int64_t pm_device_bytes(const pm_ctx* ctx);
  * Times, on `reps` kicks of this context with the given particles (kick
  * factor 0, so velocities are unchanged), each candidate of
  *   wide_y / wide_z   column tiles of the y / z FFT passes: 0 = 64-byte row
- *                     segments (8 FP32 columns), 1 = 128-byte segments
+ *                     segments (8 FP32 columns), 1 = 128-byte segments;
+ *                     wide_z also 2 = 128-byte segments staged in shared
+ *                     memory by TMA, the next tile's copy overlapping the
+ *                     current tile's transform (power-of-two grids of 256
+ *                     and more)
  *   ctas_per_sm       CTAs per SM of the particle kernels (row sort, CIC
  *                     gather): 4, 8, 16, 32
  * one knob at a time, keeps the fastest and writes HOST tuned[3] = {wide_y,
@@ -270,7 +286,9 @@ NUPM_API int64_t pm_device_bytes(const pm_ctx* ctx);
  * depends on.  The paper has no counterpart (it is a property of this GPU). */
 NUPM_API int pm_autotune(pm_ctx* ctx, const void* pos, void* vel, double a, const double* a_hist,
                          const double* sqrtPM_hist, int32_t n_hist, int32_t reps, int32_t* tuned);
-/* Set the three knobs directly (-1 = built-in choice for wide_y / wide_z). */
+/* Set the three knobs directly (-1 = built-in choice for wide_y / wide_z).
+ * PM_ERR_INVALID for a value out of range, PM_ERR_UNSUPPORTED for wide_z = 2
+ * on a grid that does not offer it. */
 NUPM_API int pm_set_tuning(pm_ctx* ctx, const int32_t* tuned);
 
 /* ---- CUDA graphs of whole kicks (batched form) ----

@@ -322,9 +322,10 @@ k_fft_col(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
 //   out_phi = IFFT_z(G F),   out_dz = IFFT_z(-i D(kz) G F)
 // G = gtab[n^2] (x wtab^3 with deconvolution).  The packed column x2 = 0
 // (A + i B of the kx = 0 / N/2 planes, whose G differ) comes pre-multiplied
-// from plane0[ky][kz] (k_green_plane0).  grid = (M / W, N)
+// from plane0[ky][kz] (k_green_plane0).  NOUT = 1: the potential alone (the
+// gradient is then taken in real space by the gather).  grid = (M / W, N)
 // ---------------------------------------------------------------------------
-template <typename T, int N, class Cfg = ColWide<T, N>>
+template <typename T, int N, class Cfg = ColWide<T, N>, int NOUT = 2>
 __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MIN_BLOCKS)
 k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, cx<T>* __restrict__ out_dz,
                   const cx<T>* __restrict__ plane0, const T* __restrict__ gtab, const T* __restrict__ dtab,
@@ -377,7 +378,7 @@ k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, c
   const cx<T>* src = col0 ? plane0 + (int64_t)iy * N : spec + off;
   const int64_t sstride = col0 ? 1 : ES;
 #pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < NOUT; ++pass) {
     cx<T> v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = src[(int64_t)(t + NT * i) * sstride];
@@ -396,7 +397,7 @@ k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, c
     for (int b = 0; b < E / RL; ++b)
 #pragma unroll
       for (int i = 0; i < RL; ++i) dst[off + (int64_t)(t + NT * b + i * (N / RL)) * ES] = v[b * RL + i];
-    __syncthreads();   // the next transform reuses the shared memory
+    if (NOUT > 1) __syncthreads();   // the next transform reuses the shared memory
   }
 }
 

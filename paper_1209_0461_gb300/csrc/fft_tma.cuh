@@ -67,7 +67,9 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-enum ColMode { kColFwdY = 0, kColFwdZ = 1, kColInvZGreen = 2, kColInvYGrad = 3 };
+// kColInvZPhi: the Green z pass with the potential as its only output (the
+// gradient then comes from the real-space stencil of the gather)
+enum ColMode { kColFwdY = 0, kColFwdZ = 1, kColInvZGreen = 2, kColInvYGrad = 3, kColInvZPhi = 4 };
 
 template <typename T>
 struct ColTmaArgs {
@@ -248,6 +250,159 @@ k_col_tma(const __grid_constant__ CUtensorMap map, ColTmaArgs<T> A) {
       for (int b = 0; b < E / RL; ++b)
 #pragma unroll
         for (int i = 0; i < RL; ++i) dst[(int64_t)(t + NT * b + i * (N / RL)) * ES] = v[b * RL + i];
+    }
+  }
+}
+
+}  // namespace nupm
+
+namespace nupm {
+
+// ---------------------------------------------------------------------------
+// z passes with 128-byte row segments (16 FP32 / 8 FP64 columns) staged by
+// TMA in a single shared buffer that afterwards serves as the exchange buffer
+// of the transform.  One CTA per SM walks the (x2 tile, y) items; as soon as
+// the exchange of item k has been read back (its data now in registers), the
+// copy of item k + gridDim.x is issued into the buffer, so it travels while
+// item k finishes its butterflies and its stores.  The Green pass takes its
+// second transform's input from global memory (the tile it just staged is
+// still in L2).
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+struct ColTmaZCfg {
+  static constexpr int M = N / 2;
+  static constexpr int E = Plan<T, N>::R1;
+  static constexpr int NT = N / E;
+  static constexpr int W = sizeof(T) == 4 ? 16 : 8;          // 128-byte row segments
+  static constexpr int THREADS = W * NT;
+  static constexpr int PAD = ColCfg<T, N>::PAD;
+  static constexpr int BOX = N < 256 ? N : 256;             // TMA box extent along z
+  static constexpr int NBOX = N / BOX;
+  static constexpr size_t TILE_BYTES = (size_t)N * W * sizeof(cx<T>);
+  static constexpr size_t XCH_BYTES = (size_t)ColSmem<T, W, PAD>::words(N) * sizeof(cx<T>);
+  static constexpr size_t BUF_BYTES = XCH_BYTES > TILE_BYTES ? XCH_BYTES : TILE_BYTES;
+  static constexpr size_t FAC_BYTES = sizeof(T) == 4 ? 2048 * sizeof(float) : 0;
+  static constexpr size_t SMEM = BUF_BYTES + FAC_BYTES + 64;
+  static constexpr int TILES_PER_ROW = M / W;
+};
+
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(ColTmaZCfg<T, N>::THREADS, 1)
+k_col_tma_z(const __grid_constant__ CUtensorMap map, ColTmaArgs<T> A) {
+  static_assert(MODE == kColFwdZ || MODE == kColInvZGreen || MODE == kColInvZPhi, "z passes only");
+  constexpr int NTR = MODE == kColInvZGreen ? 2 : 1;   // transforms per Green tile
+  using Cfg = ColTmaZCfg<T, N>;
+  constexpr int M = N / 2, E = Cfg::E, NT = Cfg::NT, W = Cfg::W, RL = last_radix<T, N>();
+  constexpr int64_t ES = (int64_t)N * M;      // element stride along z
+  constexpr int DIR = MODE == kColFwdZ ? -1 : +1;
+  constexpr bool kFac = sizeof(T) == 4;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  float* fac_s = reinterpret_cast<float*>(smem_raw + Cfg::BUF_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::BUF_BYTES + Cfg::FAC_BYTES);
+  const int items = Cfg::TILES_PER_ROW * N;   // (x2 tile, y)
+  const int c = threadIdx.x % W;
+  const int t = threadIdx.x / W;
+  ColSmem<T, W, Cfg::PAD> sm{buf, c};
+
+  auto issue = [&](int item) {
+    const int xt = item % Cfg::TILES_PER_ROW, y = item / Cfg::TILES_PER_ROW;
+    const int xcoord = xt * W * (sizeof(T) == 4 ? 1 : 2);
+    mbar_expect_tx(bar, (uint32_t)Cfg::TILE_BYTES);
+#pragma unroll
+    for (int bx = 0; bx < Cfg::NBOX; ++bx)
+      tma_load_4d(buf + (size_t)bx * Cfg::BOX * W, &map, bar, xcoord, y, bx * Cfg::BOX, 0);
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if constexpr (MODE != kColFwdZ && kFac)
+    for (int j = threadIdx.x; j < 2048; j += blockDim.x) fac_s[j] = A.fac[j];
+  __syncthreads();
+  const int first = blockIdx.x, step = gridDim.x;
+  if (threadIdx.x == 0 && first < items) issue(first);
+  int k = 0;
+  for (int item = first; item < items; item += step, ++k) {
+    const bool ok = mbar_wait_bounded(bar, (uint32_t)(k & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicCAS(A.status, 0, PM_ERR_TIMEOUT);
+        mbar_wait_bounded(bar, (uint32_t)(k & 1));   // this CTA's one copy in flight (bounded)
+      }
+      return;
+    }
+    const int xt = item % Cfg::TILES_PER_ROW, y = item / Cfg::TILES_PER_ROW;
+    const int x2 = xt * W + c;
+    cx<T> v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = buf[(t + NT * i) * W + c];   // the staged tile (dense)
+    __syncthreads();   // every read of the tile is done before the exchange overwrites it
+    if constexpr (MODE == kColFwdZ) {
+      fft_regs<T, N, DIR>(v, sm, t, A.tw);
+      fence_proxy_async_shared();
+      __syncthreads();   // exchange read back: the buffer may take the next tile
+      if (threadIdx.x == 0 && item + step < items) issue(item + step);
+      cx<T>* dst = A.spec + (int64_t)y * M + x2;
+#pragma unroll
+      for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+        for (int i = 0; i < RL; ++i) dst[(int64_t)(t + NT * b + i * (N / RL)) * ES] = v[b * RL + i];
+    } else {
+      const int ky = y < N / 2 ? y : y - N;
+      const int base2 = ky * ky + x2 * x2;
+      const T wyx = A.wtab ? A.wtab[y] * A.wtab[x2] : (T)1;
+#pragma unroll 1
+      for (int tr = 0; tr < NTR; ++tr) {
+        if (tr == 1) {   // the second transform reads its input again (L2)
+#pragma unroll
+          for (int i = 0; i < E; ++i) v[i] = A.spec[(int64_t)(t + NT * i) * ES + (int64_t)y * M + x2];
+        }
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int iz = t + NT * i;
+          cx<T> f;
+          if (x2 == 0) {   // packed column: its pre-multiplied kx = 0 / N/2 values
+            f = A.plane0[(int64_t)y * N + iz];
+          } else {
+            const int kz = iz < N / 2 ? iz : iz - N;
+            const int n2 = base2 + kz * kz;
+            T gval;
+            if constexpr (kFac) {
+              const float tt = 0.5f * __logf((float)n2) * A.fac_inv_du;
+              const int j = min((int)tt, 2048 - 2);
+              const float fr = tt - (float)j;
+              gval = (T)(A.coeff * (fac_s[j] + fr * (fac_s[j + 1] - fac_s[j])) / (float)n2);
+            } else {
+              gval = A.gtab[n2];
+            }
+            if (A.wtab) gval *= wyx * A.wtab[iz];
+            f = cscale(v[i], gval);
+          }
+          if (tr == 1) {
+            const T d = A.dtab[iz];
+            f = {d * f.y, -d * f.x};   // -i D(kz)
+          }
+          v[i] = f;
+        }
+        if (tr == 1) __syncthreads();   // the first transform's exchange reads are done
+        fft_regs<T, N, DIR>(v, sm, t, A.tw);
+        if (tr == NTR - 1) {
+          fence_proxy_async_shared();
+          __syncthreads();
+          if (threadIdx.x == 0 && item + step < items) issue(item + step);
+        }
+        cx<T>* dst = A.g + (tr == 0 ? 0 : 2 * A.field_elems) + (int64_t)y * M + x2;
+#pragma unroll
+        for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+          for (int i = 0; i < RL; ++i) dst[(int64_t)(t + NT * b + i * (N / RL)) * ES] = v[b * RL + i];
+      }
     }
   }
 }

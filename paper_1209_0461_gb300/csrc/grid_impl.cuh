@@ -35,6 +35,9 @@ void col_attrs() {
   cudaFuncSetAttribute(k_fft_col<T, N, -1, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem<CC>());
   cudaFuncSetAttribute(k_fft_z_inv_green<T, N, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)green_smem<N, CC>());
+  cudaFuncSetAttribute(k_fft_z_inv_green<T, N, CC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)green_smem<N, CC>());
+  cudaFuncSetAttribute(k_fft_col<T, N, +1, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem<CC>());
   cudaFuncSetAttribute(k_fft_y_inv_grad<T, N, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)col_smem<CC>());
 }
@@ -67,13 +70,24 @@ void col_pass(const GridArgs& g, int pass, cudaStream_t s) {
     case kPassZFwd:
       k_fft_col<T, N, -1, CC><<<grid, CC::THREADS, col_smem<CC>(), s>>>(spec, (int64_t)M, (int64_t)N * M, 0, twn);
       break;
-    case kPassZInv:   // Green + z: spectrum -> g0 (phi), g2 (d/dz phi)
+    case kPassZInv:   // Green + z: spectrum -> g0 (phi), g2 (d/dz phi); real-space gradient: g0 only
+      if (g.fd_grad) {
+        k_fft_z_inv_green<T, N, CC, 1><<<grid, CC::THREADS, green_smem<N, CC>(), s>>>(
+            spec, f, f + 2 * fe, reinterpret_cast<const C*>(g.plane0), reinterpret_cast<const T*>(g.gtab),
+            reinterpret_cast<const T*>(g.dtab), reinterpret_cast<const T*>(g.wtab), twn, g.fac, g.fac_inv_du,
+            g.green_coeff);
+        break;
+      }
       k_fft_z_inv_green<T, N, CC><<<grid, CC::THREADS, green_smem<N, CC>(), s>>>(
           spec, f, f + 2 * fe, reinterpret_cast<const C*>(g.plane0), reinterpret_cast<const T*>(g.gtab),
           reinterpret_cast<const T*>(g.dtab), reinterpret_cast<const T*>(g.wtab), twn, g.fac, g.fac_inv_du,
           g.green_coeff);
       break;
     case kPassYInv:   // y with the y gradient: g0 -> g1 (d/dy), g0 -> g0, g2 -> g2
+      if (g.fd_grad) {   // the potential alone, in place
+        k_fft_col<T, N, +1, CC><<<grid, CC::THREADS, col_smem<CC>(), s>>>(f, (int64_t)N * M, (int64_t)M, 0, twn);
+        break;
+      }
       k_fft_y_inv_grad<T, N, CC><<<grid, CC::THREADS, col_smem<CC>(), s>>>(
           f, f + fe, f + 2 * fe, reinterpret_cast<const T*>(g.dtab), twn);
       break;
@@ -108,9 +122,44 @@ void col_tma_n(const GridArgs& g, const CUtensorMap* map, cudaStream_t s) {
   k_col_tma<T, N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*map, a);
 }
 
+// TMA-staged z pass of size N with 128-byte segments (one resident CTA per
+// SM; a persistent grid of one CTA per SM).
+template <int N, int MODE>
+void col_tma_z_n(const GridArgs& g, cudaStream_t s) {
+  using Cfg = ColTmaZCfg<T, N>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_col_tma_z<T, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    attr = true;
+  }
+  ColTmaArgs<T> a;
+  a.spec = reinterpret_cast<C*>(g.spec);
+  a.g = reinterpret_cast<C*>(g.g);
+  a.field_elems = g.field_elems;
+  a.tw = reinterpret_cast<const C*>(g.tw_n);
+  a.plane0 = reinterpret_cast<const C*>(g.plane0);
+  a.dtab = reinterpret_cast<const T*>(g.dtab);
+  a.wtab = reinterpret_cast<const T*>(g.wtab);
+  a.gtab = reinterpret_cast<const T*>(g.gtab);
+  a.fac = g.fac;
+  a.fac_inv_du = g.fac_inv_du;
+  a.coeff = g.green_coeff;
+  a.status = g.status;
+  const int items = Cfg::TILES_PER_ROW * N;
+  const int grid = items < g.sm_count ? items : g.sm_count;
+  k_col_tma_z<T, N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*g.tmap_z16, a);
+}
+
 // One FFT pass of size N (pass: kPassXFwd .. kPassXInv, see nupm_internal.h).
 template <int N>
 void fft_pass_n(const GridArgs& g, int pass, cudaStream_t s) {
+  if constexpr ((N & (N - 1)) == 0 && N >= 256) {   // TMA-staged z passes (tuning choice)
+    if (g.wide_z == 2 && g.tmap_z16) {
+      if (pass == kPassZFwd) { col_tma_z_n<N, kColFwdZ>(g, s); return; }
+      if (pass == kPassZInv && g.fd_grad) { col_tma_z_n<N, kColInvZPhi>(g, s); return; }
+      if (pass == kPassZInv) { col_tma_z_n<N, kColInvZGreen>(g, s); return; }
+    }
+  }
   if constexpr ((N & (N - 1)) == 0) {   // TMA column passes: power-of-two grids
   if (g.tmap_spec_y) {
     switch (pass) {
@@ -136,15 +185,17 @@ void fft_pass_n(const GridArgs& g, int pass, cudaStream_t s) {
           reinterpret_cast<const unsigned long long*>(g.g), reinterpret_cast<C*>(g.spec), g.scale, twm, twn);
       break;
     case kPassXInv:
-      // x with the x gradient on field 0 (phi -> d/dx phi); fields 1, 2 as they are
-      k_fft_x_inv<T, N><<<dim3((unsigned)(rows / RC::ROWS), 1, 3), RC::THREADS, row_smem, s>>>(
-          reinterpret_cast<C*>(g.g), g.field_elems, twm, twn, reinterpret_cast<const T*>(g.dtab), 1);
+      // x with the x gradient on field 0 (phi -> d/dx phi); fields 1, 2 as they
+      // are.  Real-space gradient: the potential alone.
+      k_fft_x_inv<T, N><<<dim3((unsigned)(rows / RC::ROWS), 1, g.fd_grad ? 1 : 3), RC::THREADS, row_smem, s>>>(
+          reinterpret_cast<C*>(g.g), g.field_elems, twm, twn, reinterpret_cast<const T*>(g.dtab),
+          g.fd_grad ? 0 : 1);
       break;
     default: {
       // y passes narrow, z passes wide from N >= 256 on, unless tuned
       const bool zpass = pass == kPassZFwd || pass == kPassZInv;
       const int tuned = zpass ? g.wide_z : g.wide_y;
-      const bool wide = tuned >= 0 ? tuned == 1 : (zpass && N >= 256);
+      const bool wide = tuned >= 0 ? tuned >= 1 : (zpass && N >= 256);
       if (wide) col_pass<N, ColWide<T, N>>(g, pass, s);
       else col_pass<N, ColNarrow<T, N>>(g, pass, s);
     }
@@ -278,6 +329,12 @@ int NUPM_FN(green)(const GridArgs& g, cudaStream_t s) {
 }
 
 int NUPM_FN(interp)(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, cudaStream_t s) {
+  if (g.np > 0 && g.fd_grad) {
+    k_interp_kick_fd<T><<<grid_blocks(g.np, 128, 2 * g.part_ctas_per_sm), 128, 0, s>>>(
+        pos, g.np, g.n, g.delta, reinterpret_cast<const T*>(g.g), reinterpret_cast<T*>(vel), (T)kick,
+        reinterpret_cast<T*>(acc_out), g.status);
+    return PM_OK;
+  }
   if (g.np > 0)
     // 128-thread CTAs: the gather's ~96 registers per thread then fit 5 CTAs
     // (20 warps) per SM instead of 2 x 256 threads
@@ -285,6 +342,13 @@ int NUPM_FN(interp)(const GridArgs& g, const void* pos, void* vel, double kick, 
                                                            reinterpret_cast<const T*>(g.g),
                                                            2 * g.field_elems, reinterpret_cast<T*>(vel), (T)kick,
                                                            reinterpret_cast<T*>(acc_out), g.status);
+  return PM_OK;
+}
+
+int NUPM_FN(fd_field)(const GridArgs& g, int comp, void* dst, cudaStream_t s) {
+  const int64_t total = (int64_t)g.n * g.n * g.n;
+  k_fd_force_field<T><<<grid_blocks(total, 256), 256, 0, s>>>(reinterpret_cast<const T*>(g.g), g.n, comp, g.delta,
+                                                             reinterpret_cast<T*>(dst));
   return PM_OK;
 }
 

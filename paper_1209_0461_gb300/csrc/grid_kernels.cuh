@@ -392,6 +392,157 @@ __global__ void k_interp_kick(const void* __restrict__ pos, int64_t np, int n, d
 }
 
 // ---------------------------------------------------------------------------
+// a6-a7 with the gradient taken in real space.  The 4-point central
+// difference whose Fourier multiplier is -i D(k) (D(k) = [8 sin(k d) -
+// sin(2 k d)] / (6 d), d the cell size) is, on the periodic grid,
+//   (S f)(x) = [f(x-2) - 8 f(x-1) + 8 f(x+1) - f(x+2)] / (12 d),
+// so acc = -S phi on the potential grid equals the inverse transform of
+// -i D G delta in exact arithmetic (the multiplier and the stencil both
+// vanish on the Nyquist index).  The gather applies S at the particle's eight
+// CIC corners; along an axis the corners c and c + 1 see the potential at
+// c - 2 .. c + 3 with the folded weights
+//   e_j = w0 s(j - 2) + w1 s(j - 3),  s(-2..2) = (1, -8, 0, 8, -1),
+// so each particle reads 56 potential values (four 6-point runs along x,
+// eight 4-point runs along y and along z) instead of 3 x 8 force values.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrap_near(int c, int d, int n) {
+  int v = c + d;   // d in [-2, 3], c in [0, n), n >= 16
+  if ((n & (n - 1)) == 0) return v & (n - 1);
+  v = v < 0 ? v + n : v;
+  return v >= n ? v - n : v;
+}
+
+template <typename T>
+__device__ __forceinline__ void fold_weights(T f0, T f1, T (&e)[6]) {
+  e[0] = f0;
+  e[1] = (T)-8 * f0 + f1;
+  e[2] = (T)-8 * f1;
+  e[3] = (T)8 * f0;
+  e[4] = -f0 + (T)8 * f1;
+  e[5] = -f1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_interp_kick_fd(const void* __restrict__ pos, int64_t np, int n, double delta, const T* __restrict__ phi,
+                 T* __restrict__ vel, T kick, T* __restrict__ acc_out, int* status) {
+  const T scale = (T)(-1.0 / (12.0 * delta));   // acc = -S phi
+  const T inv = (T)1.0 / (T)kWeightOne;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // the next particle's position words are fetched while this one's
+  // potential values are in flight (one memory round trip per particle)
+  typename Quant<T>::Raw next;
+  if (p < np) next = Quant<T>::load(pos, np, p);
+  for (; p < np; p += stride) {
+    const typename Quant<T>::Raw raw = next;
+    if (p + stride < np) next = Quant<T>::load(pos, np, p + stride);
+    const T u0 = vel[p], u1 = vel[np + p], u2 = vel[2 * np + p];
+    int c[3], w[3];
+    if (!Quant<T>::get(raw, n, delta, c, w, status)) continue;
+    int xs[6], ys[6], zs[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      xs[j] = wrap_near(c[0], j - 2, n);
+      ys[j] = wrap_near(c[1], j - 2, n);
+      zs[j] = wrap_near(c[2], j - 2, n);
+    }
+    // (y, z) row starts; indices < 2^30 for n <= 1024
+    auto row = [&](int y, int z) { return ((uint32_t)z * (uint32_t)n + (uint32_t)y) * (uint32_t)n; };
+    T px[2][2][6];   // [dz][dy][x0-2 .. x0+3]
+    T py[2][2][4];   // [dz][dx][y0-2, y0-1, y0+2, y0+3]
+    T pz[2][2][4];   // [dy][dx][z0-2, z0-1, z0+2, z0+3]
+    constexpr int kFar[4] = {0, 1, 4, 5};
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const T* r = phi + row(ys[2 + dy], zs[2 + dz]);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) px[dz][dy][j] = r[xs[j]];
+      }
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T* r = phi + row(ys[kFar[q]], zs[2 + dz]);
+        py[dz][0][q] = r[xs[2]];
+        py[dz][1][q] = r[xs[3]];
+      }
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T* r = phi + row(ys[2 + dy], zs[kFar[q]]);
+        pz[dy][0][q] = r[xs[2]];
+        pz[dy][1][q] = r[xs[3]];
+      }
+    T f[3][2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      f[d][1] = (T)w[d] * inv;
+      f[d][0] = (T)1 - f[d][1];
+    }
+    T ex[6], ey[6], ez[6];
+    fold_weights(f[0][0], f[0][1], ex);
+    fold_weights(f[1][0], f[1][1], ey);
+    fold_weights(f[2][0], f[2][1], ez);
+    T a[3] = {(T)0, (T)0, (T)0};
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        T sx = (T)0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) sx += ex[j] * px[dz][dy][j];
+        a[0] += f[1][dy] * f[2][dz] * sx;
+      }
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const T sy = ey[0] * py[dz][dx][0] + ey[1] * py[dz][dx][1] + ey[2] * px[dz][0][2 + dx] +
+                     ey[3] * px[dz][1][2 + dx] + ey[4] * py[dz][dx][2] + ey[5] * py[dz][dx][3];
+        a[1] += f[0][dx] * f[2][dz] * sy;
+      }
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const T sz = ez[0] * pz[dy][dx][0] + ez[1] * pz[dy][dx][1] + ez[2] * px[0][dy][2 + dx] +
+                     ez[3] * px[1][dy][2 + dx] + ez[4] * pz[dy][dx][2] + ez[5] * pz[dy][dx][3];
+        a[2] += f[0][dx] * f[1][dy] * sz;
+      }
+    const T u[3] = {u0, u1, u2};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T ad = a[d] * scale;
+      vel[d * np + p] = u[d] + ad * kick;
+      if (acc_out) acc_out[d * np + p] = ad;
+    }
+  }
+}
+
+// Inspection: one component of acc = -S phi on the whole grid (real [N][N][N]).
+template <typename T>
+__global__ void k_fd_force_field(const T* __restrict__ phi, int n, int comp, double delta, T* __restrict__ out) {
+  const T scale = (T)(-1.0 / (12.0 * delta));
+  const int64_t total = (int64_t)n * n * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % n), y = (int)((i / n) % n), z = (int)(i / ((int64_t)n * n));
+    int idx[5];
+#pragma unroll
+    for (int o = -2; o <= 2; ++o) {
+      const int xx = comp == 0 ? wrap_near(x, o, n) : x;
+      const int yy = comp == 1 ? wrap_near(y, o, n) : y;
+      const int zz = comp == 2 ? wrap_near(z, o, n) : z;
+      idx[o + 2] = (zz * n + yy) * n + xx;
+    }
+    out[i] = scale * ((phi[idx[0]] - phi[idx[4]]) + (T)8 * (phi[idx[3]] - phi[idx[1]]));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Inspection: packed [N][N][M] -> rfftn layout [N][N][M+1].
 // ---------------------------------------------------------------------------
 template <typename T>

@@ -88,14 +88,20 @@ struct GridArgs {
   const CUtensorMap* tmap_spec_y;  // TMA maps of the column passes (nullptr: plain kernels)
   const CUtensorMap* tmap_spec_z;
   const CUtensorMap* tmap_g_y;
+  const CUtensorMap* tmap_z16 = nullptr;  // spectrum along z, 128-byte segments (wide_z = 2), or nullptr
   int sm_count;
   const float* fac;               // FP32 path: fac table (kFacTable points)
   float fac_inv_du;               // 1 / table spacing in u = ln sqrt(n^2)
   float green_coeff;              // -1.5 Omega_M / (a kf^2 N^3)
   // tuning (pm_autotune): wide (1) or narrow (0) column tiles of the y and z
-  // passes, -1 = the built-in choice; CTAs per SM of the particle kernels
+  // passes, 2 = TMA-staged wide z passes, -1 = the built-in choice; CTAs per
+  // SM of the particle kernels
   int wide_y = -1, wide_z = -1;
   int part_ctas_per_sm = 16;
+  // gradient: false = -i D(k) in Fourier space (three inverse transforms of
+  // force spectra); true = the 4-point stencil on the real potential grid,
+  // applied by the gather (one inverse transform)
+  bool fd_grad = false;
 };
 #define NUPM_DECLARE_GRID(SFX)                                                              \
   int deposit##SFX(const GridArgs& g, const void* pos, cudaStream_t s);                     \
@@ -109,7 +115,8 @@ struct GridArgs {
                   cudaStream_t s);                                                          \
   int xinv_interp##SFX(const GridArgs& g, const void* pos, void* vel, double kick,          \
                        void* acc_out, cudaStream_t s);                                      \
-  int unpack##SFX(const GridArgs& g, void* dst, cudaStream_t s);
+  int unpack##SFX(const GridArgs& g, void* dst, cudaStream_t s);                            \
+  int fd_field##SFX(const GridArgs& g, int comp, void* dst, cudaStream_t s);
 NUPM_DECLARE_GRID(_f32)
 NUPM_DECLARE_GRID(_f64)
 #undef NUPM_DECLARE_GRID

@@ -63,6 +63,9 @@ struct pm_ctx {
   // TMA tensor maps of the column passes (spectrum along y / z, fields along y)
   bool tma = false;
   alignas(64) CUtensorMap tm_spec_y, tm_spec_z, tm_g_y;
+  // spectrum along z with 128-byte segments: the TMA-staged z passes (wide_z = 2)
+  bool tma_z16 = false;
+  alignas(64) CUtensorMap tm_z16;
   int sm_count = 152;
   double green_coeff = 0;     // -1.5 Omega_M / (a kf^2 N^3) of the last response
   int* d_status = nullptr;
@@ -307,8 +310,8 @@ void drain_timing(pm_ctx* c) {
 }
 
 // Encode a 4-D tensor map over a packed complex field array [F][N][N][M]
-// (x2 fastest) with a box of W x2-columns by `box` elements along y or z.
-int encode_col_map(pm_ctx* c, CUtensorMap* map, void* base, int fields, bool along_z) {
+// (x2 fastest) with a box of w x2-columns by `box` elements along y or z.
+int encode_col_map(pm_ctx* c, CUtensorMap* map, void* base, int fields, bool along_z, int w) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -323,7 +326,6 @@ int encode_col_map(pm_ctx* c, CUtensorMap* map, void* base, int fields, bool alo
   }
   const int n = c->n, m = c->m;
   const bool f64 = c->fp64;
-  const int w = f64 ? 4 : 8;                       // column tile width (64-byte segments)
   const int box = n < 256 ? n : 256;
   const cuuint64_t e0 = f64 ? 2 * (cuuint64_t)m : (cuuint64_t)m;   // elements of 8 bytes
   cuuint64_t dims[4] = {e0, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)fields};
@@ -343,6 +345,7 @@ GridArgs grid_args(const pm_ctx* c) {
   g.wide_y = c->wide_y;
   g.wide_z = c->wide_z;
   g.part_ctas_per_sm = c->part_cps;
+  g.fd_grad = !(c->p.flags & (PM_SPECTRAL_GRADIENT | PM_FUSED_GATHER | PM_TMA_COLUMNS));
   g.n = c->n;
   g.np = c->np;
   g.box = c->box;
@@ -367,6 +370,7 @@ GridArgs grid_args(const pm_ctx* c) {
   g.tmap_spec_y = c->tma ? &c->tm_spec_y : nullptr;
   g.tmap_spec_z = c->tma ? &c->tm_spec_z : nullptr;
   g.tmap_g_y = c->tma ? &c->tm_g_y : nullptr;
+  g.tmap_z16 = c->tma_z16 ? &c->tm_z16 : nullptr;
   g.sm_count = c->sm_count;
   g.fac = c->d_fac;
   g.fac_inv_du = (float)((kFacTable - 1) / (0.5 * log((double)c->n2max)));
@@ -447,7 +451,8 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   else if (p.precision != PM_FP64 && p.precision != PM_FP32) bad(PM_ERR_INVALID, "precision must be PM_FP64 or PM_FP32");
   else if (p.iters < 1 || p.iters > 16) bad(PM_ERR_INVALID, "iters must be 1..16");
   else if (p.quad_nodes < 2 || p.quad_nodes > kMaxQuad) bad(PM_ERR_INVALID, "quad_nodes must be 2..16");
-  else if (p.flags & ~(PM_I_FIT | PM_DECONV_CIC | PM_KEEP_DEPOSIT | PM_UNFUSED_DEPOSIT | PM_TMA_COLUMNS | PM_FUSED_GATHER))
+  else if (p.flags & ~(PM_I_FIT | PM_DECONV_CIC | PM_KEEP_DEPOSIT | PM_UNFUSED_DEPOSIT | PM_TMA_COLUMNS | PM_FUSED_GATHER |
+                       PM_SPECTRAL_GRADIENT))
     bad(PM_ERR_INVALID, "unknown flag bits");
   if (rc != PM_OK) {
     // report through a context so pm_last_error works; caller still gets NULL
@@ -612,10 +617,18 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (p.flags & PM_TMA_COLUMNS) {
-      rc = encode_col_map(c, &c->tm_spec_y, c->spec, 1, false);
-      if (rc == PM_OK) rc = encode_col_map(c, &c->tm_spec_z, c->spec, 1, true);
-      if (rc == PM_OK) rc = encode_col_map(c, &c->tm_g_y, c->g, 3, false);
+      const int w = c->fp64 ? 4 : 8;   // 64-byte row segments
+      rc = encode_col_map(c, &c->tm_spec_y, c->spec, 1, false, w);
+      if (rc == PM_OK) rc = encode_col_map(c, &c->tm_spec_z, c->spec, 1, true, w);
+      if (rc == PM_OK) rc = encode_col_map(c, &c->tm_g_y, c->g, 3, false, w);
       c->tma = rc == PM_OK;
+    }
+    // TMA-staged z passes (a tuning choice, power-of-two grids from 256 on):
+    // without the driver's encoder they are simply not offered
+    if (rc == PM_OK && pow2 && c->n >= 256) {
+      const std::string keep = c->err;
+      c->tma_z16 = encode_col_map(c, &c->tm_z16, c->spec, 1, true, c->fp64 ? 8 : 16) == PM_OK;
+      c->err = keep;
     }
   }
   if (rc == PM_OK) {
@@ -1031,10 +1044,23 @@ int pm_copy_field(pm_ctx* c, int32_t which, void* dst) {
     case PM_FIELD_ACC_Y:
     case PM_FIELD_ACC_Z: {
       if (!c->have_kick)
-        return fail(c, PM_ERR_ORDER, "no force grids (pm_kick ran with PM_FUSED_GATHER)");
+        return fail(c, PM_ERR_ORDER, "no force grids (before pm_kick, or pm_kick ran with PM_FUSED_GATHER)");
       const int comp = which - PM_FIELD_ACC_X;
+      GridArgs g = grid_args(c);
+      if (g.fd_grad) {   // the stencil on the potential grid, as the gather applies it
+        const int rc = c->fp64 ? fd_field_f64(g, comp, dst, c->stream) : fd_field_f32(g, comp, dst, c->stream);
+        if (rc != PM_OK) return fail(c, rc, "force field failed");
+        e = cudaGetLastError();
+        break;
+      }
       const char* src = reinterpret_cast<const char*>(c->g) + (size_t)comp * c->field_elems * c->cplx;
       e = cudaMemcpyAsync(dst, src, (size_t)n3 * real, cudaMemcpyDeviceToDevice, c->stream);
+      break;
+    }
+    case PM_FIELD_PHI: {
+      if (!c->have_kick || !grid_args(c).fd_grad)
+        return fail(c, PM_ERR_ORDER, "no potential grid (before pm_kick, or the gradient ran in Fourier space)");
+      e = cudaMemcpyAsync(dst, c->g, (size_t)n3 * real, cudaMemcpyDeviceToDevice, c->stream);
       break;
     }
     default:
@@ -1111,6 +1137,14 @@ int pm_autotune(pm_ctx* c, const void* pos, void* vel, double a, const double* a
     rc = measure(st, 2, &t1);
     if (rc != PM_OK) break;
     knob = t1 < t0 ? 1 : 0;
+    if (pass == 1 && c->tma_z16) {   // TMA-staged z passes
+      double t2 = 0.0;
+      const int prev = knob;
+      knob = 2;
+      rc = measure(st, 2, &t2);
+      if (rc != PM_OK) break;
+      knob = t2 < (t1 < t0 ? t1 : t0) ? 2 : prev;
+    }
   }
   // CTAs per SM of the particle kernels (row sort, gather + kick)
   if (rc == PM_OK) {
@@ -1142,8 +1176,10 @@ int pm_autotune(pm_ctx* c, const void* pos, void* vel, double a, const double* a
 
 int pm_set_tuning(pm_ctx* c, const int32_t* tuned) {
   if (!c || !tuned) return PM_ERR_INVALID;
-  if (tuned[0] < -1 || tuned[0] > 1 || tuned[1] < -1 || tuned[1] > 1 || tuned[2] < 1 || tuned[2] > 64)
-    return fail(c, PM_ERR_INVALID, "pm_set_tuning: wide_y, wide_z in -1..1, ctas_per_sm in 1..64");
+  if (tuned[0] < -1 || tuned[0] > 1 || tuned[1] < -1 || tuned[1] > 2 || tuned[2] < 1 || tuned[2] > 64)
+    return fail(c, PM_ERR_INVALID, "pm_set_tuning: wide_y in -1..1, wide_z in -1..2, ctas_per_sm in 1..64");
+  if (tuned[1] == 2 && !c->tma_z16)
+    return fail(c, PM_ERR_UNSUPPORTED, "pm_set_tuning: wide_z = 2 needs a power-of-two grid of 256 or more");
   c->wide_y = tuned[0];
   c->wide_z = tuned[1];
   c->part_cps = tuned[2];

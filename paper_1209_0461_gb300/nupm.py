@@ -22,8 +22,8 @@ ERRORS = {-1: "PM_ERR_INVALID", -2: "PM_ERR_RANGE", -3: "PM_ERR_OVERFLOW", -4: "
           -5: "PM_ERR_ALLOC", -6: "PM_ERR_TIMEOUT", -7: "PM_ERR_ORDER", -8: "PM_ERR_UNSUPPORTED"}
 PM_FP64, PM_FP32 = 0, 1
 PM_I_FIT, PM_DECONV_CIC, PM_KEEP_DEPOSIT, PM_UNFUSED_DEPOSIT = 0x1, 0x2, 0x4, 0x8
-PM_TMA_COLUMNS, PM_FUSED_GATHER = 0x10, 0x20
-FIELD_DEPOSIT, FIELD_DELTA_K, FIELD_ACC_X, FIELD_ACC_Y, FIELD_ACC_Z = range(5)
+PM_TMA_COLUMNS, PM_FUSED_GATHER, PM_SPECTRAL_GRADIENT = 0x10, 0x20, 0x40
+FIELD_DEPOSIT, FIELD_DELTA_K, FIELD_ACC_X, FIELD_ACC_Y, FIELD_ACC_Z, FIELD_PHI = range(6)
 MLP_FEATURES, MLP_WIDTH = 12, 128
 STAGES = ["deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_fwd", "bins", "response", "green",
           "fft_z_inv", "fft_y_inv", "fft_x_inv", "interp"]
@@ -272,7 +272,8 @@ class PM:
 
     # -- tuning
     def autotune(self, pos, vel, a, a_hist, sqrtPM_hist, reps=2):
-        """pm_autotune: returns (wide_y, wide_z, ctas_per_sm)."""
+        """pm_autotune: returns (wide_y, wide_z, ctas_per_sm); wide_z = 2 is the
+        TMA-staged z pass."""
         self._check_pos(pos)
         ah, n = self._history(a_hist, sqrtPM_hist)
         t = (C.c_int32 * 3)()

@@ -32,10 +32,13 @@ def make_inputs(w, npart=None, seed_shift=0):
 KEEP_DEPOSIT = 0x4
 UNFUSED_DEPOSIT = 0x8
 FUSED_GATHER = 0x20
+SPECTRAL_GRADIENT = 0x40
 
 
-def gpu_kick(w, inp, K=0.01, iters=1, flags=KEEP_DEPOSIT, n_hist=None, prev=None, quad=8, keep_fields=False):
-    """Deposit, response and kick through the C ABI.  Returns numpy results."""
+def gpu_kick(w, inp, K=0.01, iters=1, flags=KEEP_DEPOSIT, n_hist=None, prev=None, quad=8, keep_fields=False,
+             tuning=None):
+    """Deposit, response and kick through the C ABI (tuning: pm_set_tuning
+    knobs, or None for the built-in choices).  Returns numpy results."""
     import torch
     dev = torch.device("cuda")
     fp64 = w.precision == "fp64"
@@ -47,6 +50,8 @@ def gpu_kick(w, inp, K=0.01, iters=1, flags=KEEP_DEPOSIT, n_hist=None, prev=None
                  a_init=w.a_init, n_kbins=w.n_kbins, n_hist_max=max(len(a_hist), 1),
                  precision=w.precision, flags=flags, iters=iters, quad_nodes=quad,
                  sqrtPnu_init=inp["pi"], theta_over_delta_init=inp["ti"])
+    if tuning is not None:
+        pm.set_tuning(*tuning)
     if fp64:
         pos = torch.from_numpy(inp["pos64"]).to(dev).contiguous()
         vel = torch.from_numpy(inp["vel"]).to(dev).contiguous()
@@ -73,6 +78,8 @@ def gpu_kick(w, inp, K=0.01, iters=1, flags=KEEP_DEPOSIT, n_hist=None, prev=None
                pos=pos)
     if keep_fields:
         out["fields"] = [pm.field(nupm.FIELD_ACC_X + c).cpu().numpy() for c in range(3)]
+        if not flags & (SPECTRAL_GRADIENT | FUSED_GATHER | 0x10):   # real-space gradient: the potential grid
+            out["phi"] = pm.field(nupm.FIELD_PHI).cpu().numpy()
     pm.close()
     return out
 

@@ -13,8 +13,8 @@ from paper_1209_0461_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
-from gpu_common import (KEEP_DEPOSIT, FUSED_GATHER, UNFUSED_DEPOSIT, build_lib, force_errors,  # noqa: E402
-                        gpu_kick, make_inputs, oracle_kick)
+from gpu_common import (KEEP_DEPOSIT, FUSED_GATHER, SPECTRAL_GRADIENT, UNFUSED_DEPOSIT, build_lib,  # noqa: E402
+                        cosmo_of, force_errors, gpu_kick, make_inputs, oracle_kick)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -125,14 +125,41 @@ def test_fft_and_bins_sizes(n, prec):
     assert np.array_equal(g["bins"][0], b["count"])
 
 
-def test_inverse_fields_against_oracle():
+@pytest.mark.parametrize("flags", [KEEP_DEPOSIT, KEEP_DEPOSIT | SPECTRAL_GRADIENT])
+def test_inverse_fields_against_oracle(flags):
+    # force grids: by default the 4-point stencil on the potential grid, with
+    # PM_SPECTRAL_GRADIENT the inverse transforms of -i D(k) phi(k)
     w = synth.with_(synth.WORKLOADS["pm32_fp64"], n_hist=6)
     inp = make_inputs(w)
-    g = gpu_kick(w, inp, keep_fields=True)
+    g = gpu_kick(w, inp, keep_fields=True, n_hist=6, flags=flags)
     r = oracle_kick(w, inp, n_hist=6)
     for c in range(3):
         ref = r.extras["fields"][c]
         assert np.max(np.abs(g["fields"][c] - ref)) < 1e-11 * np.max(np.abs(ref))
+    if flags & SPECTRAL_GRADIENT:
+        assert "phi" not in g
+        return
+    # the potential grid itself: inverse transform of G delta_M (Eq. Poisson)
+    phi_k = O.potential_spectrum(r.extras["spec"], w.box, w.a_kick, cosmo_of(w), r.bins["k"], r.response["R"],
+                                 r.bins["nonempty"])
+    ref = O.inverse_fft(phi_k, w.ngrid)
+    assert np.max(np.abs(g["phi"] - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec,n", [("fp64", 64), ("fp32", 128), ("fp32", 192)])
+def test_real_space_gradient_equals_spectral(prec, n):
+    # the gather's stencil on the potential against the Fourier multiplier
+    # -i D(k): equal in exact arithmetic, so only rounding separates them
+    w = synth.Workload(f"fd{n}", n, n // 2, 2.0 * n, 0.3, 3, 4, 16, prec)
+    inp = make_inputs(w)
+    a = gpu_kick(w, inp)
+    b = gpu_kick(w, inp, flags=KEEP_DEPOSIT | SPECTRAL_GRADIENT)
+    emax, erms = force_errors(a["acc"], b["acc"])
+    print(f"{prec} N={n}: stencil vs multiplier max {emax:.2e} rms {erms:.2e} (of rms |F|)")
+    if prec == "fp64":
+        assert emax < 1e-10
+    else:   # FP32 differences of the potential: cancellation bounded by eps * phi / (d |grad phi|)
+        assert erms < 3e-5
 
 
 def test_options_iters_fit_deconv_nohist_prev():
@@ -266,10 +293,34 @@ def test_tma_column_passes_equal_plain(prec, n):
     # as the plain column kernels: identical spectra and forces
     w = synth.Workload(f"tma{n}", n, n, 2.0 * n, 0.15, 3, 4, 16, prec)
     inp = make_inputs(w)
-    a = gpu_kick(w, inp, flags=KEEP_DEPOSIT | 0x10)     # PM_TMA_COLUMNS
-    b = gpu_kick(w, inp, flags=KEEP_DEPOSIT)
+    a = gpu_kick(w, inp, flags=KEEP_DEPOSIT | 0x10)     # PM_TMA_COLUMNS (gradient in Fourier space)
+    b = gpu_kick(w, inp, flags=KEEP_DEPOSIT | SPECTRAL_GRADIENT)
     assert np.array_equal(a["spec"], b["spec"])
     assert np.array_equal(a["acc"], b["acc"])
+
+
+@pytest.mark.parametrize("prec,flags", [("fp32", KEEP_DEPOSIT), ("fp64", KEEP_DEPOSIT),
+                                        ("fp32", KEEP_DEPOSIT | SPECTRAL_GRADIENT)])
+def test_tma_staged_z_passes(prec, flags):
+    # wide_z = 2: z passes whose 128-byte-segment tiles are staged by TMA in
+    # the exchange buffer; against the oracle, and the same arithmetic as the
+    # plain wide z kernels (Green pass with one output, or two with the
+    # gradient in Fourier space)
+    w = synth.Workload("tmaz256", 256, 40, 512.0, 0.15, 3, 4, 16, prec)
+    inp = make_inputs(w)
+    g = gpu_kick(w, inp, tuning=(-1, 2, 16), flags=flags)
+    _check_common(w, g, oracle_kick(w, inp), prec == "fp64")
+    b = gpu_kick(w, inp, tuning=(-1, 1, 16), flags=flags)
+    assert np.array_equal(g["spec"], b["spec"])
+    # the two kernels inline the same butterflies, but the compiler may fuse
+    # their multiply-adds differently: potentials an ulp apart, which the
+    # real-space stencil's differences amplify by about phi / (cell |grad phi|)
+    # (~40 here)
+    emax, erms = force_errors(g["acc"], b["acc"])
+    if prec == "fp64":
+        assert emax < 1e-12
+    else:
+        assert erms < (1e-6 if flags & SPECTRAL_GRADIENT else 1e-5)
 
 
 @pytest.mark.parametrize("prec,n,npart", [("fp64", 32, 32 ** 3), ("fp32", 64, 64 ** 3 - 37),
@@ -280,7 +331,7 @@ def test_fused_interpolation_equals_separate(prec, n, npart):
     side = round(npart ** (1 / 3)) + 1
     w = synth.Workload(f"xint{n}", n, min(side, n), 2.0 * n, 0.3, 3, 4, 16, prec)
     inp = make_inputs(w, npart=min(npart, w.npart))
-    a = gpu_kick(w, inp, flags=KEEP_DEPOSIT)
+    a = gpu_kick(w, inp, flags=KEEP_DEPOSIT | SPECTRAL_GRADIENT)
     b = gpu_kick(w, inp, flags=KEEP_DEPOSIT | FUSED_GATHER)
     scale = np.max(np.abs(a["acc"]))
     tol = 1e-12 if prec == "fp64" else 1e-6
