@@ -265,7 +265,10 @@ def run_gpu(args, w, rank, world):
         torch.cuda.synchronize()
 
     tuning = None
-    if not args.no_autotune:
+    if args.tuning:
+        tuning = [int(v) for v in args.tuning.split(",")]
+        pm.set_tuning(*tuning)
+    elif not args.no_autotune:
         # kick factor 0 inside: velocities unchanged
         tuning = list(pm.autotune(pos, vel, a, a_hist, hist_d, reps=2))
 
@@ -558,6 +561,8 @@ def main():
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64 / surrogate comparisons")
     ap.add_argument("--no-autotune", action="store_true", help="built-in tile choices instead of pm_autotune")
+    ap.add_argument("--tuning", default=None,
+                    help="wide_y,wide_z,ctas_per_sm for pm_set_tuning (implies --no-autotune)")
     ap.add_argument("--spectral-gradient", action="store_true",
                     help="gradient as its Fourier multiplier (three force grids) instead of the real-space stencil")
     args = ap.parse_args()

@@ -302,20 +302,43 @@ int NUPM_FN(fft_pass)(const GridArgs& g, int pass, cudaStream_t s) {
   return PM_OK;
 }
 
-int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const short* bin_of, double kf, double* partials,
-                  int nblk, double* out, cudaStream_t s) {
+int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const int* thr, float inv_lr, double kf,
+                  double* partials, int nblk, double* out, cudaStream_t s) {
   const int nv = lattice ? 2 : 1;
-  const size_t sh = kBinWarps * (size_t)nv * nk * sizeof(double) + (lattice ? 0 : kBinWarps * (size_t)nk * sizeof(float));
-  static size_t attr_l = 48 * 1024, attr_p = 48 * 1024;
-  size_t& attr = lattice ? attr_l : attr_p;
-  if (sh > attr) {
-    if (lattice) cudaFuncSetAttribute(k_bin_power<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-    else cudaFuncSetAttribute(k_bin_power<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-    attr = sh;
-  }
+  const int E = g.n / 64;
   const C* spec = reinterpret_cast<const C*>(g.spec);
-  if (lattice) k_bin_power<T, true><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, bin_of, kf, partials);
-  else k_bin_power<T, false><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, bin_of, kf, partials);
+  // one wave of resident CTAs (fewer than the partial rows when registers or
+  // shared memory limit the residency), so no SM idles through a second wave
+  auto wave = [&](const void* kern, size_t sh) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kBinWarps * 32, sh);
+    const int resident = (o < 1 ? 1 : o) * g.sm_count;
+    return resident < nblk ? resident : nblk;
+  };
+  bool done = false;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 power sums of grids with a bins tensor map: rows staged by TMA
+    if (!lattice && g.tmap_bins && (E == 2 || E == 4 || E == 8 || E == 16)) {
+      decltype(&k_bin_power_tma<16>) kern = E == 2 ? k_bin_power_tma<2> : E == 4 ? k_bin_power_tma<4>
+                                            : E == 8 ? k_bin_power_tma<8> : k_bin_power_tma<16>;
+      const size_t sh = bin_tma_smem(nk, E);
+      nblk = wave((const void*)kern, sh);
+      kern<<<nblk, kBinWarps * 32, sh, s>>>(*g.tmap_bins, reinterpret_cast<const cx<float>*>(spec), g.n, nk, thr,
+                                            inv_lr, partials, g.status);
+      done = true;
+    }
+  }
+  if (!done) {
+    const size_t sh = kBinWarps * (size_t)nv * nk * sizeof(double) + (size_t)(nk + 1) * sizeof(int);
+    if (lattice) {
+      nblk = wave((const void*)k_bin_power<T, true>, sh);
+      k_bin_power<T, true><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, thr, inv_lr, kf, partials);
+    } else {
+      nblk = wave((const void*)k_bin_power<T, false>, sh);
+      k_bin_power<T, false><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, thr, inv_lr, kf, partials);
+    }
+  }
   k_bin_reduce<<<(nv * nk + 127) / 128, 128, 0, s>>>(partials, nblk, nv * nk, out);
   return PM_OK;
 }

@@ -12,6 +12,7 @@
 
 #include <type_traits>
 
+#include "async_copy.cuh"
 #include "fft.cuh"
 #include "nupm_internal.h"
 
@@ -155,141 +156,403 @@ __device__ __forceinline__ int signed_freq(int i, int n) { return i < n / 2 ? i 
 
 // ---------------------------------------------------------------------------
 // a3: binned power of the packed spectrum, deterministic.  One warp per row
-// (z, y); lanes take consecutive x2.  Along a row n^2 = kz^2 + ky^2 + x2^2 grows
-// with x2, so the bins of a 32-lane chunk are contiguous lane segments: a
-// segmented shuffle scan sums each segment and its last lane adds the sum to
-// the warp's private accumulator (one writer per bin, no atomics).  Warps and
-// CTAs are then summed in a fixed order (k_bin_reduce).  The bin of each n^2
-// comes from a lookup table (bin_of[n2], -1 outside the bins).
+// (z, y); lane L takes the E = ceil(M / 32) consecutive x2 from L E.  Along a
+// row n^2 = kz^2 + ky^2 + x2^2 grows with x2, so a lane's modes fall into runs
+// of equal bin, and the lanes' runs follow each other in bin order:
+//   * a run that neither starts nor ends the lane's range holds every mode of
+//     its bin in this row: the lane adds it to the warp's accumulator;
+//   * the first and the last run of each lane may continue into neighbouring
+//     lanes: a segmented shuffle scan over the lanes' last runs (a lane whose
+//     range is one run passes the sum through) joins them, and each joined
+//     segment is added once, by the lane where it ends (a lane with several
+//     runs closes the incoming segment with its first run).
+// Every add has one writer in a fixed order, so the sums are reproducible;
+// warps and CTAs are then summed in a fixed order (k_bin_reduce).
+// The bin of n^2 is the b with T_b <= n^2 < T_{b+1} (integer thresholds in
+// shared memory): floor(nk ln n^2 / ln r^2) for the lane's first mode,
+// corrected against T, then advanced while n^2 >= T_{b+1}.
 //   LATTICE = true : accumulate the mode count sum w and sum w |k| (depends on
 //                    the lattice only; run once per context)
-//   LATTICE = false: accumulate sum w |delta_k|^2; per-mode arithmetic in the
-//                    grid precision T, one FP64 add per segment
+//   LATTICE = false: accumulate sum w |delta_k|^2 in the grid precision T
+//                    along runs and lanes, one FP64 add per run or segment
 // The packed slot x2 = 0 is unpacked with the row at (-z, -y):
 //   A = (F(k) + conj F(-k)) / 2   (kx = 0),  B = (F(k) - conj F(-k)) / (2i)  (kx = N/2).
-// Shared memory: [kBinWarps][NV][nk] doubles (NV = 2 lattice sums or 1).
+// Shared memory: [kBinWarps][NV][nk] doubles (NV = 2 lattice sums or 1), then
+// T[0..nk].
 // ---------------------------------------------------------------------------
 constexpr int kBinWarps = 4;
-constexpr int kBinBatch = 8;   // chunks loaded per batch (bytes in flight)
+constexpr int kBinLaneMax = 16;   // modes per lane (M <= 512)
 
+__device__ __forceinline__ int bin_of_n2(int n2, const int* T, int nk, float inv_lr) {
+  int b = (int)(__logf((float)n2) * inv_lr);
+  b = min(max(b, 0), nk - 1);
+  while (b < nk - 1 && T[b + 1] <= n2) ++b;
+  while (b > 0 && T[b] > n2) --b;
+  return (T[b] <= n2 && n2 < T[b + 1]) ? b : -1;
+}
+
+// FP32 power sums accumulate per bin as an unevaluated pair hi + lo of
+// floats (error-free two-sum of each added run or segment): about twice
+// float precision without GB300's narrow FP64 pipe, which otherwise limits
+// the kernel.  The pair is summed into FP64 once per CTA.
 template <typename T, bool LATTICE>
-__global__ void __launch_bounds__(kBinWarps * 32)
-k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const short* __restrict__ bin_of,
-            double kf, double* __restrict__ partials) {
-  constexpr int NV = LATTICE ? 2 : 1;
-  using A = typename std::conditional<LATTICE, double, T>::type;   // scan type
-  // FP32 power: per-row sums in FP32 (at most M modes a bin), added to the
-  // warp's FP64 sums once per row (GB300's FP64 pipe is narrow)
-  constexpr bool ROWF = !LATTICE && sizeof(T) == 4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* all = reinterpret_cast<double*>(smem_raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* acc = all + warp * NV * nk;
-  float* racc = reinterpret_cast<float*>(all + kBinWarps * NV * nk) + warp * nk;
-  for (int i = threadIdx.x; i < kBinWarps * NV * nk; i += blockDim.x) all[i] = 0.0;
-  if constexpr (ROWF)
-    for (int i = threadIdx.x; i < kBinWarps * nk; i += blockDim.x) racc[i - warp * nk] = 0.0f;
-  __syncthreads();
+constexpr bool kBinPair = !LATTICE && sizeof(T) == 4;
+
+__device__ __forceinline__ void pair_add(float2* a, float x) {
+  float2 v = *a;
+  const float s = v.x + x;
+  const float bp = s - v.x;
+  const float err = (v.x - (s - bp)) + (x - bp);
+  v.x = s;
+  v.y += err;
+  *a = v;
+}
+
+// One row's modes into the warp's accumulator acc (see above).  f: this
+// lane's E modes (power sums only), g: lane 0's partner slot.
+template <typename T, bool LATTICE>
+__device__ __forceinline__ void bin_row(const cx<T> (&f)[kBinLaneMax], cx<T> g, int base2, int m, int E, int lane,
+                                        const int* Ts, int nk, float inv_lr, double kf, double* acc) {
+  using A = typename std::conditional<LATTICE, double, T>::type;   // run / segment sums
   const unsigned full = 0xffffffffu;
-  const int m = n / 2;
-  const int rows = n * n;
-  for (int row = blockIdx.x * kBinWarps + warp; row < rows; row += gridDim.x * kBinWarps) {
-    const int iz = row / n, iy = row - (row / n) * n;
-    const int kz = signed_freq(iz, n), ky = signed_freq(iy, n);
-    const int base2 = kz * kz + ky * ky;
-    const cx<T>* r = spec + (int64_t)row * m;
-    for (int x0 = 0; x0 < m; x0 += 32 * kBinBatch) {
-      cx<T> f[kBinBatch];
-      if constexpr (!LATTICE) {
+  const int xb = lane * E;
+  auto add0 = [&](int b, A v) {
+    if constexpr (kBinPair<T, LATTICE>) pair_add(reinterpret_cast<float2*>(acc) + b, (float)v);
+    else acc[b] += (double)v;
+  };
+  // runs of this lane's modes
+  int bF = -1, bL = -1, tnext = 0;
+  bool multi = false;
+  A sF0 = 0, sF1 = 0, c0 = 0, c1 = 0;
 #pragma unroll
-        for (int j = 0; j < kBinBatch; ++j) {
-          const int x2 = x0 + 32 * j + lane;
-          f[j] = x2 < m ? r[x2] : cx<T>{(T)0, (T)0};
-        }
+  for (int i = 0; i < kBinLaneMax; ++i) {
+    const int x2 = xb + i;
+    const int n2 = base2 + x2 * x2;
+    if (i < E && x2 < m && n2 > 0) {
+      A v0, v1 = 0;
+      if constexpr (LATTICE) {
+        v0 = x2 == 0 ? 1.0 : 2.0;
+        v1 = v0 * kf * sqrt((double)n2);
+      } else if (x2 == 0) {
+        const T ax = (T)0.5 * (f[i].x + g.x), ay = (T)0.5 * (f[i].y - g.y);
+        v0 = ax * ax + ay * ay;
+      } else {
+        v0 = (T)2 * (f[i].x * f[i].x + f[i].y * f[i].y);
       }
-#pragma unroll
-      for (int j = 0; j < kBinBatch; ++j) {
-        const int x2 = x0 + 32 * j + lane;
-        if (x0 + 32 * j >= m) break;                     // warp-uniform
-        A v0 = 0, v1 = 0;
-        int b = -1;
-        if (x2 > 0 && x2 < m) {
-          const int n2 = base2 + x2 * x2;
-          b = bin_of[n2];
-          if constexpr (LATTICE) {
-            v0 = 2.0;
-            v1 = 2.0 * kf * sqrt((double)n2);
-          } else {
-            v0 = (T)2 * (f[j].x * f[j].x + f[j].y * f[j].y);
-          }
-        } else if (x2 == 0) {
-          const int n2b = base2 + m * m;                 // kx = N/2 mode: added directly
-          const int bb = bin_of[n2b];
-          b = bin_of[base2];                             // kx = 0 mode joins the scan
-          if constexpr (LATTICE) {
-            v0 = 1.0;
-            v1 = kf * sqrt((double)base2);
-            if (bb >= 0) {
-              acc[bb] += 1.0;
-              acc[nk + bb] += kf * sqrt((double)n2b);
-            }
-          } else {
-            const int jz = partner_index(iz, n), jy = partner_index(iy, n);
-            const cx<T> g = spec[((int64_t)jz * n + jy) * m];
-            const T ax = (T)0.5 * (f[j].x + g.x), ay = (T)0.5 * (f[j].y - g.y);
-            const T bx = (T)0.5 * (f[j].y + g.y), by = (T)-0.5 * (f[j].x - g.x);
-            v0 = ax * ax + ay * ay;
-            if (bb >= 0) {
-              if constexpr (ROWF) racc[bb] += (float)(bx * bx + by * by);
-              else acc[bb] += (double)(bx * bx + by * by);
-            }
-          }
+      if (bL < 0) {
+        const int b0 = bin_of_n2(n2, Ts, nk, inv_lr);   // >= 0 for every 0 < n^2 <= 3 N^2 / 4
+        if (b0 >= 0) {
+          bL = bF = b0;
+          tnext = Ts[b0 + 1];
+        } else {
+          v0 = v1 = 0;
         }
-        if (b < 0) v0 = v1 = 0;
-        __syncwarp();
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const A p0 = __shfl_up_sync(full, v0, off);
-          A p1 = 0;
-          if constexpr (LATTICE) p1 = __shfl_up_sync(full, v1, off);
-          const int b2 = __shfl_up_sync(full, b, off);
-          if (lane >= off && b2 == b) {
-            v0 += p0;
-            if constexpr (LATTICE) v1 += p1;
-          }
+      } else if (n2 >= tnext) {
+        if (!multi) {          // the first run waits for the lane combine
+          sF0 = c0;
+          sF1 = c1;
+          multi = true;
+        } else {               // an inner run: the whole bin of this row
+          add0(bL, c0);
+          if constexpr (LATTICE) acc[nk + bL] += (double)c1;
         }
-        const int bn = __shfl_down_sync(full, b, 1);
-        if (b >= 0 && (lane == 31 || bn != b)) {
-          if constexpr (ROWF) {
-            racc[b] += (float)v0;
-          } else {
-            acc[b] += (double)v0;
-            if constexpr (LATTICE) acc[nk + b] += (double)v1;
-          }
-        }
-        __syncwarp();
+        c0 = c1 = 0;
+        do {
+          ++bL;
+          tnext = Ts[bL + 1];
+        } while (n2 >= tnext);
       }
-    }
-    if constexpr (ROWF) {
-      // the row's modes have n^2 in [base2, base2 + m^2]: bins b_lo .. b_hi
-      // (bin_of is non-decreasing where it is >= 0; -1 ends fall back to all bins)
-      int b_lo = bin_of[base2 == 0 ? 1 : base2], b_hi = bin_of[base2 + m * m];
-      if (b_lo < 0) b_lo = 0;
-      if (b_hi < 0) b_hi = nk - 1;
-      for (int b = b_lo + lane; b <= b_hi; b += 32) {
-        acc[b] += (double)racc[b];
-        racc[b] = 0.0f;
-      }
-      __syncwarp();
+      c0 += v0;
+      c1 += v1;
     }
   }
+  // join the boundary runs across lanes: element (key, sums, open), where a
+  // single-run lane is open (its run continues the previous lane's)
+  int k = bL;
+  bool open = !multi && bL >= 0;
+  A s0 = c0, s1 = c1;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int pk = __shfl_up_sync(full, k, off);
+    const A p0 = __shfl_up_sync(full, s0, off);
+    A p1 = 0;
+    if constexpr (LATTICE) p1 = __shfl_up_sync(full, s1, off);
+    const bool popen = __shfl_up_sync(full, (int)open, off) != 0;
+    if (lane >= off && open && pk == k) {
+      s0 += p0;
+      if constexpr (LATTICE) s1 += p1;
+      open = popen;
+    }
+  }
+  // segment ending in the previous lane, and the first bin of the next lane
+  const int qk = __shfl_up_sync(full, k, 1);
+  const A q0 = __shfl_up_sync(full, s0, 1);
+  A q1 = 0;
+  if constexpr (LATTICE) q1 = __shfl_up_sync(full, s1, 1);
+  const int nextF = __shfl_down_sync(full, bF, 1);
+  __syncwarp();
+  if (multi) {   // first run closes the incoming segment of its bin
+    const bool join = lane > 0 && qk == bF;
+    add0(bF, sF0 + (join ? q0 : (A)0));
+    if constexpr (LATTICE) acc[nk + bF] += (double)(sF1 + (join ? q1 : (A)0));
+  }
+  __syncwarp();
+  if (k >= 0 && (lane == 31 || nextF != k)) {   // the segment ends here
+    add0(k, s0);
+    if constexpr (LATTICE) acc[nk + k] += (double)s1;
+  }
+  __syncwarp();
+  if (lane == 0) {   // the kx = N/2 mode of the packed slot, weight 1
+    const int n2b = base2 + m * m;
+    const int bb = bin_of_n2(n2b, Ts, nk, inv_lr);
+    if (bb >= 0) {
+      if constexpr (LATTICE) {
+        acc[bb] += 1.0;
+        acc[nk + bb] += kf * sqrt((double)n2b);
+      } else {
+        const T bx = (T)0.5 * (f[0].y + g.y), by = (T)-0.5 * (f[0].x - g.x);
+        add0(bb, bx * bx + by * by);
+      }
+    }
+  }
+  __syncwarp();
+}
+
+template <typename T, bool LATTICE>
+__device__ __forceinline__ void bin_flush_partials(const double* all, int nk, double* partials) {
+  constexpr int NV = LATTICE ? 2 : 1;
   __syncthreads();
   for (int i = threadIdx.x; i < NV * nk; i += blockDim.x) {
     double sum = 0.0;
 #pragma unroll
-    for (int wi = 0; wi < kBinWarps; ++wi) sum += all[wi * NV * nk + i];
+    for (int wi = 0; wi < kBinWarps; ++wi) {
+      if constexpr (kBinPair<T, LATTICE>) {
+        const float2 p = reinterpret_cast<const float2*>(all)[wi * NV * nk + i];
+        sum += (double)p.x + (double)p.y;
+      } else {
+        sum += all[wi * NV * nk + i];
+      }
+    }
     partials[(int64_t)blockIdx.x * NV * nk + i] = sum;
   }
+}
+
+// Rows read by each lane from global memory (lattice sums, and grids whose
+// lane segments are not whole 16-byte units).
+template <typename T, bool LATTICE>
+__global__ void __launch_bounds__(kBinWarps * 32)
+k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const int* __restrict__ thr, float inv_lr,
+            double kf, double* __restrict__ partials) {
+  constexpr int NV = LATTICE ? 2 : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* all = reinterpret_cast<double*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* acc = all + warp * NV * nk;
+  int* Ts = reinterpret_cast<int*>(all + kBinWarps * NV * nk);
+  for (int i = threadIdx.x; i < kBinWarps * NV * nk; i += blockDim.x) all[i] = 0.0;
+  for (int i = threadIdx.x; i <= nk; i += blockDim.x) Ts[i] = thr[i];
+  __syncthreads();
+  const int m = n / 2;
+  const int E = (m + 31) >> 5;
+  const int xb = lane * E;
+  const int rows = n * n;
+  for (int row = blockIdx.x * kBinWarps + warp; row < rows; row += gridDim.x * kBinWarps) {
+    const int iz = row / n, iy = row - (row / n) * n;
+    const int kz = signed_freq(iz, n), ky = signed_freq(iy, n);
+    const cx<T>* r = spec + (int64_t)row * m;
+    cx<T> g = {(T)0, (T)0};   // lane 0: the packed slot of the partner row (-z, -y)
+    cx<T> f[kBinLaneMax];
+    if constexpr (!LATTICE) {
+      if (lane == 0) g = spec[((int64_t)partner_index(iz, n) * n + partner_index(iy, n)) * m];
+#pragma unroll
+      for (int i = 0; i < kBinLaneMax; ++i)
+        if (i < E && xb + i < m) f[i] = r[xb + i];
+    }
+    bin_row<T, LATTICE>(f, g, kz * kz + ky * ky, m, E, lane, Ts, nk, inv_lr, kf, acc);
+  }
+  bin_flush_partials<T, LATTICE>(all, nk, partials);
+}
+
+// bin_row for the staged power sums: E (compile time) modes per lane, all
+// inside the row; the lane's first bin is found once, the run keys carry
+// their open flag in bit 0 so the lane scan moves two words per step.
+template <typename T, int E>
+__device__ __forceinline__ void bin_row_staged(const cx<T> (&f)[kBinLaneMax], cx<T> g, int base2, int m, int lane,
+                                               const int* Ts, int nk, float inv_lr, double* acc) {
+  auto add0 = [&](int b, T v) {
+    if constexpr (sizeof(T) == 4) pair_add(reinterpret_cast<float2*>(acc) + b, (float)v);
+    else acc[b] += (double)v;
+  };
+  const unsigned full = 0xffffffffu;
+  const int xb = lane * E;
+  int n2 = base2 + xb * xb;
+  int bL = bin_of_n2(n2 > 0 ? n2 : 1, Ts, nk, inv_lr);   // n^2 = 0 (the mean) adds nothing
+  const int bF = bL;
+  int tnext = Ts[bL + 1];
+  bool multi = false;
+  T sF = 0, c = 0;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int x2 = xb + i;
+    if (i > 0) n2 = base2 + x2 * x2;
+    T v;
+    if (i == 0 && lane == 0) {   // x2 = 0: the kx = 0 mode of the packed slot, weight 1
+      const T ax = (T)0.5 * (f[0].x + g.x), ay = (T)0.5 * (f[0].y - g.y);
+      v = n2 > 0 ? ax * ax + ay * ay : (T)0;
+    } else {
+      v = (T)2 * (f[i].x * f[i].x + f[i].y * f[i].y);
+    }
+    if (n2 >= tnext) {
+      if (!multi) {          // the first run waits for the lane combine
+        sF = c;
+        multi = true;
+      } else {               // an inner run: the whole bin of this row
+        add0(bL, c);
+      }
+      c = 0;
+      do {
+        ++bL;
+        tnext = Ts[bL + 1];
+      } while (n2 >= tnext);
+    }
+    c += v;
+  }
+  int kk = (bL << 1) | (multi ? 0 : 1);   // key, open (a single-run lane continues the previous one)
+  T s0 = c;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int pkk = __shfl_up_sync(full, kk, off);
+    const T p0 = __shfl_up_sync(full, s0, off);
+    if (lane >= off && (kk & 1) && (pkk >> 1) == (kk >> 1)) {
+      s0 += p0;
+      kk = (kk & ~1) | (pkk & 1);
+    }
+  }
+  const int k = kk >> 1;
+  const int qk = __shfl_up_sync(full, k, 1);
+  const T q0 = __shfl_up_sync(full, s0, 1);
+  const int nextF = __shfl_down_sync(full, bF, 1);
+  __syncwarp();
+  if (multi) add0(bF, sF + ((lane > 0 && qk == bF) ? q0 : (T)0));
+  __syncwarp();
+  if (lane == 31 || nextF != k) add0(k, s0);
+  __syncwarp();
+  if (lane == 0) {   // the kx = N/2 mode of the packed slot, weight 1
+    const int n2b = base2 + m * m;
+    const int bb = bin_of_n2(n2b, Ts, nk, inv_lr);
+    const T bx = (T)0.5 * (f[0].y + g.y), by = (T)-0.5 * (f[0].x - g.x);
+    if (bb >= 0) add0(bb, bx * bx + by * by);
+  }
+  __syncwarp();
+}
+
+// FP32 power sums with the rows staged by TMA: each warp runs a
+// kBinStages-deep ring of row buffers in shared memory.  A tensor map views
+// the spectrum as [rows][32 lanes][E modes] (8-byte elements); one 3-D copy
+// brings a whole row, swizzled with the span equal to a lane's segment
+// (E = 4, 8, 16: 32-, 64-, 128-byte swizzle; E = 2: none), so lane L reading
+// its own E modes as 16-byte units hits a different bank group from its
+// neighbours.  Each row buffer holds 4 KB whatever E.  A 16-byte bulk copy
+// brings the partner row's packed slot.  The copies of row r + kBinStages
+// steps are issued as soon as row r is in registers.  Waits are bounded: on a
+// timeout the kernel records PM_ERR_TIMEOUT, waits (bounded) for its own
+// copies still in flight and stops.
+constexpr int kBinStages = 3;
+
+// Bytes of one staged row buffer: 32 lines of 128 bytes (a whole number of
+// swizzle atoms for every span), also when the row itself is smaller.
+__host__ __device__ constexpr int bin_stage_row_bytes(int) { return 32 * 128; }
+// Shared memory of k_bin_power_tma: accumulators and thresholds (rounded up
+// to 1024 bytes), the warps' row rings, partner slots, mbarriers.
+__host__ __device__ constexpr size_t bin_tma_head(int nk) {
+  return ((size_t)kBinWarps * nk * sizeof(double) + (size_t)(nk + 1) * sizeof(int) + 1023) & ~(size_t)1023;
+}
+__host__ __device__ constexpr size_t bin_tma_smem(int nk, int E) {
+  return bin_tma_head(nk) + (size_t)kBinWarps * kBinStages * (bin_stage_row_bytes(E) + 16 + sizeof(uint64_t)) +
+         1024;   // slack to align the dynamic base to 1024 bytes
+}
+
+// Byte offset of linear offset lin under the TMA swizzle whose span is the
+// E * 8-byte lane segment: 16-byte unit bits [4, 4 + s) XOR address bits
+// [7, 7 + s), s = log2(E * 8 / 16).
+template <int E>
+__device__ __forceinline__ int swizzle_lane(int lin) {
+  constexpr int mask = E == 16 ? 0x70 : E == 8 ? 0x30 : E == 4 ? 0x10 : 0;
+  return lin ^ ((lin >> 3) & mask);
+}
+
+template <int E>
+__global__ void __launch_bounds__(kBinWarps * 32)
+k_bin_power_tma(const __grid_constant__ CUtensorMap map, const cx<float>* __restrict__ spec, int n, int nk,
+                const int* __restrict__ thr, float inv_lr, double* __restrict__ partials, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_dyn[];
+  unsigned char* smem_raw = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
+  double* all = reinterpret_cast<double*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* acc = all + warp * nk;
+  int* Ts = reinterpret_cast<int*>(all + kBinWarps * nk);
+  constexpr int RB = bin_stage_row_bytes(E);
+  const size_t head = bin_tma_head(nk);
+  unsigned char* rows_s = smem_raw + head + (size_t)warp * kBinStages * RB;
+  unsigned char* part_s = smem_raw + head + (size_t)kBinWarps * kBinStages * RB + (size_t)warp * kBinStages * 16;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + head + (size_t)kBinWarps * kBinStages * (RB + 16)) +
+                   warp * kBinStages;
+  for (int i = threadIdx.x; i < kBinWarps * nk; i += blockDim.x) all[i] = 0.0;
+  for (int i = threadIdx.x; i <= nk; i += blockDim.x) Ts[i] = thr[i];
+  if (lane == 0) {
+    for (int st = 0; st < kBinStages; ++st) mbar_init(&bars[st], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const unsigned full = 0xffffffffu;
+  const int m = n / 2;                            // = 32 E
+  const int rows = n * n;
+  const int step = gridDim.x * kBinWarps;
+  const int row0 = blockIdx.x * kBinWarps + warp;
+  auto issue = [&](int row, int st) {   // lane 0
+    mbar_expect_tx(&bars[st], (uint32_t)(32 * E * 8 + 16));
+    tma_load_3d(rows_s + (size_t)st * RB, &map, &bars[st], 0, 0, row);
+    const int iz = row / n, iy = row - (row / n) * n;
+    bulk_load(part_s + st * 16, spec + ((int64_t)partner_index(iz, n) * n + partner_index(iy, n)) * m, 16u,
+              &bars[st]);
+  };
+  if (lane == 0)
+    for (int st = 0; st < kBinStages; ++st)
+      if (row0 + st * step < rows) issue(row0 + st * step, st);
+  int k = 0;
+  for (int row = row0; row < rows; row += step, ++k) {
+    const int st = k % kBinStages;
+    const uint32_t parity = (uint32_t)((k / kBinStages) & 1);
+    const bool ok = mbar_wait_bounded(&bars[st], parity);
+    if (!__all_sync(full, ok)) {
+      if (lane == 0) {
+        atomicCAS(status, 0, PM_ERR_TIMEOUT);
+        // this warp's copies still in flight: rows row .. row + (kBinStages - 1) steps
+        for (int j = 0; j < kBinStages; ++j)
+          if (row + j * step < rows)
+            mbar_wait_bounded(&bars[(k + j) % kBinStages], (uint32_t)(((k + j) / kBinStages) & 1));
+      }
+      __syncwarp();
+      break;
+    }
+    const unsigned char* buf = rows_s + (size_t)st * RB;
+    cx<float> f[kBinLaneMax];
+#pragma unroll
+    for (int j = 0; j < E / 2; ++j) {
+      const float4 v = *reinterpret_cast<const float4*>(buf + swizzle_lane<E>(lane * E * 8 + 16 * j));
+      f[2 * j] = {v.x, v.y};
+      f[2 * j + 1] = {v.z, v.w};
+    }
+    const cx<float> g = *reinterpret_cast<const cx<float>*>(part_s + st * 16);
+    fence_proxy_async_shared();   // these reads come before the buffer's next copy
+    __syncwarp();
+    if (lane == 0 && row + kBinStages * step < rows) issue(row + kBinStages * step, st);
+    const int iz = row / n, iy = row - (row / n) * n;
+    const int kz = signed_freq(iz, n), ky = signed_freq(iy, n);
+    bin_row_staged<float, E>(f, g, kz * kz + ky * ky, m, lane, Ts, nk, inv_lr, acc);
+  }
+  bin_flush_partials<float, false>(all, nk, partials);
 }
 
 // ---------------------------------------------------------------------------
@@ -453,14 +716,34 @@ k_interp_kick_fd(const void* __restrict__ pos, int64_t np, int n, double delta, 
     T py[2][2][4];   // [dz][dx][y0-2, y0-1, y0+2, y0+3]
     T pz[2][2][4];   // [dy][dx][z0-2, z0-1, z0+2, z0+3]
     constexpr int kFar[4] = {0, 1, 4, 5};
+    // FP32 x runs away from the row ends: three aligned 16-byte loads from
+    // a = (x0 - 2) rounded down to 4 cover x0 - 2 .. x0 + 3, picked by o = (x0 - 2) & 3
+    const int a4 = (c[0] - 2) & ~3;
+    if (sizeof(T) == 4 && c[0] >= 2 && a4 + 12 <= n) {
+      const int o = (c[0] - 2) & 3;
 #pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
+      for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
-        const T* r = phi + row(ys[2 + dy], zs[2 + dz]);
+        for (int dy = 0; dy < 2; ++dy) {
+          const float4* r4 = reinterpret_cast<const float4*>(phi + row(ys[2 + dy], zs[2 + dz]) + a4);
+          const float4 q0 = r4[0], q1 = r4[1], q2 = r4[2];
+          const float w9[9] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x};
+          float u[7];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) px[dz][dy][j] = r[xs[j]];
-      }
+          for (int j = 0; j < 7; ++j) u[j] = (o & 2) ? w9[j + 2] : w9[j];
+#pragma unroll
+          for (int j = 0; j < 6; ++j) px[dz][dy][j] = (T)((o & 1) ? u[j + 1] : u[j]);
+        }
+    } else {
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const T* r = phi + row(ys[2 + dy], zs[2 + dz]);
+#pragma unroll
+          for (int j = 0; j < 6; ++j) px[dz][dy][j] = r[xs[j]];
+        }
+    }
 #pragma unroll
     for (int dz = 0; dz < 2; ++dz)
 #pragma unroll

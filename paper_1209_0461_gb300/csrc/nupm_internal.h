@@ -88,6 +88,7 @@ struct GridArgs {
   const CUtensorMap* tmap_spec_y;  // TMA maps of the column passes (nullptr: plain kernels)
   const CUtensorMap* tmap_spec_z;
   const CUtensorMap* tmap_g_y;
+  const CUtensorMap* tmap_bins = nullptr; // FP32 spectrum as [rows][32][E] 8-byte elements, 128-byte swizzle
   const CUtensorMap* tmap_z16 = nullptr;  // spectrum along z, 128-byte segments (wide_z = 2), or nullptr
   int sm_count;
   const float* fac;               // FP32 path: fac table (kFacTable points)
@@ -108,8 +109,8 @@ struct GridArgs {
   int row_sort##SFX(const GridArgs& g, const void* pos, cudaStream_t s);                    \
   int deposit_fft_x##SFX(const GridArgs& g, const void* pos, bool keep, cudaStream_t s);    \
   int fft_pass##SFX(const GridArgs& g, int pass, cudaStream_t s);                           \
-  int bins##SFX(const GridArgs& g, bool lattice, int nk, const short* bin_of, double kf,      \
-                double* partials, int nblk, double* out, cudaStream_t s);                   \
+  int bins##SFX(const GridArgs& g, bool lattice, int nk, const int* thr, float inv_lr,       \
+                double kf, double* partials, int nblk, double* out, cudaStream_t s);        \
   int green##SFX(const GridArgs& g, cudaStream_t s);                                        \
   int interp##SFX(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, \
                   cudaStream_t s);                                                          \

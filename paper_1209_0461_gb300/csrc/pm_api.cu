@@ -34,7 +34,8 @@ struct pm_ctx {
   void* g = nullptr;          // 3 packed fields (deposit grid aliases the first two)
   void* tw_n = nullptr;
   void* tw_m = nullptr;
-  short* d_binof = nullptr;    // bin of each n^2 (-1: none)
+  int* d_thr = nullptr;        // bin thresholds T_0..T_nk (int32)
+  float bin_inv_lr = 0;        // nk / ln r^2: the bin of n^2 is floor(nk ln n^2 / ln r^2)
   double* d_partials = nullptr;
   double* d_bins = nullptr;   // [3][nk]
   double* d_pi = nullptr;     // [ns][nk]
@@ -66,6 +67,9 @@ struct pm_ctx {
   // spectrum along z with 128-byte segments: the TMA-staged z passes (wide_z = 2)
   bool tma_z16 = false;
   alignas(64) CUtensorMap tm_z16;
+  // FP32 spectrum rows as [N^2][32][N/64] for the staged bin sums
+  bool tma_bins = false;
+  alignas(64) CUtensorMap tm_bins;
   int sm_count = 152;
   double green_coeff = 0;     // -1.5 Omega_M / (a kf^2 N^3) of the last response
   int* d_status = nullptr;
@@ -311,7 +315,7 @@ void drain_timing(pm_ctx* c) {
 
 // Encode a 4-D tensor map over a packed complex field array [F][N][N][M]
 // (x2 fastest) with a box of w x2-columns by `box` elements along y or z.
-int encode_col_map(pm_ctx* c, CUtensorMap* map, void* base, int fields, bool along_z, int w) {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -320,10 +324,36 @@ int encode_col_map(pm_ctx* c, CUtensorMap* map, void* base, int fields, bool alo
             cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !fn) {
       cudaGetLastError();
-      return fail(c, PM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+      return nullptr;
     }
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
+  return encode;
+}
+
+// The FP32 packed spectrum [N^2 rows][M] viewed as [rows][32 lanes][E = M / 32]
+// 8-byte elements; box = one whole row, swizzle span = E * 8 bytes.
+int encode_bins_map(pm_ctx* c) {
+  const auto encode = tensor_map_encoder();
+  if (!encode) return fail(c, PM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  const cuuint64_t E = (cuuint64_t)c->m / 32;
+  cuuint64_t dims[3] = {E, 32, (cuuint64_t)c->n * c->n};
+  cuuint64_t strides[2] = {E * 8, (cuuint64_t)c->m * 8};
+  cuuint32_t boxd[3] = {(cuuint32_t)E, 32u, 1u};
+  cuuint32_t estr[3] = {1, 1, 1};
+  // the swizzle span equals a lane's segment (E * 8 bytes), so the box lands densely
+  const CUtensorMapSwizzle sw = E == 16 ? CU_TENSOR_MAP_SWIZZLE_128B : E == 8 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                : E == 4 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE;
+  const CUresult r = encode(&c->tm_bins, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, c->spec, dims, strides, boxd, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(c, PM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return PM_OK;
+}
+
+int encode_col_map(pm_ctx* c, CUtensorMap* map, void* base, int fields, bool along_z, int w) {
+  const auto encode = tensor_map_encoder();
+  if (!encode) return fail(c, PM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   const int n = c->n, m = c->m;
   const bool f64 = c->fp64;
   const int box = n < 256 ? n : 256;
@@ -371,6 +401,7 @@ GridArgs grid_args(const pm_ctx* c) {
   g.tmap_spec_z = c->tma ? &c->tm_spec_z : nullptr;
   g.tmap_g_y = c->tma ? &c->tm_g_y : nullptr;
   g.tmap_z16 = c->tma_z16 ? &c->tm_z16 : nullptr;
+  g.tmap_bins = c->tma_bins ? &c->tm_bins : nullptr;
   g.sm_count = c->sm_count;
   g.fac = c->d_fac;
   g.fac_inv_du = (float)((kFacTable - 1) / (0.5 * log((double)c->n2max)));
@@ -380,7 +411,7 @@ GridArgs grid_args(const pm_ctx* c) {
 
 void release(pm_ctx* c) {
   void* ptrs[] = {c->d_bins_lattice, c->d_X, c->d_lnR,
-                  c->spec, c->g, c->tw_n, c->tw_m, c->d_binof, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
+                  c->spec, c->g, c->tw_n, c->tw_m, c->d_thr, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
                   c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_rlist, c->d_gtab,
                   c->d_dtab, c->d_wtab, c->d_plane0, c->d_fac, c->d_rowc, c->d_rows, c->d_rowcur,
                   c->d_scantot, c->d_perm, c->d_rec, c->d_status};
@@ -544,7 +575,7 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) rc = dalloc(c, &c->g, 3 * fbytes, "force fields");
   if (rc == PM_OK) rc = dalloc(c, &c->tw_n, (size_t)n * c->cplx, "twiddles N");
   if (rc == PM_OK) rc = dalloc(c, &c->tw_m, (size_t)(n / 2) * c->cplx, "twiddles M");
-  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_binof, (size_t)(c->n2max + 1) * sizeof(short), "bin table");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_thr, (size_t)(c->nk + 1) * sizeof(int), "bin thresholds");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_partials, (size_t)c->nblk_bins * 2 * c->nk * sizeof(double), "bin partials");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_bins, 3 * (size_t)c->nk * sizeof(double), "bins");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_bins_lattice, 2 * (size_t)c->nk * sizeof(double), "lattice bins");
@@ -584,14 +615,10 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
     const double r = sqrt(3.0) * n / 2.0 * (1.0 + 1e-12);
     c->thr.resize(c->nk + 1);
     for (int b = 0; b <= c->nk; ++b) c->thr[b] = (long long)ceil(pow(r, 2.0 * b / c->nk));
-    std::vector<short> bo((size_t)c->n2max + 1);
-    int b = -1;
-    for (long long n2 = 0; n2 <= c->n2max; ++n2) {
-      while (b + 1 <= c->nk && c->thr[b + 1] <= n2) ++b;
-      bo[n2] = (short)((b >= 0 && b < c->nk) ? b : -1);
-    }
-    rc = cuda_check(c, cudaMemcpy(c->d_binof, bo.data(), bo.size() * sizeof(short), cudaMemcpyHostToDevice),
-                    "bin table upload");
+    std::vector<int> t32(c->thr.begin(), c->thr.end());   // T_nk <= 3 N^2 / 4 + 1 fits int32
+    c->bin_inv_lr = (float)(c->nk / (2.0 * log(r)));
+    rc = cuda_check(c, cudaMemcpy(c->d_thr, t32.data(), t32.size() * sizeof(int), cudaMemcpyHostToDevice),
+                    "bin threshold upload");
   }
   if (rc == PM_OK) {
     std::vector<double> gl(2 * kMaxQuad, 0.0);
@@ -630,12 +657,18 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
       c->tma_z16 = encode_col_map(c, &c->tm_z16, c->spec, 1, true, c->fp64 ? 8 : 16) == PM_OK;
       c->err = keep;
     }
+    // TMA-staged FP32 bin sums (N / 64 modes of a row per lane: 2 .. 16)
+    if (rc == PM_OK && pow2 && !c->fp64 && c->n >= 128) {
+      const std::string keep = c->err;
+      c->tma_bins = encode_bins_map(c) == PM_OK;
+      c->err = keep;
+    }
   }
   if (rc == PM_OK) {
     // mode counts and sum |k| per bin depend on the lattice only: once per context
     GridArgs g = grid_args(c);
-    rc = c->fp64 ? bins_f64(g, true, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins, 0)
-                 : bins_f32(g, true, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins, 0);
+    rc = c->fp64 ? bins_f64(g, true, c->nk, c->d_thr, c->bin_inv_lr, c->kf, c->d_partials, c->nblk_bins, c->d_bins, 0)
+                 : bins_f32(g, true, c->nk, c->d_thr, c->bin_inv_lr, c->kf, c->d_partials, c->nblk_bins, c->d_bins, 0);
     if (rc == PM_OK) rc = cuda_check(c, cudaGetLastError(), "lattice bins");
     if (rc == PM_OK)
       rc = cuda_check(c, cudaMemcpy(c->d_bins_lattice, c->d_bins, 2 * (size_t)c->nk * sizeof(double),
@@ -693,9 +726,9 @@ int pm_deposit(pm_ctx* c, const void* pos) {
   }
   if (rc == PM_OK) {
     Stage st(c, PM_ST_BINS, 2);
-    rc = c->fp64 ? bins_f64(g, false, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins + 2 * c->nk,
+    rc = c->fp64 ? bins_f64(g, false, c->nk, c->d_thr, c->bin_inv_lr, c->kf, c->d_partials, c->nblk_bins, c->d_bins + 2 * c->nk,
                             c->stream)
-                 : bins_f32(g, false, c->nk, c->d_binof, c->kf, c->d_partials, c->nblk_bins, c->d_bins + 2 * c->nk,
+                 : bins_f32(g, false, c->nk, c->d_thr, c->bin_inv_lr, c->kf, c->d_partials, c->nblk_bins, c->d_bins + 2 * c->nk,
                             c->stream);
   }
   if (rc != PM_OK) return fail(c, rc, "pm_deposit: unsupported grid");

@@ -106,10 +106,11 @@ def test_fp32_kick_ragged_64():
     _check_common(w, g, r, False)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("n", [16, 32, 64, 128, 192, 256])
+@pytest.mark.parametrize("prec,n", [(p, n) for p in ("fp64", "fp32") for n in (16, 32, 64, 128, 192, 256)] +
+                         [("fp32", 512)])
 def test_fft_and_bins_sizes(n, prec):
-    # spectrum of the deposit at every built grid size, both precisions
+    # spectrum of the deposit and its bin sums at every built grid size, both
+    # precisions (the FP32 sums of 128^3 .. 1024^3 grids stage rows by TMA)
     w = synth.Workload(f"fft{n}", n, min(n, 64), 2.0 * n, 0.15, 3, 2, 12, prec)
     inp = make_inputs(w)
     g = gpu_kick(w, inp)
@@ -122,7 +123,16 @@ def test_fft_and_bins_sizes(n, prec):
     else:
         assert np.sqrt(np.mean(d ** 2)) < 2e-6 * scale
     b = O.bin_power(spec, w.box, w.n_kbins)
-    assert np.array_equal(g["bins"][0], b["count"])
+    cnt, ks, ps = g["bins"]
+    assert np.array_equal(cnt, b["count"])
+    ne = b["count"] > 0
+    rk = np.max(np.abs(ks[ne] - b["ksum"][ne]) / b["ksum"][ne])
+    rp = np.max(np.abs(ps[ne] - b["psum"][ne]) / b["psum"][ne])
+    print(f"{prec} N={n}: ksum max rel {rk:.1e}, psum max rel {rp:.1e}")
+    # FP64 sums of up to ~7e7 |k| values per bin, summed in different orders
+    # (the oracle's bincount runs sequentially: error up to ~n eps)
+    assert rk < 1e-10
+    assert rp < (1e-10 if prec == "fp64" else 2e-5)
 
 
 @pytest.mark.parametrize("flags", [KEEP_DEPOSIT, KEEP_DEPOSIT | SPECTRAL_GRADIENT])
