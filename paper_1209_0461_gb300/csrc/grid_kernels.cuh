@@ -375,34 +375,31 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const int* __restrict
 
 // bin_row for the staged power sums: E (compile time) modes per lane, all
 // inside the row; the lane's first bin is found once, the run keys carry
-// their open flag in bit 0 so the lane scan moves two words per step.
+// their open flag in bit 0 so the lane scan moves two words per step.  The
+// kx = N/2 mode of the packed slot (n^2 = base2 + M^2, weight 1) is lane 31's
+// last mode, so it joins the runs instead of a separate add.
 template <typename T, int E>
-__device__ __forceinline__ void bin_row_staged(const cx<T> (&f)[kBinLaneMax], cx<T> g, int base2, int m, int lane,
+__device__ __forceinline__ void bin_row_staged(const cx<T> (&f)[kBinLaneMax], cx<T> g, int base2, int lane,
                                                const int* Ts, int nk, float inv_lr, double* acc) {
+  constexpr int M = 32 * E;
   auto add0 = [&](int b, T v) {
     if constexpr (sizeof(T) == 4) pair_add(reinterpret_cast<float2*>(acc) + b, (float)v);
     else acc[b] += (double)v;
   };
   const unsigned full = 0xffffffffu;
   const int xb = lane * E;
+  // lane 0 unpacks the slot: A (kx = 0) stays, B (kx = N/2) goes to lane 31
+  const T ax = (T)0.5 * (f[0].x + g.x), ay = (T)0.5 * (f[0].y - g.y);
+  const T bx = (T)0.5 * (f[0].y + g.y), by = (T)-0.5 * (f[0].x - g.x);
+  const T vB = __shfl_sync(full, bx * bx + by * by, 0);
   int n2 = base2 + xb * xb;
   int bL = bin_of_n2(n2 > 0 ? n2 : 1, Ts, nk, inv_lr);   // n^2 = 0 (the mean) adds nothing
   const int bF = bL;
   int tnext = Ts[bL + 1];
   bool multi = false;
   T sF = 0, c = 0;
-#pragma unroll
-  for (int i = 0; i < E; ++i) {
-    const int x2 = xb + i;
-    if (i > 0) n2 = base2 + x2 * x2;
-    T v;
-    if (i == 0 && lane == 0) {   // x2 = 0: the kx = 0 mode of the packed slot, weight 1
-      const T ax = (T)0.5 * (f[0].x + g.x), ay = (T)0.5 * (f[0].y - g.y);
-      v = n2 > 0 ? ax * ax + ay * ay : (T)0;
-    } else {
-      v = (T)2 * (f[i].x * f[i].x + f[i].y * f[i].y);
-    }
-    if (n2 >= tnext) {
+  auto mode = [&](int n2m, T v) {
+    if (n2m >= tnext) {
       if (!multi) {          // the first run waits for the lane combine
         sF = c;
         multi = true;
@@ -413,10 +410,20 @@ __device__ __forceinline__ void bin_row_staged(const cx<T> (&f)[kBinLaneMax], cx
       do {
         ++bL;
         tnext = Ts[bL + 1];
-      } while (n2 >= tnext);
+      } while (n2m >= tnext);
     }
     c += v;
+  };
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int x2 = xb + i;
+    if (i > 0) n2 = base2 + x2 * x2;
+    T v;
+    if (i == 0 && lane == 0) v = n2 > 0 ? ax * ax + ay * ay : (T)0;   // kx = 0 mode, weight 1
+    else v = (T)2 * (f[i].x * f[i].x + f[i].y * f[i].y);
+    mode(n2, v);
   }
+  if (lane == 31) mode(base2 + M * M, vB);
   int kk = (bL << 1) | (multi ? 0 : 1);   // key, open (a single-run lane continues the previous one)
   T s0 = c;
 #pragma unroll
@@ -436,13 +443,6 @@ __device__ __forceinline__ void bin_row_staged(const cx<T> (&f)[kBinLaneMax], cx
   if (multi) add0(bF, sF + ((lane > 0 && qk == bF) ? q0 : (T)0));
   __syncwarp();
   if (lane == 31 || nextF != k) add0(k, s0);
-  __syncwarp();
-  if (lane == 0) {   // the kx = N/2 mode of the packed slot, weight 1
-    const int n2b = base2 + m * m;
-    const int bb = bin_of_n2(n2b, Ts, nk, inv_lr);
-    const T bx = (T)0.5 * (f[0].y + g.y), by = (T)-0.5 * (f[0].x - g.x);
-    if (bb >= 0) add0(bb, bx * bx + by * by);
-  }
   __syncwarp();
 }
 
@@ -506,15 +506,15 @@ k_bin_power_tma(const __grid_constant__ CUtensorMap map, const cx<float>* __rest
   }
   __syncthreads();
   const unsigned full = 0xffffffffu;
-  const int m = n / 2;                            // = 32 E
-  const int rows = n * n;
+  constexpr int N = 64 * E, M = 32 * E;            // n == N
+  const int rows = N * N;
   const int step = gridDim.x * kBinWarps;
   const int row0 = blockIdx.x * kBinWarps + warp;
   auto issue = [&](int row, int st) {   // lane 0
     mbar_expect_tx(&bars[st], (uint32_t)(32 * E * 8 + 16));
     tma_load_3d(rows_s + (size_t)st * RB, &map, &bars[st], 0, 0, row);
-    const int iz = row / n, iy = row - (row / n) * n;
-    bulk_load(part_s + st * 16, spec + ((int64_t)partner_index(iz, n) * n + partner_index(iy, n)) * m, 16u,
+    const int iz = row / N, iy = row % N;
+    bulk_load(part_s + st * 16, spec + ((int64_t)partner_index(iz, N) * N + partner_index(iy, N)) * M, 16u,
               &bars[st]);
   };
   if (lane == 0)
@@ -548,9 +548,9 @@ k_bin_power_tma(const __grid_constant__ CUtensorMap map, const cx<float>* __rest
     fence_proxy_async_shared();   // these reads come before the buffer's next copy
     __syncwarp();
     if (lane == 0 && row + kBinStages * step < rows) issue(row + kBinStages * step, st);
-    const int iz = row / n, iy = row - (row / n) * n;
-    const int kz = signed_freq(iz, n), ky = signed_freq(iy, n);
-    bin_row_staged<float, E>(f, g, kz * kz + ky * ky, m, lane, Ts, nk, inv_lr, acc);
+    const int iz = row / N, iy = row % N;
+    const int kz = signed_freq(iz, N), ky = signed_freq(iy, N);
+    bin_row_staged<float, E>(f, g, kz * kz + ky * ky, lane, Ts, nk, inv_lr, acc);
   }
   bin_flush_partials<float, false>(all, nk, partials);
 }
