@@ -235,8 +235,10 @@ struct ColTmaZCfg {
   static constexpr size_t XCH_BYTES = (size_t)ColSmem<T, W, PAD>::words(N) * sizeof(cx<T>);
   static constexpr size_t BUF_BYTES = XCH_BYTES > TILE_BYTES ? XCH_BYTES : TILE_BYTES;
   static constexpr size_t FAC_BYTES = sizeof(T) == 4 ? 2048 * sizeof(float) : 0;
-  static constexpr size_t SMEM = BUF_BYTES + FAC_BYTES + 64;
+  static constexpr size_t GS_BYTES = (size_t)E * THREADS * sizeof(T);   // Green factors [E][THREADS]
+  static constexpr size_t SMEM = BUF_BYTES + FAC_BYTES + GS_BYTES + 64;
   static constexpr int TILES_PER_ROW = M / W;
+  static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
 };
 
 template <typename T, int N, int MODE>
@@ -252,7 +254,8 @@ k_col_tma_z(const __grid_constant__ CUtensorMap map, ColTmaArgs<T> A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   float* fac_s = reinterpret_cast<float*>(smem_raw + Cfg::BUF_BYTES);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::BUF_BYTES + Cfg::FAC_BYTES);
+  T* gs = reinterpret_cast<T*>(smem_raw + Cfg::BUF_BYTES + Cfg::FAC_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::BUF_BYTES + Cfg::FAC_BYTES + Cfg::GS_BYTES);
   const int items = Cfg::TILES_PER_ROW * N;   // (x2 tile, y)
   const int c = threadIdx.x % W;
   const int t = threadIdx.x / W;
@@ -278,6 +281,33 @@ k_col_tma_z(const __grid_constant__ CUtensorMap map, ColTmaArgs<T> A) {
   if (threadIdx.x == 0 && first < items) issue(first);
   int k = 0;
   for (int item = first; item < items; item += step, ++k) {
+    if constexpr (MODE != kColFwdZ) {
+      // Green factors of this tile (each thread its own slots) while its copy
+      // is in flight; the packed column x2 = 0 reads its plane0 values later
+      const int x2 = (item % Cfg::TILES_PER_ROW) * W + c, y = item / Cfg::TILES_PER_ROW;
+      const int ky = y < N / 2 ? y : y - N;
+      const int base2 = ky * ky + x2 * x2;
+      const T wyx = A.wtab ? A.wtab[y] * A.wtab[x2] : (T)1;
+      if (x2 != 0) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int iz = t + NT * i;
+          const int kz = iz < N / 2 ? iz : iz - N;
+          const int n2 = base2 + kz * kz;
+          T gval;
+          if constexpr (kFac) {
+            const float tt = 0.5f * __logf((float)n2) * A.fac_inv_du;
+            const int j = min((int)tt, 2048 - 2);
+            const float fr = tt - (float)j;
+            gval = (T)(A.coeff * (fac_s[j] + fr * (fac_s[j + 1] - fac_s[j])) / (float)n2);
+          } else {
+            gval = A.gtab[n2];
+          }
+          if (A.wtab) gval *= wyx * A.wtab[iz];
+          gs[i * Cfg::THREADS + threadIdx.x] = gval;
+        }
+      }
+    }
     const bool ok = mbar_wait_bounded(bar, (uint32_t)(k & 1));
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
@@ -303,9 +333,6 @@ k_col_tma_z(const __grid_constant__ CUtensorMap map, ColTmaArgs<T> A) {
 #pragma unroll
         for (int i = 0; i < RL; ++i) dst[(int64_t)(t + NT * b + i * (N / RL)) * ES] = v[b * RL + i];
     } else {
-      const int ky = y < N / 2 ? y : y - N;
-      const int base2 = ky * ky + x2 * x2;
-      const T wyx = A.wtab ? A.wtab[y] * A.wtab[x2] : (T)1;
 #pragma unroll 1
       for (int tr = 0; tr < NTR; ++tr) {
         if (tr == 1) {   // the second transform reads its input again (L2)
@@ -319,19 +346,7 @@ k_col_tma_z(const __grid_constant__ CUtensorMap map, ColTmaArgs<T> A) {
           if (x2 == 0) {   // packed column: its pre-multiplied kx = 0 / N/2 values
             f = A.plane0[(int64_t)y * N + iz];
           } else {
-            const int kz = iz < N / 2 ? iz : iz - N;
-            const int n2 = base2 + kz * kz;
-            T gval;
-            if constexpr (kFac) {
-              const float tt = 0.5f * __logf((float)n2) * A.fac_inv_du;
-              const int j = min((int)tt, 2048 - 2);
-              const float fr = tt - (float)j;
-              gval = (T)(A.coeff * (fac_s[j] + fr * (fac_s[j + 1] - fac_s[j])) / (float)n2);
-            } else {
-              gval = A.gtab[n2];
-            }
-            if (A.wtab) gval *= wyx * A.wtab[iz];
-            f = cscale(v[i], gval);
+            f = cscale(v[i], gs[i * Cfg::THREADS + threadIdx.x]);
           }
           if (tr == 1) {
             const T d = A.dtab[iz];
