@@ -686,7 +686,7 @@ __device__ __forceinline__ void fold_weights(T f0, T f1, T (&e)[6]) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 4)   // FP32: 72 registers, 7 CTAs per SM
 k_interp_kick_fd(const void* __restrict__ pos, int64_t np, int n, double delta, const T* __restrict__ phi,
                  T* __restrict__ vel, T kick, T* __restrict__ acc_out, int* status) {
   const T scale = (T)(-1.0 / (12.0 * delta));   // acc = -S phi
