@@ -255,6 +255,8 @@ def run_gpu(args, w, rank, world):
     K = pm.kick_factor(a, a * 1.01)
 
     def step(p_, v_):
+        # the response's history panels overlap the deposit on the context's side stream
+        pm.nu_prepare(a, a_hist, hist_d)
         pm.deposit(p_)
         pm.nu_response(a, a_hist, hist_d, None, out_R, None, out_Pm)
         pm.kick(p_, v_, a, K)

@@ -161,6 +161,27 @@ NUPM_API int pm_nu_response(pm_ctx* ctx, double a, const double* a_hist, const d
                    double* sqrtPnu_out, double* sqrtPM_out);
 
 /*
+ * Optional: start the history part of the next pm_nu_response before the
+ * deposit.  The integral of Eq. P-final is linear in the current node of
+ * P_M^{1/2} (the only part that needs this step's P_cdm), so its panels over
+ * the stored history depend on the bins' |k| and the history alone.  This
+ * launches them on the context's own side stream (forked from the context's
+ * stream, so it runs after everything enqueued so far) where they overlap
+ * pm_deposit's passes; the next pm_nu_response joins them and computes only
+ * the current node, R and the tables.  Arguments as pm_nu_response; the
+ * response uses the prepared panels when it gets the same a, a_hist values,
+ * n_hist and sqrtPM_hist pointer and no pm_set_power came between (else it
+ * recomputes them); the history must not change in between.  The results are
+ * bit-identical to pm_nu_response alone.  A second pm_nu_prepare before the
+ * response is PM_ERR_ORDER.  Under stream capture the side stream joins the
+ * capture and the next pm_nu_response (or pm_nu_response_mlp,
+ * pm_response_features) rejoins it.  The paper has no counterpart (the split
+ * restates its integral, Sec. 4.3 (iii)).
+ */
+NUPM_API int pm_nu_prepare(pm_ctx* ctx, double a, const double* a_hist, const double* sqrtPM_hist,
+                           int32_t n_hist);
+
+/*
  * Steps a5-a7 (Eq. phases, Sec. 4.3 (iv), Eq. Poisson): Green function with the
  * neutrino factor (1-f_nu) + f_nu R(|k|), 4-point finite-difference gradient,
  * inverse FFTs, CIC interpolation with the deposit's weights and

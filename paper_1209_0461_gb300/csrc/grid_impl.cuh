@@ -347,7 +347,7 @@ int NUPM_FN(green)(const GridArgs& g, cudaStream_t s) {
   const int total = g.n * g.n;
   k_green_plane0<T><<<grid_blocks(total, 256), 256, 0, s>>>(
       reinterpret_cast<const C*>(g.spec), reinterpret_cast<C*>(g.plane0), g.n, reinterpret_cast<const T*>(g.gtab),
-      reinterpret_cast<const T*>(g.wtab));
+      reinterpret_cast<const T*>(g.wtab), g.fac, g.fac_inv_du, g.green_coeff);
   return PM_OK;
 }
 

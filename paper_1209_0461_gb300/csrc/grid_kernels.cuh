@@ -563,7 +563,21 @@ k_bin_power_tma(const __grid_constant__ CUtensorMap map, const cx<float>* __rest
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_green_plane0(const cx<T>* __restrict__ spec, cx<T>* __restrict__ plane0, int n,
-                               const T* __restrict__ gtab, const T* __restrict__ wtab) {
+                               const T* __restrict__ gtab, const T* __restrict__ wtab, const float* __restrict__ fac,
+                               float fac_inv_du, float coeff) {
+  // G(n^2): the FP64 table, or (FP32) coeff fac(u) / n^2 from the fac table as
+  // in the inverse z passes; G(0) = 0
+  auto green = [&](int n2) -> T {
+    if constexpr (sizeof(T) == 4) {
+      if (n2 == 0) return (T)0;
+      const float tt = 0.5f * __logf((float)n2) * fac_inv_du;
+      const int j = min((int)tt, kFacTableDev - 2);
+      const float fr = tt - (float)j;
+      return (T)(coeff * (fac[j] + fr * (fac[j + 1] - fac[j])) / (float)n2);
+    } else {
+      return gtab[n2];
+    }
+  };
   const int m = n / 2;
   const int total = n * n;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
@@ -575,7 +589,7 @@ __global__ void k_green_plane0(const cx<T>* __restrict__ spec, cx<T>* __restrict
     const cx<T> A = {(T)0.5 * (f.x + h.x), (T)0.5 * (f.y - h.y)};
     const cx<T> B = {(T)0.5 * (f.y + h.y), (T)-0.5 * (f.x - h.x)};
     const int n2a = ky * ky + kz * kz;
-    T ga = gtab[n2a], gb = gtab[n2a + m * m];
+    T ga = green(n2a), gb = green(n2a + m * m);
     if (wtab) {
       const T wyz = wtab[iy] * wtab[iz];
       ga *= wtab[0] * wyz;

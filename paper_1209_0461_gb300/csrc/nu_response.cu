@@ -300,11 +300,19 @@ __global__ void k_nu_rlist(const double* __restrict__ bins, const double* __rest
   if (b == blockDim.x - 1) rlist[2 * nk] = (double)(base + __popc(m));
 }
 
-void launch_nu_response(const NuArgs& a, cudaStream_t s) {
+void launch_nu_panels(const NuArgs& a, cudaStream_t s) {
   const int items = a.nk * a.ns * kNuChunks;
   if (items > 0) k_nu_panels<<<(items + 3) / 4, 128, 0, s>>>(a);
+}
+
+void launch_nu_finish(const NuArgs& a, cudaStream_t s) {
   k_nu_finish<<<(a.nk + 127) / 128, 128, 0, s>>>(a);
   k_nu_rlist<<<1, ((a.nk + 31) / 32) * 32, 0, s>>>(a.bins, a.R, a.nk, a.rlist);
+}
+
+void launch_nu_response(const NuArgs& a, cudaStream_t s) {
+  launch_nu_panels(a, s);
+  launch_nu_finish(a, s);
 }
 
 // ---------------------------------------------------------------- surrogate

@@ -44,6 +44,10 @@ struct NuArgs {
 };
 
 void launch_nu_response(const NuArgs& a, cudaStream_t s);
+// the two halves of launch_nu_response: the history panels (they read the
+// bins' |k| only, not P_cdm) and the current node, R and the bin list
+void launch_nu_panels(const NuArgs& a, cudaStream_t s);
+void launch_nu_finish(const NuArgs& a, cudaStream_t s);
 // Surrogate: features [nk][12] of the bins and history in a (FP64 -> float),
 // and the finish from the surrogate's ln R (R, P_nu, P_M, rlist).
 void launch_nu_features(const NuArgs& a, double m_nu, double omega_nu, float* X, cudaStream_t s);

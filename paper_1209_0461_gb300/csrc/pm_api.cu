@@ -75,6 +75,16 @@ struct pm_ctx {
   int* d_status = nullptr;
   // pinned host staging
   double* h_hist_u = nullptr;
+  // history panels of the response launched ahead of the deposit (pm_nu_prepare)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool prep_pending = false;           // launched on the side stream, not yet joined
+  double prep_a = 0;
+  int prep_n = -1;
+  const double* prep_hist = nullptr;
+  std::vector<double> prep_ahist;
+  double* d_hist_u2 = nullptr;         // ln a_hist of the prepared panels
+  double* h_hist_u2 = nullptr;
   int* h_status = nullptr;
   // state
   bool deposited = false, deposit_grid_valid = false, have_response = false, have_kick = false;
@@ -414,10 +424,14 @@ void release(pm_ctx* c) {
                   c->spec, c->g, c->tw_n, c->tw_m, c->d_thr, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
                   c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_rlist, c->d_gtab,
                   c->d_dtab, c->d_wtab, c->d_plane0, c->d_fac, c->d_rowc, c->d_rows, c->d_rowcur,
-                  c->d_scantot, c->d_perm, c->d_rec, c->d_status};
+                  c->d_scantot, c->d_perm, c->d_rec, c->d_status, c->d_hist_u2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_hist_u) cudaFreeHost(c->h_hist_u);
+  if (c->h_hist_u2) cudaFreeHost(c->h_hist_u2);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->h_status) cudaFreeHost(c->h_status);
   for (auto& r : c->pending) {
     cudaEventDestroy(r.a);
@@ -584,6 +598,7 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_pi, (size_t)nspec * c->nk * sizeof(double), "nu ICs");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_ti, (size_t)nspec * c->nk * sizeof(double), "nu theta ICs");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_hist_u, (size_t)(p.n_hist_max + 1) * sizeof(double), "history ln a");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_hist_u2, (size_t)(p.n_hist_max + 1) * sizeof(double), "history ln a");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_gl, 2 * kMaxQuad * sizeof(double), "quadrature");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_parts, (size_t)nspec * c->nk * kNuChunks * 3 * sizeof(double), "response parts");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rlist, (2 * (size_t)c->nk + 1) * sizeof(double), "ratio list");
@@ -604,6 +619,11 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
     rc = dalloc(c, (void**)&c->d_perm, (size_t)c->np * sizeof(int), "row permutation");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rec, (size_t)c->np * sizeof(unsigned long long), "sorted records");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_status, sizeof(int), "status");
+  if (rc == PM_OK && (cudaMallocHost((void**)&c->h_hist_u2, (size_t)(p.n_hist_max + 1) * sizeof(double)) != cudaSuccess ||
+                      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess))
+    rc = fail(c, PM_ERR_ALLOC, "side stream or pinned history allocation failed");
   if (rc == PM_OK && cudaMallocHost((void**)&c->h_hist_u, (size_t)(p.n_hist_max + 1) * sizeof(double)) != cudaSuccess)
     rc = fail(c, PM_ERR_ALLOC, "pinned host allocation failed");
   if (rc == PM_OK && cudaMallocHost((void**)&c->h_status, sizeof(int)) != cudaSuccess)
@@ -797,11 +817,66 @@ NuArgs surrogate_args(pm_ctx* c, double a, const double* sqrtPM_hist, int32_t n_
 }
 
 // Green and fac tables from the response's rlist (both response forms).
+// A side-stream launch of pm_nu_prepare that no pm_nu_response consumed:
+// joined into the context's stream (and dropped).
+int join_prepared(pm_ctx* c) {
+  if (!c->prep_pending) return PM_OK;
+  c->prep_pending = false;
+  return cuda_check(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0), "side stream join");
+}
+
+// NuArgs of the exact response (bins, history, tables, outputs).
+NuArgs nu_args(pm_ctx* c, double a, const double* sqrtPM_hist, int32_t n_hist, const double* sqrtPnu_prev,
+               double* ratio_out, double* sqrtPnu_out, double* sqrtPM_out) {
+  NuArgs A{};
+  A.nk = c->nk;
+  A.ns = (c->ns > 0 && c->f_nu > 0) ? c->ns : 0;
+  A.n_hist = n_hist;
+  A.quad = c->quad;
+  A.iters = A.ns > 0 ? c->iters : 1;
+  A.use_fit = (c->p.flags & PM_I_FIT) ? 1 : 0;
+  A.ngrid = c->n;
+  A.a = a;
+  A.ue = log(a);
+  A.ui = log(c->a_init);
+  A.omega_m = c->omega_m;
+  A.omega_l = c->omega_l;
+  A.f_nu = c->f_nu;
+  A.a_init = c->a_init;
+  A.box = c->box;
+  for (int s = 0; s < c->ns; ++s) {
+    A.kappa_scale[s] = kCOverH0 * kTnu0eV / c->mass[s];
+    A.w_species[s] = c->wsp[s];
+  }
+  A.bins = c->d_bins;
+  A.hist_u = c->d_hist_u;
+  A.hist = sqrtPM_hist;
+  A.prev = sqrtPnu_prev;
+  A.pnu_init = c->d_pi;
+  A.theta_init = c->d_ti;
+  A.stab = c->d_stab;
+  A.n_stab = c->n_stab;
+  A.stab_u0 = c->stab_u0;
+  A.stab_h = c->stab_h;
+  A.stab_inv_h = 1.0 / c->stab_h;
+  A.gl = c->d_gl;
+  A.parts = c->d_parts;
+  A.rlist = c->d_rlist;
+  A.R = c->d_R;
+  A.pnu = c->d_pnu;
+  A.pm = c->d_pm;
+  A.R_user = ratio_out;
+  A.pnu_user = sqrtPnu_out;
+  A.pm_user = sqrtPM_out;
+  return A;
+}
+
 int response_tables(pm_ctx* c, double a) {
   const double coeff = -1.5 * c->omega_m / (a * c->kf * c->kf * (double)c->n * c->n * c->n);
-  launch_green_table(c->fp64, c->d_gtab, c->n2max, c->kf, coeff, c->f_nu, c->d_rlist, c->nk, c->stream);
-  if (!c->fp64)
-    launch_fac_table(c->d_fac, 0.5 * log((double)c->n2max), c->kf, c->f_nu, c->d_rlist, c->nk, c->stream);
+  // FP64: the exact G(n^2) table; FP32: the fac(ln k) table (its Green values
+  // are evaluated per mode by the passes that need them)
+  if (c->fp64) launch_green_table(true, c->d_gtab, c->n2max, c->kf, coeff, c->f_nu, c->d_rlist, c->nk, c->stream);
+  else launch_fac_table(c->d_fac, 0.5 * log((double)c->n2max), c->kf, c->f_nu, c->d_rlist, c->nk, c->stream);
   c->green_coeff = coeff;
   const int rc = cuda_check(c, cudaGetLastError(), "pm_nu_response launch");
   if (rc != PM_OK) return rc;
@@ -817,83 +892,87 @@ extern "C" {
 int pm_nu_response(pm_ctx* c, double a, const double* a_hist, const double* sqrtPM_hist, int32_t n_hist,
                    const double* sqrtPnu_prev, double* ratio_out, double* sqrtPnu_out, double* sqrtPM_out) {
   if (!c) return PM_ERR_INVALID;
-  {
+  // panels launched by pm_nu_prepare: joined first, whatever happens next
+  const bool had_prep = c->prep_pending;
+  if (had_prep) {
+    const int rc = cuda_check(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0), "side stream join");
+    if (rc != PM_OK) return rc;
+    c->prep_pending = false;
+  }
+  bool use_prep = had_prep && !c->power_set && a == c->prep_a && n_hist == c->prep_n && sqrtPM_hist == c->prep_hist;
+  for (int j = 0; use_prep && j < n_hist; ++j) use_prep = a_hist[j] == c->prep_ahist[j];
+  if (!use_prep) {
     const int rc = response_prepare(c, a, a_hist, sqrtPM_hist, n_hist);
     if (rc != PM_OK) return rc;
+  } else if (!c->deposited) {
+    return fail(c, PM_ERR_ORDER, "pm_nu_response before pm_deposit");
   }
-  const double ue = log(a);
-  Stage stage(c, PM_ST_RESPONSE, ((c->ns > 0 && c->f_nu > 0) ? 4 : 3) + (c->fp64 ? 0 : 1));
-  if (c->ns > 0 && c->f_nu > 0) {
-    NuArgs A{};
-    A.nk = c->nk;
-    A.ns = c->ns;
-    A.n_hist = n_hist;
-    A.quad = c->quad;
-    A.iters = c->iters;
-    A.use_fit = (c->p.flags & PM_I_FIT) ? 1 : 0;
-    A.ngrid = c->n;
-    A.a = a;
-    A.ue = ue;
-    A.ui = log(c->a_init);
-    A.omega_m = c->omega_m;
-    A.omega_l = c->omega_l;
-    A.f_nu = c->f_nu;
-    A.a_init = c->a_init;
-    A.box = c->box;
-    for (int s = 0; s < c->ns; ++s) {
-      A.kappa_scale[s] = kCOverH0 * kTnu0eV / c->mass[s];
-      A.w_species[s] = c->wsp[s];
-    }
-    A.bins = c->d_bins;
-    A.hist_u = c->d_hist_u;
-    A.hist = sqrtPM_hist;
-    A.prev = sqrtPnu_prev;
-    A.pnu_init = c->d_pi;
-    A.theta_init = c->d_ti;
-    A.stab = c->d_stab;
-    A.n_stab = c->n_stab;
-    A.stab_u0 = c->stab_u0;
-    A.stab_h = c->stab_h;
-    A.stab_inv_h = 1.0 / c->stab_h;
-    A.gl = c->d_gl;
-    A.parts = c->d_parts;
-    A.rlist = c->d_rlist;
-    A.R = c->d_R;
-    A.pnu = c->d_pnu;
-    A.pm = c->d_pm;
-    A.R_user = ratio_out;
-    A.pnu_user = sqrtPnu_out;
-    A.pm_user = sqrtPM_out;
-    launch_nu_response(A, c->stream);
-  } else {
-    // no neutrinos: R = 0, P_nu = 0, P_M^{1/2} = P_cdm^{1/2}
-    NuArgs A{};
-    A.nk = c->nk;
-    A.ns = 0;
-    A.iters = 1;
-    A.f_nu = c->f_nu;   // (1 - f_nu) P_cdm^{1/2} for the total-matter spectrum
-    A.ngrid = c->n;
-    A.box = c->box;
-    A.bins = c->d_bins;
-    A.parts = c->d_parts;
-    A.rlist = c->d_rlist;
-    A.pnu_init = c->d_pi;
-    A.R = c->d_R;
-    A.pnu = c->d_pnu;
-    A.pm = c->d_pm;
-    A.R_user = ratio_out;
-    A.pnu_user = sqrtPnu_out;
-    A.pm_user = sqrtPM_out;
-    launch_nu_response(A, c->stream);   // zero items in the panel kernel; finish sets outputs
-  }
+  const bool nu = c->ns > 0 && c->f_nu > 0;
+  Stage stage(c, PM_ST_RESPONSE, (nu && !use_prep ? 1 : 0) + 3);   // [panels,] finish, bin list, table
+  NuArgs A = nu_args(c, a, sqrtPM_hist, n_hist, sqrtPnu_prev, ratio_out, sqrtPnu_out, sqrtPM_out);
+  if (use_prep) A.hist_u = c->d_hist_u2;
+  if (nu && !use_prep) launch_nu_panels(A, c->stream);
+  launch_nu_finish(A, c->stream);   // without neutrinos: R = 0, P_nu = 0, P_M^{1/2} = (1 - f) P_cdm^{1/2}
   return response_tables(c, a);
+}
+
+int pm_nu_prepare(pm_ctx* c, double a, const double* a_hist, const double* sqrtPM_hist, int32_t n_hist) {
+  if (!c) return PM_ERR_INVALID;
+  if (c->prep_pending) return fail(c, PM_ERR_ORDER, "pm_nu_prepare twice without pm_nu_response");
+  if (!(isfinite(a) && a >= c->a_init)) return fail(c, PM_ERR_RANGE, "a must be finite and >= a_init");
+  if (n_hist < 0 || n_hist > c->p.n_hist_max) return fail(c, PM_ERR_INVALID, "n_hist outside 0..n_hist_max");
+  if (n_hist > 0 && (!a_hist || !sqrtPM_hist)) return fail(c, PM_ERR_INVALID, "history pointers are NULL");
+  for (int j = 0; j < n_hist; ++j) {
+    if (!isfinite(a_hist[j])) return fail(c, PM_ERR_RANGE, "non-finite a_hist");
+    if (j == 0 && a_hist[0] < c->a_init) return fail(c, PM_ERR_RANGE, "a_hist[0] < a_init");
+    if (j > 0 && !(a_hist[j] > a_hist[j - 1])) return fail(c, PM_ERR_RANGE, "a_hist not strictly increasing");
+  }
+  if (n_hist > 0 && !(a_hist[n_hist - 1] < a)) return fail(c, PM_ERR_RANGE, "a_hist[n-1] must be < a");
+  const double ue = log(a);
+  if (ue > c->stab_umax) {
+    const int rc = build_s_table(c, ue + 1.0);
+    if (rc != PM_OK) return rc;
+  }
+  c->prep_a = a;
+  c->prep_n = n_hist;
+  c->prep_hist = sqrtPM_hist;
+  c->prep_ahist.assign(a_hist ? a_hist : &a, a_hist ? a_hist + n_hist : &a);
+  for (int j = 0; j < n_hist; ++j) c->h_hist_u2[j] = log(a_hist[j]);
+  int rc = cuda_check(c, cudaEventRecord(c->ev_fork, c->stream), "side stream fork");
+  if (rc == PM_OK) rc = cuda_check(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0), "side stream fork");
+  if (rc != PM_OK) return rc;
+  if (n_hist > 0)
+    rc = cuda_check(c, cudaMemcpyAsync(c->d_hist_u2, c->h_hist_u2, n_hist * sizeof(double), cudaMemcpyHostToDevice,
+                                       c->side), "history upload");
+  if (rc == PM_OK && c->ns > 0 && c->f_nu > 0) {
+    cudaEvent_t t0 = nullptr;
+    if (c->timing) {
+      t0 = take_event(c);
+      cudaEventRecord(t0, c->side);
+    }
+    NuArgs A = nu_args(c, a, sqrtPM_hist, n_hist, nullptr, nullptr, nullptr, nullptr);
+    A.hist_u = c->d_hist_u2;
+    A.bins = c->d_bins_lattice;   // |k| of the bins: the lattice's (the deposit may rewrite d_bins meanwhile)
+    launch_nu_panels(A, c->side);
+    c->st_launch[PM_ST_RESPONSE] += 1;
+    if (t0) {
+      cudaEvent_t t1 = take_event(c);
+      cudaEventRecord(t1, c->side);
+      c->pending.push_back({PM_ST_RESPONSE, t0, t1});
+    }
+    rc = cuda_check(c, cudaGetLastError(), "pm_nu_prepare launch");
+  }
+  if (rc == PM_OK) rc = cuda_check(c, cudaEventRecord(c->ev_join, c->side), "side stream join");
+  if (rc == PM_OK) c->prep_pending = true;
+  return rc;
 }
 
 int pm_response_features(pm_ctx* c, double a, const double* a_hist, const double* sqrtPM_hist, int32_t n_hist,
                          float* X) {
   if (!c) return PM_ERR_INVALID;
   if (!X) return fail(c, PM_ERR_INVALID, "pm_response_features: X is NULL");
-  int rc = response_prepare(c, a, a_hist, sqrtPM_hist, n_hist);
+  int rc = join_prepared(c);
+  if (rc == PM_OK) rc = response_prepare(c, a, a_hist, sqrtPM_hist, n_hist);
   if (rc != PM_OK) return rc;
   NuArgs A = surrogate_args(c, a, sqrtPM_hist, n_hist, nullptr, nullptr, nullptr);
   launch_nu_features(A, c->p.m_nu_total_eV, c->omega_nu, X, c->stream);
@@ -903,6 +982,7 @@ int pm_response_features(pm_ctx* c, double a, const double* a_hist, const double
 int pm_nu_response_mlp(pm_ctx* c, pm_mlp* mlp, double a, const double* a_hist, const double* sqrtPM_hist,
                        int32_t n_hist, double* ratio_out, double* sqrtPnu_out, double* sqrtPM_out) {
   if (!c) return PM_ERR_INVALID;
+  if (join_prepared(c) != PM_OK) return PM_ERR_CUDA;
   if (!mlp) return fail(c, PM_ERR_INVALID, "pm_nu_response_mlp: mlp is NULL");
   if (mlp_inputs(mlp) != PM_MLP_FEATURES) return fail(c, PM_ERR_INVALID, "surrogate needs 12 input features");
   int rc = response_prepare(c, a, a_hist, sqrtPM_hist, n_hist);
@@ -1009,6 +1089,7 @@ int pm_check(pm_ctx* c) {
 
 void pm_free(pm_ctx* c) {
   if (!c) return;
+  if (c->side) cudaStreamSynchronize(c->side);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   release(c);

@@ -61,6 +61,7 @@ def lib():
         "pm_init": (C.c_int, [C.POINTER(PmParams), dp, dp, vp, C.POINTER(vp)]),
         "pm_deposit": (C.c_int, [vp, vp]),
         "pm_nu_response": (C.c_int, [vp, d, dp, vp, i32, vp, vp, vp, vp]),
+        "pm_nu_prepare": (C.c_int, [vp, d, dp, vp, i32]),
         "pm_kick": (C.c_int, [vp, vp, vp, d, d, vp]),
         "pm_check": (C.c_int, [vp]),
         "pm_free": (None, [vp]),
@@ -215,6 +216,13 @@ class PM:
         self._ok(lib().pm_nu_response(self.ctx, float(a), _dptr(ah) if n else None,
                                       _tptr(sqrtPM_hist) if n else None, n, _tptr(sqrtPnu_prev),
                                       _tptr(ratio), _tptr(sqrtPnu), _tptr(sqrtPM)), "pm_nu_response")
+
+    def nu_prepare(self, a, a_hist, sqrtPM_hist):
+        """pm_nu_prepare: launch the history panels of the next nu_response with
+        the same arguments on the context's side stream (before deposit)."""
+        ah, n = self._history(a_hist, sqrtPM_hist)
+        self._ok(lib().pm_nu_prepare(self.ctx, float(a), _dptr(ah) if n else None,
+                                     _tptr(sqrtPM_hist) if n else None, n), "pm_nu_prepare")
 
     def kick(self, pos, vel, a, kick_factor, acc_out=None):
         self._check_pos(pos)

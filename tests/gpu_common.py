@@ -36,9 +36,10 @@ SPECTRAL_GRADIENT = 0x40
 
 
 def gpu_kick(w, inp, K=0.01, iters=1, flags=KEEP_DEPOSIT, n_hist=None, prev=None, quad=8, keep_fields=False,
-             tuning=None):
+             tuning=None, prepare_a=None):
     """Deposit, response and kick through the C ABI (tuning: pm_set_tuning
-    knobs, or None for the built-in choices).  Returns numpy results."""
+    knobs, or None for the built-in choices; prepare_a: call pm_nu_prepare at
+    that scale factor before the deposit).  Returns numpy results."""
     import torch
     dev = torch.device("cuda")
     fp64 = w.precision == "fp64"
@@ -60,10 +61,12 @@ def gpu_kick(w, inp, K=0.01, iters=1, flags=KEEP_DEPOSIT, n_hist=None, prev=None
         vel = torch.from_numpy(inp["vel"].astype(np.float32)).to(dev).contiguous()
     vel0 = vel.clone()
     acc = torch.empty_like(vel)
+    hist_t = torch.from_numpy(np.ascontiguousarray(hist)).to(dev) if len(a_hist) else None
+    if prepare_a is not None:
+        pm.nu_prepare(prepare_a, a_hist, hist_t)
     pm.deposit(pos)
     F = pm.field(nupm.FIELD_DEPOSIT).cpu().numpy().view(np.uint64)
     spec = pm.field(nupm.FIELD_DELTA_K).cpu().numpy()
-    hist_t = torch.from_numpy(np.ascontiguousarray(hist)).to(dev) if len(a_hist) else None
     nk = w.n_kbins
     R = torch.zeros(nk, dtype=torch.float64, device=dev)
     Pn = torch.zeros_like(R)

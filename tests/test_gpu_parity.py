@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import pm_oracle as O
-from paper_1209_0461_gb300 import synth
+from paper_1209_0461_gb300 import nupm, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -170,6 +170,40 @@ def test_real_space_gradient_equals_spectral(prec, n):
         assert emax < 1e-10
     else:   # FP32 differences of the potential: cancellation bounded by eps * phi / (d |grad phi|)
         assert erms < 3e-5
+
+
+@pytest.mark.parametrize("prec,n", [("fp64", 32), ("fp32", 64)])
+def test_prepared_response_is_identical(prec, n):
+    # pm_nu_prepare runs the history panels on the side stream ahead of the
+    # deposit: the response that joins them is bit-identical to one without,
+    # and a prepare at another a makes the response recompute them
+    w = synth.with_(synth.WORKLOADS["pm32_fp64"], name=f"prep{n}", ngrid=n, npart_side=n, precision=prec,
+                    n_hist=10)
+    inp = make_inputs(w)
+    a = gpu_kick(w, inp)
+    b = gpu_kick(w, inp, prepare_a=w.a_kick)
+    c = gpu_kick(w, inp, prepare_a=w.a_kick * 1.01)
+    for key in ("R", "Pnu", "PM", "acc", "vel"):
+        assert np.array_equal(a[key], b[key]), key
+        assert np.array_equal(a[key], c[key]), key
+    _check_common(w, b, oracle_kick(w, inp), prec == "fp64")
+
+
+def test_prepare_twice_is_an_order_error():
+    w = synth.with_(synth.WORKLOADS["pm32_fp64"], n_hist=4)
+    inp = make_inputs(w)
+    pm = nupm.PM(w.ngrid, w.npart, w.box, w.omega_cdm, w.omega_nu, w.h, w.m_nu_total, w.n_species,
+                 a_init=w.a_init, n_kbins=w.n_kbins, n_hist_max=4, precision="fp64",
+                 sqrtPnu_init=inp["pi"], theta_over_delta_init=inp["ti"])
+    h = torch.from_numpy(np.ascontiguousarray(inp["hist"])).cuda()
+    pm.nu_prepare(w.a_kick, inp["a_hist"], h)
+    with pytest.raises(nupm.PMError) as e:
+        pm.nu_prepare(w.a_kick, inp["a_hist"], h)
+    assert e.value.code == -7
+    pm.deposit(torch.from_numpy(inp["pos64"]).cuda())
+    pm.nu_response(w.a_kick, inp["a_hist"], h)
+    pm.check()
+    pm.close()
 
 
 def test_options_iters_fit_deconv_nohist_prev():
