@@ -293,18 +293,21 @@ def run_gpu(args, w, rank, world):
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
     # end to end through the same API with host buffers: every step copies its
     # positions and velocities in from pinned host memory, kicks, and copies the
-    # velocities out.  Copies run on their own streams with two device buffer
-    # pairs, so step i+1's inputs travel while step i kicks.
+    # velocities out.  Copies run on their own streams with three device buffer
+    # pairs, so step i+1's inputs travel while step i kicks and step i-1's
+    # velocities travel out (with two pairs, step i+1's inputs would wait for
+    # step i-1's output copy, which waits for its kick).
     e2e = None
     if not args.no_e2e:
+        NBUF = 3
         vel_out = torch.empty_like(vel_h).pin_memory()
-        # the inputs travel as 4 pieces on 4 streams (several copy engines)
+        # the inputs travel as 4 pieces on 4 streams
         h2d = [torch.cuda.Stream() for _ in range(4)]
         d2h = torch.cuda.Stream()
-        bufs = [(pos, vel), (torch.empty_like(pos), torch.empty_like(vel))]
-        ev_in = [[torch.cuda.Event() for _ in h2d] for _ in range(2)]
-        ev_done = [torch.cuda.Event() for _ in range(2)]
-        ev_out = [torch.cuda.Event() for _ in range(2)]
+        bufs = [(pos, vel)] + [(torch.empty_like(pos), torch.empty_like(vel)) for _ in range(NBUF - 1)]
+        ev_in = [[torch.cuda.Event() for _ in h2d] for _ in range(NBUF)]
+        ev_done = [torch.cuda.Event() for _ in range(NBUF)]
+        ev_out = [torch.cuda.Event() for _ in range(NBUF)]
         pieces_h = list(pos_h.view(-1).chunk(3)) + [vel_h.view(-1)]
 
         def e2e_steps(n):
@@ -313,7 +316,7 @@ def run_gpu(args, w, rank, world):
             for hs in h2d:
                 hs.wait_event(start)
             for i in range(n):
-                b = i % 2
+                b = i % NBUF
                 p_, v_ = bufs[b]
                 pieces_d = list(p_.view(-1).chunk(3)) + [v_.view(-1)]
                 for hs, src, dst, ev in zip(h2d, pieces_h, pieces_d, ev_in[b]):
@@ -328,9 +331,9 @@ def run_gpu(args, w, rank, world):
                 with torch.cuda.stream(d2h):
                     vel_out.copy_(v_, non_blocking=True)
                 ev_out[b].record(d2h)
-            stream.wait_event(ev_out[(n - 1) % 2])
+            stream.wait_event(ev_out[(n - 1) % NBUF])
 
-        e2e_steps(2)
+        e2e_steps(NBUF)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)

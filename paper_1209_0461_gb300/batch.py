@@ -2,8 +2,9 @@
 
 Each box is its own context (grid 64^3, 128^3 or 192^3, its own seed and
 neutrino mass).  The boxes are spread over a few CUDA streams; one capture
-(pm_graph_begin .. pm_graph_end) records every box's deposit, response and
-kick with the streams forked from and joined back to the capture stream, so
+(pm_graph_begin .. pm_graph_end) records every box's response panels (on
+the context's side stream), deposit, response and kick with the streams
+forked from and joined back to the capture stream, so
 each pm_graph_launch replays all of them with the boxes on independent graph
 branches.  Before the capture each distinct grid size is autotuned once
 (pm_autotune) and its choice shared by the boxes of that size.  Torch supplies
@@ -54,6 +55,7 @@ class Batch:
 
     def _kick(self, it):
         pm = it["pm"]
+        pm.nu_prepare(it["a"], it["a_hist"], it["hist"])   # history panels beside the deposit
         pm.deposit(it["pos"])
         pm.nu_response(it["a"], it["a_hist"], it["hist"])
         pm.kick(it["pos"], it["vel"], it["a"], it["K"])
