@@ -300,14 +300,19 @@ NUPM_API int64_t pm_device_bytes(const pm_ctx* ctx);
  *                     and more)
  *   ctas_per_sm       CTAs per SM of the particle kernels (row sort, CIC
  *                     gather): 4, 8, 16, 32
- * one knob at a time, keeps the fastest and writes HOST tuned[3] = {wide_y,
- * wide_z, ctas_per_sm} (may be NULL).  a, a_hist, sqrtPM_hist, n_hist: as
+ *   gather_rows       0 = the CIC gather walks the particles in storage
+ *                     order, 1 = in the row order of pm_deposit's sort (a
+ *                     warp per grid row; used when pm_kick gets the same
+ *                     position pointer as the deposit; needs the sorted
+ *                     deposit and the real-space gradient)
+ * one knob at a time, keeps the fastest and writes HOST tuned[4] = {wide_y,
+ * wide_z, ctas_per_sm, gather_rows} (may be NULL).  a, a_hist, sqrtPM_hist, n_hist: as
  * pm_nu_response (the tuning kicks need a response).  Results are bit-identical
  * across choices except for the order of atomic arrival, which no output
  * depends on.  The paper has no counterpart (it is a property of this GPU). */
 NUPM_API int pm_autotune(pm_ctx* ctx, const void* pos, void* vel, double a, const double* a_hist,
                          const double* sqrtPM_hist, int32_t n_hist, int32_t reps, int32_t* tuned);
-/* Set the three knobs directly (-1 = built-in choice for wide_y / wide_z).
+/* Set the four knobs directly, HOST tuned[4] (-1 = built-in choice for wide_y / wide_z).
  * PM_ERR_INVALID for a value out of range, PM_ERR_UNSUPPORTED for wide_z = 2
  * on a grid that does not offer it. */
 NUPM_API int pm_set_tuning(pm_ctx* ctx, const int32_t* tuned);

@@ -352,6 +352,12 @@ int NUPM_FN(green)(const GridArgs& g, cudaStream_t s) {
 }
 
 int NUPM_FN(interp)(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, cudaStream_t s) {
+  if (g.np > 0 && g.fd_grad && g.rows_ready) {   // row order of the deposit's sort: a warp per row
+    k_interp_rows_fd<T><<<grid_blocks((int64_t)g.n * g.n * 32, 128, 2 * g.part_ctas_per_sm), 128, 0, s>>>(
+        g.rec, g.row_start, g.perm, g.np, g.n, g.delta, reinterpret_cast<const T*>(g.g), reinterpret_cast<T*>(vel),
+        (T)kick, reinterpret_cast<T*>(acc_out));
+    return PM_OK;
+  }
   if (g.np > 0 && g.fd_grad) {
     k_interp_kick_fd<T><<<grid_blocks(g.np, 128, 2 * g.part_ctas_per_sm), 128, 0, s>>>(
         pos, g.np, g.n, g.delta, reinterpret_cast<const T*>(g.g), reinterpret_cast<T*>(vel), (T)kick,

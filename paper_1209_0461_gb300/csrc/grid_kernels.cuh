@@ -699,12 +699,112 @@ __device__ __forceinline__ void fold_weights(T f0, T f1, T (&e)[6]) {
   e[5] = -f1;
 }
 
+// -S phi at one particle (cell c, 16-bit weights w), before the -1/(12 d)
+// scale: the CIC sum of the 4-point stencil at its 8 corners (see above).
+template <typename T>
+__device__ __forceinline__ void fd_stencil(const T* __restrict__ phi, int n, const int (&c)[3], const int (&w)[3],
+                                           T (&a)[3]) {
+  const T inv = (T)1.0 / (T)kWeightOne;
+  int xs[6], ys[6], zs[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    xs[j] = wrap_near(c[0], j - 2, n);
+    ys[j] = wrap_near(c[1], j - 2, n);
+    zs[j] = wrap_near(c[2], j - 2, n);
+  }
+  // (y, z) row starts; indices < 2^30 for n <= 1024
+  auto row = [&](int y, int z) { return ((uint32_t)z * (uint32_t)n + (uint32_t)y) * (uint32_t)n; };
+  T px[2][2][6];   // [dz][dy][x0-2 .. x0+3]
+  T py[2][2][4];   // [dz][dx][y0-2, y0-1, y0+2, y0+3]
+  T pz[2][2][4];   // [dy][dx][z0-2, z0-1, z0+2, z0+3]
+  constexpr int kFar[4] = {0, 1, 4, 5};
+  // FP32 x runs away from the row ends: three aligned 16-byte loads from
+  // a = (x0 - 2) rounded down to 4 cover x0 - 2 .. x0 + 3, picked by o = (x0 - 2) & 3
+  const int a4 = (c[0] - 2) & ~3;
+  if (sizeof(T) == 4 && c[0] >= 2 && a4 + 12 <= n) {
+    const int o = (c[0] - 2) & 3;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const float4* r4 = reinterpret_cast<const float4*>(phi + row(ys[2 + dy], zs[2 + dz]) + a4);
+        const float4 q0 = r4[0], q1 = r4[1], q2 = r4[2];
+        const float w9[9] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x};
+        float u[7];
+#pragma unroll
+        for (int j = 0; j < 7; ++j) u[j] = (o & 2) ? w9[j + 2] : w9[j];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) px[dz][dy][j] = (T)((o & 1) ? u[j + 1] : u[j]);
+      }
+  } else {
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const T* r = phi + row(ys[2 + dy], zs[2 + dz]);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) px[dz][dy][j] = r[xs[j]];
+      }
+  }
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T* r = phi + row(ys[kFar[q]], zs[2 + dz]);
+      py[dz][0][q] = r[xs[2]];
+      py[dz][1][q] = r[xs[3]];
+    }
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T* r = phi + row(ys[2 + dy], zs[kFar[q]]);
+      pz[dy][0][q] = r[xs[2]];
+      pz[dy][1][q] = r[xs[3]];
+    }
+  T f[3][2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    f[d][1] = (T)w[d] * inv;
+    f[d][0] = (T)1 - f[d][1];
+  }
+  T ex[6], ey[6], ez[6];
+  fold_weights(f[0][0], f[0][1], ex);
+  fold_weights(f[1][0], f[1][1], ey);
+  fold_weights(f[2][0], f[2][1], ez);
+  a[0] = a[1] = a[2] = (T)0;
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      T sx = (T)0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) sx += ex[j] * px[dz][dy][j];
+      a[0] += f[1][dy] * f[2][dz] * sx;
+    }
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const T sy = ey[0] * py[dz][dx][0] + ey[1] * py[dz][dx][1] + ey[2] * px[dz][0][2 + dx] +
+                   ey[3] * px[dz][1][2 + dx] + ey[4] * py[dz][dx][2] + ey[5] * py[dz][dx][3];
+      a[1] += f[0][dx] * f[2][dz] * sy;
+    }
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const T sz = ez[0] * pz[dy][dx][0] + ez[1] * pz[dy][dx][1] + ez[2] * px[0][dy][2 + dx] +
+                   ez[3] * px[1][dy][2 + dx] + ez[4] * pz[dy][dx][2] + ez[5] * pz[dy][dx][3];
+      a[2] += f[0][dx] * f[1][dy] * sz;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 4)   // FP32: 72 registers, 7 CTAs per SM
 k_interp_kick_fd(const void* __restrict__ pos, int64_t np, int n, double delta, const T* __restrict__ phi,
                  T* __restrict__ vel, T kick, T* __restrict__ acc_out, int* status) {
   const T scale = (T)(-1.0 / (12.0 * delta));   // acc = -S phi
-  const T inv = (T)1.0 / (T)kWeightOne;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // the next particle's position words are fetched while this one's
@@ -717,105 +817,51 @@ k_interp_kick_fd(const void* __restrict__ pos, int64_t np, int n, double delta, 
     const T u0 = vel[p], u1 = vel[np + p], u2 = vel[2 * np + p];
     int c[3], w[3];
     if (!Quant<T>::get(raw, n, delta, c, w, status)) continue;
-    int xs[6], ys[6], zs[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      xs[j] = wrap_near(c[0], j - 2, n);
-      ys[j] = wrap_near(c[1], j - 2, n);
-      zs[j] = wrap_near(c[2], j - 2, n);
-    }
-    // (y, z) row starts; indices < 2^30 for n <= 1024
-    auto row = [&](int y, int z) { return ((uint32_t)z * (uint32_t)n + (uint32_t)y) * (uint32_t)n; };
-    T px[2][2][6];   // [dz][dy][x0-2 .. x0+3]
-    T py[2][2][4];   // [dz][dx][y0-2, y0-1, y0+2, y0+3]
-    T pz[2][2][4];   // [dy][dx][z0-2, z0-1, z0+2, z0+3]
-    constexpr int kFar[4] = {0, 1, 4, 5};
-    // FP32 x runs away from the row ends: three aligned 16-byte loads from
-    // a = (x0 - 2) rounded down to 4 cover x0 - 2 .. x0 + 3, picked by o = (x0 - 2) & 3
-    const int a4 = (c[0] - 2) & ~3;
-    if (sizeof(T) == 4 && c[0] >= 2 && a4 + 12 <= n) {
-      const int o = (c[0] - 2) & 3;
-#pragma unroll
-      for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-          const float4* r4 = reinterpret_cast<const float4*>(phi + row(ys[2 + dy], zs[2 + dz]) + a4);
-          const float4 q0 = r4[0], q1 = r4[1], q2 = r4[2];
-          const float w9[9] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x};
-          float u[7];
-#pragma unroll
-          for (int j = 0; j < 7; ++j) u[j] = (o & 2) ? w9[j + 2] : w9[j];
-#pragma unroll
-          for (int j = 0; j < 6; ++j) px[dz][dy][j] = (T)((o & 1) ? u[j + 1] : u[j]);
-        }
-    } else {
-#pragma unroll
-      for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-          const T* r = phi + row(ys[2 + dy], zs[2 + dz]);
-#pragma unroll
-          for (int j = 0; j < 6; ++j) px[dz][dy][j] = r[xs[j]];
-        }
-    }
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const T* r = phi + row(ys[kFar[q]], zs[2 + dz]);
-        py[dz][0][q] = r[xs[2]];
-        py[dz][1][q] = r[xs[3]];
-      }
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const T* r = phi + row(ys[2 + dy], zs[kFar[q]]);
-        pz[dy][0][q] = r[xs[2]];
-        pz[dy][1][q] = r[xs[3]];
-      }
-    T f[3][2];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      f[d][1] = (T)w[d] * inv;
-      f[d][0] = (T)1 - f[d][1];
-    }
-    T ex[6], ey[6], ez[6];
-    fold_weights(f[0][0], f[0][1], ex);
-    fold_weights(f[1][0], f[1][1], ey);
-    fold_weights(f[2][0], f[2][1], ez);
-    T a[3] = {(T)0, (T)0, (T)0};
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
-        T sx = (T)0;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) sx += ex[j] * px[dz][dy][j];
-        a[0] += f[1][dy] * f[2][dz] * sx;
-      }
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        const T sy = ey[0] * py[dz][dx][0] + ey[1] * py[dz][dx][1] + ey[2] * px[dz][0][2 + dx] +
-                     ey[3] * px[dz][1][2 + dx] + ey[4] * py[dz][dx][2] + ey[5] * py[dz][dx][3];
-        a[1] += f[0][dx] * f[2][dz] * sy;
-      }
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        const T sz = ez[0] * pz[dy][dx][0] + ez[1] * pz[dy][dx][1] + ez[2] * px[0][dy][2 + dx] +
-                     ez[3] * px[1][dy][2 + dx] + ez[4] * pz[dy][dx][2] + ez[5] * pz[dy][dx][3];
-        a[2] += f[0][dx] * f[1][dy] * sz;
-      }
+    T a[3];
+    fd_stencil<T>(phi, n, c, w, a);
     const T u[3] = {u0, u1, u2};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const T ad = a[d] * scale;
       vel[d * np + p] = u[d] + ad * kick;
       if (acc_out) acc_out[d * np + p] = ad;
+    }
+  }
+}
+
+// The same gather in the row order of the deposit's sort: one warp per grid
+// row (z, y), its lanes over the row's records (x cell and weights; y and z
+// are the row's) and perm[] giving each record's particle for the velocity
+// update.  Particles far from their storage order (clustered inputs) then
+// still read neighbouring potential rows warp by warp.  The arithmetic is
+// fd_stencil's: forces bit-identical to the particle-order gather.
+template <typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 4)
+k_interp_rows_fd(const unsigned long long* __restrict__ rec, const int* __restrict__ row_start,
+                 const int* __restrict__ perm, int64_t np, int n, double delta, const T* __restrict__ phi,
+                 T* __restrict__ vel, T kick, T* __restrict__ acc_out) {
+  const T scale = (T)(-1.0 / (12.0 * delta));
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int rows = n * n;
+  for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += gridDim.x * wpb) {
+    const int beg = row_start[row], end = row_start[row + 1];
+    const int cz = row / n, cy = row - cz * n;
+    for (int i = beg + lane; i < end; i += 32) {
+      const unsigned long long r = rec[i];
+      const int64_t p = perm[i];
+      const T u0 = vel[p], u1 = vel[np + p], u2 = vel[2 * np + p];
+      const int c[3] = {(int)(r >> 48) & 0x7ff, cy, cz};
+      const int w[3] = {(int)(r & 0xffffu), (int)((r >> 16) & 0xffffu), (int)((r >> 32) & 0xffffu)};
+      T a[3];
+      fd_stencil<T>(phi, n, c, w, a);
+      const T u[3] = {u0, u1, u2};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T ad = a[d] * scale;
+        vel[d * np + p] = u[d] + ad * kick;
+        if (acc_out) acc_out[d * np + p] = ad;
+      }
     }
   }
 }

@@ -107,6 +107,10 @@ struct GridArgs {
   // force spectra); true = the 4-point stencil on the real potential grid,
   // applied by the gather (one inverse transform)
   bool fd_grad = false;
+  // tuning: 1 = gather in the row order of the deposit's sort (records +
+  // perm), used when rows_ready (same positions as the deposit, perm written)
+  int gather_rows = 0;
+  bool rows_ready = false;
 };
 #define NUPM_DECLARE_GRID(SFX)                                                              \
   int deposit##SFX(const GridArgs& g, const void* pos, cudaStream_t s);                     \

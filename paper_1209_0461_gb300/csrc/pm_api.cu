@@ -90,6 +90,9 @@ struct pm_ctx {
   bool deposited = false, deposit_grid_valid = false, have_response = false, have_kick = false;
   bool power_set = false;         // bins replaced by pm_set_power (no spectrum behind them)
   int wide_y = -1, wide_z = -1, part_cps = 16;   // tuning (pm_autotune)
+  int gather_rows = 0;                            // tuning: gather in the sort's row order
+  bool perm_valid = false;                        // the last deposit's sort wrote perm
+  const void* dep_pos = nullptr;                  // positions of the last deposit
   double* d_bins_lattice = nullptr;   // [2][nk] lattice count / ksum, restored after pm_set_power
   float* d_X = nullptr;           // [nk][12] surrogate features
   float* d_lnR = nullptr;         // [nk] surrogate output
@@ -405,7 +408,8 @@ GridArgs grid_args(const pm_ctx* c) {
   g.row_start = c->d_rows;
   g.row_cursor = c->d_rowcur;
   g.scan_tot = c->d_scantot;
-  g.perm = c->d_perm;
+  g.perm = ((c->p.flags & PM_FUSED_GATHER) || c->gather_rows == 1) ? c->d_perm : nullptr;
+  g.gather_rows = c->gather_rows;
   g.rec = c->d_rec;
   g.tmap_spec_y = c->tma ? &c->tm_spec_y : nullptr;
   g.tmap_spec_z = c->tma ? &c->tm_spec_z : nullptr;
@@ -615,7 +619,7 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rows, nrow1 * sizeof(int), "row starts");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rowcur, nrow1 * sizeof(int), "row cursors");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_scantot, 2048 * sizeof(int), "scan totals");
-  if (rc == PM_OK && (p.flags & PM_FUSED_GATHER))
+  if (rc == PM_OK && !(p.flags & PM_UNFUSED_DEPOSIT))
     rc = dalloc(c, (void**)&c->d_perm, (size_t)c->np * sizeof(int), "row permutation");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rec, (size_t)c->np * sizeof(unsigned long long), "sorted records");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_status, sizeof(int), "status");
@@ -756,6 +760,8 @@ int pm_deposit(pm_ctx* c, const void* pos) {
   if (rc != PM_OK) return rc;
   c->deposited = true;
   c->deposit_grid_valid = unfused || keep;   // the fixed-point grid stays intact until pm_kick
+  c->perm_valid = !unfused && g.perm != nullptr;
+  c->dep_pos = pos;
   c->have_response = false;
   c->have_kick = false;
   return PM_OK;
@@ -1041,6 +1047,8 @@ int pm_kick(pm_ctx* c, const void* pos, void* vel, double a, double kick_factor,
     rc = c->fp64 ? green_f64(g, c->stream) : green_f32(g, c->stream);
   }
   c->deposit_grid_valid = false;
+  // the row-order gather walks the deposit's sort: only for the same positions
+  g.rows_ready = c->gather_rows == 1 && c->perm_valid && pos == c->dep_pos && g.fd_grad;
   // the fused gather walks the row sort of pm_deposit, absent on the unfused path
   const bool separate = !(c->p.flags & PM_FUSED_GATHER) || (c->p.flags & PM_UNFUSED_DEPOSIT);
   const int inv[3] = {kPassZInv, kPassYInv, kPassXInv};
@@ -1276,6 +1284,18 @@ int pm_autotune(pm_ctx* c, const void* pos, void* vel, double a, const double* a
     }
     c->part_cps = best_c;
   }
+  // gather order: particle order, or the row order of the deposit's sort
+  // (records + permutation; the default real-space gradient on the sorted path)
+  if (rc == PM_OK && c->d_perm && !(c->p.flags & (PM_SPECTRAL_GRADIENT | PM_FUSED_GATHER | PM_TMA_COLUMNS))) {
+    double t0 = 0.0, t1 = 0.0;
+    c->gather_rows = 0;
+    rc = measure(kStP, 2, &t0);
+    if (rc == PM_OK) {
+      c->gather_rows = 1;
+      rc = measure(kStP, 2, &t1);
+    }
+    c->gather_rows = (rc == PM_OK && t1 < t0) ? 1 : 0;
+  }
   const int rc2 = pm_timing(c, was_timing ? 1 : 0);
   if (rc != PM_OK) return rc;
   if (rc2 != PM_OK) return rc2;
@@ -1284,19 +1304,23 @@ int pm_autotune(pm_ctx* c, const void* pos, void* vel, double a, const double* a
     tuned[0] = c->wide_y;
     tuned[1] = c->wide_z;
     tuned[2] = c->part_cps;
+    tuned[3] = c->gather_rows;
   }
   return PM_OK;
 }
 
 int pm_set_tuning(pm_ctx* c, const int32_t* tuned) {
   if (!c || !tuned) return PM_ERR_INVALID;
-  if (tuned[0] < -1 || tuned[0] > 1 || tuned[1] < -1 || tuned[1] > 2 || tuned[2] < 1 || tuned[2] > 64)
-    return fail(c, PM_ERR_INVALID, "pm_set_tuning: wide_y in -1..1, wide_z in -1..2, ctas_per_sm in 1..64");
+  if (tuned[0] < -1 || tuned[0] > 1 || tuned[1] < -1 || tuned[1] > 2 || tuned[2] < 1 || tuned[2] > 64 ||
+      tuned[3] < 0 || tuned[3] > 1)
+    return fail(c, PM_ERR_INVALID,
+                "pm_set_tuning: wide_y in -1..1, wide_z in -1..2, ctas_per_sm in 1..64, gather_rows 0 or 1");
   if (tuned[1] == 2 && !c->tma_z16)
     return fail(c, PM_ERR_UNSUPPORTED, "pm_set_tuning: wide_z = 2 needs a power-of-two grid of 256 or more");
   c->wide_y = tuned[0];
   c->wide_z = tuned[1];
   c->part_cps = tuned[2];
+  c->gather_rows = tuned[3];
   return PM_OK;
 }
 

@@ -280,17 +280,17 @@ class PM:
 
     # -- tuning
     def autotune(self, pos, vel, a, a_hist, sqrtPM_hist, reps=2):
-        """pm_autotune: returns (wide_y, wide_z, ctas_per_sm); wide_z = 2 is the
-        TMA-staged z pass."""
+        """pm_autotune: returns (wide_y, wide_z, ctas_per_sm, gather_rows); wide_z = 2
+        is the TMA-staged z pass, gather_rows = 1 the gather in the sort's row order."""
         self._check_pos(pos)
         ah, n = self._history(a_hist, sqrtPM_hist)
-        t = (C.c_int32 * 3)()
+        t = (C.c_int32 * 4)()
         self._ok(lib().pm_autotune(self.ctx, _tptr(pos), _tptr(vel), float(a), _dptr(ah) if n else None,
                                    _tptr(sqrtPM_hist) if n else None, n, int(reps), t), "pm_autotune")
         return tuple(int(x) for x in t)
 
-    def set_tuning(self, wide_y=-1, wide_z=-1, ctas_per_sm=16):
-        t = (C.c_int32 * 3)(int(wide_y), int(wide_z), int(ctas_per_sm))
+    def set_tuning(self, wide_y=-1, wide_z=-1, ctas_per_sm=16, gather_rows=0):
+        t = (C.c_int32 * 4)(int(wide_y), int(wide_z), int(ctas_per_sm), int(gather_rows))
         self._ok(lib().pm_set_tuning(self.ctx, t), "pm_set_tuning")
 
     # -- background

@@ -28,7 +28,7 @@ def test_graph_step_equals_direct_launches():
     boxes = synth.batched_boxes(6, n_hist=8, n_kbins=32)
     b = batch.Batch(boxes, n_streams=3, autotune=True)
     for n, t in b.tuning.items():
-        assert t[0] in (0, 1) and t[1] in (0, 1) and t[2] in (4, 8, 16, 32), (n, t)
+        assert t[0] in (0, 1) and t[1] in (0, 1) and t[2] in (4, 8, 16, 32) and t[3] in (0, 1), (n, t)
     b.eager_step()
     b.check()
     ref = _dv(b)
