@@ -447,7 +447,8 @@ __device__ __forceinline__ void bin_row_staged(const cx<T> (&f)[kBinLaneMax], cx
 }
 
 // FP32 power sums with the rows staged by TMA: each warp runs a
-// kBinStages-deep ring of row buffers in shared memory.  A tensor map views
+// kBinStages-deep ring of row buffers in shared memory (two: 5 CTAs per SM
+// at 1024^3, where three allowed 3 and the combine went short of warps).  A tensor map views
 // the spectrum as [rows][32 lanes][E modes] (8-byte elements); one 3-D copy
 // brings a whole row, swizzled with the span equal to a lane's segment
 // (E = 4, 8, 16: 32-, 64-, 128-byte swizzle; E = 2: none), so lane L reading
@@ -457,7 +458,7 @@ __device__ __forceinline__ void bin_row_staged(const cx<T> (&f)[kBinLaneMax], cx
 // steps are issued as soon as row r is in registers.  Waits are bounded: on a
 // timeout the kernel records PM_ERR_TIMEOUT, waits (bounded) for its own
 // copies still in flight and stops.
-constexpr int kBinStages = 3;
+constexpr int kBinStages = 2;
 
 // Bytes of one staged row buffer: 32 lines of 128 bytes (a whole number of
 // swizzle atoms for every span), also when the row itself is smaller.
