@@ -338,7 +338,7 @@ NUPM_API void pm_graph_free(pm_graph* graph);
 /* ---- learned response surrogate ----
  * The paper has no learned part; this stands in for the response integral of
  * pm_nu_response (Eq. P-final with Eq. deltaI-nu), which stays the fallback
- * and the judge of its error.  A 3-layer perceptron
+ * and the yardstick its error is measured against.  A 3-layer perceptron
  *   h1 = tanh(W1 xh + b1), h2 = tanh(W2 h1 + b2), out = w3 . h2 + b3,
  *   xh = (x - mu) / sigma,  ln R = y_mu + y_sigma out,
  * width 128, BF16 weight matrices (W1, W2, w3), FP32 biases, FP32 accumulation,
