@@ -225,6 +225,7 @@ def run_gpu(args, w, rank, world):
     b.build()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
+    torch.cuda.set_stream(torch.cuda.Stream(dev))   # a capturable stream for the context and the timing
     wr = replica(w, rank)
     t0 = time.time()
     parts = synth.particles(wr)
@@ -279,18 +280,40 @@ def run_gpu(args, w, rank, world):
     pm.check()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     pm.timing(True)
     with ClockSampler(dev.index) as clk:
         barrier()
         ev0.record(stream)
-        for _ in range(args.steps):
+        for i in range(args.steps):
+            evs[i].record(stream)
             step(pos, vel)
+        evs[-1].record(stream)
         ev1.record(stream)
         barrier()
     stages = pm.get_timing()
     pm.timing(False)
     pm.check()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
+    ms_median = float(np.median([evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]))
+    # the same step captured once into a CUDA graph and replayed
+    try:
+        g = nupm.Graph.capture(stream, lambda: step(pos, vel))
+        for _ in range(args.warmup):
+            g.launch(stream)
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            g.launch(stream)
+        g1.record(stream)
+        barrier()
+        pm.check()
+        msg = max_over_ranks(g0.elapsed_time(g1) / args.steps, world, dev)
+        graph = {"ms_per_step": round(msg, 4), "value": whole_job_rate(wr.npart, world, msg), "nodes": g.nodes()}
+        g.close()
+    except nupm.PMError as e:
+        graph = {"unavailable": str(e)}
     # end to end through the same API with host buffers: every step copies its
     # positions and velocities in from pinned host memory, kicks, and copies the
     # velocities out.  Copies run on their own streams with three device buffer
@@ -364,7 +387,8 @@ def run_gpu(args, w, rank, world):
     total_launch = sum(v[1] for v in stages.values())
     step_alg = sum(stage_bytes(wr, k, fused, spectral) * (v[2] if k in ("deposit", "bins") else v[1])
                    for k, v in stages.items() if k != "response") / args.steps
-    res = dict(value=whole_job_rate(wr.npart, world, ms), ms_per_step=ms, e2e=e2e, roofline=roof,
+    res = dict(value=whole_job_rate(wr.npart, world, ms), ms_per_step=ms, ms_per_step_median=ms_median,
+               graph=graph, e2e=e2e, roofline=roof,
                stages={k: {"ms_per_step": round(v[0] / args.steps, 4), "launches_per_step": v[1] // args.steps}
                        for k, v in stages.items()},
                gpu_launches=int(total_launch), clocks=clk.summary(), gen_s=round(gen_s, 1), tuning=tuning,
@@ -633,7 +657,8 @@ def main():
     forms = None
     if world == 1 and not args.no_forms and args.workload == "pm1024_p512_fp32":
         forms = run_forms()
-    line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"], e2e=res["e2e"],
+    line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"],
+                ms_per_step_median=res["ms_per_step_median"], graph=res["graph"], e2e=res["e2e"],
                 roofline=res["roofline"], cpu_baseline=cpu, gpu_launches=res["gpu_launches"],
                 clocks=res["clocks"], step_model_gb=res["step_alg_gb"], step_hbm_frac=res["step_frac"],
                 stages_ms=res["stages"], tuning=res["tuning"], forms=forms)
