@@ -428,7 +428,12 @@ class Cosmo:
         return self.omega_nu / self.omega_m
 
     def species_weights(self):
-        """Omega_nu,i / Omega_nu = m_i / M_nu (Sec. 2.1 per species)."""
+        """Omega_nu,i / Omega_nu = m_i / M_nu (Sec. 2.1 per species).
+
+        Pinned by: a light second species (m_2 = m_1/50) leaves the heavy
+        species' response scaled by m_1/M_nu, in either order; a three-mass
+        hierarchy equals the mass-weighted sum of single-species responses.
+        """
         m = np.asarray(self.m_nu_ev, dtype=np.float64)
         tot = m.sum()
         return m / tot if tot > 0 else np.zeros_like(m)
@@ -608,7 +613,11 @@ def potential_spectrum(spec, box, a, cosmo: Cosmo, kb, R, nonempty, deconvolve=F
     """phi(k) = G(k) delta_M(k) of ``green_gradient`` (Eq. Poisson with the
     neutrino-corrected delta_M), before the gradient.  By default over the
     whole half spectrum; with modes = (iz, iy, ix) and ngrid, at those modes
-    (spec holding delta_k there)."""
+    (spec holding delta_k there).
+
+    Pinned by (deconvolution): the divisor equals the square of the CIC
+    assignment window measured from the oracle's own deposit and FFT (the
+    single-particle DFT times e^{+ik.x}, averaged over sub-cell offsets)."""
     n = spec.shape[0] if modes is None else ngrid
     kf = 2.0 * math.pi / box
     iz, iy, ix = mode_indices(n) if modes is None else modes

@@ -331,3 +331,59 @@ def test_bin_power_over_complete_bins_equals_full_bins():
     phis = O.potential_spectrum(spec[sel], box, 0.1, cos, full["k"], R, full["nonempty"],
                                 modes=(iz[sel[0], 0, 0], iy[0, sel[1], 0], ix[0, 0, sel[2]]), ngrid=n)
     assert np.array_equal(phis, phi[sel])
+
+
+def _mean_window(n, offsets, weights, axes):
+    """Average over particle offsets of the single-particle CIC deposit's DFT
+    (oracle deposit + forward FFT, unit mass) times e^{+2 pi i k.x / N}: the
+    assignment window W(k) at every half-spectrum mode.  offsets [P, 3] in cell
+    units, exact multiples of 2^-16; only the axes listed move."""
+    iz, iy, ix = O.mode_indices(n)
+    acc = np.zeros((n, n, n // 2 + 1), dtype=complex)
+    base = np.array([3, 5, 2])
+    for o, wt in zip(offsets, weights):
+        u = base + o
+        c = np.floor(u).astype(np.int64)[:, None]
+        w = np.round((u - np.floor(u)) * 65536).astype(np.int64)[:, None]
+        F = O.cic_deposit(c, w, n).astype(np.float64) / O.MASS_ONE
+        spec = O.forward_fft(F)
+        ph = np.exp(2j * np.pi * (ix * u[0] + iy * u[1] + iz * u[2]) / n)
+        acc += wt * spec * ph
+    return acc
+
+
+def test_cic_window_and_its_deconvolution():
+    # The CIC assignment window: averaged over a uniform sub-cell offset o, the
+    # DFT of one particle's deposit times e^{+2 pi i n x / N} is, per axis,
+    #   2 int_0^1 (1 - o) cos(theta o) do = sinc^2(theta / 2),  theta = 2 pi n / N.
+    # The deconvolution of potential_spectrum divides by the square of this
+    # window (assignment and interpolation): prod sinc^4(pi n_i / N).
+    n = 8
+    # 1-D: the x offset on the midpoint rule of 1024 exact points
+    J = 1024
+    o = (np.arange(J) + 0.5) / J
+    offs = np.stack([o, np.zeros(J), np.zeros(J)], axis=1)
+    W1 = _mean_window(n, offs, np.full(J, 1.0 / J), (0,))
+    ix = np.arange(n // 2 + 1)
+    t = np.pi * ix / n
+    sinc2 = np.where(ix == 0, 1.0, (np.sin(t) / np.where(ix == 0, 1.0, t)) ** 2)
+    assert np.allclose(W1, np.broadcast_to(sinc2, W1.shape), atol=2e-6, rtol=0)
+    # 3-D: 8-point Gauss-Legendre in each axis (offsets rounded to 2^-16)
+    g, gw = np.polynomial.legendre.leggauss(8)
+    g = np.round((g + 1) / 2 * 65536) / 65536
+    gw = gw / 2
+    oz, oy, ox = np.meshgrid(g, g, g, indexing="ij")
+    wz, wy, wx = np.meshgrid(gw, gw, gw, indexing="ij")
+    offs3 = np.stack([ox.ravel(), oy.ravel(), oz.ravel()], axis=1)
+    W3 = _mean_window(n, offs3, (wx * wy * wz).ravel(), (0, 1, 2))
+    assert np.max(np.abs(W3.imag)) < 1e-4
+    # the oracle's deconvolution factor of the Green function is 1 / W^2
+    cos = O.Cosmo(0.3, 0.0, 0.7, (), 0.02)
+    rng = np.random.default_rng(3)
+    spec = rng.normal(size=W3.shape) + 1j * rng.normal(size=W3.shape)
+    kb, R, ne = np.ones(4), np.zeros(4), np.zeros(4, bool)
+    plain = O.potential_spectrum(spec, 100.0, 0.5, cos, kb, R, ne, deconvolve=False)
+    dec = O.potential_spectrum(spec, 100.0, 0.5, cos, kb, R, ne, deconvolve=True)
+    sel = plain != 0
+    ratio = (dec[sel] / plain[sel]).real
+    assert np.allclose(ratio * W3.real[sel] ** 2, 1.0, rtol=3e-4, atol=0)

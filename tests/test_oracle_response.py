@@ -197,3 +197,45 @@ def test_empty_bins_and_ic_only():
     assert np.allclose(r0["sqrtPnu"], pi[0], rtol=1e-14)
     with pytest.raises(ValueError):
         O.nu_response(kb, cur, 0.05, c, ah, hist, pi, ti)      # a < last history node
+
+
+def test_species_weights_follow_the_mass():
+    # Sec. 2.1: Omega_nu h^2 = sum m / 93.14 eV, so species i carries the
+    # fraction m_i / M_nu of the neutrino density.  A light second species
+    # (m_2 = m_1 / 50: free streaming suppresses its response by ~(m_2/m_1)^2)
+    # must leave the heavy species' response scaled by m_1 / M_nu ~ 0.98 plus
+    # at most a percent of m_2 / M_nu; equal weights (1 / n_species) would
+    # halve it.
+    c, _, ah, hist, _, ti, _ = _lcdm_inputs(nb=4)
+    kb = np.array([0.01, 0.02, 0.04, 0.08])
+    cur = 10.0 / (1 + kb / 0.2) ** 1.5 * 0.1 / c.a_init
+    pi = np.tile(10.0 / (1 + kb / 0.2) ** 1.5 / (1 + kb / 0.01) ** 2, (3, 1))
+    m1, m2 = 0.1, 0.002
+    one = O.Cosmo(c.omega_cdm, c.omega_nu, c.h, (m1,), c.a_init)
+    r1 = O.nu_response(kb, cur, 0.1, one, ah, hist, pi[:1], ti[:1])
+    w1, w2 = m1 / (m1 + m2), m2 / (m1 + m2)
+    for masses in ((m1, m2), (m2, m1)):      # the weight goes with its own species
+        two = O.Cosmo(c.omega_cdm, c.omega_nu, c.h, masses, c.a_init)
+        assert np.allclose(two.species_weights(), np.array(masses) / (m1 + m2), rtol=1e-15)
+        # same initial arrays for both species: the first-iteration guess is unchanged
+        r2 = O.nu_response(kb, cur, 0.1, two, ah, hist, pi[:2], ti[:2])
+        extra = r2["R"] / r1["R"] - w1
+        assert np.all(extra >= 0) and np.all(extra < 0.01 * w2)
+
+
+def test_hierarchy_is_the_mass_weighted_sum_of_species():
+    # Sec. 6.2 / Table 1 (S03NH masses): a hierarchy of unequal masses sums
+    # the single-species responses with weights m_i / M_nu.  The single-species
+    # runs use the same first-iteration guess (identical initial arrays).
+    c, kb, ah, hist, pi, ti, cur = _lcdm_inputs(nb=3)
+    masses = (0.022, 0.024, 0.054)
+    tot = sum(masses)
+    full = O.nu_response(kb, cur, 0.1, O.Cosmo(c.omega_cdm, c.omega_nu, c.h, masses, c.a_init),
+                         ah, hist, pi, ti)
+    parts = [O.nu_response(kb, cur, 0.1, O.Cosmo(c.omega_cdm, c.omega_nu, c.h, (m,), c.a_init),
+                           ah, hist, pi[:1], ti[:1])["sqrtPnu"] for m in masses]
+    want = sum(m / tot * p for m, p in zip(masses, parts))
+    assert np.allclose(full["sqrtPnu"], want, rtol=1e-9)
+    # the heaviest species responds most: R ordered by mass in every bin
+    Rs = [p / cur for p in parts]
+    assert np.all(Rs[0] < Rs[1]) and np.all(Rs[1] < Rs[2])
