@@ -277,10 +277,14 @@ NUPM_API int pm_get_timing(pm_ctx* ctx, double* ms, int64_t* launches, int64_t* 
  *   count, ksum, psum   DEVICE double[n_kbins] or NULL: sum w, sum w |k|,
  *               sum w |delta_k|^2 with the bins and weights of pm_get_bins
  *   cuda_stream stream to issue the work on
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Calls share the scratch: each call rewrites all
- * of it that it reads, but calls that overlap on the GPU race.
+ * spec, the outputs and the stream must belong to the current device (a
+ * stream on another device is rejected with PM_ERR_INVALID).  Each call made
+ * outside a stream capture looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with the device current; a call under capture uses
+ * the address of the last uncaptured call on that device, so make a first
+ * call before any stream capture.  All calls on a device share the scratch:
+ * each call rewrites all of it that it reads, but calls that overlap on the
+ * GPU (different streams, no ordering between them) race.
  */
 NUPM_API int pm_bin_power_static(const void* spec, int32_t ngrid, double box, int32_t n_kbins,
                                  int32_t precision, double* count, double* ksum, double* psum,

@@ -113,16 +113,64 @@ def nu_I_fit(x) -> np.ndarray:
 # --------------------------------------------------------------------------
 # Background (Sec. 3.2 superconformal time; Sec. 3.1 kick/drift)
 # --------------------------------------------------------------------------
-def hubble(a, omega_m: float):
-    """H(a)/H0 for flat matter + Lambda: sqrt(Om a^-3 + 1 - Om)."""
+def hubble(a, omega_m):
+    """H(a)/H0.  ``omega_m`` a number: flat matter + Lambda,
+    sqrt(Om a^-3 + 1 - Om).  A ``Cosmo``: the same from its Omega_M, or, with
+    ``relativistic`` set, the background of Sec. 4.4 (``Cosmo.e2``)."""
     a = np.asarray(a, dtype=np.float64)
+    if isinstance(omega_m, Cosmo):
+        if omega_m.relativistic:
+            return np.sqrt(omega_m.e2(a))
+        omega_m = omega_m.omega_m
     return np.sqrt(omega_m / a ** 3 + (1.0 - omega_m))
+
+
+# Radiation today (Sec. 4.4 adds it to the background): photons at
+# T_cmb = 2.7255 K, Omega_gamma h^2 = 2.4728e-5; each massless neutrino species
+# carries (7/8)(4/11)^{4/3} of the photon density (T_nu / T_gamma = (4/11)^{1/3}).
+OMEGA_GAMMA_H2 = 2.4728e-5
+NU_TO_GAMMA = 7.0 / 8.0 * (4.0 / 11.0) ** (4.0 / 3.0)
+N_NU_SPECIES = 3
+_FD_X, _FD_W = np.polynomial.legendre.leggauss(32)
+
+
+def nu_energy_ratio(y):
+    """rho_nu(a) / rho_nu,NR(a) of one massive species, from Eq. relativistic:
+    rho = a^-3 int eps(q, a) f0(q) 4 pi q^2 dq with eps = sqrt(m^2 + q^2/a^2)
+    and f0 the relativistic Fermi-Dirac distribution at T_nu0, against its
+    non-relativistic limit a^-3 m int f0 4 pi q^2 dq.  With x = q / T_nu0 and
+    y = m a / T_nu0,
+
+        R(y) = int_0^inf sqrt(1 + x^2/y^2) x^2 / (e^x + 1) dx / ((3/2) zeta(3)),
+
+    (3/2) zeta(3) being int x^2 / (e^x + 1) dx.  Composite 32-point
+    Gauss-Legendre on [0, 64] split at 1, 2, 4, ..., 64 and at 2y, 4y, 8y, ...
+    (the square root's poles x = +-iy then lie at least a panel half-width
+    from every panel); the tail beyond x = 64 is below 1e-24 of the total.
+
+    Pinned by: R -> 1 + (15 zeta(5) / zeta(3)) / (2 y^2) at large y; y R ->
+    7 pi^4 / (180 zeta(3)) at small y (the relativistic fermion energy density
+    (7/8)(pi^2/15) T^4 per species); adaptive quadrature at y = 0.3 .. 30.
+    """
+    y = np.asarray(y, dtype=np.float64)
+    yf = y.reshape(-1, 1)
+    fixed = np.broadcast_to(2.0 ** np.arange(-1, 7, dtype=np.float64), (yf.shape[0], 8)).copy()
+    fixed[:, 0] = 0.0
+    geo = np.minimum(2.0 * yf * 2.0 ** np.arange(24, dtype=np.float64), 64.0)
+    edges = np.sort(np.concatenate([fixed, geo], axis=1), axis=1)        # [ny, 32]
+    lo, hi = edges[:, :-1, None], edges[:, 1:, None]
+    half = 0.5 * (hi - lo)
+    x = lo + half * (_FD_X + 1.0)
+    yy = yf[:, :, None]
+    f = np.sqrt(1.0 + (x / yy) ** 2) * x * x / (np.exp(x) + 1.0)
+    val = (half * f * _FD_W).sum(axis=(1, 2))
+    return (val / (1.5 * ZETA3)).reshape(y.shape)
 
 
 _GL_X, _GL_W = np.polynomial.legendre.leggauss(64)
 
 
-def delta_s(a_lo, a_hi, omega_m: float):
+def delta_s(a_lo, a_hi, omega_m):
     """s(a_hi) - s(a_lo) = int_{a_lo}^{a_hi} da / (a^3 H)  (Sec. 3.2: ds = dtau/a,
     dtau = da / (a^2 H)).
 
@@ -150,7 +198,7 @@ def s_of_a(a, a_init: float, omega_m: float):
     return delta_s(np.full_like(np.asarray(a, dtype=np.float64), a_init), a, omega_m)
 
 
-def kick_factor(a0: float, a1: float, omega_m: float) -> float:
+def kick_factor(a0: float, a1: float, omega_m) -> float:
     """K = int_{a0}^{a1} dt = int da / (a H): the velocity u = a^2 dx/dt obeys
     du/dt = -grad phi (Eq. dot.q.2 with q = m u).  Adaptive quadrature.
 
@@ -161,7 +209,7 @@ def kick_factor(a0: float, a1: float, omega_m: float) -> float:
     return val
 
 
-def drift_factor(a0: float, a1: float, omega_m: float) -> float:
+def drift_factor(a0: float, a1: float, omega_m) -> float:
     """Delta s = int da / (a^3 H): dx/dt = u / a^2 (Sec. 3.1 definition of q)."""
     val, _ = integrate.quad(lambda a: 1.0 / (a ** 3 * float(hubble(a, omega_m))), a0, a1,
                             epsabs=0.0, epsrel=1e-13, limit=200)
@@ -418,6 +466,7 @@ class Cosmo:
     h: float
     m_nu_ev: tuple = ()
     a_init: float = 0.02
+    relativistic: bool = False   # Sec. 4.4 background: rho_nu(a) of Eq. relativistic + radiation
 
     @property
     def omega_m(self) -> float:
@@ -426,6 +475,32 @@ class Cosmo:
     @property
     def f_nu(self) -> float:
         return self.omega_nu / self.omega_m
+
+    @property
+    def omega_r(self) -> float:
+        """Radiation today: photons plus the massless neutrino species (of
+        N_NU_SPECIES, those not listed with a mass)."""
+        n_massive = sum(1 for m in self.m_nu_ev if m > 0) if self.omega_nu > 0 else 0
+        return OMEGA_GAMMA_H2 / self.h ** 2 * (1.0 + (N_NU_SPECIES - n_massive) * NU_TO_GAMMA)
+
+    def e2(self, a):
+        """(H/H0)^2 of the Sec. 4.4 background: CDM (a^-3), each massive
+        species Omega_nu,i R(m_i a / T_nu0) a^-3 (Eq. relativistic), radiation
+        Omega_r a^-4, and Lambda closing the universe at a = 1."""
+        a = np.asarray(a, dtype=np.float64)
+        out = self.omega_cdm / a ** 3 + self.omega_r / a ** 4
+        nu_today = 0.0
+        masses = np.asarray(self.m_nu_ev, dtype=np.float64)
+        if self.omega_nu > 0 and masses.size and masses.sum() > 0:
+            for m, wi in zip(masses, self.species_weights()):
+                if m > 0:
+                    onu = self.omega_nu * wi
+                    out = out + onu * nu_energy_ratio(m * a / T_NU0_EV) / a ** 3
+                    nu_today += onu * float(nu_energy_ratio(m / T_NU0_EV))
+        elif self.omega_nu > 0:
+            out = out + self.omega_nu / a ** 3
+            nu_today = self.omega_nu
+        return out + (1.0 - self.omega_cdm - nu_today - self.omega_r)
 
     def species_weights(self):
         """Omega_nu,i / Omega_nu = m_i / M_nu (Sec. 2.1 per species).
@@ -474,6 +549,7 @@ def response_integral(kb, a, cosmo: Cosmo, m_ev: float, a_nodes, h_nodes,
     """
     kb = np.asarray(kb, dtype=np.float64)
     om = cosmo.omega_m
+    bg = cosmo                                          # background of s(a) and H(a)
     kappa = kb * C_OVER_H0 * T_NU0_EV / m_ev            # x = kappa (s - s')
     lna_nodes = np.log(np.asarray(a_nodes, dtype=np.float64))
     h_nodes = np.asarray(h_nodes, dtype=np.float64)
@@ -481,10 +557,10 @@ def response_integral(kb, a, cosmo: Cosmo, m_ev: float, a_nodes, h_nodes,
 
     def integrand(u):
         ap = math.exp(u)
-        ds = float(delta_s(ap, a, om))
+        ds = float(delta_s(ap, a, bg))
         h = _interp_lna(lna_nodes, h_nodes, u)[0]
         x = kappa * ds
-        return I_func(x) * ds * h / (ap * float(hubble(ap, om)))   # dtau'/dln a' = 1/(a' H)
+        return I_func(x) * ds * h / (ap * float(hubble(ap, bg)))   # dtau'/dln a' = 1/(a' H)
 
     u_lo, u_hi = math.log(ai), math.log(a)
     if u_hi <= u_lo:
@@ -500,7 +576,7 @@ def ic_term(kb, a, cosmo: Cosmo, m_ev: float, sqrtPnu_init, theta_over_delta_ini
     """Initial-condition term of Eq. P-final (Eq. deltaI-nu):
     I_{s_i,s} P_nu,i^{1/2}(k) {1 - (s - s_i) a_i [theta/delta]_i(k)}."""
     kb = np.asarray(kb, dtype=np.float64)
-    ds = float(delta_s(cosmo.a_init, a, cosmo.omega_m))
+    ds = float(delta_s(cosmo.a_init, a, cosmo))
     x = kb * C_OVER_H0 * T_NU0_EV / m_ev * ds
     return I_func(x) * np.asarray(sqrtPnu_init) * (
         1.0 - ds * cosmo.a_init * np.asarray(theta_over_delta_init))

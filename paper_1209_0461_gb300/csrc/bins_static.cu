@@ -34,8 +34,8 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) double g_bin_scratch[(size_t)kStaticBlocks * 3 * kStaticMaxBins];
 
-// Device address of g_bin_scratch per device, filled on the first call made
-// with that device current.
+// Device address of g_bin_scratch per device, refreshed by every call made
+// outside a stream capture with that device current.
 double* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
@@ -155,12 +155,28 @@ extern "C" int pm_bin_power_static(const void* spec, int32_t ngrid, double box, 
     cudaGetLastError();
     return PM_ERR_CUDA;
   }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (s) {   // the scratch address below is the current device's: the stream must be on it
+    int sdev = -1;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess || sdev != dev) {
+      cudaGetLastError();
+      fprintf(stderr, "pm_bin_power_static: the stream is not on the current device\n");
+      return PM_ERR_INVALID;
+    }
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return PM_ERR_CUDA;
+  }
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-      // host code cannot use the symbol's name as a device address: look it
-      // up once per device, with that device current
+    // host code cannot use the symbol's name as a device address: look it up
+    // with the device current, on every call made outside a stream capture
+    // (a context created anew after cudaDeviceReset has the array elsewhere);
+    // under capture the address of the last uncaptured call is used
+    if (cap == cudaStreamCaptureStatusNone || !g_scratch_ptr[dev]) {
       void* p = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&p, g_bin_scratch);
       if (e != cudaSuccess || !p) {
@@ -174,9 +190,7 @@ extern "C" int pm_bin_power_static(const void* spec, int32_t ngrid, double box, 
   }
   Thresholds thr;
   memset(&thr, 0, sizeof thr);
-  const double r = sqrt(3.0) * ngrid / 2.0 * (1.0 + 1e-12);
-  for (int b = 0; b <= n_kbins; ++b) thr.t[b] = (long long)ceil(pow(r, 2.0 * b / n_kbins));
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  bin_thresholds(ngrid, n_kbins, thr.t);
   const double kf = 2.0 * M_PI / box;
   if (precision == PM_FP64)
     k_bin_rfft<double><<<kStaticBlocks, kStaticWarps * 32, 0, s>>>(

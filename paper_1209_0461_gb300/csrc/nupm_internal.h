@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "../../include/nupm.h"
@@ -15,6 +16,16 @@ constexpr double kOmegaNuEv = 93.14;      // Omega_nu h^2 = sum m / 93.14 eV, Se
 constexpr int kMaxQuad = 16;
 constexpr int kMaxPanels = 320;           // history nodes + graded points + ends
 constexpr int kNuChunks = 10;             // warps per (bin, species), 32 panels each
+
+// Integer n^2 thresholds of the |k| bins: T_b = ceil((e_b L / 2 pi)^2), b = 0..nk,
+// for edges e_b log-spaced on [2 pi / L, sqrt(3) pi N / L (1 + 1e-12)]; a mode is in
+// bin b iff T_b <= n^2 < T_{b+1}.  Shared by the context and the allocation-free
+// binning entry point so that both bin every mode alike.
+inline void bin_thresholds(int ngrid, int nk, long long* t) {
+  const double r = sqrt(3.0) * ngrid / 2.0 * (1.0 + 1e-12);
+  for (int b = 0; b <= nk; ++b) t[b] = (long long)ceil(pow(r, 2.0 * b / nk));
+}
+inline double bin_log_ratio(int ngrid) { return log(sqrt(3.0) * ngrid / 2.0 * (1.0 + 1e-12)); }
 
 // Device inputs of the response kernels (one struct, passed by value).
 struct NuArgs {

@@ -636,11 +636,10 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   if (rc == PM_OK) {
     // bin thresholds T_b = ceil((e_b L / 2 pi)^2), e_b log-spaced on [kmin, kmax];
     // mode n^2 is in bin b iff T_b <= n^2 < T_{b+1}
-    const double r = sqrt(3.0) * n / 2.0 * (1.0 + 1e-12);
     c->thr.resize(c->nk + 1);
-    for (int b = 0; b <= c->nk; ++b) c->thr[b] = (long long)ceil(pow(r, 2.0 * b / c->nk));
+    bin_thresholds(n, c->nk, c->thr.data());
     std::vector<int> t32(c->thr.begin(), c->thr.end());   // T_nk <= 3 N^2 / 4 + 1 fits int32
-    c->bin_inv_lr = (float)(c->nk / (2.0 * log(r)));
+    c->bin_inv_lr = (float)(c->nk / (2.0 * bin_log_ratio(n)));
     rc = cuda_check(c, cudaMemcpy(c->d_thr, t32.data(), t32.size() * sizeof(int), cudaMemcpyHostToDevice),
                     "bin threshold upload");
   }

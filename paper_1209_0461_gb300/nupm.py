@@ -129,10 +129,16 @@ def bin_power_static(spec, ngrid, box, n_kbins, count=None, ksum=None, psum=None
     for t in (count, ksum, psum):
         if t is not None and (t.dtype != torch.float64 or not t.is_cuda or t.numel() < n_kbins):
             raise ValueError("outputs must be CUDA float64 [n_kbins]")
+    for t in (count, ksum, psum):
+        if t is not None and t.device != spec.device:
+            raise ValueError("outputs must be on the spectrum's device")
+    if stream is not None and stream.device != spec.device:
+        raise ValueError("stream must be on the spectrum's device")
     prec = PM_FP64 if spec.dtype == torch.complex128 else PM_FP32
-    st = stream if stream is not None else torch.cuda.current_stream()
-    rc = lib().pm_bin_power_static(_tptr(spec), int(ngrid), float(box), int(n_kbins), prec, _tptr(count),
-                                   _tptr(ksum), _tptr(psum), C.c_void_p(st.cuda_stream))
+    with torch.cuda.device(spec.device):     # the library's scratch is the current device's
+        st = stream if stream is not None else torch.cuda.current_stream(spec.device)
+        rc = lib().pm_bin_power_static(_tptr(spec), int(ngrid), float(box), int(n_kbins), prec, _tptr(count),
+                                       _tptr(ksum), _tptr(psum), C.c_void_p(st.cuda_stream))
     if rc != PM_OK:
         raise PMError(rc, "pm_bin_power_static failed")
 

@@ -53,6 +53,7 @@ class Workload:
     n_s: float = 0.96
     sigma8: float = 0.8
     clustered: bool = False     # Zel'dovich at a = 1 (contention variant)
+    m_species: tuple = ()       # unequal species masses [eV] (sum = m_nu_total); () = degenerate
 
     @property
     def npart(self) -> int:
@@ -70,6 +71,8 @@ class Workload:
     def masses(self):
         if self.m_nu_total <= 0 or self.n_species <= 0:
             return ()
+        if self.m_species:
+            return tuple(float(m) for m in self.m_species)
         return tuple([self.m_nu_total / self.n_species] * self.n_species)
 
 
@@ -92,6 +95,15 @@ WORKLOADS = {
 
 def with_(w: Workload, **kw) -> Workload:
     return replace(w, **kw)
+
+
+# Normal-hierarchy masses of the paper's S03NH run (Sec. 6.2, Table 1) [eV]
+HIERARCHY_NH = (0.022, 0.024, 0.054)
+
+
+def hierarchy(w: Workload, masses=HIERARCHY_NH) -> Workload:
+    """w with unequal species masses (M_nu = their sum)."""
+    return replace(w, m_nu_total=float(sum(masses)), n_species=len(masses), m_species=tuple(masses))
 
 
 # ---------------------------------------------------------------- cosmology

@@ -48,6 +48,7 @@ def gpu_kick(w, inp, K=0.01, iters=1, flags=KEEP_DEPOSIT, n_hist=None, prev=None
     if n_hist is not None:
         a_hist, hist = a_hist[:n_hist], hist[:n_hist]
     pm = nupm.PM(w.ngrid, np_, w.box, w.omega_cdm, w.omega_nu, w.h, w.m_nu_total, w.n_species,
+                 m_nu=w.m_species or None,
                  a_init=w.a_init, n_kbins=w.n_kbins, n_hist_max=max(len(a_hist), 1),
                  precision=w.precision, flags=flags, iters=iters, quad_nodes=quad,
                  sqrtPnu_init=inp["pi"], theta_over_delta_init=inp["ti"])

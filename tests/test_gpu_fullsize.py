@@ -13,7 +13,9 @@ outputs one at a time from the particles:
 
 and checks properties that hold at any size: the CIC gather of an
 antisymmetric stencil conserves momentum (sum_p acc_p = 0), and the kick
-adds acc K to every velocity."""
+adds acc K to every velocity.  The per-particle FP32 forces are compared with
+the FP64 kick of the same particles (FP64 positions, grids and transforms),
+which the oracle checks element by element at every smaller size."""
 import math
 
 import numpy as np
@@ -50,8 +52,9 @@ def run():
     n = w.ngrid
     parts = synth.particles(w)
     packed = synth.to_cell_offset(parts["pos64"], w.box, n)
-    del parts["pos64"]
-    vel_h = parts.pop("vel").astype(np.float32)
+    pos64_h = parts.pop("pos64")
+    vel64_h = parts.pop("vel")
+    vel_h = vel64_h.astype(np.float32)
     a_hist, hist = synth.history(w)
     pi, ti = synth.nu_initial(w)
     dev = torch.device("cuda")
@@ -93,6 +96,8 @@ def run():
     out["K"] = K
     out["acc_sum"] = acc.double().sum(dim=1).cpu().numpy()
     out["acc_abs"] = acc.double().abs().sum(dim=1).cpu().numpy()
+    fidx = torch.from_numpy(np.sort(rng.choice(w.npart, 1 << 17, replace=False))).to(dev)
+    out["acc32_f"] = acc[:, fidx].double().cpu().numpy()
     sidx = torch.from_numpy(rng.integers(0, w.npart, 4096)).to(dev)
     out["v_new"] = vel_t[:, sidx].double().cpu().numpy()
     out["dv"] = (vel_t[:, sidx].double() - vel[:, sidx].double()).cpu().numpy()
@@ -129,6 +134,23 @@ def run():
     out["F_total"] = sum(int(v) for v in rows.tolist())
     del F
     pmk.close()
+    # the FP64 kick of the same particles (FP64 positions), same response inputs
+    del pos, vel
+    torch.cuda.empty_cache()
+    pm64 = nupm.PM(n, w.npart, w.box, w.omega_cdm, w.omega_nu, w.h, w.m_nu_total, w.n_species,
+                   a_init=w.a_init, n_kbins=nk, n_hist_max=w.n_hist, precision="fp64",
+                   sqrtPnu_init=pi, theta_over_delta_init=ti, flags=0)
+    p64 = torch.from_numpy(pos64_h).to(dev)
+    v64 = torch.from_numpy(vel64_h).to(dev)
+    a64 = torch.empty_like(v64)
+    pm64.deposit(p64)
+    pm64.nu_response(a, a_hist, hist_d)
+    pm64.kick(p64, v64, a, K, acc_out=a64)
+    pm64.check()
+    out["acc64_f"] = a64[:, fidx].cpu().numpy()
+    out["acc64_rms"] = float(torch.sqrt((a64 * a64).sum(dim=0).mean()).item())
+    del p64, v64, a64
+    pm64.close()
     # oracle inputs: the same seeded particles, quantised by the oracle
     cell, off = synth.split_cell_offset(packed)
     c, q = O.quantise_positions_cell(cell, off, n)
@@ -225,3 +247,15 @@ def test_momentum_conservation_and_kick(run):
     bound = 1.5e-7 * (np.abs(run["v_new"]) + np.abs(acc * run["K"])) + 1e-30
     assert np.all(np.abs(dv - acc * run["K"]) <= bound)
     assert np.max(np.abs(dv)) > 0
+
+
+def test_fp32_forces_against_the_fp64_kick(run):
+    # 2^17 sampled particles of the 1024^3 / 512^3 kick: FP32 (int32 cell +
+    # FP32 offset positions, FP32 grids) against the FP64 kick
+    a32, a64 = run["acc32_f"], run["acc64_f"]
+    d = np.sqrt(((a32 - a64) ** 2).sum(0))
+    rms = run["acc64_rms"]
+    erms, emax = float(np.sqrt((d ** 2).mean()) / rms), float(d.max() / rms)
+    print(f"FP32 vs FP64 forces at 1024^3: rms {erms:.2e}, max {emax:.2e} of the rms force")
+    assert erms < 2e-4
+    assert emax < 2e-3
