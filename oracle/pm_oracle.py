@@ -784,3 +784,98 @@ def pm_kick(c, w, vel, ngrid, box, a, kick, cosmo: Cosmo, n_kbins, a_hist, sqrtP
     vnew = np.asarray(vel, dtype=np.float64) + acc * kick
     ex = dict(spec=spec, fields=fields) if keep_fields else {}
     return KickResult(F=F, bins=bins, response=resp, acc=acc, vel=vnew, extras=ex)
+
+
+# --------------------------------------------------------------------------
+# The step loop around the kick (Sec. 4.3: evolve the particles to the next
+# time step, steps (ii)-(iv), store the total-matter spectrum, repeat)
+# --------------------------------------------------------------------------
+def drift_f64(x, u, ds, box):
+    """FP64 positions moved by Delta x = u Delta s (u = a^2 dx/dt, ds = dt / a^2,
+    Sec. 3.1), wrapped into [0, L): x' = x + (u * Delta s) as two IEEE FP64
+    roundings (product, then sum; no fused multiply-add), then one add or
+    subtract of L; a sum that rounds onto L itself becomes 0.
+    Pinned by: a particle crossing either face wraps; the exact rational result
+    within one rounding."""
+    x = np.asarray(x, dtype=np.float64)
+    xn = x + np.asarray(u, dtype=np.float64) * np.float64(ds)
+    xn = np.where(xn < 0.0, xn + box, xn)
+    xn = np.where(xn >= box, xn - box, xn)
+    return np.where(xn >= box, 0.0, xn)
+
+
+def drift_cell(cell, off, u, g, ngrid):
+    """Int cell + FP32 offset positions moved by u Delta s, in FP32 with g =
+    Delta s / Delta (cells per unit velocity) rounded to FP32 once:
+      d = fl32(u g), o' = fl32(o + d), k = floor(o'), o'' = fl32(o' - k);
+      o'' = 1 (a slightly negative o') becomes 0 with k + 1; cell = (cell + k) mod N.
+    Each operation is one IEEE FP32 rounding (no fused multiply-add), so the
+    cell decision is the same on every machine that follows it.
+    Pinned by: the exact displacement within FP32 rounding; crossings of both
+    faces; the o' -> 1 case."""
+    u32 = np.asarray(u, dtype=np.float32)
+    o = np.asarray(off, dtype=np.float32)
+    d = u32 * np.float32(g)
+    o1 = o + d
+    k = np.floor(o1)
+    o2 = o1 - k
+    bump = o2 >= np.float32(1.0)
+    o2 = np.where(bump, np.float32(0.0), o2).astype(np.float32)
+    cn = np.mod(np.asarray(cell, dtype=np.int64) + k.astype(np.int64) + bump, ngrid)
+    return cn, o2
+
+
+@dataclass
+class StepRun:
+    """State of a run of steps: particles, velocities and the stored history.
+    FP64 form: pos [3, Np] float64; FP32 form: (cell int64 [3, Np], off
+    float32 [3, Np]), velocities kept as float32 values."""
+    precision: str
+    pos: object
+    vel: np.ndarray
+    a_hist: list
+    hist: list               # rows P_M^{1/2}(k_b, a_j)
+    prev: object = None      # P_nu^{1/2} of the last step (first-iteration guess)
+
+
+def pm_step(run: StepRun, ngrid, box, a, kick, drift, cosmo: Cosmo, n_kbins, sqrtPnu_init,
+            theta_over_delta_init, iters=1, I_func=nu_I, epsrel=1e-11):
+    """One time step of Sec. 4.3: with the particles at a, steps (ii)-(iv)
+    (deposit, P_cdm, neutrino response from the stored history with the last
+    step's P_nu^{1/2} as the guess, Poisson, gradient, interpolation) and the
+    kick u += acc * kick; then the total-matter row P_M^{1/2}(k_b, a) is stored
+    and the particles move on by u * drift (drift = Delta s to the next step;
+    0 after the last step).  Returns the KickResult of the step."""
+    if run.precision == "fp64":
+        c, w = quantise_positions_f64(run.pos, box, ngrid)
+    else:
+        c, w = quantise_positions_cell(run.pos[0], run.pos[1], ngrid)
+    nh = len(run.a_hist)
+    hist = np.asarray(run.hist, dtype=np.float64).reshape(nh, n_kbins)
+    r = pm_kick(c, w, run.vel, ngrid, box, a, kick, cosmo, n_kbins, np.asarray(run.a_hist, dtype=np.float64),
+                hist, sqrtPnu_init, theta_over_delta_init, sqrtPnu_prev=run.prev, iters=iters, I_func=I_func,
+                epsrel=epsrel)
+    run.vel = r.vel if run.precision == "fp64" else r.vel.astype(np.float32).astype(np.float64)
+    run.a_hist.append(float(a))
+    run.hist.append(r.response["sqrtPM"].copy())
+    run.prev = r.response["sqrtPnu"].copy()
+    if drift != 0.0:
+        if run.precision == "fp64":
+            run.pos = drift_f64(run.pos, run.vel, drift, box)
+        else:
+            run.pos = drift_cell(run.pos[0], run.pos[1], run.vel, np.float32(drift / (box / ngrid)), ngrid)
+    return r
+
+
+def leapfrog_factors(a_steps, cosmo):
+    """Kick and drift factors of a leapfrog over the step epochs a_0 < ... < a_n:
+    the kick at a_j spans the half steps around it, K(a_{j-1/2}, a_{j+1/2})
+    with a_{j+1/2} = sqrt(a_j a_{j+1}) (half steps at the two ends), and the
+    drift after it Delta s(a_j, a_{j+1}) (0 after the last)."""
+    a = [float(v) for v in a_steps]
+    mid = [math.sqrt(a[j] * a[j + 1]) for j in range(len(a) - 1)]
+    lo = [a[0]] + mid
+    hi = mid + [a[-1]]
+    kicks = [kick_factor(l, h, cosmo) for l, h in zip(lo, hi)]
+    drifts = [drift_factor(a[j], a[j + 1], cosmo) for j in range(len(a) - 1)] + [0.0]
+    return kicks, drifts
