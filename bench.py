@@ -131,6 +131,7 @@ def stage_bytes(w, stage, fused_interp=True, spectral=False):
             "fft_y_inv": 2 * c * Mc,                      # phi in place
             "fft_x_inv": c * Mc + r * M,                  # packed rows -> real potential
             "interp": p * Np + min(r * M, 56 * r * Np) + 2 * 3 * v * Np,
+            "drift": 2 * p * Np + 3 * v * Np,
         }.get(stage)
     return {
         "deposit": (p + 8) * Np,                         # row sort: positions in, 8-byte records out
@@ -143,6 +144,7 @@ def stage_bytes(w, stage, fused_interp=True, spectral=False):
         "fft_y_inv": 2 * c * Mc + 3 * c * Mc,             # 2 fields -> 3 fields
         "fft_x_inv": (3 * c * Mc + (p + 4 + 2 * 3 * v) * Np) if fused_interp else 3 * (c * Mc + r * M),
         "interp": p * Np + min(3 * r * M, 24 * r * Np) + 2 * 3 * v * Np,
+        "drift": 2 * p * Np + 3 * v * Np,                # positions read and written, velocities read
     }.get(stage)
 
 
@@ -386,7 +388,7 @@ def run_gpu(args, w, rank, world):
             "ms_per_launch": round(per_launch_ms, 4)}
     total_launch = sum(v[1] for v in stages.values())
     step_alg = sum(stage_bytes(wr, k, fused, spectral) * (v[2] if k in ("deposit", "bins") else v[1])
-                   for k, v in stages.items() if k != "response") / args.steps
+                   for k, v in stages.items() if k != "response" and v[1] > 0) / args.steps
     res = dict(value=whole_job_rate(wr.npart, world, ms), ms_per_step=ms, ms_per_step_median=ms_median,
                graph=graph, e2e=e2e, roofline=roof,
                stages={k: {"ms_per_step": round(v[0] / args.steps, 4), "launches_per_step": v[1] // args.steps}

@@ -81,6 +81,13 @@ extern "C" {
                                  (equal in exact arithmetic).  PM_FUSED_GATHER and
                                  PM_TMA_COLUMNS imply it. */
 
+#define PM_RELATIVISTIC 0x80u /* Sec. 4.4 background in H(a): each massive species with the
+                                 energy density of Eq. relativistic (relativistic Fermi-Dirac
+                                 momenta, T_nu0 = 1.68e-4 eV), radiation (photons, Omega_gamma
+                                 h^2 = 2.4728e-5, and the massless of three neutrino species),
+                                 Lambda closing the universe at a = 1.  Default: matter +
+                                 Lambda with Omega_nu as matter.  Poisson keeps Omega_M. */
+
 /*
  * Problem statement (Sec. 4.3-4.4, Table 1).  Omega_M = omega_cdm + omega_nu
  * (baryons folded into cdm), flat: Omega_Lambda = 1 - Omega_M.
@@ -195,12 +202,67 @@ NUPM_API int pm_nu_prepare(pm_ctx* ctx, double a, const double* a_hist, const do
 NUPM_API int pm_kick(pm_ctx* ctx, const void* pos, void* vel, double a, double kick_factor,
             void* acc_out);
 
+/*
+ * Sec. 4.3 step (ii), "evolve the CDM ... up to the next timestep": move the
+ * particles by Delta x = u Delta s (u = a^2 dx/dt, ds = dt / a^2, Sec. 3.1),
+ * drift_factor = Delta s = pm_drift_factor(a0, a1).  In place on DEVICE pos,
+ * with DEVICE vel (layouts of pm_deposit / pm_kick).  Each step is a fixed
+ * sequence of IEEE roundings (no fused multiply-add), so results are the same
+ * on every GPU:
+ *   PM_FP64  x' = x + (u * ds); x' += L if x' < 0; x' -= L if x' >= L; a sum
+ *            that rounds onto L becomes 0
+ *   PM_FP32  g = (float)(ds / cell size); d = u * g; o' = o + d; k = floor(o');
+ *            o'' = o' - k (o'' = 1 becomes 0 with k + 1); cell = (cell + k) mod N
+ * A particle with a non-finite result, or an FP32 offset outside [0,1) on
+ * entry, is left unchanged and sets PM_ERR_RANGE in the device status.
+ */
+NUPM_API int pm_drift(pm_ctx* ctx, void* pos, const void* vel, double drift_factor);
+
+/*
+ * The stored history of Sec. 4.3 kept by the context (pm_step appends to it).
+ *   pm_history_set  replace it: a_hist HOST double[n_hist] (as pm_nu_response),
+ *                   sqrtPM_hist DEVICE double[n_hist][n_kbins] (copied,
+ *                   stream-ordered), sqrtPnu_prev DEVICE double[n_kbins] or NULL
+ *                   (the next step's first-iteration guess; NULL = initial value);
+ *                   n_hist 0..n_hist_max
+ *   pm_history_get  HOST a_hist[n] and n_hist, DEVICE sqrtPM_hist[n][n_kbins]
+ *                   and sqrtPnu_prev[n_kbins] (any may be NULL; DEVICE copies
+ *                   are stream-ordered; sqrtPnu_prev is left unchanged when the
+ *                   context has none)
+ */
+NUPM_API int pm_history_set(pm_ctx* ctx, const double* a_hist, const double* sqrtPM_hist, int32_t n_hist,
+                            const double* sqrtPnu_prev);
+NUPM_API int pm_history_get(pm_ctx* ctx, double* a_hist, double* sqrtPM_hist, double* sqrtPnu_prev,
+                            int32_t* n_hist);
+
+/*
+ * One time step of Sec. 4.3 with the particles at scale factor a: steps
+ * (ii)-(iv) -- pm_deposit, the response of Eq. P-final over the context's
+ * stored history with the last step's P_nu^{1/2} as the first-iteration guess
+ * (its history panels overlapping the deposit, as pm_nu_prepare), pm_kick
+ * with kick_factor -- then "store the total matter power spectrum": the row
+ * P_M^{1/2}(k_b, a) is appended to the context's history on the device and
+ * P_nu^{1/2}(k_b, a) kept as the next guess, and finally pm_drift by
+ * drift_factor (Delta s to the next step; 0 = no drift, e.g. after the last
+ * step).  a must exceed the history's last scale factor; PM_ERR_RANGE when the
+ * history already holds n_hist_max rows.  A leapfrog takes kick_factor =
+ * K(a_{j-1/2}, a_{j+1/2}) (half steps at both ends) and drift_factor =
+ * Delta s(a_j, a_{j+1}).  acc_out as pm_kick.
+ */
+NUPM_API int pm_step(pm_ctx* ctx, void* pos, void* vel, double a, double kick_factor, double drift_factor,
+                     void* acc_out);
+
 /* Synchronise the stream and report the first device-side error recorded
  * since the previous pm_check (then clear it). */
 NUPM_API int pm_check(pm_ctx* ctx);
 
 NUPM_API void pm_free(pm_ctx* ctx);
 NUPM_API const char* pm_last_error(const pm_ctx* ctx);
+
+/* H(a) / H0 of the background a problem statement describes (matter + Lambda,
+ * or with PM_RELATIVISTIC in p->flags the Sec. 4.4 background), host FP64,
+ * without a context or a GPU; NaN for a <= 0 or a NULL p. */
+NUPM_API double pm_hubble(const pm_params* p, double a);
 
 /* K = int_{a0}^{a1} da / (a H(a)) and Delta s = int da / (a^3 H(a)) of the
  * context's background, host FP64 (16-point Gauss-Legendre on panels of
@@ -252,7 +314,8 @@ NUPM_API int pm_copy_field(pm_ctx* ctx, int32_t which, void* dst);
 #define PM_ST_FFT_Y_INV  8
 #define PM_ST_FFT_X_INV  9   /* inverse x transform (+ CIC gather + kick with PM_FUSED_GATHER) */
 #define PM_ST_INTERP    10   /* CIC gather + kick (not launched with PM_FUSED_GATHER) */
-#define PM_NSTAGES      11
+#define PM_ST_DRIFT     11   /* pm_drift (also inside pm_step) */
+#define PM_NSTAGES      12
 /* enable != 0: record an event pair around every stage from now on and
  * clear the totals; 0: stop recording. */
 NUPM_API int pm_timing(pm_ctx* ctx, int32_t enable);

@@ -353,13 +353,14 @@ int NUPM_FN(green)(const GridArgs& g, cudaStream_t s) {
 
 int NUPM_FN(interp)(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, cudaStream_t s) {
   if (g.np > 0 && g.fd_grad && g.rows_ready) {   // row order of the deposit's sort: a warp per row
-    k_interp_rows_fd<T><<<grid_blocks((int64_t)g.n * g.n * 32, 128, 2 * g.part_ctas_per_sm), 128, 0, s>>>(
+    k_interp_rows_fd<T><<<(unsigned)(((int64_t)g.n * g.n + kRowsPerCta - 1) / kRowsPerCta), kGatherTPB, 0, s>>>(
         g.rec, g.row_start, g.perm, g.np, g.n, g.delta, reinterpret_cast<const T*>(g.g), reinterpret_cast<T*>(vel),
         (T)kick, reinterpret_cast<T*>(acc_out));
     return PM_OK;
   }
   if (g.np > 0 && g.fd_grad) {
-    k_interp_kick_fd<T><<<grid_blocks(g.np, 128, 2 * g.part_ctas_per_sm), 128, 0, s>>>(
+    k_interp_kick_fd<T><<<(unsigned)((g.np + kGatherTPB * kGatherChunk - 1) / (kGatherTPB * kGatherChunk)),
+                          kGatherTPB, 0, s>>>(
         pos, g.np, g.n, g.delta, reinterpret_cast<const T*>(g.g), reinterpret_cast<T*>(vel), (T)kick,
         reinterpret_cast<T*>(acc_out), g.status);
     return PM_OK;
@@ -393,6 +394,13 @@ int NUPM_FN(xinv_interp)(const GridArgs& g, const void* pos, void* vel, double k
     case 1024: xinv_interp_n<1024>(g, pos, vel, kick, acc_out, s); break;
     default: return PM_ERR_UNSUPPORTED;
   }
+  return PM_OK;
+}
+
+int NUPM_FN(drift)(const GridArgs& g, void* pos, const void* vel, double ds, cudaStream_t s) {
+  if (g.np > 0)
+    k_drift<T><<<grid_blocks(g.np, 256, 8), 256, 0, s>>>(pos, reinterpret_cast<const T*>(vel), g.np, g.n, g.box, ds,
+                                                          (float)(ds / g.delta), g.status);
   return PM_OK;
 }
 

@@ -125,7 +125,7 @@ __global__ void k_nu_panels(NuArgs A) {
   const double kb = A.bins[A.nk + b] / cnt;
   const double s_end = s_table(A, A.ue);
   const double kappa = kb * A.kappa_scale[s];
-  const double Ha = sqrt(A.omega_m * exp(-3.0 * A.ue) + A.omega_l);
+  const double Ha = A.rel ? sqrt(rel_e2(A.a, A.bg)) : sqrt(A.omega_m * exp(-3.0 * A.ue) + A.omega_l);
   const double ell = (kappa > 0.0) ? A.a * A.a * Ha / kappa : 1e300;
   const int n = A.n_hist;
   Panel* P = panels[warp];
@@ -192,7 +192,7 @@ __global__ void k_nu_panels(NuArgs A) {
       const double u = pn.lo + half * (A.gl[q] + 1.0);
       const double wq = half * A.gl[kMaxQuad + q];
       const double ap = exp(u);
-      const double Hp = sqrt(A.omega_m / (ap * ap * ap) + A.omega_l);
+      const double Hp = A.rel ? sqrt(rel_e2(ap, A.bg)) : sqrt(A.omega_m / (ap * ap * ap) + A.omega_l);
       const double ds = s_end - s_table(A, u);
       const double x = kappa * ds;
       const double I = A.use_fit ? nu_I_fit(x) : nu_I_exact(x);

@@ -27,6 +27,50 @@ inline void bin_thresholds(int ngrid, int nk, long long* t) {
 }
 inline double bin_log_ratio(int ngrid) { return log(sqrt(3.0) * ngrid / 2.0 * (1.0 + 1e-12)); }
 
+// ---- Sec. 4.4 background (PM_RELATIVISTIC) ----
+// Radiation today: photons at T_cmb = 2.7255 K (Omega_gamma h^2 = 2.4728e-5)
+// and each massless neutrino species (7/8)(4/11)^{4/3} of that; of three
+// neutrino species, those without a mass are massless.
+constexpr double kOmegaGammaH2 = 2.4728e-5;
+constexpr int kNuSpeciesTotal = 3;
+inline double nu_to_gamma() { return 7.0 / 8.0 * pow(4.0 / 11.0, 4.0 / 3.0); }
+// R(y) = rho_nu / rho_nu,NR of one massive species (Eq. relativistic), y = m a / T_nu0,
+// tabulated as ln R and d ln R / d ln y on t = ln y = kRelT0 + i kRelH (cubic
+// Hermite in t); beyond the table the ultra- and non-relativistic series.
+constexpr double kRelT0 = -9.210340371976182;    // ln 1e-4
+constexpr double kRelH = 1.0 / 256.0;
+constexpr int kRelN = 5896;                       // up to ln y = kRelT0 + (kRelN - 1) kRelH > ln 1e6
+constexpr double kRelZeta3 = 1.2020569031595942, kRelZeta5 = 1.0369277551433699, kRelPi = 3.141592653589793;
+// y R -> 7 pi^4 / (180 zeta 3) (1 + 5 y^2 / (7 pi^2)) as y -> 0; R - 1 -> 15 zeta(5) / (2 zeta(3) y^2) as y -> inf
+constexpr double kRelUR = 7.0 * kRelPi * kRelPi * kRelPi * kRelPi / (180.0 * kRelZeta3);
+constexpr double kRelUR2 = 5.0 / (7.0 * kRelPi * kRelPi);
+constexpr double kRelNR = 15.0 * kRelZeta5 / (2.0 * kRelZeta3);
+__host__ __device__ inline double nu_rho_ratio(double y, const double* tab) {
+  const double t = log(y);
+  const double u = (t - kRelT0) * (1.0 / kRelH);
+  if (u < 0.0) return kRelUR / y * (1.0 + kRelUR2 * y * y);
+  if (u >= (double)(kRelN - 1)) return 1.0 + kRelNR / (y * y);
+  const int i = (int)u;
+  const double f = u - i;
+  const double y0 = tab[2 * i], d0 = tab[2 * i + 1] * kRelH, y1 = tab[2 * i + 2], d1 = tab[2 * i + 3] * kRelH;
+  const double f2 = f * f, f3 = f2 * f;
+  return exp((2 * f3 - 3 * f2 + 1) * y0 + (f3 - 2 * f2 + f) * d0 + (-2 * f3 + 3 * f2) * y1 + (f3 - f2) * d1);
+}
+// (H / H0)^2 of the Sec. 4.4 background: CDM a^-3, radiation a^-4, Lambda, and
+// each massive species Omega_nu,s R(y1_s a) a^-3 (y1_s = m_s / T_nu0).
+struct RelBackground {
+  double om_cdm, om_r, om_lam;
+  int ns;
+  double om_nu[3], y1[3];
+  const double* tab;
+};
+__host__ __device__ inline double rel_e2(double a, const RelBackground& B) {
+  const double a3 = a * a * a;
+  double e = B.om_cdm / a3 + B.om_r / (a3 * a) + B.om_lam;
+  for (int s = 0; s < B.ns; ++s) e += B.om_nu[s] * nu_rho_ratio(B.y1[s] * a, B.tab) / a3;
+  return e;
+}
+
 // Device inputs of the response kernels (one struct, passed by value).
 struct NuArgs {
   int nk, ns, n_hist, quad, iters, use_fit, ngrid;
@@ -52,6 +96,8 @@ struct NuArgs {
   double* R_user;                 // optional copies
   double* pnu_user;
   double* pm_user;
+  int rel;                        // 1: H(a) of the Sec. 4.4 background (bg), else matter + Lambda
+  RelBackground bg;
 };
 
 void launch_nu_response(const NuArgs& a, cudaStream_t s);
@@ -136,6 +182,7 @@ struct GridArgs {
   int xinv_interp##SFX(const GridArgs& g, const void* pos, void* vel, double kick,          \
                        void* acc_out, cudaStream_t s);                                      \
   int unpack##SFX(const GridArgs& g, void* dst, cudaStream_t s);                            \
+  int drift##SFX(const GridArgs& g, void* pos, const void* vel, double ds, cudaStream_t s);   \
   int fd_field##SFX(const GridArgs& g, int comp, void* dst, cudaStream_t s);
 NUPM_DECLARE_GRID(_f32)
 NUPM_DECLARE_GRID(_f64)

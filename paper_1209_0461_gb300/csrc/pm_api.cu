@@ -10,6 +10,7 @@
 
 #include <cudaTypedefs.h>
 
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -86,6 +87,17 @@ struct pm_ctx {
   double* d_hist_u2 = nullptr;         // ln a_hist of the prepared panels
   double* h_hist_u2 = nullptr;
   int* h_status = nullptr;
+  // Sec. 4.4 background (PM_RELATIVISTIC): host copy uses the host R(y) table
+  bool rel = false;
+  RelBackground bg{};
+  double* d_rtab = nullptr;
+  // history owned by the context (pm_history_set, pm_step): P_M^{1/2} rows and
+  // their scale factors, and P_nu^{1/2} of the last step (two buffers, swapped)
+  double* d_hist_own = nullptr;        // [n_hist_max][nk]
+  std::vector<double> own_a;
+  double* d_prev[2] = {nullptr, nullptr};
+  int prev_cur = 0;
+  bool have_prev = false;
   // state
   bool deposited = false, deposit_grid_valid = false, have_response = false, have_kick = false;
   bool power_set = false;         // bins replaced by pm_set_power (no spectrum behind them)
@@ -152,7 +164,10 @@ int dalloc(pm_ctx* c, void** p, size_t bytes, const char* what) {
   return PM_OK;
 }
 
-double hubble(const pm_ctx* c, double a) { return sqrt(c->omega_m / (a * a * a) + c->omega_l); }
+double hubble(const pm_ctx* c, double a) {
+  if (c->rel) return sqrt(rel_e2(a, c->bg));
+  return sqrt(c->omega_m / (a * a * a) + c->omega_l);
+}
 
 // Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_q (long double).
 void gauss_legendre(int q, double* x, double* w) {
@@ -198,6 +213,61 @@ double integrate_u(double u0, double u1, F f) {
     s += 0.5 * h * ps;
   }
   return s;
+}
+
+// Adaptive Gauss-Legendre bisection: a panel's 16-point value is replaced by
+// the sum over its halves until the two agree to tol (absolute).
+template <class F>
+double gl16_panel(F f, double a, double b, const double* gx, const double* gw) {
+  const double h = 0.5 * (b - a), m = 0.5 * (a + b);
+  double s = 0.0;
+  for (int i = 0; i < 16; ++i) s += gw[i] * f(m + h * gx[i]);
+  return s * h;
+}
+template <class F>
+double gl16_adapt(F f, double a, double b, double whole, double tol, int depth, const double* gx, const double* gw) {
+  const double m = 0.5 * (a + b);
+  const double l = gl16_panel(f, a, m, gx, gw), r = gl16_panel(f, m, b, gx, gw);
+  if (depth >= 48 || fabs(l + r - whole) <= tol) return l + r;
+  return gl16_adapt(f, a, m, l, tol, depth + 1, gx, gw) + gl16_adapt(f, m, b, r, tol, depth + 1, gx, gw);
+}
+
+// The R(y) table of the Sec. 4.4 background (Eq. relativistic): at t = ln y on
+// the kRel grid, ln R and d ln R / d ln y with
+//   N(y)     = int_0^64 sqrt(1 + x^2/y^2) x^2 / (e^x + 1) dx,   R = N / ((3/2) zeta(3)),
+//   y N'(y)  = -int_0^64 (x/y)^2 / sqrt(1 + x^2/y^2) x^2 / (e^x + 1) dx
+// (x = q / T_nu0; the tail beyond x = 64 is below 1e-24 of N), each on
+// [0, y] and [y, 64] by adaptive bisection to 1e-15.  Built once per process.
+const double* rel_table() {
+  static std::vector<double> tab;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    double gx[16], gw[16];
+    gauss_legendre(16, gx, gw);
+    tab.resize(2 * (size_t)kRelN);
+    for (int i = 0; i < kRelN; ++i) {
+      const double y = exp(kRelT0 + i * kRelH);
+      auto fn = [y](double x) {
+        const double r = x / y;
+        return sqrt(1.0 + r * r) * x * x / (exp(x) + 1.0);
+      };
+      auto fd = [y](double x) {
+        const double r = x / y;
+        return -r * r / sqrt(1.0 + r * r) * x * x / (exp(x) + 1.0);
+      };
+      const double cut = y < 64.0 ? y : 64.0;
+      double N = 0.0, D = 0.0;
+      const double e0[2] = {0.0, cut}, e1[2] = {cut, 64.0};
+      for (int k = 0; k < 2; ++k) {
+        if (!(e1[k] > e0[k])) continue;
+        N += gl16_adapt(fn, e0[k], e1[k], gl16_panel(fn, e0[k], e1[k], gx, gw), 1e-15, 0, gx, gw);
+        D += gl16_adapt(fd, e0[k], e1[k], gl16_panel(fd, e0[k], e1[k], gx, gw), 1e-15, 0, gx, gw);
+      }
+      tab[2 * (size_t)i] = log(N / (1.5 * kRelZeta3));
+      tab[2 * (size_t)i + 1] = D / N;
+    }
+  });
+  return tab.data();
 }
 
 // s(u) table on u in [ln a_i, u_max], spacing 1/512: values and ds/du = 1/(a^2 H).
@@ -428,7 +498,8 @@ void release(pm_ctx* c) {
                   c->spec, c->g, c->tw_n, c->tw_m, c->d_thr, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
                   c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_rlist, c->d_gtab,
                   c->d_dtab, c->d_wtab, c->d_plane0, c->d_fac, c->d_rowc, c->d_rows, c->d_rowcur,
-                  c->d_scantot, c->d_perm, c->d_rec, c->d_status, c->d_hist_u2};
+                  c->d_scantot, c->d_perm, c->d_rec, c->d_status, c->d_hist_u2, c->d_rtab, c->d_hist_own,
+                  c->d_prev[0], c->d_prev[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_hist_u) cudaFreeHost(c->h_hist_u);
@@ -445,6 +516,57 @@ void release(pm_ctx* c) {
 }
 
 bool finite_pos(double x) { return isfinite(x) && x > 0; }
+
+// Species masses of a problem statement (Sec. 2.1): the listed masses, or
+// m_nu_total shared equally; Omega_nu from the total mass when not given.
+void species_setup(const pm_params& p, double (&ms)[3], int& ns, double& mtot, double& onu) {
+  mtot = p.m_nu_total_eV;
+  ns = (mtot > 0) ? p.n_species : 0;
+  ms[0] = ms[1] = ms[2] = 0.0;
+  if (ns > 0) {
+    double sum = 0;
+    for (int i = 0; i < ns; ++i) sum += p.m_nu_eV[i] > 0 ? p.m_nu_eV[i] : 0;
+    if (sum > 0) {
+      for (int i = 0; i < ns; ++i) ms[i] = p.m_nu_eV[i] > 0 ? p.m_nu_eV[i] : 0;
+      mtot = sum;
+    } else {
+      for (int i = 0; i < ns; ++i) ms[i] = mtot / ns;
+    }
+  }
+  onu = p.omega_nu < 0 ? mtot / (kOmegaNuEv * p.h * p.h) : p.omega_nu;
+  if (ns == 0) onu = p.omega_nu > 0 ? p.omega_nu : 0.0;
+}
+
+int n_massive_of(const double* ms, int ns, double onu) {
+  int k = 0;
+  for (int i = 0; i < ns && onu > 0; ++i) k += ms[i] > 0 ? 1 : 0;
+  return k;
+}
+
+// The Sec. 4.4 background of species with masses m[s] and weights w[s]
+// (Omega_nu,s = Omega_nu w[s]): massive species with the energy density of
+// Eq. relativistic, radiation (photons and the massless of three species),
+// Lambda closing the universe at a = 1.
+void fill_background(const pm_params& p, const double* m, const double* w, int ns, double onu, int n_massive,
+                     RelBackground& B) {
+  B.tab = rel_table();
+  B.om_r = kOmegaGammaH2 / (p.h * p.h) * (1.0 + (kNuSpeciesTotal - n_massive) * nu_to_gamma());
+  B.om_cdm = p.omega_cdm;
+  double nu_today = 0.0;
+  B.ns = 0;
+  if (ns > 0 && onu > 0) {
+    B.ns = ns;
+    for (int s = 0; s < ns; ++s) {
+      B.om_nu[s] = onu * w[s];
+      B.y1[s] = m[s] / kTnu0eV;
+      nu_today += B.om_nu[s] * nu_rho_ratio(B.y1[s], B.tab);
+    }
+  } else {
+    B.om_cdm += onu;   // Omega_nu without a massive species: clustering matter
+    nu_today = onu;
+  }
+  B.om_lam = 1.0 - p.omega_cdm - nu_today - B.om_r;
+}
 
 }  // namespace
 
@@ -501,7 +623,7 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   else if (p.iters < 1 || p.iters > 16) bad(PM_ERR_INVALID, "iters must be 1..16");
   else if (p.quad_nodes < 2 || p.quad_nodes > kMaxQuad) bad(PM_ERR_INVALID, "quad_nodes must be 2..16");
   else if (p.flags & ~(PM_I_FIT | PM_DECONV_CIC | PM_KEEP_DEPOSIT | PM_UNFUSED_DEPOSIT | PM_TMA_COLUMNS | PM_FUSED_GATHER |
-                       PM_SPECTRAL_GRADIENT))
+                       PM_SPECTRAL_GRADIENT | PM_RELATIVISTIC))
     bad(PM_ERR_INVALID, "unknown flag bits");
   if (rc != PM_OK) {
     // report through a context so pm_last_error works; caller still gets NULL
@@ -522,21 +644,10 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   c->iters = p.iters;
   c->a_init = p.a_init;
   // neutrinos (Sec. 2.1): Omega_nu from the total mass when not given
-  double mtot = p.m_nu_total_eV;
-  int ns = (mtot > 0) ? p.n_species : 0;
+  double mtot = 0.0, onu = 0.0;
+  int ns = 0;
   double ms[3] = {0, 0, 0};
-  if (ns > 0) {
-    double sum = 0;
-    for (int i = 0; i < ns; ++i) sum += p.m_nu_eV[i] > 0 ? p.m_nu_eV[i] : 0;
-    if (sum > 0) {
-      for (int i = 0; i < ns; ++i) ms[i] = p.m_nu_eV[i] > 0 ? p.m_nu_eV[i] : 0;
-      mtot = sum;
-    } else {
-      for (int i = 0; i < ns; ++i) ms[i] = mtot / ns;
-    }
-  }
-  double onu = p.omega_nu < 0 ? mtot / (kOmegaNuEv * p.h * p.h) : p.omega_nu;
-  if (ns == 0) onu = p.omega_nu > 0 ? p.omega_nu : 0.0;
+  species_setup(p, ms, ns, mtot, onu);
   if (!(isfinite(onu) && onu >= 0)) {
     fprintf(stderr, "pm_init: bad omega_nu\n");
     delete c;
@@ -580,6 +691,10 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
     }
   }
   c->ns = used;
+  if (p.flags & PM_RELATIVISTIC) {
+    c->rel = true;
+    fill_background(p, c->mass, c->wsp, c->ns, onu, n_massive_of(ms, ns, onu), c->bg);
+  }
   c->n2max = 3LL * (n / 2) * (n / 2);
   c->field_elems = (int64_t)n * n * (n / 2);
   c->cplx = c->fp64 ? 16 : 8;
@@ -623,6 +738,17 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
     rc = dalloc(c, (void**)&c->d_perm, (size_t)c->np * sizeof(int), "row permutation");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_rec, (size_t)c->np * sizeof(unsigned long long), "sorted records");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_status, sizeof(int), "status");
+  if (rc == PM_OK)
+    rc = dalloc(c, (void**)&c->d_hist_own, (size_t)(p.n_hist_max > 0 ? p.n_hist_max : 1) * c->nk * sizeof(double),
+                "stored history");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_prev[0], (size_t)c->nk * sizeof(double), "previous P_nu");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_prev[1], (size_t)c->nk * sizeof(double), "previous P_nu");
+  if (rc == PM_OK && c->rel) {
+    rc = dalloc(c, (void**)&c->d_rtab, 2 * (size_t)kRelN * sizeof(double), "relativistic background table");
+    if (rc == PM_OK)
+      rc = cuda_check(c, cudaMemcpy(c->d_rtab, c->bg.tab, 2 * (size_t)kRelN * sizeof(double), cudaMemcpyHostToDevice),
+                      "background table upload");
+  }
   if (rc == PM_OK && (cudaMallocHost((void**)&c->h_hist_u2, (size_t)(p.n_hist_max + 1) * sizeof(double)) != cudaSuccess ||
                       cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
                       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -873,6 +999,9 @@ NuArgs nu_args(pm_ctx* c, double a, const double* sqrtPM_hist, int32_t n_hist, c
   A.R_user = ratio_out;
   A.pnu_user = sqrtPnu_out;
   A.pm_user = sqrtPM_out;
+  A.rel = c->rel ? 1 : 0;
+  A.bg = c->bg;
+  A.bg.tab = c->d_rtab;
   return A;
 }
 
@@ -1078,6 +1207,93 @@ int pm_kick(pm_ctx* c, const void* pos, void* vel, double a, double kick_factor,
   return rc;
 }
 
+int pm_drift(pm_ctx* c, void* pos, const void* vel, double drift_factor) {
+  if (!c) return PM_ERR_INVALID;
+  if (!pos || !vel) return fail(c, PM_ERR_INVALID, "pm_drift: pos/vel is NULL");
+  if (!isfinite(drift_factor)) return fail(c, PM_ERR_INVALID, "pm_drift: drift_factor must be finite");
+  GridArgs g = grid_args(c);
+  {
+    Stage st(c, PM_ST_DRIFT, 1);
+    const int rc = c->fp64 ? drift_f64(g, pos, vel, drift_factor, c->stream)
+                           : drift_f32(g, pos, vel, drift_factor, c->stream);
+    if (rc != PM_OK) return fail(c, rc, "pm_drift failed");
+  }
+  // the particles moved: a sort of the old positions no longer describes them
+  c->perm_valid = false;
+  return cuda_check(c, cudaGetLastError(), "pm_drift launch");
+}
+
+int pm_history_set(pm_ctx* c, const double* a_hist, const double* sqrtPM_hist, int32_t n_hist,
+                   const double* sqrtPnu_prev) {
+  if (!c) return PM_ERR_INVALID;
+  if (n_hist < 0 || n_hist > c->p.n_hist_max) return fail(c, PM_ERR_INVALID, "pm_history_set: n_hist outside 0..n_hist_max");
+  if (n_hist > 0 && (!a_hist || !sqrtPM_hist)) return fail(c, PM_ERR_INVALID, "pm_history_set: NULL history");
+  for (int j = 0; j < n_hist; ++j) {
+    if (!isfinite(a_hist[j]) || (j == 0 && a_hist[0] < c->a_init) || (j > 0 && !(a_hist[j] > a_hist[j - 1])))
+      return fail(c, PM_ERR_RANGE, "pm_history_set: a_hist must be finite, >= a_init and strictly increasing");
+  }
+  int rc = PM_OK;
+  if (n_hist > 0)
+    rc = cuda_check(c, cudaMemcpyAsync(c->d_hist_own, sqrtPM_hist, (size_t)n_hist * c->nk * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, c->stream), "pm_history_set copy");
+  if (rc == PM_OK && sqrtPnu_prev)
+    rc = cuda_check(c, cudaMemcpyAsync(c->d_prev[0], sqrtPnu_prev, (size_t)c->nk * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, c->stream), "pm_history_set copy");
+  if (rc != PM_OK) return rc;
+  c->own_a.assign(a_hist ? a_hist : a_hist, a_hist ? a_hist + n_hist : a_hist);
+  c->prev_cur = 0;
+  c->have_prev = sqrtPnu_prev != nullptr;
+  return PM_OK;
+}
+
+int pm_history_get(pm_ctx* c, double* a_hist, double* sqrtPM_hist, double* sqrtPnu_prev, int32_t* n_hist) {
+  if (!c) return PM_ERR_INVALID;
+  const int n = (int)c->own_a.size();
+  if (n_hist) *n_hist = n;
+  if (a_hist)
+    for (int j = 0; j < n; ++j) a_hist[j] = c->own_a[j];
+  int rc = PM_OK;
+  if (sqrtPM_hist && n > 0)
+    rc = cuda_check(c, cudaMemcpyAsync(sqrtPM_hist, c->d_hist_own, (size_t)n * c->nk * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, c->stream), "pm_history_get copy");
+  if (rc == PM_OK && sqrtPnu_prev && c->have_prev)
+    rc = cuda_check(c, cudaMemcpyAsync(sqrtPnu_prev, c->d_prev[c->prev_cur], (size_t)c->nk * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, c->stream), "pm_history_get copy");
+  return rc;
+}
+
+int pm_step(pm_ctx* c, void* pos, void* vel, double a, double kick_factor, double drift_factor, void* acc_out) {
+  if (!c) return PM_ERR_INVALID;
+  if (!pos || !vel) return fail(c, PM_ERR_INVALID, "pm_step: pos/vel is NULL");
+  if (!isfinite(drift_factor)) return fail(c, PM_ERR_INVALID, "pm_step: drift_factor must be finite");
+  const int n = (int)c->own_a.size();
+  if (n >= c->p.n_hist_max) return fail(c, PM_ERR_RANGE, "pm_step: the stored history is full (n_hist_max rows)");
+  if (n > 0 && !(a > c->own_a.back())) return fail(c, PM_ERR_RANGE, "pm_step: a must exceed the last stored a");
+  const double* ah = n > 0 ? c->own_a.data() : nullptr;
+  const double* hist = n > 0 ? c->d_hist_own : nullptr;
+  // (iii) history panels on the side stream, overlapping the deposit
+  int rc = pm_nu_prepare(c, a, ah, hist, n);
+  // (ii) deposit, P_cdm
+  if (rc == PM_OK) rc = pm_deposit(c, pos);
+  // (iii) response; its P_M^{1/2} row is written straight into the history
+  const int nxt = 1 - c->prev_cur;
+  if (rc == PM_OK)
+    rc = pm_nu_response(c, a, ah, hist, n, c->have_prev ? c->d_prev[c->prev_cur] : nullptr, nullptr, c->d_prev[nxt],
+                        c->d_hist_own + (size_t)n * c->nk);
+  // (iv) delta_M, Poisson, forces, kick
+  if (rc == PM_OK) rc = pm_kick(c, pos, vel, a, kick_factor, acc_out);
+  if (rc != PM_OK) {
+    join_prepared(c);
+    return rc;
+  }
+  c->own_a.push_back(a);
+  c->prev_cur = nxt;
+  c->have_prev = true;
+  // (ii) of the next step: the particles move on
+  if (drift_factor != 0.0) rc = pm_drift(c, pos, vel, drift_factor);
+  return rc;
+}
+
 int pm_check(pm_ctx* c) {
   if (!c) return PM_ERR_INVALID;
   int rc = cuda_check(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
@@ -1119,6 +1335,30 @@ double pm_drift_factor(const pm_ctx* c, double a0, double a1) {
     const double a = exp(u);
     return 1.0 / (a * a * hubble(c, a));
   });
+}
+
+double pm_hubble(const pm_params* p, double a) {
+  if (!p || !(a > 0) || !isfinite(a) || !(p->h > 0)) return NAN;
+  double ms[3], mtot = 0.0, onu = 0.0;
+  int ns = 0;
+  species_setup(*p, ms, ns, mtot, onu);
+  if (!(p->flags & PM_RELATIVISTIC)) {
+    const double om = p->omega_cdm + onu;
+    return sqrt(om / (a * a * a) + (1.0 - om));
+  }
+  // species weights m_s / M_nu over the massive species
+  double w[3] = {0, 0, 0}, m[3] = {0, 0, 0}, wsum = 0.0;
+  int k = 0;
+  for (int i = 0; i < ns; ++i) wsum += ms[i];
+  for (int i = 0; i < ns; ++i)
+    if (ms[i] > 0) {
+      m[k] = ms[i];
+      w[k] = ms[i] / wsum;
+      ++k;
+    }
+  RelBackground B{};
+  fill_background(*p, m, w, k, onu, n_massive_of(ms, ns, onu), B);
+  return sqrt(rel_e2(a, B));
 }
 
 int pm_get_bins(pm_ctx* c, double* count, double* ksum, double* psum) {

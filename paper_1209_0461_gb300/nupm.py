@@ -22,11 +22,11 @@ ERRORS = {-1: "PM_ERR_INVALID", -2: "PM_ERR_RANGE", -3: "PM_ERR_OVERFLOW", -4: "
           -5: "PM_ERR_ALLOC", -6: "PM_ERR_TIMEOUT", -7: "PM_ERR_ORDER", -8: "PM_ERR_UNSUPPORTED"}
 PM_FP64, PM_FP32 = 0, 1
 PM_I_FIT, PM_DECONV_CIC, PM_KEEP_DEPOSIT, PM_UNFUSED_DEPOSIT = 0x1, 0x2, 0x4, 0x8
-PM_TMA_COLUMNS, PM_FUSED_GATHER, PM_SPECTRAL_GRADIENT = 0x10, 0x20, 0x40
+PM_TMA_COLUMNS, PM_FUSED_GATHER, PM_SPECTRAL_GRADIENT, PM_RELATIVISTIC = 0x10, 0x20, 0x40, 0x80
 FIELD_DEPOSIT, FIELD_DELTA_K, FIELD_ACC_X, FIELD_ACC_Y, FIELD_ACC_Z, FIELD_PHI = range(6)
 MLP_FEATURES, MLP_WIDTH = 12, 128
 STAGES = ["deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_fwd", "bins", "response", "green",
-          "fft_z_inv", "fft_y_inv", "fft_x_inv", "interp"]
+          "fft_z_inv", "fft_y_inv", "fft_x_inv", "interp", "drift"]
 
 
 class PmParams(C.Structure):
@@ -68,6 +68,11 @@ def lib():
         "pm_last_error": (C.c_char_p, [vp]),
         "pm_kick_factor": (d, [vp, d, d]),
         "pm_drift_factor": (d, [vp, d, d]),
+        "pm_hubble": (d, [C.POINTER(PmParams), d]),
+        "pm_drift": (C.c_int, [vp, vp, vp, d]),
+        "pm_history_set": (C.c_int, [vp, dp, vp, i32, vp]),
+        "pm_history_get": (C.c_int, [vp, dp, vp, vp, C.POINTER(C.c_int32)]),
+        "pm_step": (C.c_int, [vp, vp, vp, d, d, d, vp]),
         "pm_get_bins": (C.c_int, [vp, dp, dp, dp]),
         "pm_get_thresholds": (C.c_int, [vp, C.POINTER(C.c_int64)]),
         "pm_copy_field": (C.c_int, [vp, i32, vp]),
@@ -115,6 +120,19 @@ def _dptr(arr):
 
 def _tptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def hubble(a, omega_cdm, omega_nu=-1.0, h=0.7, m_nu_total=0.0, n_species=3, m_nu=None, flags=0):
+    """pm_hubble: H(a)/H0 of a problem statement's background, host only."""
+    L = lib()
+    p = PmParams()
+    L.pm_default_params(C.byref(p))
+    p.omega_cdm, p.omega_nu, p.h = float(omega_cdm), float(omega_nu), float(h)
+    p.m_nu_total_eV, p.n_species = float(m_nu_total), int(n_species)
+    for i, m in enumerate(m_nu or ()):
+        p.m_nu_eV[i] = float(m)
+    p.flags = int(flags)
+    return float(L.pm_hubble(C.byref(p), float(a)))
 
 
 def bin_power_static(spec, ngrid, box, n_kbins, count=None, ksum=None, psum=None, stream=None):
@@ -242,6 +260,48 @@ class PM:
 
     def check(self):
         self._ok(lib().pm_check(self.ctx), "pm_check")
+
+    # -- the step loop (Sec. 4.3)
+    def _check_vel(self, *ts):
+        n = self.params.npart
+        for t in ts:
+            if t is not None and (t.dtype != self.dtype or tuple(t.shape) != (3, n) or not t.is_cuda
+                                  or not t.is_contiguous()):
+                raise ValueError(f"velocities / accelerations: contiguous CUDA {self.dtype} [3, npart]")
+
+    def drift(self, pos, vel, drift_factor):
+        """pm_drift: positions moved by vel * drift_factor, in place."""
+        self._check_pos(pos)
+        self._check_vel(vel)
+        self._ok(lib().pm_drift(self.ctx, _tptr(pos), _tptr(vel), float(drift_factor)), "pm_drift")
+
+    def history_set(self, a_hist, sqrtPM_hist, sqrtPnu_prev=None):
+        """pm_history_set: the context's stored history (host a_hist [n], CUDA
+        float64 [n, n_kbins]) and optional previous P_nu^{1/2} (CUDA [n_kbins])."""
+        ah, n = self._history(a_hist, sqrtPM_hist)
+        self._ok(lib().pm_history_set(self.ctx, _dptr(ah) if n else None, _tptr(sqrtPM_hist) if n else None, n,
+                                      _tptr(sqrtPnu_prev)), "pm_history_set")
+
+    def history_get(self):
+        """(a_hist numpy [n], sqrtPM_hist CUDA float64 [n, n_kbins], sqrtPnu_prev CUDA [n_kbins] or None)."""
+        import torch
+        cnt = C.c_int32()
+        self._ok(lib().pm_history_get(self.ctx, None, None, None, C.byref(cnt)), "pm_history_get")
+        n = cnt.value
+        ah = np.zeros(max(n, 1))
+        rows = torch.zeros((max(n, 1), self.nk), dtype=torch.float64, device="cuda")
+        prev = torch.full((self.nk,), float("nan"), dtype=torch.float64, device="cuda")
+        self._ok(lib().pm_history_get(self.ctx, _dptr(ah), _tptr(rows), _tptr(prev), C.byref(cnt)), "pm_history_get")
+        self.stream.synchronize()
+        return ah[:n], rows[:n], (None if bool(torch.isnan(prev).all()) else prev)
+
+    def step(self, pos, vel, a, kick_factor, drift_factor, acc_out=None):
+        """pm_step: one Sec. 4.3 time step at a (deposit, response over the stored
+        history, kick, store P_M, drift)."""
+        self._check_pos(pos)
+        self._check_vel(vel, acc_out)
+        self._ok(lib().pm_step(self.ctx, _tptr(pos), _tptr(vel), float(a), float(kick_factor), float(drift_factor),
+                               _tptr(acc_out)), "pm_step")
 
     def _history(self, a_hist, sqrtPM_hist):
         import torch

@@ -32,7 +32,7 @@ def test_params_struct_layout(L):
 @pytest.mark.parametrize("field,value,code", [
     ("ngrid", 17, -8), ("ngrid", 2048, -8), ("npart", 0, -1), ("box", -1.0, -1),
     ("omega_cdm", 0.0, -1), ("a_init", 0.0, -2), ("n_kbins", 0, -1), ("iters", 0, -1),
-    ("quad_nodes", 1, -1), ("precision", 7, -1), ("m_nu_total_eV", -0.1, -2), ("flags", 0x80, -1),
+    ("quad_nodes", 1, -1), ("precision", 7, -1), ("m_nu_total_eV", -0.1, -2), ("flags", 0x100, -1),
 ])
 def test_host_validation_without_gpu(L, field, value, code):
     p = nupm.PmParams()
@@ -64,3 +64,22 @@ def test_surrogate_entry_points_validate_without_gpu(L):
     assert L.pm_set_power(None, None, None, None) == -1
     assert L.pm_response_features(None, 0.1, None, None, 0, None) == -1
     assert L.pm_nu_response_mlp(None, None, 0.1, None, None, 0, None, None, None) == -1
+
+
+@pytest.mark.parametrize("masses", [(0.1, 0.1, 0.1), (0.022, 0.024, 0.054), (0.06,), ()])
+def test_host_background_against_the_oracle(L, masses):
+    # pm_hubble (host only, no GPU): matter + Lambda, and the Sec. 4.4
+    # background of Eq. relativistic with radiation, against the oracle's
+    # H(a) (its own quadrature of the Fermi-Dirac energy density)
+    from oracle import pm_oracle as O
+    from paper_1209_0461_gb300 import nupm
+    h, om = 0.7, 0.3
+    tot = sum(masses)
+    onu = tot / (93.14 * h * h)
+    for rel in (False, True):
+        cos = O.Cosmo(om - onu, onu, h, tuple(masses), 0.02, relativistic=rel)
+        for a in (1e-6, 1e-3, 0.02, 0.1, 0.5, 1.0, 2.0):
+            got = nupm.hubble(a, om - onu, -1.0, h, tot, len(masses), list(masses),
+                              flags=nupm.PM_RELATIVISTIC if rel else 0)
+            want = float(O.hubble(a, cos))
+            assert abs(got / want - 1) < (1e-15 if not rel else 2e-12), (rel, a, got, want)
