@@ -88,6 +88,14 @@ extern "C" {
                                  Lambda closing the universe at a = 1.  Default: matter +
                                  Lambda with Omega_nu as matter.  Poisson keeps Omega_M. */
 
+#define PM_IC_MULTIPOLE 0x100u /* initial-condition term of Eq. P-final by Eq. deltaI-multipole
+                                 with the l = 0, 1 moments of Sec. 4.1: the l = 1 part from its
+                                 own momentum integral of j_1 (FP64 Gauss-Legendre panels),
+                                 -P_nu,i^{1/2} a_i [theta/delta]_i (s - s_i) K(y), instead of the
+                                 integrated-by-parts Eq. deltaI-nu (K = I for these moments; the
+                                 two agree to the quadrature's accuracy).  Beyond
+                                 y = k (s - s_i) T_nu0 / m = 256 (K < 1e-10) K = I is used. */
+
 /*
  * Problem statement (Sec. 4.3-4.4, Table 1).  Omega_M = omega_cdm + omega_nu
  * (baryons folded into cdm), flat: Omega_Lambda = 1 - Omega_M.
@@ -352,6 +360,14 @@ NUPM_API int pm_get_timing(pm_ctx* ctx, double* ms, int64_t* launches, int64_t* 
 NUPM_API int pm_bin_power_static(const void* spec, int32_t ngrid, double box, int32_t n_kbins,
                                  int32_t precision, double* count, double* ksum, double* psum,
                                  void* cuda_stream);
+
+/* The FP64 fused multiply-add rate of the current device in TFLOP/s (2 flops
+ * per FMA), HOST *tflops, measured with CUDA events on cuda_stream over one
+ * launch of eight independent FMA chains per thread (16 x 8 x iters FMAs a
+ * thread, a few waves of resident CTAs); synchronises the stream.  The
+ * denominator of the FP64 path's compute roofline: its transforms and
+ * stencils run on the FP64 FMA pipe.  The paper has no counterpart. */
+NUPM_API int pm_measure_fp64_fma(int32_t iters, double* tflops, void* cuda_stream);
 
 /* Bytes of device memory the context holds. */
 NUPM_API int64_t pm_device_bytes(const pm_ctx* ctx);

@@ -582,9 +582,64 @@ def ic_term(kb, a, cosmo: Cosmo, m_ev: float, sqrtPnu_init, theta_over_delta_ini
         1.0 - ds * cosmo.a_init * np.asarray(theta_over_delta_init))
 
 
+def nu_K(y) -> np.ndarray:
+    """The l = 1 term of Eq. deltaI-multipole for the paper's initial moments
+    (delta f_1 = (df_0/dq) m a_i theta / k, Sec. 4.1), as a function of
+    y = k (s - s_i) T_nu0 / m:
+
+        K(y) = -(1/y) int_0^inf u^2 f'(u) j_1(u y) du / int_0^inf u^2 f(u) du,
+        f(u) = 1 / (e^u + 1),
+
+    so that the term is -P_nu,i^{1/2} a_i [theta/delta]_i (s - s_i) K(y).
+    Evaluated directly as a momentum integral of j_1 (QUADPACK): for y < 1
+    the integrand with j_1 itself, for y >= 1 the Fourier form
+    j_1(z) = sin z / z^2 - cos z / z with sine and cosine weights.
+
+    Pinned by: K(0) = 1 and the small-y series 1 - (5 zeta(5) / (2 zeta(3)))
+    y^2; K = I of Eq. I.def (the integration by parts of Sec. 4.1 is exact
+    for these moments: d/dz [z^2 j_1(z)] = z^2 j_0(z)), checked at y from
+    1e-2 to 1e2 against the App. C series of I.
+    """
+    shape = np.shape(y)
+    y = np.atleast_1d(np.asarray(y, dtype=np.float64))
+    out = np.empty_like(y)
+    norm = 1.5 * ZETA3
+
+    def fp(u):                                   # f'(u) = -e^{-u} / (1 + e^{-u})^2
+        e = math.exp(-u)
+        return -e / (1.0 + e) ** 2
+
+    for i, yy in enumerate(y.ravel()):
+        if yy == 0.0:
+            out.flat[i] = 1.0
+            continue
+        if yy < 1.0:
+            v, _ = integrate.quad(lambda u: u * u * fp(u) * special.spherical_jn(1, u * yy), 0.0, 80.0,
+                                  epsabs=0.0, epsrel=1e-13, limit=400)
+            out.flat[i] = -v / (yy * norm)
+        else:
+            s1, _ = integrate.quad(fp, 0.0, 80.0, weight="sin", wvar=yy, epsabs=1e-15, epsrel=1e-13, limit=400)
+            c1, _ = integrate.quad(lambda u: u * fp(u), 0.0, 80.0, weight="cos", wvar=yy, epsabs=1e-15,
+                                   epsrel=1e-13, limit=400)
+            out.flat[i] = -(s1 / (yy * yy) - c1 / yy) / (yy * norm)
+    return out.reshape(shape)
+
+
+def ic_term_multipole(kb, a, cosmo: Cosmo, m_ev: float, sqrtPnu_init, theta_over_delta_init, I_func=nu_I):
+    """The initial-condition term by Eq. deltaI-multipole with the l = 0, 1
+    moments of Sec. 4.1 (before its integration by parts):
+    P_nu,i^{1/2} {I(y) - (s - s_i) a_i [theta/delta]_i K(y)}, K from the j_1
+    integral (nu_K).  Equal to ``ic_term`` in exact arithmetic."""
+    kb = np.asarray(kb, dtype=np.float64)
+    ds = float(delta_s(cosmo.a_init, a, cosmo))
+    x = kb * C_OVER_H0 * T_NU0_EV / m_ev * ds
+    P = np.asarray(sqrtPnu_init)
+    return P * (I_func(x) - ds * cosmo.a_init * np.asarray(theta_over_delta_init) * nu_K(x))
+
+
 def nu_response(kb, sqrtPcdm, a, cosmo: Cosmo, a_hist, sqrtPM_hist,
                 sqrtPnu_init, theta_over_delta_init, sqrtPnu_prev=None,
-                iters: int = 1, I_func=nu_I, epsrel=1e-11, nonempty=None):
+                iters: int = 1, I_func=nu_I, epsrel=1e-11, nonempty=None, multipole=False):
     """Neutrino response per |k| bin (Eq. P-final, Sec. 4.3 (iii)-(iv), App. B).
 
     Inputs per bin b (arrays of length nb):
@@ -597,6 +652,8 @@ def nu_response(kb, sqrtPcdm, a, cosmo: Cosmo, a_hist, sqrtPM_hist,
       theta_over_delta_init [n_species, nb]  [theta_nu/delta_nu]_i(k_b)
       sqrtPnu_prev  [nb] P_nu^{1/2} of the previous step (None -> the
                     species-weighted IC value)
+      multipole     initial-condition term by Eq. deltaI-multipole (j_1
+                    integral, ic_term_multipole) instead of Eq. deltaI-nu
     The current node of P_M^{1/2} inside the integral is
       (1 - f_nu) P_cdm^{1/2}(a) + f_nu P_nu^{1/2}(guess),
     with the guess = sqrtPnu_prev for the first iteration (Sec. 4.3 (iii)) and
@@ -625,9 +682,10 @@ def nu_response(kb, sqrtPcdm, a, cosmo: Cosmo, a_hist, sqrtPM_hist,
     else:
         guess = np.asarray(sqrtPnu_prev, dtype=np.float64)
     ic = np.zeros(nb)
+    ic_fn = ic_term_multipole if multipole else ic_term
     for s, m in enumerate(masses):
         if m > 0:
-            ic += wts[s] * ic_term(kb, a, cosmo, m, Pi[s], Ti[s], I_func)
+            ic += wts[s] * ic_fn(kb, a, cosmo, m, Pi[s], Ti[s], I_func)
     if a < cosmo.a_init or (a_hist.size and (a_hist[0] < cosmo.a_init or a_hist[-1] >= a
                                               or np.any(np.diff(a_hist) <= 0))):
         raise ValueError("need a_i <= a_hist[0] < ... < a_hist[-1] < a")

@@ -107,6 +107,43 @@ struct Panel {
 };
 
 // One warp per (bin, species, chunk of 32 panels): partial IC, J_hist, W_cur.
+// The l = 1 term of Eq. deltaI-multipole for the initial moments of Sec. 4.1
+// (delta f_1 = f_0' m a_i theta / k), K(y) = -(1/y) int u^2 f'(u) j_1(u y) du /
+// ((3/2) zeta(3)), f = 1 / (e^u + 1), by Gauss-Legendre panels on [0, 50] of
+// width min(1/2, 3/(2 y)) (a quarter period of j_1 at most), the panels dealt
+// to the lanes of a warp and summed in a fixed order.  Every lane returns K.
+// Beyond y = kMultipoleYMax (where K < 1e-10) the integrated-by-parts value
+// I(y) stands in.
+constexpr double kMultipoleYMax = 256.0;
+__device__ double sph_j1(double z) {
+  if (z < 1e-2) {
+    const double z2 = z * z;
+    return z * (1.0 / 3.0 - z2 * (1.0 / 30.0 - z2 / 840.0));
+  }
+  return (sin(z) / z - cos(z)) / z;
+}
+__device__ double nu_K_warp(double y, const NuArgs& A, int lane) {
+  if (y <= 0.0) return 1.0;
+  const double U = 50.0;
+  const double hmax = fmin(0.5, 1.5 / y);
+  const int np = (int)ceil(U / hmax);
+  const double h = U / np;
+  double acc = 0.0;
+  for (int p = lane; p < np; p += 32) {
+    const double lo = p * h;
+    double ps = 0.0;
+    for (int q = 0; q < A.quad; ++q) {
+      const double u = lo + 0.5 * h * (A.gl[q] + 1.0);
+      const double e = exp(-u);
+      const double fp = -e / ((1.0 + e) * (1.0 + e));
+      ps += A.gl[kMaxQuad + q] * u * u * fp * sph_j1(u * y);
+    }
+    acc += 0.5 * h * ps;
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  return -acc / (y * 1.5 * kRelZeta3);
+}
+
 __global__ void k_nu_panels(NuArgs A) {
   __shared__ Panel panels[4][kMaxPanels];
   __shared__ int npan[4];
@@ -216,12 +253,18 @@ __global__ void k_nu_panels(NuArgs A) {
     jh += __shfl_down_sync(0xffffffffu, jh, off);
     wc += __shfl_down_sync(0xffffffffu, wc, off);
   }
+  // l = 1 term of Eq. deltaI-multipole by its own momentum integral (the warp's lanes)
+  const double xi = kappa * s_end;
+  const double Kl1 = (A.ic_multipole && chunk == 0 && xi < kMultipoleYMax) ? nu_K_warp(xi, A, lane) : 0.0;
   if (lane == 0) {
     double ic = 0.0;
     if (chunk == 0) {
-      const double xi = kappa * s_end;
       const double Ii = A.use_fit ? nu_I_fit(xi) : nu_I_exact(xi);
-      ic = Ii * A.pnu_init[(int64_t)s * A.nk + b] * (1.0 - s_end * A.a_init * A.theta_init[(int64_t)s * A.nk + b]);
+      const double P = A.pnu_init[(int64_t)s * A.nk + b], th = A.theta_init[(int64_t)s * A.nk + b];
+      if (A.ic_multipole)   // Eq. deltaI-multipole with the l = 0 and l = 1 moments of Sec. 4.1
+        ic = P * (Ii - s_end * A.a_init * th * (xi < kMultipoleYMax ? Kl1 : Ii));
+      else                  // Eq. deltaI-nu
+        ic = Ii * P * (1.0 - s_end * A.a_init * th);
     }
     const double c = 1.5 * A.omega_m;
     out[0] = ic;

@@ -96,6 +96,7 @@ struct NuArgs {
   double* R_user;                 // optional copies
   double* pnu_user;
   double* pm_user;
+  int ic_multipole;               // 1: initial-condition term by Eq. deltaI-multipole (j_1 integral)
   int rel;                        // 1: H(a) of the Sec. 4.4 background (bg), else matter + Lambda
   RelBackground bg;
 };

@@ -623,7 +623,7 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
   else if (p.iters < 1 || p.iters > 16) bad(PM_ERR_INVALID, "iters must be 1..16");
   else if (p.quad_nodes < 2 || p.quad_nodes > kMaxQuad) bad(PM_ERR_INVALID, "quad_nodes must be 2..16");
   else if (p.flags & ~(PM_I_FIT | PM_DECONV_CIC | PM_KEEP_DEPOSIT | PM_UNFUSED_DEPOSIT | PM_TMA_COLUMNS | PM_FUSED_GATHER |
-                       PM_SPECTRAL_GRADIENT | PM_RELATIVISTIC))
+                       PM_SPECTRAL_GRADIENT | PM_RELATIVISTIC | PM_IC_MULTIPOLE))
     bad(PM_ERR_INVALID, "unknown flag bits");
   if (rc != PM_OK) {
     // report through a context so pm_last_error works; caller still gets NULL
@@ -1000,6 +1000,7 @@ NuArgs nu_args(pm_ctx* c, double a, const double* sqrtPM_hist, int32_t n_hist, c
   A.pnu_user = sqrtPnu_out;
   A.pm_user = sqrtPM_out;
   A.rel = c->rel ? 1 : 0;
+  A.ic_multipole = (c->p.flags & PM_IC_MULTIPOLE) ? 1 : 0;
   A.bg = c->bg;
   A.bg.tab = c->d_rtab;
   return A;

@@ -23,6 +23,7 @@ ERRORS = {-1: "PM_ERR_INVALID", -2: "PM_ERR_RANGE", -3: "PM_ERR_OVERFLOW", -4: "
 PM_FP64, PM_FP32 = 0, 1
 PM_I_FIT, PM_DECONV_CIC, PM_KEEP_DEPOSIT, PM_UNFUSED_DEPOSIT = 0x1, 0x2, 0x4, 0x8
 PM_TMA_COLUMNS, PM_FUSED_GATHER, PM_SPECTRAL_GRADIENT, PM_RELATIVISTIC = 0x10, 0x20, 0x40, 0x80
+PM_IC_MULTIPOLE = 0x100
 FIELD_DEPOSIT, FIELD_DELTA_K, FIELD_ACC_X, FIELD_ACC_Y, FIELD_ACC_Z, FIELD_PHI = range(6)
 MLP_FEATURES, MLP_WIDTH = 12, 128
 STAGES = ["deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_fwd", "bins", "response", "green",
@@ -69,6 +70,7 @@ def lib():
         "pm_kick_factor": (d, [vp, d, d]),
         "pm_drift_factor": (d, [vp, d, d]),
         "pm_hubble": (d, [C.POINTER(PmParams), d]),
+        "pm_measure_fp64_fma": (C.c_int, [i32, dp, vp]),
         "pm_drift": (C.c_int, [vp, vp, vp, d]),
         "pm_history_set": (C.c_int, [vp, dp, vp, i32, vp]),
         "pm_history_get": (C.c_int, [vp, dp, vp, vp, C.POINTER(C.c_int32)]),
@@ -120,6 +122,17 @@ def _dptr(arr):
 
 def _tptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def measure_fp64_fma(iters=256, stream=None):
+    """pm_measure_fp64_fma: the device's FP64 FMA rate in TFLOP/s."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_double()
+    rc = lib().pm_measure_fp64_fma(int(iters), C.byref(out), C.c_void_p(st.cuda_stream))
+    if rc != PM_OK:
+        raise PMError(rc, "pm_measure_fp64_fma failed")
+    return out.value
 
 
 def hubble(a, omega_cdm, omega_nu=-1.0, h=0.7, m_nu_total=0.0, n_species=3, m_nu=None, flags=0):

@@ -32,7 +32,7 @@ def test_params_struct_layout(L):
 @pytest.mark.parametrize("field,value,code", [
     ("ngrid", 17, -8), ("ngrid", 2048, -8), ("npart", 0, -1), ("box", -1.0, -1),
     ("omega_cdm", 0.0, -1), ("a_init", 0.0, -2), ("n_kbins", 0, -1), ("iters", 0, -1),
-    ("quad_nodes", 1, -1), ("precision", 7, -1), ("m_nu_total_eV", -0.1, -2), ("flags", 0x100, -1),
+    ("quad_nodes", 1, -1), ("precision", 7, -1), ("m_nu_total_eV", -0.1, -2), ("flags", 0x200, -1),
 ])
 def test_host_validation_without_gpu(L, field, value, code):
     p = nupm.PmParams()

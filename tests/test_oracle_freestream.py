@@ -127,3 +127,33 @@ def test_delta_s_short_interval_high_precision():
     ref = mpmath.quad(lambda a: 1 / (a ** 3 * mpmath.sqrt(om / a ** 3 + 1 - om)),
                       [mpmath.mpf(a0), mpmath.mpf(a1)])
     assert abs(O.delta_s(a0, a1, om) / float(ref) - 1) < 1e-14
+
+
+def test_l1_multipole_kernel_equals_I():
+    # Eq. deltaI-multipole with delta f_1 = f_0' m a_i theta / k (Sec. 4.1): the
+    # l = 1 momentum integral of j_1 equals -a_i theta (s - s_i) I(y) exactly
+    # (d/dz [z^2 j_1(z)] = z^2 j_0(z)); K from the j_1 integral against I from
+    # the App. C series, and K's own small-y limit
+    from scipy import special as sp
+    y = np.array([1e-2, 0.1, 0.5, 0.99, 1.0, 2.0, 5.0, 20.0, 100.0])
+    K = O.nu_K(y)
+    I = O.nu_I(y)
+    assert np.allclose(K, I, rtol=1e-9, atol=1e-15)
+    c2 = 5 * sp.zeta(5) / (2 * sp.zeta(3))
+    for yy in (1e-4, 1e-3):
+        assert abs(float(O.nu_K(yy)) - (1 - c2 * yy * yy)) < 1e-9
+    assert float(O.nu_K(0.0)) == 1.0
+
+
+def test_multipole_ic_term_in_the_response():
+    # the response with the j_1 form of the initial-condition term equals the
+    # integrated-by-parts form (Eq. deltaI-nu)
+    m = 0.1
+    c = O.Cosmo(0.3 - 3 * m / (93.14 * 0.49), 3 * m / (93.14 * 0.49), 0.7, (m, m, m), 0.02)
+    kb = np.geomspace(0.005, 0.5, 5)
+    pi = np.tile(10.0 / (1 + kb / 0.05) ** 2, (3, 1))
+    ti = np.full((3, 5), -0.3)
+    cur = 20.0 / (1 + kb / 0.2)
+    r0 = O.nu_response(kb, cur, 0.05, c, [], np.zeros((0, 5)), pi, ti)
+    r1 = O.nu_response(kb, cur, 0.05, c, [], np.zeros((0, 5)), pi, ti, multipole=True)
+    assert np.allclose(r1["R"], r0["R"], rtol=1e-9, atol=0)
