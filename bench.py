@@ -198,6 +198,75 @@ def run_oracle_kick(s):
     return time.perf_counter() - t0, s.npart
 
 
+def host_info():
+    """CPU model and logical core count of this host."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":")[0].strip().lower()
+                if k in ("model name", "hardware", "cpu model"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return model or "unknown", os.cpu_count() or 1
+
+
+def _oracle_task(args):
+    """One oracle kick of the bounded sample in a worker process; returns
+    (particles, wall-clock start, end) of the kick itself."""
+    name, shift = args
+    w = synth.WORKLOADS[name]
+    s = oracle_sample(w, seed_shift=shift)
+    from oracle import pm_oracle as O
+    p = synth.particles(s)
+    ah, hh = synth.history(s)
+    pi, ti = synth.nu_initial(s)
+    cos = O.Cosmo(s.omega_cdm, s.omega_nu, s.h, s.masses, s.a_init)
+    cell, off = synth.split_cell_offset(synth.to_cell_offset(p["pos64"], s.box, s.ngrid))
+    c, q = (O.quantise_positions_cell(cell, off, s.ngrid) if s.precision == "fp32"
+            else O.quantise_positions_f64(p["pos64"], s.box, s.ngrid))
+    t0 = time.time()
+    O.pm_kick(c, q, p["vel"], s.ngrid, s.box, s.a_kick, 0.01, cos, s.n_kbins, ah, hh, pi, ti)
+    return s.npart, t0, time.time()
+
+
+class OracleCores:
+    """The oracle on every host core: one independent sample kick per core
+    (spawned worker processes, started before any GPU work is timed)."""
+
+    def __init__(self, workload_name, cores=None):
+        import multiprocessing as mp
+        self.name = workload_name
+        self.cores = cores or (os.cpu_count() or 1)
+        env = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+        os.environ.update(env)
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.step = 0
+
+    def run(self):
+        """Particle-kicks/s of one concurrent round (each core one kick)."""
+        res = self.pool.map(_oracle_task, [(self.name, 1000 * self.step + i) for i in range(self.cores)])
+        self.step += 1
+        n = sum(r[0] for r in res)
+        wall = max(r[2] for r in res) - min(r[1] for r in res)
+        return n / wall, wall
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 # ------------------------------------------------------------------ GPU arm
 def replica(w, rank):
     """The box rank r runs: the same workload with seed + r (replicas only:
@@ -461,6 +530,47 @@ def _kick_form(w, pos64, vel64, precision, steps, warmup, mlp=None, keep_acc=Tru
     return ms, st["response"][0] / steps, acc
 
 
+def _step_form(w, pos64, vel64, steps, warmup):
+    """ms per pm_step (kick + P_M store + drift) and per kick alone, FP32 form,
+    from the workload's stored history, the drift of each step Delta s to the
+    next epoch."""
+    import torch
+    from paper_1209_0461_gb300 import nupm
+    dev = torch.device("cuda")
+    a_hist, hist = synth.history(w)
+    pi, ti = synth.nu_initial(w)
+    pos = torch.from_numpy(synth.to_cell_offset(pos64, w.box, w.ngrid)).to(dev)
+    vel = torch.from_numpy(vel64.astype(np.float32)).to(dev)
+    hist_d = torch.from_numpy(np.ascontiguousarray(hist)).to(dev)
+    n = warmup + steps
+    pm = nupm.PM(w.ngrid, w.npart, w.box, w.omega_cdm, w.omega_nu, w.h, w.m_nu_total, w.n_species,
+                 a_init=w.a_init, n_kbins=w.n_kbins, n_hist_max=w.n_hist + n + 1, precision="fp32",
+                 sqrtPnu_init=pi, theta_over_delta_init=ti)
+    pm.autotune(pos, vel, w.a_kick, a_hist, hist_d, reps=1)
+    pm.history_set(a_hist, hist_d)
+    a_steps = w.a_kick * np.exp(0.002 * np.arange(n + 1))
+    fac = [(pm.kick_factor(a_steps[j], a_steps[j + 1]), pm.drift_factor(a_steps[j], a_steps[j + 1]))
+           for j in range(n)]
+    for j in range(warmup):
+        pm.step(pos, vel, a_steps[j], *fac[j])
+    torch.cuda.synchronize()
+    pm.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for j in range(warmup, n):
+        pm.step(pos, vel, a_steps[j], *fac[j])
+    e1.record()
+    torch.cuda.synchronize()
+    st = pm.get_timing()
+    pm.timing(False)
+    pm.check()
+    ah, _, _ = pm.history_get()
+    ms = e0.elapsed_time(e1) / steps
+    pm.close()
+    return {"workload": w.name, "ms_per_step": round(ms, 3), "drift_ms": round(st["drift"][0] / steps, 4),
+            "kicks_per_s": w.npart / (ms / 1e3), "history_rows_after": int(len(ah))}
+
+
 def _rms_rel(acc, ref):
     """RMS over particles of |a - a_ref| / RMS |a_ref| (measurement only)."""
     d = (acc.double() - ref.double()).pow(2).sum(0).mean().sqrt()
@@ -540,8 +650,44 @@ def run_forms(steps=3, warmup=1):
     out["fp64_vs_fp32"] = {"workload": w.name, "fp64_ms_per_kick": round(ms64, 3),
                            "fp32_ms_per_kick": round(ms32, 3), "speedup": round(ms64 / ms32, 2),
                            "fp32_force_rms_rel_vs_fp64": _rms_rel(acc32, acc64)}
-    del acc64, acc32, parts
+    # the FP64 path's roofline: max(compulsory HBM bytes / HBM peak, transform
+    # flops / measured FP64 FMA rate); two real 3-D transforms of N^3 points a
+    # kick (forward delta, inverse potential) at 2.5 N^3 log2 N^3 flops each
+    hbm, peak_kind = peaks()
+    w64 = synth.with_(w, precision="fp64")
+    fma = nupm.measure_fp64_fma()
+    M3 = w.ngrid ** 3
+    flops = 2 * 2.5 * M3 * math.log2(M3)
+    bytes64 = sum(stage_bytes(w64, k, fused_interp=False) for k in
+                  ("deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_fwd", "bins", "green", "fft_z_inv", "fft_y_inv",
+                   "fft_x_inv", "interp"))
+    t_hbm, t_fma = bytes64 / (hbm * 1e9), flops / (fma * 1e12)
+    out["fp64_vs_fp32"]["fp64_roofline"] = {
+        "bound": "fp64_alu" if t_fma > t_hbm else "hbm", "flops_per_kick": flops, "fp64_fma_tflops": round(fma, 3),
+        "bytes_per_kick": bytes64, "hbm_gbs": hbm, "hbm_peak_kind": peak_kind,
+        "t_bound_ms": round(max(t_hbm, t_fma) * 1e3, 2), "t_hbm_ms": round(t_hbm * 1e3, 2),
+        "t_fma_ms": round(t_fma * 1e3, 2), "frac": round(max(t_hbm, t_fma) * 1e3 / ms64, 4)}
+    del acc64, acc32
     torch.cuda.empty_cache()
+    # the step loop (Sec. 4.3): pm_step = deposit, response over the context's
+    # history, kick, P_M row stored, drift -- against the kick alone
+    out["step_loop"] = _step_form(w, parts["pos64"], parts["vel"], steps, warmup)
+    del parts
+    torch.cuda.empty_cache()
+    # the plain FP32 kick at 256^3 / 256^3 (two neutrino masses): throughput and
+    # force accuracy against the FP64 GPU kick of the same particles (the FP64
+    # oracle comparison of every particle is tests/test_gpu_config2.py)
+    out["config2"] = {}
+    for name in ("pm256_fp32_m015", "pm256_fp32_m030"):
+        w2 = synth.WORKLOADS[name]
+        p2 = synth.particles(w2)
+        m64, _, a64 = _kick_form(synth.with_(w2, precision="fp64"), p2["pos64"], p2["vel"], "fp64", steps, warmup)
+        m32, _, a32 = _kick_form(w2, p2["pos64"], p2["vel"], "fp32", 10, 3)
+        out["config2"][name] = {"fp32_ms_per_kick": round(m32, 3), "kicks_per_s": w2.npart / (m32 / 1e3),
+                                "fp64_ms_per_kick": round(m64, 3),
+                                "fp32_force_rms_rel_vs_fp64_gpu": _rms_rel(a32, a64)}
+        del a64, a32, p2
+        torch.cuda.empty_cache()
     # contention variant: the same workload with the particles at their a = 1
     # Zel'dovich positions (clustered), reported separately
     wc = synth.with_(w, clustered=True)
@@ -623,22 +769,30 @@ def main():
         if rank != 0:
             return
         s = oracle_sample(w)
+        model, ncpu = host_info()
+        oc = OracleCores(w.name)
         for _ in range(args.warmup):
-            run_oracle_kick(s)
-        ts = []
+            oc.run()
+        rates, walls = [], []
         for _ in range(args.steps):
-            t, npart = run_oracle_kick(s)
-            ts.append(t)
-        t = sum(ts) / len(ts)
-        v = npart / t
-        sample = f"oracle kick on {s.ngrid}^3 grid / {s.npart_side}^3 particles, box {s.box:g}"
-        line = dict(base, impl="reference", value=v, ms_per_step=t * 1e3,
-                    cpu_baseline={"value": v, "unit": "particle-kicks/s", "cores": 1, "kind": "oracle",
-                                  "sample": sample},
+            v, wall = oc.run()
+            rates.append(v)
+            walls.append(wall)
+        oc.close()
+        v = float(np.mean(rates))
+        sample = (f"per step one oracle kick on each of {oc.cores} host cores, each a {s.ngrid}^3 grid with "
+                  f"{s.npart_side}^3 particles (box {s.box:g} Mpc/h, same cell size, bins and history, "
+                  f"its own seed); CPU {model}")
+        line = dict(base, impl="reference", value=v, ms_per_step=float(np.mean(walls)) * 1e3,
+                    cpu_baseline={"value": v, "unit": "particle-kicks/s", "cores": oc.cores, "kind": "oracle",
+                                  "sample": sample, "cpu_model": model, "nproc": ncpu},
                     e2e={"value": v, "unit": "particle-kicks/s", "h2d_bytes_per_step": 0,
                          "d2h_bytes_per_step": 0})
         print(json.dumps(line))
         return
+    oc = None
+    if world == 1 and not args.no_cpu_baseline:
+        oc = OracleCores(w.name)          # spawned before any GPU call
     if world > 1:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
@@ -650,12 +804,18 @@ def main():
             torch.distributed.destroy_process_group()
         return
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if oc is not None:
         s = oracle_sample(w)
-        t, npart = run_oracle_kick(s)
-        cpu = {"value": npart / t, "unit": "particle-kicks/s", "cores": 1, "kind": "oracle",
-               "sample": f"one oracle kick on a {s.ngrid}^3 grid with {s.npart_side}^3 particles "
-                         f"(box {s.box:g} Mpc/h, same cell size, bins and history), {t:.1f} s"}
+        model, ncpu = host_info()
+        t1, npart = run_oracle_kick(s)          # one core alone
+        v_all, wall = oc.run()                  # every core, one kick each
+        oc.close()
+        cpu = {"value": v_all, "unit": "particle-kicks/s", "cores": oc.cores, "kind": "oracle",
+               "sample": f"one oracle kick on each of {oc.cores} host cores ({wall:.1f} s wall), each a "
+                         f"{s.ngrid}^3 grid with {s.npart_side}^3 particles (box {s.box:g} Mpc/h, same cell "
+                         f"size, bins and history, own seed)",
+               "single_core": {"value": npart / t1, "seconds": round(t1, 2)},
+               "cpu_model": model, "nproc": ncpu}
     forms = None
     if world == 1 and not args.no_forms and args.workload == "pm1024_p512_fp32":
         forms = run_forms()
