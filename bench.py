@@ -580,9 +580,11 @@ def _rms_rel(acc, ref):
 def run_batched(steps=10, warmup=3):
     """The batched form: 32 boxes (64^3 / 128^3 / 192^3, one particle per cell,
     seeds 0-31, M_nu in {0, 0.06, 0.15, 0.3, 0.6} eV) stepped by one CUDA-graph
-    launch after autotuning, against the same 32 kicks launched one after
-    another on one stream in FP32 and in FP64; force accuracy per box as the
-    RMS of the velocity change against the FP64 kick."""
+    launch -- of the persistent batched passes (one pm_batch per grid size), and
+    of the per-box launches on 8 streams after autotuning -- against the same
+    32 kicks launched one after another on one stream in FP32 and in FP64;
+    force accuracy per box as the RMS of the velocity change against the FP64
+    kick."""
     import torch
     from paper_1209_0461_gb300 import batch
     boxes = synth.batched_boxes(32)
@@ -599,15 +601,20 @@ def run_batched(steps=10, warmup=3):
 
     out = {"boxes": len(boxes), "particles": int(sum(w.npart for w in boxes))}
     dv = {}
-    for name, prec, streams, tune, graph in (("fp64_sequential", "fp64", 1, False, False),
-                                             ("fp32_sequential", "fp32", 1, False, False),
-                                             ("fp32_graph", "fp32", 8, True, True)):
-        b = batch.Batch(boxes, n_streams=streams, autotune=tune, precision=prec)
+    for name, prec, streams, tune, graph, pers in (("fp64_sequential", "fp64", 1, False, False, False),
+                                                   ("fp32_sequential", "fp32", 1, False, False, False),
+                                                   ("fp32_graph", "fp32", 8, True, True, False),
+                                                   ("fp32_persistent_graph", "fp32", 1, False, True, True)):
+        b = batch.Batch(boxes, n_streams=streams, autotune=tune, precision=prec, persistent=pers)
         if graph:
             b.capture()
             step = b.step
-            out["graph_nodes"] = b.graph.nodes()
-            out["tuning"] = {str(k): list(v) for k, v in b.tuning.items()}
+            if pers:
+                out["persistent_graph_nodes"] = b.graph.nodes()
+                out["persistent_launches_per_step"] = b.launches_per_step()
+            else:
+                out["graph_nodes"] = b.graph.nodes()
+                out["tuning"] = {str(k): list(v) for k, v in b.tuning.items()}
         else:
             step = b.eager_step
         b.reset_velocities()
@@ -622,7 +629,7 @@ def run_batched(steps=10, warmup=3):
         out[name] = {"ms_per_step": round(ms, 3), "kicks_per_s": b.npart / (ms / 1e3)}
         b.close()
         torch.cuda.empty_cache()
-    for name in ("fp32_sequential", "fp32_graph"):
+    for name in ("fp32_sequential", "fp32_graph", "fp32_persistent_graph"):
         errs = [float(((x - r).pow(2).sum(0).mean().sqrt() / r.pow(2).sum(0).mean().sqrt()).item())
                 for x, r in zip(dv[name], dv["fp64_sequential"])]
         out[name]["force_rms_rel_vs_fp64_max"] = max(errs)
@@ -630,6 +637,8 @@ def run_batched(steps=10, warmup=3):
                                                      out["fp32_graph"]["ms_per_step"], 2)
     out["graph_speedup_vs_fp64_sequential"] = round(out["fp64_sequential"]["ms_per_step"] /
                                                      out["fp32_graph"]["ms_per_step"], 2)
+    out["persistent_speedup_vs_per_box_graph"] = round(out["fp32_graph"]["ms_per_step"] /
+                                                        out["fp32_persistent_graph"]["ms_per_step"], 2)
     return out
 
 

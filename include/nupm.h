@@ -418,6 +418,46 @@ NUPM_API int pm_graph_launch(pm_graph* graph, void* cuda_stream);
 NUPM_API int64_t pm_graph_nodes(const pm_graph* graph);
 NUPM_API void pm_graph_free(pm_graph* graph);
 
+/* ---- batched kicks (the batched form) ----
+ * Boxes of ONE grid size stepped together: each pass of the kick (row count,
+ * row scan, row scatter, deposit + x, y, z, bin sums and their reduction,
+ * response panels, finish, bin list, fac table, Green plane, Green + z
+ * inverse, y inverse, x inverse, gather + kick) is one persistent kernel over
+ * all boxes, whose CTAs take (box, item) pairs -- particle chunks, row or
+ * column tiles, response panels -- from an atomic counter until the pass's
+ * work is done (no CTA waits on another).  Each box keeps its own context
+ * (its grids, cosmology, neutrino masses, initial conditions, bins); the
+ * batch only lists them.  A kick is pm_batch_launches(batch) kernel launches
+ * plus three copies/memsets whatever the number of boxes, so a CUDA graph of it
+ * (pm_graph_begin on the batch's stream) holds O(passes) nodes.  The paper
+ * has no counterpart (its code steps one box).
+ *   ctxs        HOST array of nbox contexts made by pm_init: PM_FP32, one grid
+ *               size N (16..256 power of two, or 192), one n_kbins (<= 1024),
+ *               the default path (none of PM_SPECTRAL_GRADIENT, PM_FUSED_GATHER,
+ *               PM_TMA_COLUMNS, PM_UNFUSED_DEPOSIT); PM_ERR_UNSUPPORTED else
+ *   cuda_stream the stream every batched kick is issued on
+ * pm_batch_kick: per box b (HOST arrays of nbox entries): DEVICE pos[b] and
+ * vel[b] (layouts of pm_kick, vel updated in place), scale factor a[b], kick
+ * factor kick_factor[b], HOST a_hist[b][n_hist[b]] and DEVICE
+ * sqrtPM_hist[b][n_hist[b]][n_kbins] (as pm_nu_response; a_hist, sqrtPM_hist
+ * and n_hist may be NULL for no history).  Each box gets the kick pm_deposit +
+ * pm_nu_response + pm_kick would give it (the same device code; the bin sums
+ * are added in another order, so results agree to rounding, not bit for bit),
+ * and its context holds that kick's bins, response and fields afterwards.
+ * The host argument checks are those of pm_nu_response (PM_ERR_RANGE /
+ * PM_ERR_INVALID, message in pm_batch_last_error); a context with a pending
+ * pm_nu_prepare is PM_ERR_ORDER.  Under stream capture the kick's per-box
+ * arguments are staged in a buffer kept for the graph: capture one kick per
+ * batch, after an uncaptured one.  Contexts must outlive the batch. */
+typedef struct pm_batch pm_batch;
+NUPM_API int pm_batch_create(pm_ctx* const* ctxs, int32_t nbox, void* cuda_stream, pm_batch** out);
+NUPM_API int pm_batch_kick(pm_batch* batch, const void* const* pos, void* const* vel, const double* a,
+                           const double* kick_factor, const double* const* a_hist,
+                           const double* const* sqrtPM_hist, const int32_t* n_hist);
+NUPM_API int64_t pm_batch_launches(const pm_batch* batch);
+NUPM_API const char* pm_batch_last_error(const pm_batch* batch);
+NUPM_API void pm_batch_free(pm_batch* batch);
+
 /* ---- learned response surrogate ----
  * The paper has no learned part; this stands in for the response integral of
  * pm_nu_response (Eq. P-final with Eq. deltaI-nu), which stays the fallback

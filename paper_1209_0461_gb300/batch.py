@@ -1,14 +1,17 @@
 """Batched form: many independent boxes stepped by one CUDA-graph launch.
 
 Each box is its own context (grid 64^3, 128^3 or 192^3, its own seed and
-neutrino mass).  The boxes are spread over a few CUDA streams; one capture
-(pm_graph_begin .. pm_graph_end) records every box's response panels (on
-the context's side stream), deposit, response and kick with the streams
-forked from and joined back to the capture stream, so
-each pm_graph_launch replays all of them with the boxes on independent graph
-branches.  Before the capture each distinct grid size is autotuned once
-(pm_autotune) and its choice shared by the boxes of that size.  Torch supplies
-device memory, streams and events only.
+neutrino mass).  Two ways to step them:
+
+* persistent (default): the boxes of each grid size form one pm_batch, whose
+  kick is one persistent kernel per pass over all of its boxes (CTAs take
+  (box, item) work from an atomic counter); the sizes run on their own
+  streams, and one capture records the few launches of every size;
+* per box: the boxes are spread over a few CUDA streams and one capture
+  records every box's response panels, deposit, response and kick (each grid
+  size autotuned once with pm_autotune).
+
+Torch supplies device memory, streams and events only.
 """
 from __future__ import annotations
 
@@ -18,9 +21,11 @@ from . import nupm, synth
 
 
 class Batch:
-    def __init__(self, boxes, n_streams: int = 8, autotune: bool = True, precision: str = "fp32"):
+    def __init__(self, boxes, n_streams: int = 8, autotune: bool = True, precision: str = "fp32",
+                 persistent: bool = False):
         import torch
         self.boxes = list(boxes)
+        self.persistent = persistent and precision == "fp32"
         self.main = torch.cuda.Stream()
         self.streams = [torch.cuda.Stream() for _ in range(max(1, n_streams))]
         self.items = []
@@ -45,6 +50,15 @@ class Batch:
             self.items.append(dict(w=w, pm=pm, pos=pos, vel=vel, vel0=vel.clone(), a=a, K=pm.kick_factor(a, a * 1.01),
                                    a_hist=np.ascontiguousarray(a_hist), hist=hist_d, stream=st))
         torch.cuda.synchronize()
+        self.groups = []
+        if self.persistent:
+            # one pm_batch per grid size, each on its own stream
+            sizes = sorted({it["w"].ngrid for it in self.items})
+            for n in sizes:
+                its = [it for it in self.items if it["w"].ngrid == n]
+                st = torch.cuda.Stream()
+                self.groups.append(dict(items=its, stream=st, batch=nupm.BatchPM([it["pm"] for it in its], st)))
+            autotune = False
         if autotune:
             for it in self.items:
                 n = it["w"].ngrid
@@ -60,8 +74,31 @@ class Batch:
         pm.nu_response(it["a"], it["a_hist"], it["hist"])
         pm.kick(it["pos"], it["vel"], it["a"], it["K"])
 
+    def _group_kick(self, g):
+        its = g["items"]
+        g["batch"].kick([it["pos"] for it in its], [it["vel"] for it in its], [it["a"] for it in its],
+                        [it["K"] for it in its], [it["a_hist"] for it in its], [it["hist"] for it in its])
+
+    def launches_per_step(self):
+        """Kernel launches of one step."""
+        if self.persistent:
+            return sum(g["batch"].launches() for g in self.groups)
+        return None
+
     def eager_step(self):
         """Every box's kick, launched directly (no graph)."""
+        if self.persistent:
+            import torch
+            fork = torch.cuda.Event()
+            fork.record(self.main)
+            for g in self.groups:
+                g["stream"].wait_event(fork)
+                self._group_kick(g)
+            for g in self.groups:
+                ev = torch.cuda.Event()
+                ev.record(g["stream"])
+                self.main.wait_event(ev)
+            return
         for it in self.items:
             self._kick(it)
 
@@ -76,6 +113,15 @@ class Batch:
         def body():
             fork = torch.cuda.Event()
             fork.record(self.main)
+            if self.persistent:
+                for g in self.groups:
+                    g["stream"].wait_event(fork)
+                    self._group_kick(g)
+                for g in self.groups:
+                    ev = torch.cuda.Event()
+                    ev.record(g["stream"])
+                    self.main.wait_event(ev)
+                return
             for st in self.streams:
                 st.wait_event(fork)
             for it in self.items:
@@ -111,5 +157,7 @@ class Batch:
     def close(self):
         if self.graph is not None:
             self.graph.close()
+        for g in self.groups:
+            g["batch"].close()
         for it in self.items:
             it["pm"].close()

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libnupm.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["grid_f32.cu", "grid_f64.cu", "nu_response.cu", "pm_api.cu", "bins_static.cu", "sort.cu", "mlp.cu",
-           "peaks.cu"]
+           "peaks.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden"]

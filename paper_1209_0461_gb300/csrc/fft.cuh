@@ -292,17 +292,16 @@ struct RowCfg {
 //   data + field * field_stride + blockIdx.y * other_stride + x2 + e * elem_stride
 // grid = (M / W, N, nfields)
 // ---------------------------------------------------------------------------
-template <typename T, int N, int DIR, class Cfg = ColCfg<T, N>>
-__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MIN_BLOCKS)
-k_fft_col(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
-          int64_t field_stride, const cx<T>* __restrict__ tw) {
+// Body of one tile (bx: W-column group, by: the other axis) of field `data`.
+template <typename T, int N, int DIR, class Cfg>
+__device__ __forceinline__ void fft_col_tile(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
+                                             const cx<T>* __restrict__ tw, int bx, int by) {
   using P = typename Cfg::P;
   constexpr int E = Cfg::E, NT = Cfg::NT, W = Cfg::W, RL = last_radix<T, N, P>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = threadIdx.x % W;
   const int t = threadIdx.x / W;
-  cx<T>* col = data + (int64_t)blockIdx.z * field_stride + (int64_t)blockIdx.y * other_stride +
-               (int64_t)blockIdx.x * W + c;
+  cx<T>* col = data + (int64_t)by * other_stride + (int64_t)bx * W + c;
   ColSmem<T, W, Cfg::PAD> sm{reinterpret_cast<cx<T>*>(smem_raw), c};
   cx<T> v[E];
 #pragma unroll
@@ -315,6 +314,14 @@ k_fft_col(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
       col[(int64_t)(t + NT * b + i * (N / RL)) * elem_stride] = v[b * RL + i];
 }
 
+template <typename T, int N, int DIR, class Cfg = ColCfg<T, N>>
+__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MIN_BLOCKS)
+k_fft_col(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
+          int64_t field_stride, const cx<T>* __restrict__ tw) {
+  fft_col_tile<T, N, DIR, Cfg>(data + (int64_t)blockIdx.z * field_stride, other_stride, elem_stride, tw, blockIdx.x,
+                               blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // Inverse z pass with the Green function (a5 + first third of a6).  Columns
 // (x2, ky), transform along kz.  Two transforms per tile from the same input
@@ -325,12 +332,13 @@ k_fft_col(cx<T>* __restrict__ data, int64_t other_stride, int64_t elem_stride,
 // from plane0[ky][kz] (k_green_plane0).  NOUT = 1: the potential alone (the
 // gradient is then taken in real space by the gather).  grid = (M / W, N)
 // ---------------------------------------------------------------------------
-template <typename T, int N, class Cfg = ColWide<T, N>, int NOUT = 2>
-__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MIN_BLOCKS)
-k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, cx<T>* __restrict__ out_dz,
-                  const cx<T>* __restrict__ plane0, const T* __restrict__ gtab, const T* __restrict__ dtab,
-                  const T* __restrict__ wtab, const cx<T>* __restrict__ tw, const float* __restrict__ fac,
-                  float fac_inv_du, float coeff) {
+template <typename T, int N, class Cfg, int NOUT>
+__device__ __forceinline__ void fft_z_inv_green_tile(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi,
+                                                     cx<T>* __restrict__ out_dz, const cx<T>* __restrict__ plane0,
+                                                     const T* __restrict__ gtab, const T* __restrict__ dtab,
+                                                     const T* __restrict__ wtab, const cx<T>* __restrict__ tw,
+                                                     const float* __restrict__ fac, float fac_inv_du, float coeff,
+                                                     int bx, int by) {
   using P = typename Cfg::P;
   constexpr int M = N / 2, E = Cfg::E, NT = Cfg::NT, W = Cfg::W, RL = last_radix<T, N, P>();
   constexpr int64_t ES = (int64_t)N * M;   // element stride along z
@@ -343,8 +351,8 @@ k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, c
     for (int j = threadIdx.x; j < kFacTableDev; j += blockDim.x) fac_s[j] = fac[j];
     __syncthreads();
   }
-  const int x2 = blockIdx.x * W + c;
-  const int iy = blockIdx.y;
+  const int x2 = bx * W + c;
+  const int iy = by;
   const int ky = iy < N / 2 ? iy : iy - N;
   const int base2 = ky * ky + x2 * x2;
   const int64_t off = (int64_t)iy * M + x2;
@@ -399,6 +407,16 @@ k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, c
       for (int i = 0; i < RL; ++i) dst[off + (int64_t)(t + NT * b + i * (N / RL)) * ES] = v[b * RL + i];
     if (NOUT > 1) __syncthreads();   // the next transform reuses the shared memory
   }
+}
+
+template <typename T, int N, class Cfg = ColWide<T, N>, int NOUT = 2>
+__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MIN_BLOCKS)
+k_fft_z_inv_green(const cx<T>* __restrict__ spec, cx<T>* __restrict__ out_phi, cx<T>* __restrict__ out_dz,
+                  const cx<T>* __restrict__ plane0, const T* __restrict__ gtab, const T* __restrict__ dtab,
+                  const T* __restrict__ wtab, const cx<T>* __restrict__ tw, const float* __restrict__ fac,
+                  float fac_inv_du, float coeff) {
+  fft_z_inv_green_tile<T, N, Cfg, NOUT>(spec, out_phi, out_dz, plane0, gtab, dtab, wtab, tw, fac, fac_inv_du, coeff,
+                                        blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -549,10 +567,11 @@ __device__ __forceinline__ unsigned int carry_of(unsigned int old, unsigned int 
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(FusedCfg<T, N>::THREADS, FusedCfg<T, N>::MIN_BLOCKS)
-k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restrict__ row_start,
-                cx<T>* __restrict__ spec, double scale, const cx<T>* __restrict__ tw_m, const cx<T>* __restrict__ tw_n,
-                unsigned long long* __restrict__ keep) {
+__device__ __forceinline__ void deposit_fft_x_tile(const unsigned long long* __restrict__ rec,
+                                                   const int* __restrict__ row_start, cx<T>* __restrict__ spec,
+                                                   double scale, const cx<T>* __restrict__ tw_m,
+                                                   const cx<T>* __restrict__ tw_n, unsigned long long* __restrict__ keep,
+                                                   int bx, int by) {
   using Cfg = FusedCfg<T, N>;
   using P = typename Cfg::P;
   constexpr int TZ = Cfg::TZ, TY = Cfg::TY, ROWS = Cfg::ROWS, M = N / 2, E = Cfg::E, NT = Cfg::NT;
@@ -564,7 +583,7 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
   // when ty0 = 0: NSEG segments, concatenated in a virtual index j.
   constexpr int NSEG = 2 * (TZ + 1);
   __shared__ int seg_pre[NSEG + 1], seg_beg[NSEG];
-  const int ty0 = blockIdx.x * TY, tz0 = blockIdx.y * TZ;
+  const int ty0 = bx * TY, tz0 = by * TZ;
   for (int i = threadIdx.x; i < ROWS * N / 2; i += blockDim.x)
     reinterpret_cast<ulonglong2*>(acc)[i] = ulonglong2{0ull, 0ull};
   // lanes of the (first) warp: all 32, or the whole block when it is smaller
@@ -742,6 +761,14 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
   }
 }
 
+template <typename T, int N>
+__global__ void __launch_bounds__(FusedCfg<T, N>::THREADS, FusedCfg<T, N>::MIN_BLOCKS)
+k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restrict__ row_start,
+                cx<T>* __restrict__ spec, double scale, const cx<T>* __restrict__ tw_m, const cx<T>* __restrict__ tw_n,
+                unsigned long long* __restrict__ keep) {
+  deposit_fft_x_tile<T, N>(rec, row_start, spec, scale, tw_m, tw_n, keep, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // Inverse x pass, in place: packed half-spectrum rows -> N reals (unscaled),
 // fields with bit f of grad_mask set are first multiplied by -i D(kx):
@@ -750,19 +777,20 @@ k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restric
 //   z = IFFT_M(Z');  x[2n] = Re z[n], x[2n+1] = Im z[n].
 // grid = (rows / ROWS, 1, nfields); rows = N^2.
 // ---------------------------------------------------------------------------
+// Body of one group of rows (bx) of one field (`data` its base); grad: apply -i D(kx) first.
 template <typename T, int N>
-__global__ void __launch_bounds__(RowCfg<T, N>::THREADS)
-k_fft_x_inv(cx<T>* __restrict__ data, int64_t field_stride, const cx<T>* __restrict__ tw_m,
-            const cx<T>* __restrict__ tw_n, const T* __restrict__ dtab, int grad_mask) {
+__device__ __forceinline__ void fft_x_inv_rows(cx<T>* __restrict__ data, const cx<T>* __restrict__ tw_m,
+                                               const cx<T>* __restrict__ tw_n, const T* __restrict__ dtab, bool grad,
+                                               int bx) {
   using Cfg = RowCfg<T, N>;
   constexpr int M = N / 2, E = Plan<T, M>::R1, NT = M / E, RL = last_radix<T, M>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int t = threadIdx.x % NT;
   const int r = threadIdx.x / NT;
-  const int64_t row = (int64_t)blockIdx.x * Cfg::ROWS + r;
+  const int64_t row = (int64_t)bx * Cfg::ROWS + r;
   RowSmem<T> sm{reinterpret_cast<cx<T>*>(smem_raw) + r * Cfg::ROW_WORDS};
-  cx<T>* rowp = data + (int64_t)blockIdx.z * field_stride + row * M;
-  if ((grad_mask >> blockIdx.z) & 1) {
+  cx<T>* rowp = data + row * M;
+  if (grad) {
     // x gradient first: X'[k] = -i D(k) X[k]; D vanishes on kx = 0 and N/2, so the
     // packed slot 0 (X[0] + i X[N/2]) becomes 0
 #pragma unroll
@@ -801,6 +829,14 @@ k_fft_x_inv(cx<T>* __restrict__ data, int64_t field_stride, const cx<T>* __restr
       const int n = t + NT * b + i * (M / RL);
       reinterpret_cast<cx<T>*>(out)[n] = v[b * RL + i];    // (x[2n], x[2n+1])
     }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(RowCfg<T, N>::THREADS)
+k_fft_x_inv(cx<T>* __restrict__ data, int64_t field_stride, const cx<T>* __restrict__ tw_m,
+            const cx<T>* __restrict__ tw_n, const T* __restrict__ dtab, int grad_mask) {
+  fft_x_inv_rows<T, N>(data + (int64_t)blockIdx.z * field_stride, tw_m, tw_n, dtab, (grad_mask >> blockIdx.z) & 1,
+                       blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------

@@ -319,7 +319,7 @@ __device__ __forceinline__ void bin_row(const cx<T> (&f)[kBinLaneMax], cx<T> g, 
 }
 
 template <typename T, bool LATTICE>
-__device__ __forceinline__ void bin_flush_partials(const double* all, int nk, double* partials) {
+__device__ __forceinline__ void bin_flush_partials(const double* all, int nk, double* partials, int64_t slot) {
   constexpr int NV = LATTICE ? 2 : 1;
   __syncthreads();
   for (int i = threadIdx.x; i < NV * nk; i += blockDim.x) {
@@ -333,16 +333,19 @@ __device__ __forceinline__ void bin_flush_partials(const double* all, int nk, do
         sum += all[wi * NV * nk + i];
       }
     }
-    partials[(int64_t)blockIdx.x * NV * nk + i] = sum;
+    partials[slot * NV * nk + i] = sum;
   }
 }
 
 // Rows read by each lane from global memory (lattice sums, and grids whose
 // lane segments are not whole 16-byte units).
+// Body: rows row0 + warp, row0 + warp + row_step, ... below row1 into the
+// per-warp accumulators, then their sum to partials[slot].
 template <typename T, bool LATTICE>
-__global__ void __launch_bounds__(kBinWarps * 32)
-k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const int* __restrict__ thr, float inv_lr,
-            double kf, double* __restrict__ partials) {
+__device__ __forceinline__ void bin_power_rows(const cx<T>* __restrict__ spec, int n, int nk,
+                                               const int* __restrict__ thr, float inv_lr, double kf,
+                                               double* __restrict__ partials, int row0, int row1, int row_step,
+                                               int64_t slot) {
   constexpr int NV = LATTICE ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* all = reinterpret_cast<double*>(smem_raw);
@@ -355,8 +358,7 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const int* __restrict
   const int m = n / 2;
   const int E = (m + 31) >> 5;
   const int xb = lane * E;
-  const int rows = n * n;
-  for (int row = blockIdx.x * kBinWarps + warp; row < rows; row += gridDim.x * kBinWarps) {
+  for (int row = row0 + warp; row < row1; row += row_step) {
     const int iz = row / n, iy = row - (row / n) * n;
     const int kz = signed_freq(iz, n), ky = signed_freq(iy, n);
     const cx<T>* r = spec + (int64_t)row * m;
@@ -370,7 +372,15 @@ k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const int* __restrict
     }
     bin_row<T, LATTICE>(f, g, kz * kz + ky * ky, m, E, lane, Ts, nk, inv_lr, kf, acc);
   }
-  bin_flush_partials<T, LATTICE>(all, nk, partials);
+  bin_flush_partials<T, LATTICE>(all, nk, partials, slot);
+}
+
+template <typename T, bool LATTICE>
+__global__ void __launch_bounds__(kBinWarps * 32)
+k_bin_power(const cx<T>* __restrict__ spec, int n, int nk, const int* __restrict__ thr, float inv_lr,
+            double kf, double* __restrict__ partials) {
+  bin_power_rows<T, LATTICE>(spec, n, nk, thr, inv_lr, kf, partials, blockIdx.x * kBinWarps, n * n,
+                             gridDim.x * kBinWarps, blockIdx.x);
 }
 
 // bin_row for the staged power sums: E (compile time) modes per lane, all
@@ -553,7 +563,7 @@ k_bin_power_tma(const __grid_constant__ CUtensorMap map, const cx<float>* __rest
     const int kz = signed_freq(iz, N), ky = signed_freq(iy, N);
     bin_row_staged<float, E>(f, g, kz * kz + ky * ky, lane, Ts, nk, inv_lr, acc);
   }
-  bin_flush_partials<float, false>(all, nk, partials);
+  bin_flush_partials<float, false>(all, nk, partials, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -562,10 +572,12 @@ k_bin_power_tma(const __grid_constant__ CUtensorMap map, const cx<float>* __rest
 // partner at (-ky, -kz), multiply each by its G(n^2) (and deconvolution), and
 // repack P = G_A A + i G_B B into plane0[ky][kz] for k_fft_z_inv_green.
 // ---------------------------------------------------------------------------
+// Body: plane0 entries idx0, idx0 + step, ... below idx1.
 template <typename T>
-__global__ void k_green_plane0(const cx<T>* __restrict__ spec, cx<T>* __restrict__ plane0, int n,
-                               const T* __restrict__ gtab, const T* __restrict__ wtab, const float* __restrict__ fac,
-                               float fac_inv_du, float coeff) {
+__device__ __forceinline__ void green_plane0_range(const cx<T>* __restrict__ spec, cx<T>* __restrict__ plane0, int n,
+                                                   const T* __restrict__ gtab, const T* __restrict__ wtab,
+                                                   const float* __restrict__ fac, float fac_inv_du, float coeff,
+                                                   int idx0, int idx1, int step) {
   // G(n^2): the FP64 table, or (FP32) coeff fac(u) / n^2 from the fac table as
   // in the inverse z passes; G(0) = 0
   auto green = [&](int n2) -> T {
@@ -580,8 +592,7 @@ __global__ void k_green_plane0(const cx<T>* __restrict__ spec, cx<T>* __restrict
     }
   };
   const int m = n / 2;
-  const int total = n * n;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+  for (int idx = idx0; idx < idx1; idx += step) {
     const int iy = idx / n, iz = idx - (idx / n) * n;    // plane0 layout [ky][kz]
     const int ky = signed_freq(iy, n), kz = signed_freq(iz, n);
     const int jy = partner_index(iy, n), jz = partner_index(iz, n);
@@ -598,6 +609,14 @@ __global__ void k_green_plane0(const cx<T>* __restrict__ spec, cx<T>* __restrict
     }
     plane0[idx] = {ga * A.x - gb * B.y, ga * A.y + gb * B.x};   // G_A A + i G_B B
   }
+}
+
+template <typename T>
+__global__ void k_green_plane0(const cx<T>* __restrict__ spec, cx<T>* __restrict__ plane0, int n,
+                               const T* __restrict__ gtab, const T* __restrict__ wtab, const float* __restrict__ fac,
+                               float fac_inv_du, float coeff) {
+  green_plane0_range<T>(spec, plane0, n, gtab, wtab, fac, fac_inv_du, coeff, blockIdx.x * blockDim.x + threadIdx.x,
+                        n * n, gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -812,12 +831,13 @@ __device__ __forceinline__ void fd_stencil(const T* __restrict__ phi, int n, con
 constexpr int kGatherTPB = 64;
 constexpr int kGatherChunk = 8;
 
+// Body: chunk `chunk` of kGatherTPB x kGatherChunk particles (blockDim = kGatherTPB).
 template <typename T>
-__global__ void __launch_bounds__(kGatherTPB, sizeof(T) == 4 ? 12 : 8)
-k_interp_kick_fd(const void* __restrict__ pos, int64_t np, int n, double delta, const T* __restrict__ phi,
-                 T* __restrict__ vel, T kick, T* __restrict__ acc_out, int* status) {
+__device__ __forceinline__ void interp_fd_chunk(const void* __restrict__ pos, int64_t np, int n, double delta,
+                                                const T* __restrict__ phi, T* __restrict__ vel, T kick,
+                                                T* __restrict__ acc_out, int* status, int64_t chunk) {
   const T scale = (T)(-1.0 / (12.0 * delta));   // acc = -S phi
-  const int64_t base = (int64_t)blockIdx.x * kGatherTPB * kGatherChunk + threadIdx.x;
+  const int64_t base = chunk * kGatherTPB * kGatherChunk + threadIdx.x;
   // the next particle's position words are fetched while this one's
   // potential values are in flight (one memory round trip per particle)
   typename Quant<T>::Raw next;
@@ -841,6 +861,13 @@ k_interp_kick_fd(const void* __restrict__ pos, int64_t np, int n, double delta, 
       if (acc_out) acc_out[d * np + p] = ad;
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGatherTPB, sizeof(T) == 4 ? 12 : 8)
+k_interp_kick_fd(const void* __restrict__ pos, int64_t np, int n, double delta, const T* __restrict__ phi,
+                 T* __restrict__ vel, T kick, T* __restrict__ acc_out, int* status) {
+  interp_fd_chunk<T>(pos, np, n, delta, phi, vel, kick, acc_out, status, blockIdx.x);
 }
 
 // The same gather in the row order of the deposit's sort: one warp per grid

@@ -189,6 +189,38 @@ NUPM_DECLARE_GRID(_f32)
 NUPM_DECLARE_GRID(_f64)
 #undef NUPM_DECLARE_GRID
 
+// ---- batched kicks of boxes of one grid size (batch.cu) ----
+// One box of a batched kick (device copy, rewritten at every kick).
+struct BoxArgs {
+  GridArgs g;             // the box context's grids, tables, sort buffers and scalars
+  NuArgs nu;              // its response arguments at this kick
+  const void* pos;
+  void* vel;
+  float kick;
+  int bin_chunks;         // rows of bin partial sums (row chunks of the spectrum)
+  const int* thr;         // bin thresholds (int32, nk + 1)
+  float inv_lr;
+  double kf, fac_umax;    // 2 pi / L; ln sqrt(n^2_max) of the fac table
+  double* partials;       // [bin_chunks][nk]
+  double* psum;           // the box's sum w |delta|^2 per bin
+};
+enum BatchPass {
+  kBpCount, kBpScan, kBpScatter, kBpDeposit, kBpY, kBpZ, kBpBins, kBpBinReduce, kBpPanels, kBpFinish, kBpRlist,
+  kBpFac, kBpPlane0, kBpZInv, kBpYInv, kBpXInv, kBpGather, kBpPasses
+};
+struct BatchPlan {
+  int n = 0, nbox = 0, nk = 0, sm_count = 0;
+  BoxArgs* d_boxes = nullptr;
+  int* d_first = nullptr;             // [kBpPasses][nbox + 1] first item of each box, then the total
+  const int* h_first = nullptr;       // host copy
+  int* d_counters = nullptr;          // [kBpPasses] work-queue counters, zeroed before each kick
+};
+// Items of each pass for one box (grid n, np particles, nk bins, ns response
+// species, bin_chunks partials rows); the grid sizes the batch supports.
+void batch_items(int n, int64_t np, int nk, int ns, int bin_chunks, int* items);
+bool batch_supported(int n);
+int batch_kick(const BatchPlan& p, cudaStream_t s);
+
 // out[i] = sum over blocks of partials[blk][i], i < len, in block order.
 __global__ void k_bin_reduce(const double* __restrict__ partials, int nblk, int len,
                              double* __restrict__ out);

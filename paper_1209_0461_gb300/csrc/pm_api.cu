@@ -101,6 +101,7 @@ struct pm_ctx {
   // state
   bool deposited = false, deposit_grid_valid = false, have_response = false, have_kick = false;
   bool power_set = false;         // bins replaced by pm_set_power (no spectrum behind them)
+  bool counts_dirty = true;       // row counts hold a direct row sort's values (a batched kick clears them)
   int wide_y = -1, wide_z = -1, part_cps = 16;   // tuning (pm_autotune)
   int gather_rows = 0;                            // tuning: gather in the sort's row order
   bool perm_valid = false;                        // the last deposit's sort wrote perm
@@ -861,6 +862,7 @@ int pm_deposit(pm_ctx* c, const void* pos) {
     {
       Stage st(c, PM_ST_DEPOSIT, 5);
       rc = c->fp64 ? row_sort_f64(g, pos, c->stream) : row_sort_f32(g, pos, c->stream);
+      c->counts_dirty = true;
     }
     if (rc == PM_OK) {
       Stage st(c, PM_ST_FFT_X_FWD, 1);
@@ -1616,6 +1618,241 @@ void pm_graph_free(pm_graph* g) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
   delete h;
+}
+
+}  // extern "C"
+
+// ---- batched kicks of many boxes of one grid size (batch.cu) ----
+struct pm_batch {
+  std::vector<pm_ctx*> ctx;
+  cudaStream_t stream = nullptr;
+  int n = 0, nk = 0, hist_stride = 1;
+  std::vector<int> first;              // [kBpPasses][nbox + 1]
+  std::vector<int> bin_chunks;
+  BatchPlan plan;
+  int* d_first = nullptr;
+  int* d_counters = nullptr;
+  BoxArgs* d_boxes = nullptr;
+  double* d_hist_u = nullptr;
+  // staging (pinned): [0] eager kicks (reused after its copy completed), [1] a
+  // captured kick (kept as the captured graph reads it at every replay)
+  BoxArgs* h_boxes[2] = {nullptr, nullptr};
+  double* h_hist_u[2] = {nullptr, nullptr};
+  cudaEvent_t ev_staged = nullptr;
+  bool staged_pending = false;
+  std::string err;
+};
+
+extern "C" {
+
+int pm_batch_create(pm_ctx* const* ctxs, int32_t nbox, void* cuda_stream, pm_batch** out) {
+  if (!out) return PM_ERR_INVALID;
+  *out = nullptr;
+  if (!ctxs || nbox < 1) return PM_ERR_INVALID;
+  const pm_ctx* c0 = ctxs[0];
+  if (!c0) return PM_ERR_INVALID;
+  const uint32_t bad_flags = PM_SPECTRAL_GRADIENT | PM_FUSED_GATHER | PM_TMA_COLUMNS | PM_UNFUSED_DEPOSIT;
+  for (int b = 0; b < nbox; ++b) {
+    const pm_ctx* c = ctxs[b];
+    if (!c) return PM_ERR_INVALID;
+    if (c->fp64 || c->n != c0->n || c->nk != c0->nk) {
+      fprintf(stderr, "pm_batch_create: boxes must be PM_FP32 with one grid size and bin count\n");
+      return PM_ERR_UNSUPPORTED;
+    }
+    if ((c->p.flags & bad_flags) || !batch_supported(c->n) || c->nk > 1024) {
+      fprintf(stderr, "pm_batch_create: grid %d or flags not supported by the batched form\n", c->n);
+      return PM_ERR_UNSUPPORTED;
+    }
+  }
+  pm_batch* B = new (std::nothrow) pm_batch;
+  if (!B) return PM_ERR_ALLOC;
+  B->ctx.assign(ctxs, ctxs + nbox);
+  B->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  B->n = c0->n;
+  B->nk = c0->nk;
+  for (int b = 0; b < nbox; ++b) B->hist_stride = std::max(B->hist_stride, ctxs[b]->p.n_hist_max + 1);
+  B->first.assign((size_t)kBpPasses * (nbox + 1), 0);
+  B->bin_chunks.resize(nbox);
+  for (int b = 0; b < nbox; ++b) {
+    const pm_ctx* c = ctxs[b];
+    const int64_t rows = (int64_t)c->n * c->n;
+    int chunks = (int)((rows + 31) / 32);
+    if (chunks > c->nblk_bins) chunks = c->nblk_bins;
+    B->bin_chunks[b] = chunks;
+    const int ns = (c->ns > 0 && c->f_nu > 0) ? c->ns : 0;
+    int items[kBpPasses];
+    batch_items(c->n, c->np, c->nk, ns, chunks, items);
+    for (int p = 0; p < kBpPasses; ++p) B->first[(size_t)p * (nbox + 1) + b + 1] = items[p];
+  }
+  for (int p = 0; p < kBpPasses; ++p)
+    for (int b = 0; b < nbox; ++b) B->first[(size_t)p * (nbox + 1) + b + 1] += B->first[(size_t)p * (nbox + 1) + b];
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaMalloc((void**)&B->d_first, B->first.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_counters, kBpPasses * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_boxes, (size_t)nbox * sizeof(BoxArgs));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_hist_u, (size_t)nbox * B->hist_stride * sizeof(double));
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaMallocHost((void**)&B->h_boxes[k], (size_t)nbox * sizeof(BoxArgs));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_hist_u[k], (size_t)nbox * B->hist_stride * sizeof(double));
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_staged, cudaEventDisableTiming);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(B->d_first, B->first.data(), B->first.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    pm_batch_free(B);
+    return PM_ERR_ALLOC;
+  }
+  B->plan.n = B->n;
+  B->plan.nbox = nbox;
+  B->plan.nk = B->nk;
+  B->plan.sm_count = sms;
+  B->plan.d_boxes = B->d_boxes;
+  B->plan.d_first = B->d_first;
+  B->plan.h_first = B->first.data();
+  B->plan.d_counters = B->d_counters;
+  *out = B;
+  return PM_OK;
+}
+
+int pm_batch_kick(pm_batch* B, const void* const* pos, void* const* vel, const double* a, const double* kick_factor,
+                  const double* const* a_hist, const double* const* sqrtPM_hist, const int32_t* n_hist) {
+  if (!B) return PM_ERR_INVALID;
+  const int nbox = (int)B->ctx.size();
+  if (!pos || !vel || !a || !kick_factor) {
+    B->err = "pm_batch_kick: NULL argument array";
+    return PM_ERR_INVALID;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(B->stream, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return PM_ERR_CUDA;
+  }
+  const int stage = cap == cudaStreamCaptureStatusNone ? 0 : 1;
+  if (stage == 0 && B->staged_pending) {   // the previous eager kick's copies have read the staging buffers
+    if (cudaEventSynchronize(B->ev_staged) != cudaSuccess) {
+      cudaGetLastError();
+      return PM_ERR_CUDA;
+    }
+    B->staged_pending = false;
+  }
+  BoxArgs* hb = B->h_boxes[stage];
+  double* hh = B->h_hist_u[stage];
+  bool any_hist = false;
+  for (int b = 0; b < nbox; ++b) {
+    pm_ctx* c = B->ctx[b];
+    const int nh = n_hist ? n_hist[b] : 0;
+    const double* ah = a_hist ? a_hist[b] : nullptr;
+    const double* hist = sqrtPM_hist ? sqrtPM_hist[b] : nullptr;
+    char buf[160];
+    snprintf(buf, sizeof buf, "pm_batch_kick: box %d: ", b);
+    if (!pos[b] || !vel[b]) return B->err = std::string(buf) + "pos/vel NULL", PM_ERR_INVALID;
+    if (!(isfinite(a[b]) && a[b] >= c->a_init) || !isfinite(kick_factor[b]))
+      return B->err = std::string(buf) + "a or kick factor out of range", PM_ERR_RANGE;
+    if (nh < 0 || nh > c->p.n_hist_max || (nh > 0 && (!ah || !hist)))
+      return B->err = std::string(buf) + "bad history", PM_ERR_INVALID;
+    for (int j = 0; j < nh; ++j)
+      if (!isfinite(ah[j]) || (j == 0 && ah[0] < c->a_init) || (j > 0 && !(ah[j] > ah[j - 1])) ||
+          (j == nh - 1 && !(ah[j] < a[b])))
+        return B->err = std::string(buf) + "a_hist must increase from a_init to below a", PM_ERR_RANGE;
+    if (c->prep_pending) return B->err = std::string(buf) + "pm_nu_prepare pending", PM_ERR_ORDER;
+    const double ue = log(a[b]);
+    if (ue > c->stab_umax) {
+      const int rc = build_s_table(c, ue + 1.0);
+      if (rc != PM_OK) return B->err = c->err, rc;
+    }
+    if (c->power_set) {   // the lattice count / |k| sums back in place of pm_set_power's values
+      const int rc = cuda_check(c, cudaMemcpyAsync(c->d_bins, c->d_bins_lattice, 2 * (size_t)c->nk * sizeof(double),
+                                                   cudaMemcpyDeviceToDevice, B->stream), "lattice bins restore");
+      if (rc != PM_OK) return B->err = c->err, rc;
+      c->power_set = false;
+    }
+    if (c->counts_dirty) {   // the batched count adds to zeros; its scan clears them again
+      const int rc = cuda_check(c, cudaMemsetAsync(c->d_rowc, 0, ((size_t)c->n * c->n + 1) * sizeof(int), B->stream),
+                                "row count clear");
+      if (rc != PM_OK) return B->err = c->err, rc;
+      c->counts_dirty = false;
+    }
+    for (int j = 0; j < nh; ++j) hh[(size_t)b * B->hist_stride + j] = log(ah[j]);
+    any_hist = any_hist || nh > 0;
+    BoxArgs& x = hb[b];
+    x.g = grid_args(c);
+    const double coeff = -1.5 * c->omega_m / (a[b] * c->kf * c->kf * (double)c->n * c->n * c->n);
+    x.g.green_coeff = (float)coeff;
+    x.nu = nu_args(c, a[b], hist, nh, nullptr, nullptr, nullptr, nullptr);
+    x.nu.hist_u = B->d_hist_u + (size_t)b * B->hist_stride;
+    x.pos = pos[b];
+    x.vel = vel[b];
+    x.kick = (float)kick_factor[b];
+    x.bin_chunks = B->bin_chunks[b];
+    x.thr = c->d_thr;
+    x.inv_lr = c->bin_inv_lr;
+    x.kf = c->kf;
+    x.fac_umax = 0.5 * log((double)c->n2max);
+    x.partials = c->d_partials;
+    x.psum = c->d_bins + 2 * c->nk;
+    c->green_coeff = coeff;
+  }
+  cudaError_t e = cudaMemcpyAsync(B->d_boxes, hb, (size_t)nbox * sizeof(BoxArgs), cudaMemcpyHostToDevice, B->stream);
+  if (e == cudaSuccess && any_hist)
+    e = cudaMemcpyAsync(B->d_hist_u, hh, (size_t)nbox * B->hist_stride * sizeof(double), cudaMemcpyHostToDevice,
+                        B->stream);
+  if (e == cudaSuccess && stage == 0) {
+    e = cudaEventRecord(B->ev_staged, B->stream);
+    B->staged_pending = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_counters, 0, kBpPasses * sizeof(int), B->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    B->err = std::string("pm_batch_kick: ") + cudaGetErrorString(e);
+    return PM_ERR_CUDA;
+  }
+  int rc = batch_kick(B->plan, B->stream);
+  if (rc != PM_OK) return B->err = "pm_batch_kick: unsupported grid", rc;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    B->err = std::string("pm_batch_kick launch: ") + cudaGetErrorString(e);
+    return PM_ERR_CUDA;
+  }
+  for (int b = 0; b < nbox; ++b) {   // each context now holds this kick's results
+    pm_ctx* c = B->ctx[b];
+    c->deposited = true;
+    c->have_response = true;
+    c->a_response = a[b];
+    c->have_kick = true;
+    c->deposit_grid_valid = false;
+    c->perm_valid = c->d_perm != nullptr && grid_args(c).perm != nullptr;
+    c->dep_pos = pos[b];
+  }
+  return PM_OK;
+}
+
+int64_t pm_batch_launches(const pm_batch* B) {
+  if (!B) return 0;
+  int64_t k = 0;
+  const int nbox = (int)B->ctx.size();
+  for (int p = 0; p < kBpPasses; ++p) k += B->first[(size_t)p * (nbox + 1) + nbox] > 0 ? 1 : 0;
+  return k;
+}
+
+const char* pm_batch_last_error(const pm_batch* B) { return B ? B->err.c_str() : "null batch"; }
+
+void pm_batch_free(pm_batch* B) {
+  if (!B) return;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  if (B->d_first) cudaFree(B->d_first);
+  if (B->d_counters) cudaFree(B->d_counters);
+  if (B->d_boxes) cudaFree(B->d_boxes);
+  if (B->d_hist_u) cudaFree(B->d_hist_u);
+  for (int k = 0; k < 2; ++k) {
+    if (B->h_boxes[k]) cudaFreeHost(B->h_boxes[k]);
+    if (B->h_hist_u[k]) cudaFreeHost(B->h_hist_u[k]);
+  }
+  if (B->ev_staged) cudaEventDestroy(B->ev_staged);
+  delete B;
 }
 
 }  // extern "C"

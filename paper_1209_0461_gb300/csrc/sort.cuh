@@ -68,32 +68,73 @@ __device__ __forceinline__ unsigned long long pack_record(const int (&c)[3], con
 // loads in flight first); the match below sees every lane of the warp.
 constexpr int kSortBatch = 4;
 
+// One warp's kSortBatch x 32 particles from `base` on (the warp-uniform body
+// of k_row_count; also run by the batched form).
 template <typename T>
-__global__ void k_row_count(const void* __restrict__ pos, int64_t np, int n, double delta,
-                            int* __restrict__ count, int* status) {
+__device__ __forceinline__ void row_count_warp(const void* __restrict__ pos, int64_t np, int n, double delta,
+                                               int* __restrict__ count, int* status, int64_t base) {
   constexpr int U = kSortBatch;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x * U;
-  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U; base < np; base += stride) {
-    typename RowKey<T>::Raw raw[U];
+  typename RowKey<T>::Raw raw[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t p = base + u * 32 + lane;
-      if (p < np) raw[u] = RowKey<T>::load(pos, np, p);
-    }
-    int key[U];
+  for (int u = 0; u < U; ++u) {
+    const int64_t p = base + u * 32 + lane;
+    if (p < np) raw[u] = RowKey<T>::load(pos, np, p);
+  }
+  int key[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t p = base + u * 32 + lane;
-      key[u] = p < np ? RowKey<T>::key(raw[u], n, delta) : -2;
-    }
+  for (int u = 0; u < U; ++u) {
+    const int64_t p = base + u * 32 + lane;
+    key[u] = p < np ? RowKey<T>::key(raw[u], n, delta) : -2;
+  }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const unsigned peers = __match_any_sync(full, key[u]);
-      const int leader = __ffs(peers) - 1;
-      if (key[u] >= 0 && lane == leader) atomicAdd(count + key[u], __popc(peers));
-      if (key[u] == -1) set_status(status, PM_ERR_RANGE);   // skipped by every later stage
+  for (int u = 0; u < U; ++u) {
+    const unsigned peers = __match_any_sync(full, key[u]);
+    const int leader = __ffs(peers) - 1;
+    if (key[u] >= 0 && lane == leader) atomicAdd(count + key[u], __popc(peers));
+    if (key[u] == -1) set_status(status, PM_ERR_RANGE);   // skipped by every later stage
+  }
+}
+
+template <typename T>
+__global__ void k_row_count(const void* __restrict__ pos, int64_t np, int n, double delta,
+                            int* __restrict__ count, int* status) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kSortBatch;
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * kSortBatch; base < np;
+       base += stride)
+    row_count_warp<T>(pos, np, n, delta, count, status, base);
+}
+
+// One warp's kSortBatch x 32 particles from `base` on (body of k_row_scatter).
+template <typename T>
+__device__ __forceinline__ void row_scatter_warp(const void* __restrict__ pos, int64_t np, int n, double delta,
+                                                 int* __restrict__ cursor, int* __restrict__ perm,
+                                                 unsigned long long* __restrict__ rec, int64_t base) {
+  constexpr int U = kSortBatch;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  typename Quant<T>::Raw raw[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t p = base + u * 32 + lane;
+    if (p < np) raw[u] = Quant<T>::load(pos, np, p);
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t p = base + u * 32 + lane;
+    int c[3] = {0, 0, 0}, w[3] = {0, 0, 0};
+    int key = -2;
+    if (p < np) key = Quant<T>::cells(raw[u], n, delta, c, w) ? c[2] * n + c[1] : -1;
+    const unsigned peers = __match_any_sync(full, key);
+    const int leader = __ffs(peers) - 1;
+    int start = 0;
+    if (key >= 0 && lane == leader) start = atomicAdd(cursor + key, __popc(peers));
+    start = __shfl_sync(full, start, leader);
+    if (key >= 0) {
+      const int slot = start + __popc(peers & ((1u << lane) - 1));
+      rec[slot] = pack_record(c, w);
+      if (perm) perm[slot] = (int)p;
     }
   }
 }
@@ -104,35 +145,10 @@ template <typename T>
 __global__ void k_row_scatter(const void* __restrict__ pos, int64_t np, int n, double delta,
                               int* __restrict__ cursor, int* __restrict__ perm,
                               unsigned long long* __restrict__ rec) {
-  constexpr int U = kSortBatch;
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x * U;
-  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * U; base < np; base += stride) {
-    typename Quant<T>::Raw raw[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t p = base + u * 32 + lane;
-      if (p < np) raw[u] = Quant<T>::load(pos, np, p);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t p = base + u * 32 + lane;
-      int c[3] = {0, 0, 0}, w[3] = {0, 0, 0};
-      int key = -2;
-      if (p < np) key = Quant<T>::cells(raw[u], n, delta, c, w) ? c[2] * n + c[1] : -1;
-      const unsigned peers = __match_any_sync(full, key);
-      const int leader = __ffs(peers) - 1;
-      int start = 0;
-      if (key >= 0 && lane == leader) start = atomicAdd(cursor + key, __popc(peers));
-      start = __shfl_sync(full, start, leader);
-      if (key >= 0) {
-        const int slot = start + __popc(peers & ((1u << lane) - 1));
-        rec[slot] = pack_record(c, w);
-        if (perm) perm[slot] = (int)p;
-      }
-    }
-  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kSortBatch;
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * kSortBatch; base < np;
+       base += stride)
+    row_scatter_warp<T>(pos, np, n, delta, cursor, perm, rec, base);
 }
 
 // Exclusive scan of n values in three launches: per-block scans of 2048

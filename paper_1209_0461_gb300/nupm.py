@@ -96,6 +96,12 @@ def lib():
         "pm_set_power": (C.c_int, [vp, dp, dp, dp]),
         "pm_autotune": (C.c_int, [vp, vp, vp, d, dp, vp, i32, i32, C.POINTER(C.c_int32)]),
         "pm_set_tuning": (C.c_int, [vp, C.POINTER(C.c_int32)]),
+        "pm_batch_create": (C.c_int, [C.POINTER(vp), i32, vp, C.POINTER(vp)]),
+        "pm_batch_kick": (C.c_int, [vp, C.POINTER(vp), C.POINTER(vp), dp, dp, C.POINTER(dp), C.POINTER(vp),
+                                    C.POINTER(C.c_int32)]),
+        "pm_batch_launches": (i64, [vp]),
+        "pm_batch_last_error": (C.c_char_p, [vp]),
+        "pm_batch_free": (None, [vp]),
         "pm_graph_begin": (C.c_int, [vp]),
         "pm_graph_end": (C.c_int, [vp, C.POINTER(vp)]),
         "pm_graph_launch": (C.c_int, [vp, vp]),
@@ -553,3 +559,54 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class BatchPM:
+    """pm_batch: contexts of one grid size kicked together, one persistent
+    kernel per pass over all boxes (work taken from an atomic counter)."""
+
+    def __init__(self, contexts, stream=None):
+        import torch
+        self.contexts = list(contexts)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (C.c_void_p * len(self.contexts))(*[pm.ctx.value for pm in self.contexts])
+        out = C.c_void_p()
+        rc = lib().pm_batch_create(arr, len(self.contexts), C.c_void_p(self.stream.cuda_stream), C.byref(out))
+        if rc != PM_OK:
+            raise PMError(rc, "pm_batch_create failed (see stderr)")
+        self.b = out
+
+    def launches(self):
+        return int(lib().pm_batch_launches(self.b))
+
+    def kick(self, pos, vel, a, kick_factor, a_hist=None, sqrtPM_hist=None):
+        """pos, vel: lists of CUDA tensors (one per box); a, kick_factor: per box;
+        a_hist: list of host arrays (or None); sqrtPM_hist: list of CUDA float64
+        [n, n_kbins] tensors (or None)."""
+        nb = len(self.contexts)
+        vp = C.c_void_p
+        P = (vp * nb)(*[C.c_void_p(t.data_ptr()) for t in pos])
+        V = (vp * nb)(*[C.c_void_p(t.data_ptr()) for t in vel])
+        A = np.ascontiguousarray(a, dtype=np.float64)
+        K = np.ascontiguousarray(kick_factor, dtype=np.float64)
+        keep = []
+        ah_p = (C.POINTER(C.c_double) * nb)()
+        h_p = (vp * nb)()
+        nh = (C.c_int32 * nb)()
+        for i in range(nb):
+            ah = None if a_hist is None else a_hist[i]
+            if ah is not None and len(ah):
+                arr = np.ascontiguousarray(ah, dtype=np.float64)
+                keep.append(arr)
+                ah_p[i] = arr.ctypes.data_as(C.POINTER(C.c_double))
+                h_p[i] = C.c_void_p(sqrtPM_hist[i].data_ptr())
+                nh[i] = len(arr)
+        self._keep = keep          # host arrays stay alive (and unchanged) for a captured graph
+        rc = lib().pm_batch_kick(self.b, P, V, _dptr(A), _dptr(K), ah_p, h_p, nh)
+        if rc != PM_OK:
+            raise PMError(rc, lib().pm_batch_last_error(self.b).decode())
+
+    def close(self):
+        if self.b:
+            lib().pm_batch_free(self.b)
+            self.b = None

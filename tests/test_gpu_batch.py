@@ -64,3 +64,45 @@ def test_tuning_does_not_change_results():
         b.close()
     for d0, d1 in zip(*out):
         assert np.array_equal(d0, d1)
+
+
+def test_persistent_batch_matches_direct_kicks_and_graphs_to_few_nodes():
+    # six boxes of 64^3, 128^3 and 192^3 (two each; neutrino masses 0 .. 0.6 eV):
+    # one pm_batch per grid size, each pass one persistent kernel over its boxes
+    boxes = synth.batched_boxes(6, n_hist=8, n_kbins=32)
+    direct = batch.Batch(boxes, n_streams=1, autotune=False)
+    direct.eager_step()
+    direct.check()
+    ref = _dv(direct)
+    ref_bins = [it["pm"].bins() for it in direct.items]
+    direct.close()
+    b = batch.Batch(boxes, persistent=True)
+    assert len(b.groups) == 3
+    b.eager_step()
+    b.check()
+    got = _dv(b)
+    for d0, d1, it, rb in zip(ref, got, b.items, ref_bins):
+        scale = np.abs(d0).max()
+        rms = np.sqrt(((d1 - d0) ** 2).mean()) / np.sqrt((d0 ** 2).mean())
+        print(f"box N={it['w'].ngrid} M_nu={it['w'].m_nu_total}: max {np.abs(d1 - d0).max() / scale:.2e}, rms {rms:.2e}")
+        assert np.abs(d1 - d0).max() <= 1e-5 * scale and rms <= 1e-6
+        cnt, ks, ps = it["pm"].bins()
+        assert np.array_equal(cnt, rb[0]) and np.allclose(ps, rb[2], rtol=1e-6, atol=0)
+    # the captured step: a few launches per grid size, bit for bit the eager step
+    per_step = b.launches_per_step()
+    assert per_step <= 3 * 17
+    b.reset_velocities()
+    g = b.capture()
+    assert g.nodes() <= per_step + 3 * 6 + 8
+    b.reset_velocities()
+    b.step()
+    b.check()
+    again = _dv(b)
+    for d1, d2 in zip(got, again):
+        assert np.array_equal(d1, d2)
+    b.step()
+    b.check()
+    two = _dv(b)
+    for d1, d2 in zip(got, two):
+        assert np.allclose(d2, 2 * d1, rtol=1e-5, atol=1e-6 * np.abs(d1).max())
+    b.close()
