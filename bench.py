@@ -472,7 +472,7 @@ def run_gpu(args, w, rank, world):
 
 # ------------------------------------------------------------------ other forms
 def _kick_form(w, pos64, vel64, precision, steps, warmup, mlp=None, keep_acc=True, stages_out=None,
-               tuning_out=None):
+               tuning_out=None, autotune=True):
     """Time `steps` kicks of workload w (inputs resident) in the given
     precision, exact or surrogate response, after pm_autotune (as the main
     measurement; the exact response's panels prepared beside the deposit).
@@ -495,7 +495,7 @@ def _kick_form(w, pos64, vel64, precision, steps, warmup, mlp=None, keep_acc=Tru
     a = w.a_kick
     K = pm.kick_factor(a, a * 1.01)
     acc = torch.empty_like(vel) if keep_acc else None
-    tuned = pm.autotune(pos, vel, a, a_hist, hist_d, reps=1)   # kick factor 0: velocities unchanged
+    tuned = pm.autotune(pos, vel, a, a_hist, hist_d, reps=1) if autotune else []  # kick factor 0
     if tuning_out is not None:
         tuning_out.extend(tuned)
 
@@ -589,13 +589,14 @@ def run_batched(steps=10, warmup=3):
     from paper_1209_0461_gb300 import batch
     boxes = synth.batched_boxes(32)
 
-    def timed(fn, n):
+    def timed(fn, n, stream):
+        # events on the stream the step is issued on (the batch's main stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        e0.record()
+        e0.record(stream)
         for _ in range(n):
             fn()
-        e1.record()
+        e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / n
 
@@ -624,7 +625,7 @@ def run_batched(steps=10, warmup=3):
         dv[name] = [(it["vel"] - it["vel0"]).double() for it in b.items]
         for _ in range(warmup):
             step()
-        ms = timed(step, steps)
+        ms = timed(step, steps, b.main)
         b.check()
         out[name] = {"ms_per_step": round(ms, 3), "kicks_per_s": b.npart / (ms / 1e3)}
         b.close()
@@ -697,6 +698,12 @@ def run_forms(steps=3, warmup=1):
                                 "fp32_force_rms_rel_vs_fp64_gpu": _rms_rel(a32, a64)}
         del a64, a32, p2
         torch.cuda.empty_cache()
+    # the FP64 kick at 32^3 / 32^3 (launch-bound: a few microseconds of work a pass)
+    w1 = synth.WORKLOADS["pm32_fp64"]
+    p1 = synth.particles(w1)
+    m1, r1, _ = _kick_form(w1, p1["pos64"], p1["vel"], "fp64", 50, 5, keep_acc=False, autotune=False)
+    out["config1"] = {"pm32_fp64": {"fp64_ms_per_kick": round(m1, 4), "kicks_per_s": w1.npart / (m1 / 1e3),
+                                    "response_ms": round(r1, 4)}}
     # contention variant: the same workload with the particles at their a = 1
     # Zel'dovich positions (clustered), reported separately
     wc = synth.with_(w, clustered=True)

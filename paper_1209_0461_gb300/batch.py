@@ -99,8 +99,18 @@ class Batch:
                 ev.record(g["stream"])
                 self.main.wait_event(ev)
             return
+        # per box, on the contexts' streams, forked from and joined to the main stream
+        import torch
+        fork = torch.cuda.Event()
+        fork.record(self.main)
+        for st in self.streams:
+            st.wait_event(fork)
         for it in self.items:
             self._kick(it)
+        for st in self.streams:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            self.main.wait_event(ev)
 
     def capture(self):
         """Record one step of every box into a CUDA graph (after a warm-up step)."""

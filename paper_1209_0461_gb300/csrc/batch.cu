@@ -177,16 +177,12 @@ struct PBins {
   }
 };
 
-// psum of each bin: the partials rows summed in row order.
+// psum of each bin: the partials rows summed in a fixed order (32 bins an item).
 struct PBinReduce {
-  static constexpr int THREADS = kFinishGroup;
+  static constexpr int THREADS = kReduceWarps * 32;
   static constexpr size_t SMEM = 0;
   __device__ static void run(const BoxArgs& b, int item) {
-    const int i = item * kFinishGroup + threadIdx.x;
-    if (i >= b.nu.nk) return;
-    double s = 0.0;
-    for (int k = 0; k < b.bin_chunks; ++k) s += b.partials[(int64_t)k * b.nu.nk + i];
-    b.psum[i] = s;
+    bin_reduce_group(b.partials, b.bin_chunks, b.nu.nk, b.psum, item * 32);
   }
 };
 
@@ -283,7 +279,13 @@ void launch_pass(const BatchPlan& p, int pass, size_t smem, cudaStream_t s) {
 }
 
 template <int N>
-void batch_kick_n(const BatchPlan& p, cudaStream_t s) {
+void batch_kick_n(const BatchPlan& p, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
+  // the response panels read the bins' lattice |k| sums and the history only:
+  // they run on the side stream beside the deposit and the transforms
+  cudaEventRecord(ev_fork, s);
+  cudaStreamWaitEvent(side, ev_fork, 0);
+  launch_pass<PPanels>(p, kBpPanels, 0, side);
+  cudaEventRecord(ev_join, side);
   launch_pass<PCount>(p, kBpCount, 0, s);
   launch_pass<PScan>(p, kBpScan, 0, s);
   launch_pass<PScatter>(p, kBpScatter, 0, s);
@@ -292,7 +294,7 @@ void batch_kick_n(const BatchPlan& p, cudaStream_t s) {
   launch_pass<PCol<N, -1, true, false>>(p, kBpZ, PCol<N, -1, true, false>::SMEM, s);
   launch_pass<PBins>(p, kBpBins, kBinWarps * (size_t)p.nk * sizeof(double) + (size_t)(p.nk + 1) * sizeof(int), s);
   launch_pass<PBinReduce>(p, kBpBinReduce, 0, s);
-  launch_pass<PPanels>(p, kBpPanels, 0, s);
+  cudaStreamWaitEvent(s, ev_join, 0);
   launch_pass<PFinish>(p, kBpFinish, 0, s);
   launch_pass<PRlist>(p, kBpRlist, 0, s);
   launch_pass<PFac>(p, kBpFac, 2 * (size_t)p.nk * sizeof(double), s);
@@ -339,7 +341,7 @@ void batch_items(int n, int64_t np, int nk, int ns, int bin_chunks, int* items) 
   items[kBpDeposit] = (n / FusedCfg<T, 64>::TY) * (n / FusedCfg<T, 64>::TZ);
   items[kBpY] = items[kBpZ] = items[kBpZInv] = items[kBpYInv] = (m / col_width(n)) * n;
   items[kBpBins] = bin_chunks;
-  items[kBpBinReduce] = (nk + kFinishGroup - 1) / kFinishGroup;
+  items[kBpBinReduce] = (nk + 31) / 32;
   items[kBpPanels] = (nk * ns * kNuChunks + 3) / 4;
   items[kBpFinish] = (nk + kFinishGroup - 1) / kFinishGroup;
   items[kBpRlist] = 1;
@@ -349,14 +351,14 @@ void batch_items(int n, int64_t np, int nk, int ns, int bin_chunks, int* items) 
   items[kBpGather] = (int)((np + (int64_t)kGatherTPB * kGatherChunk - 1) / ((int64_t)kGatherTPB * kGatherChunk));
 }
 
-int batch_kick(const BatchPlan& p, cudaStream_t s) {
+int batch_kick(const BatchPlan& p, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
   switch (p.n) {
-    case 16: batch_kick_n<16>(p, s); break;
-    case 32: batch_kick_n<32>(p, s); break;
-    case 64: batch_kick_n<64>(p, s); break;
-    case 128: batch_kick_n<128>(p, s); break;
-    case 192: batch_kick_n<192>(p, s); break;
-    case 256: batch_kick_n<256>(p, s); break;
+    case 16: batch_kick_n<16>(p, s, side, ev_fork, ev_join); break;
+    case 32: batch_kick_n<32>(p, s, side, ev_fork, ev_join); break;
+    case 64: batch_kick_n<64>(p, s, side, ev_fork, ev_join); break;
+    case 128: batch_kick_n<128>(p, s, side, ev_fork, ev_join); break;
+    case 192: batch_kick_n<192>(p, s, side, ev_fork, ev_join); break;
+    case 256: batch_kick_n<256>(p, s, side, ev_fork, ev_join); break;
     default: return PM_ERR_UNSUPPORTED;
   }
   return PM_OK;

@@ -339,7 +339,7 @@ int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const int* thr, float
       k_bin_power<T, false><<<nblk, kBinWarps * 32, sh, s>>>(spec, g.n, nk, thr, inv_lr, kf, partials);
     }
   }
-  k_bin_reduce<<<(nv * nk + 127) / 128, 128, 0, s>>>(partials, nblk, nv * nk, out);
+  k_bin_reduce<<<(nv * nk + 31) / 32, 1024, 0, s>>>(partials, nblk, nv * nk, out);
   return PM_OK;
 }
 
@@ -398,6 +398,14 @@ int NUPM_FN(xinv_interp)(const GridArgs& g, const void* pos, void* vel, double k
 }
 
 int NUPM_FN(drift)(const GridArgs& g, void* pos, const void* vel, double ds, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (g.np > 0 && (g.np & 3) == 0 && ((uintptr_t)pos & 15) == 0 && ((uintptr_t)vel & 15) == 0) {
+      k_drift4<<<grid_blocks(g.np / 4, 256, 8), 256, 0, s>>>(reinterpret_cast<int32_t*>(pos),
+                                                             reinterpret_cast<const float*>(vel), g.np, g.n,
+                                                             (float)(ds / g.delta), g.status);
+      return PM_OK;
+    }
+  }
   if (g.np > 0)
     k_drift<T><<<grid_blocks(g.np, 256, 8), 256, 0, s>>>(pos, reinterpret_cast<const T*>(vel), g.np, g.n, g.box, ds,
                                                           (float)(ds / g.delta), g.status);

@@ -359,4 +359,26 @@ __device__ __forceinline__ void fac_table_entries(float* __restrict__ fac, doubl
   }
 }
 
+// Outputs i0 .. i0 + 31 of out[i] = sum_blk partials[blk][i], blk < nblk: warp w
+// adds rows w, w + kReduceWarps, ... for lane i0 + lane (coalesced), then one
+// warp adds the kReduceWarps warp sums in warp order -- a fixed order, so the
+// result is the same at every run.  blockDim = kReduceWarps * 32.
+constexpr int kReduceWarps = 32;
+__device__ __forceinline__ void bin_reduce_group(const double* __restrict__ partials, int nblk, int len,
+                                                 double* __restrict__ out, int i0) {
+  __shared__ double red[kReduceWarps][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = i0 + lane;
+  double acc = 0.0;
+  if (i < len)
+    for (int b = warp; b < nblk; b += kReduceWarps) acc += partials[(int64_t)b * len + i];
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kReduceWarps; ++w) s += red[w][lane];
+    if (i < len) out[i] = s;
+  }
+}
+
 }  // namespace nupm

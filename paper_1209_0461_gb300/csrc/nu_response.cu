@@ -29,14 +29,11 @@ __global__ void k_nu_panels(NuArgs A) { nu_panels_item(A, blockIdx.x * 4 + (thre
 
 __global__ void k_nu_finish(NuArgs A) { nu_finish_bin(A, blockIdx.x * blockDim.x + threadIdx.x); }
 
-// Fixed-order sum of the per-CTA bin partials: out[i] = sum_blk partials[blk][i].
-__global__ void k_bin_reduce(const double* __restrict__ partials, int nblk, int len,
-                             double* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= len) return;
-  double acc = 0.0;
-  for (int b = 0; b < nblk; ++b) acc += partials[(int64_t)b * len + i];
-  out[i] = acc;
+// Fixed-order sum of the per-CTA bin partials: out[i] = sum_blk partials[blk][i]
+// (bin_reduce_group: a CTA of kReduceWarps warps, 32 outputs).
+__global__ void __launch_bounds__(kReduceWarps * 32) k_bin_reduce(const double* __restrict__ partials, int nblk,
+                                                                 int len, double* __restrict__ out) {
+  bin_reduce_group(partials, nblk, len, out, blockIdx.x * 32);
 }
 
 __global__ void k_nu_rlist(const double* __restrict__ bins, const double* __restrict__ R, int nk,

@@ -219,9 +219,12 @@ struct BatchPlan {
 // species, bin_chunks partials rows); the grid sizes the batch supports.
 void batch_items(int n, int64_t np, int nk, int ns, int bin_chunks, int* items);
 bool batch_supported(int n);
-int batch_kick(const BatchPlan& p, cudaStream_t s);
+// The kick's passes on stream s; the response panels on `side`, forked after
+// the staging copies (ev_fork) and joined before the finish (ev_join).
+int batch_kick(const BatchPlan& p, cudaStream_t s, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join);
 
-// out[i] = sum over blocks of partials[blk][i], i < len, in block order.
+// out[i] = sum over blocks of partials[blk][i], i < len, in a fixed order
+// (grid ceil(len / 32), 1024 threads).
 __global__ void k_bin_reduce(const double* __restrict__ partials, int nblk, int len,
                              double* __restrict__ out);
 

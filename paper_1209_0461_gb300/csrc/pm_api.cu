@@ -1640,6 +1640,8 @@ struct pm_batch {
   double* h_hist_u[2] = {nullptr, nullptr};
   cudaEvent_t ev_staged = nullptr;
   bool staged_pending = false;
+  cudaStream_t side = nullptr;             // the response panels beside the grid passes
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
 };
 
@@ -1698,6 +1700,9 @@ int pm_batch_create(pm_ctx* const* ctxs, int32_t nbox, void* cuda_stream, pm_bat
     if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_hist_u[k], (size_t)nbox * B->hist_stride * sizeof(double));
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_staged, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking);
   if (e == cudaSuccess)
     e = cudaMemcpy(B->d_first, B->first.data(), B->first.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
@@ -1810,7 +1815,7 @@ int pm_batch_kick(pm_batch* B, const void* const* pos, void* const* vel, const d
     B->err = std::string("pm_batch_kick: ") + cudaGetErrorString(e);
     return PM_ERR_CUDA;
   }
-  int rc = batch_kick(B->plan, B->stream);
+  int rc = batch_kick(B->plan, B->stream, B->side, B->ev_fork, B->ev_join);
   if (rc != PM_OK) return B->err = "pm_batch_kick: unsupported grid", rc;
   e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -1851,7 +1856,11 @@ void pm_batch_free(pm_batch* B) {
     if (B->h_boxes[k]) cudaFreeHost(B->h_boxes[k]);
     if (B->h_hist_u[k]) cudaFreeHost(B->h_hist_u[k]);
   }
+  if (B->side) cudaStreamSynchronize(B->side);
   if (B->ev_staged) cudaEventDestroy(B->ev_staged);
+  if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+  if (B->ev_join) cudaEventDestroy(B->ev_join);
+  if (B->side) cudaStreamDestroy(B->side);
   delete B;
 }
 
