@@ -41,6 +41,23 @@ __global__ void k_nu_rlist(const double* __restrict__ bins, const double* __rest
   nu_rlist_block(bins, R, nk, rlist);
 }
 
+// Chebyshev pieces of I(x) (nu_I_table): block s evaluates the exact I at the
+// kICoef points x_s + kIH (1 + cos(pi (j + 1/2) / kICoef)) / 2 and transforms
+// them to c_k = (2 / kICoef) sum_j I_j cos(pi k (j + 1/2) / kICoef), c_0 halved.
+__global__ void k_I_table(double* __restrict__ coef) {
+  __shared__ double f[kICoef];
+  const int s = blockIdx.x, j = threadIdx.x;
+  const double t = cospi((j + 0.5) / kICoef);
+  f[j] = nu_I_exact(kIX0 + kIH * s + 0.5 * kIH * (t + 1.0));
+  __syncthreads();
+  double c = 0.0;
+  for (int i = 0; i < kICoef; ++i) c += f[i] * cospi((double)j * (i + 0.5) / kICoef);
+  c *= 2.0 / kICoef;
+  coef[s * kICoef + j] = j == 0 ? 0.5 * c : c;
+}
+
+void launch_I_table(double* coef, cudaStream_t s) { k_I_table<<<kISeg, kICoef, 0, s>>>(coef); }
+
 void launch_nu_panels(const NuArgs& a, cudaStream_t s) {
   const int items = a.nk * a.ns * kNuChunks;
   if (items > 0) k_nu_panels<<<(items + 3) / 4, 128, 0, s>>>(a);

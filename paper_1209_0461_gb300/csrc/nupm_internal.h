@@ -71,6 +71,12 @@ __host__ __device__ inline double rel_e2(double a, const RelBackground& B) {
   return e;
 }
 
+// I(x) on [kIX0, kIX0 + kISeg kIH) as kISeg Chebyshev pieces of kICoef terms,
+// built once per context on the device from the exact I (launch_I_table).
+constexpr double kIX0 = 0.5, kIH = 0.25;
+constexpr int kISeg = 94, kICoef = 12;
+void launch_I_table(double* coef, cudaStream_t s);
+
 // Device inputs of the response kernels (one struct, passed by value).
 struct NuArgs {
   int nk, ns, n_hist, quad, iters, use_fit, ngrid;
@@ -88,6 +94,7 @@ struct NuArgs {
   int n_stab;
   double stab_u0, stab_inv_h, stab_h;
   const double* gl;               // [2][quad] nodes, weights on [-1, 1]
+  const double* icheb;            // [kISeg][kICoef] Chebyshev pieces of I(x)
   double* parts;                  // [ns][nk][kNuChunks][3] IC, J_hist, W_cur per panel chunk
   double* rlist;                  // [2 nk + 1]: ln k_b and R_b of the non-empty bins, then their count
   double* R;                      // [nk]

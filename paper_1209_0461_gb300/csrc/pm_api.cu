@@ -91,6 +91,7 @@ struct pm_ctx {
   bool rel = false;
   RelBackground bg{};
   double* d_rtab = nullptr;
+  double* d_icheb = nullptr;           // Chebyshev pieces of I(x)
   // history owned by the context (pm_history_set, pm_step): P_M^{1/2} rows and
   // their scale factors, and P_nu^{1/2} of the last step (two buffers, swapped)
   double* d_hist_own = nullptr;        // [n_hist_max][nk]
@@ -499,7 +500,7 @@ void release(pm_ctx* c) {
                   c->spec, c->g, c->tw_n, c->tw_m, c->d_thr, c->d_partials, c->d_bins, c->d_pi, c->d_ti,
                   c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_rlist, c->d_gtab,
                   c->d_dtab, c->d_wtab, c->d_plane0, c->d_fac, c->d_rowc, c->d_rows, c->d_rowcur,
-                  c->d_scantot, c->d_perm, c->d_rec, c->d_status, c->d_hist_u2, c->d_rtab, c->d_hist_own,
+                  c->d_scantot, c->d_perm, c->d_rec, c->d_status, c->d_hist_u2, c->d_rtab, c->d_icheb, c->d_hist_own,
                   c->d_prev[0], c->d_prev[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -744,6 +745,13 @@ int pm_init(const pm_params* params, const double* sqrtPnu_init, const double* t
                 "stored history");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_prev[0], (size_t)c->nk * sizeof(double), "previous P_nu");
   if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_prev[1], (size_t)c->nk * sizeof(double), "previous P_nu");
+  if (rc == PM_OK) rc = dalloc(c, (void**)&c->d_icheb, (size_t)kISeg * kICoef * sizeof(double), "I(x) table");
+  if (rc == PM_OK) {
+    launch_I_table(c->d_icheb, c->stream);
+    rc = cuda_check(c, cudaGetLastError(), "I(x) table");
+    // other streams (the side stream, batched kicks) read it without an event
+    if (rc == PM_OK) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "I(x) table");
+  }
   if (rc == PM_OK && c->rel) {
     rc = dalloc(c, (void**)&c->d_rtab, 2 * (size_t)kRelN * sizeof(double), "relativistic background table");
     if (rc == PM_OK)
@@ -993,6 +1001,7 @@ NuArgs nu_args(pm_ctx* c, double a, const double* sqrtPM_hist, int32_t n_hist, c
   A.stab_h = c->stab_h;
   A.stab_inv_h = 1.0 / c->stab_h;
   A.gl = c->d_gl;
+  A.icheb = c->d_icheb;
   A.parts = c->d_parts;
   A.rlist = c->d_rlist;
   A.R = c->d_R;
