@@ -3,10 +3,11 @@
 Each box is its own context (grid 64^3, 128^3 or 192^3, its own seed and
 neutrino mass).  Two ways to step them:
 
-* persistent (default): the boxes of each grid size form one pm_batch, whose
-  kick is one persistent kernel per pass over all of its boxes (CTAs take
-  (box, item) work from an atomic counter); the sizes run on their own
-  streams, and one capture records the few launches of every size;
+* persistent: the boxes of each grid size form `split` pm_batches
+  (round robin), each kick one persistent kernel per pass over the batch's
+  boxes (CTAs take (box, item) work from an atomic counter); every batch runs
+  on its own stream, so that different passes (a gather beside a transform)
+  share the GPU, and one capture records the few launches of every batch;
 * per box: the boxes are spread over a few CUDA streams and one capture
   records every box's response panels, deposit, response and kick (each grid
   size autotuned once with pm_autotune).
@@ -22,7 +23,7 @@ from . import nupm, synth
 
 class Batch:
     def __init__(self, boxes, n_streams: int = 8, autotune: bool = True, precision: str = "fp32",
-                 persistent: bool = False):
+                 persistent: bool = False, split: int = 2):
         import torch
         self.boxes = list(boxes)
         self.persistent = persistent and precision == "fp32"
@@ -52,12 +53,15 @@ class Batch:
         torch.cuda.synchronize()
         self.groups = []
         if self.persistent:
-            # one pm_batch per grid size, each on its own stream
+            # `split` pm_batches per grid size, each on its own stream
             sizes = sorted({it["w"].ngrid for it in self.items})
             for n in sizes:
-                its = [it for it in self.items if it["w"].ngrid == n]
-                st = torch.cuda.Stream()
-                self.groups.append(dict(items=its, stream=st, batch=nupm.BatchPM([it["pm"] for it in its], st)))
+                its_n = [it for it in self.items if it["w"].ngrid == n]
+                for j in range(max(1, min(split, len(its_n)))):
+                    its = its_n[j::max(1, min(split, len(its_n)))]
+                    st = torch.cuda.Stream()
+                    self.groups.append(dict(items=its, stream=st,
+                                            batch=nupm.BatchPM([it["pm"] for it in its], st)))
             autotune = False
         if autotune:
             for it in self.items:

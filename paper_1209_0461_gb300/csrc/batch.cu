@@ -14,6 +14,7 @@
 //   next kick), row scatter, deposit + x, y, z, bin sums + their fixed-order
 //   reduction, response panels, finish, bin list, fac table, Green plane,
 //   Green + z inverse, y inverse, x inverse, gather + kick.
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
@@ -28,7 +29,8 @@ namespace {
 using T = float;
 using C = cx<float>;
 
-constexpr int kSortChunk = 256 * kSortBatch;   // particles per row-sort item (a CTA of 256)
+constexpr int kSortSteps = 4;                  // warp batches per row-sort item and warp
+constexpr int kSortChunk = 256 * kSortBatch * kSortSteps;   // particles per row-sort item (a CTA of 256)
 constexpr int kFinishGroup = 128;               // bins per finish item
 constexpr int kFacGroup = 256;                  // fac-table entries per item
 constexpr int kPlaneGroup = 256;                // Green-plane entries per item
@@ -63,14 +65,19 @@ struct PCount {
   static constexpr int THREADS = 256;
   static constexpr size_t SMEM = 0;
   __device__ static void run(const BoxArgs& b, int item) {
-    const int64_t base = (int64_t)item * kSortChunk + (threadIdx.x & ~31) * kSortBatch;
-    if (base < b.g.np) row_count_warp<T>(b.pos, b.g.np, b.g.n, b.g.delta, b.g.row_count, b.g.status, base);
+#pragma unroll 1
+    for (int k = 0; k < kSortSteps; ++k) {
+      const int64_t base = (int64_t)item * kSortChunk + (k * 256 + (threadIdx.x & ~31)) * kSortBatch;
+      if (base < b.g.np) row_count_warp<T>(b.pos, b.g.np, b.g.n, b.g.delta, b.g.row_count, b.g.status, base);
+    }
   }
 };
 
 // Exclusive scan of the box's N^2 + 1 row counts into row_start and
-// row_cursor by one CTA, 4 values a thread per round with a carried offset;
-// the counts are cleared for the next kick.
+// row_cursor by one CTA, kScanPer consecutive values a thread per round
+// (16-byte loads and stores) with a carried offset; the counts are cleared
+// for the next kick.
+constexpr int kScanPer = 16;
 struct PScan {
   static constexpr int THREADS = kScanThreads;
   static constexpr size_t SMEM = 0;
@@ -81,14 +88,25 @@ struct PScan {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) carry_s = 0;
     __syncthreads();
-    for (int r0 = 0; r0 < len; r0 += 4 * kScanThreads) {
-      int v[4], s = 0;
+    for (int r0 = 0; r0 < len; r0 += kScanPer * kScanThreads) {
+      const int i0 = r0 + kScanPer * tid;
+      const bool whole = i0 + kScanPer <= len;   // i0 is a multiple of 16: 16-byte aligned
+      int v[kScanPer], s = 0;
+      if (whole) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int i = r0 + 4 * tid + k;
-        v[k] = i < len ? b.g.row_count[i] : 0;
-        s += v[k];
+        for (int q = 0; q < kScanPer / 4; ++q) {
+          const int4 x = reinterpret_cast<const int4*>(b.g.row_count + i0)[q];
+          v[4 * q] = x.x;
+          v[4 * q + 1] = x.y;
+          v[4 * q + 2] = x.z;
+          v[4 * q + 3] = x.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) v[k] = i0 + k < len ? b.g.row_count[i0 + k] : 0;
       }
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k) s += v[k];
       int incl = s;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
@@ -109,15 +127,28 @@ struct PScan {
       }
       __syncthreads();
       int e = carry_s + wsum[warp] + incl - s;
+      int ex[kScanPer];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int i = r0 + 4 * tid + k;
-        if (i < len) {
-          b.g.row_start[i] = e;
-          b.g.row_cursor[i] = e;
-          b.g.row_count[i] = 0;
-        }
+      for (int k = 0; k < kScanPer; ++k) {
+        ex[k] = e;
         e += v[k];
+      }
+      if (whole) {
+#pragma unroll
+        for (int q = 0; q < kScanPer / 4; ++q) {
+          const int4 x = make_int4(ex[4 * q], ex[4 * q + 1], ex[4 * q + 2], ex[4 * q + 3]);
+          reinterpret_cast<int4*>(b.g.row_start + i0)[q] = x;
+          reinterpret_cast<int4*>(b.g.row_cursor + i0)[q] = x;
+          reinterpret_cast<int4*>(b.g.row_count + i0)[q] = make_int4(0, 0, 0, 0);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k)
+          if (i0 + k < len) {
+            b.g.row_start[i0 + k] = ex[k];
+            b.g.row_cursor[i0 + k] = ex[k];
+            b.g.row_count[i0 + k] = 0;
+          }
       }
       __syncthreads();   // every thread has read carry_s
       if (tid == kScanThreads - 1) carry_s = e;
@@ -130,9 +161,12 @@ struct PScatter {
   static constexpr int THREADS = 256;
   static constexpr size_t SMEM = 0;
   __device__ static void run(const BoxArgs& b, int item) {
-    const int64_t base = (int64_t)item * kSortChunk + (threadIdx.x & ~31) * kSortBatch;
-    if (base < b.g.np)
-      row_scatter_warp<T>(b.pos, b.g.np, b.g.n, b.g.delta, b.g.row_cursor, b.g.perm, b.g.rec, base);
+#pragma unroll 1
+    for (int k = 0; k < kSortSteps; ++k) {
+      const int64_t base = (int64_t)item * kSortChunk + (k * 256 + (threadIdx.x & ~31)) * kSortBatch;
+      if (base < b.g.np)
+        row_scatter_warp<T>(b.pos, b.g.np, b.g.n, b.g.delta, b.g.row_cursor, b.g.perm, b.g.rec, base);
+    }
   }
 };
 
@@ -186,9 +220,13 @@ struct PBinReduce {
   }
 };
 
+// On the side stream: two CTAs per SM at most, so that the passes of the main
+// stream keep the rest of each SM (a full-occupancy persistent launch would
+// hold every slot until the panels are done and starve them).
 struct PPanels {
   static constexpr int THREADS = 128;
   static constexpr size_t SMEM = 0;
+  static constexpr int CTAS_PER_SM = 2;
   __device__ static void run(const BoxArgs& b, int item) { nu_panels_item(b.nu, item * 4 + (threadIdx.x >> 5)); }
 };
 
@@ -261,10 +299,21 @@ struct PGather {
 };
 
 // ---- host side ----
-int occupancy_grid(const void* kern, int threads, size_t smem, int sms, int items) {
+// CTAs per SM of a pass: its CTAS_PER_SM where it sets one, else occupancy
+template <class P, class = void>
+struct CtaCap {
+  static constexpr int v = 0;
+};
+template <class P>
+struct CtaCap<P, std::void_t<decltype(P::CTAS_PER_SM)>> {
+  static constexpr int v = P::CTAS_PER_SM;
+};
+
+int occupancy_grid(const void* kern, int threads, size_t smem, int sms, int items, int cap) {
   int o = 0;
   if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, threads, smem);
+  if (cap > 0 && o > cap) o = cap;
   const int g = (o < 1 ? 1 : o) * sms;
   return items < g ? (items < 1 ? 1 : items) : g;
 }
@@ -273,7 +322,7 @@ template <class Pass>
 void launch_pass(const BatchPlan& p, int pass, size_t smem, cudaStream_t s) {
   const int items = p.h_first[(size_t)pass * (p.nbox + 1) + p.nbox];
   if (items <= 0) return;
-  const int grid = occupancy_grid((const void*)k_batch<Pass>, Pass::THREADS, smem, p.sm_count, items);
+  const int grid = occupancy_grid((const void*)k_batch<Pass>, Pass::THREADS, smem, p.sm_count, items, CtaCap<Pass>::v);
   k_batch<Pass><<<grid, Pass::THREADS, smem, s>>>(p.d_boxes, p.d_first + (size_t)pass * (p.nbox + 1), p.nbox,
                                                   p.d_counters + pass);
 }

@@ -166,6 +166,7 @@ __device__ __forceinline__ void nu_panels_item(const NuArgs& A, int item) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (item >= A.nk * A.ns * kNuChunks) return;
   const int chunk = item % kNuChunks;
+  if (chunk >= A.nchunks) return;        // unused chunk: nothing written, nothing read
   const int bs = item / kNuChunks;
   const int b = bs % A.nk, s = bs / A.nk;
   double* out = A.parts + (int64_t)item * 3;
@@ -215,7 +216,7 @@ __device__ __forceinline__ void nu_panels_item(const NuArgs& A, int item) {
   const int np = npan[warp];
   const int Q = A.quad;
   double jh = 0.0, wc = 0.0;
-  for (int pi = chunk * 32 + lane; pi < np; pi += 32 * kNuChunks) {
+  for (int pi = chunk * 32 + lane; pi < np; pi += 32 * A.nchunks) {
     const Panel pn = P[pi];
     if (!(pn.hi > pn.lo)) continue;
     const double half = 0.5 * (pn.hi - pn.lo);
@@ -300,7 +301,7 @@ __device__ __forceinline__ void nu_finish_bin(const NuArgs& A, int b) {
     double ic = 0.0, jh = 0.0, wc = 0.0, guess = 0.0;
     for (int s = 0; s < A.ns; ++s) {
       double qi = 0.0, qj = 0.0, qw = 0.0;
-      for (int ch = 0; ch < kNuChunks; ++ch) {   // fixed chunk order
+      for (int ch = 0; ch < A.nchunks; ++ch) {   // fixed chunk order
         const double* q = A.parts + (((int64_t)s * A.nk + b) * kNuChunks + ch) * 3;
         qi += q[0];
         qj += q[1];

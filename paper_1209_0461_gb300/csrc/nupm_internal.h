@@ -96,6 +96,7 @@ struct NuArgs {
   const double* gl;               // [2][quad] nodes, weights on [-1, 1]
   const double* icheb;            // [kISeg][kICoef] Chebyshev pieces of I(x)
   double* parts;                  // [ns][nk][kNuChunks][3] IC, J_hist, W_cur per panel chunk
+  int nchunks;                    // chunks in use (<= kNuChunks), from a bound on the panel count
   double* rlist;                  // [2 nk + 1]: ln k_b and R_b of the non-empty bins, then their count
   double* R;                      // [nk]
   double* pnu;                    // [nk]

@@ -1002,6 +1002,23 @@ NuArgs nu_args(pm_ctx* c, double a, const double* sqrtPM_hist, int32_t n_hist, c
   A.stab_inv_h = 1.0 / c->stab_h;
   A.gl = c->d_gl;
   A.icheb = c->d_icheb;
+  // panel chunks in use: the panels are the history nodes, the graded points
+  // a - ell 2^m (m >= -2) above a_i, at most log2((ln a - ln a_i) / ell) + 3 of
+  // them with ell = a^2 H / kappa smallest at the largest |k| of the grid, and
+  // the ends; 32 panels a chunk.  A chunk's warp strides over the panels by the
+  // chunk count, so the bound sets the split of the work, not which panels count.
+  {
+    double kap = 0.0;
+    for (int s = 0; s < c->ns; ++s) kap = A.kappa_scale[s] > kap ? A.kappa_scale[s] : kap;
+    kap *= c->kf * sqrt(3.0) * 0.5 * c->n;
+    int npan = (n_hist > 0 ? n_hist : 0) + 4;
+    if (kap > 0.0 && A.ue > A.ui) {
+      const double r = (A.ue - A.ui) * kap / (a * a * hubble(c, a));
+      npan += 3 + (r > 1.0 ? (int)ceil(log2(r)) : 0);
+    }
+    const int ch = (npan + 31) / 32;
+    A.nchunks = ch < 1 ? 1 : (ch > kNuChunks ? kNuChunks : ch);
+  }
   A.parts = c->d_parts;
   A.rlist = c->d_rlist;
   A.R = c->d_R;
