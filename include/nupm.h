@@ -385,9 +385,16 @@ NUPM_API int64_t pm_device_bytes(const pm_ctx* ctx);
  *                     gather): 4, 8, 16, 32
  *   gather_rows       0 = the CIC gather walks the particles in storage
  *                     order, 1 = in the row order of pm_deposit's sort (a
- *                     warp per grid row; used when pm_kick gets the same
- *                     position pointer as the deposit; needs the sorted
- *                     deposit and the real-space gradient)
+ *                     warp per grid row, velocities updated through the
+ *                     sort's permutation), 2 = the same row order writing
+ *                     each force by sorted slot, then the velocities updated
+ *                     in storage order through the inverse permutation
+ *                     (for particles far from their storage order; 20 bytes
+ *                     a particle in FP32, 36 in FP64, allocated on first
+ *                     use and left out if that allocation fails); 1 and 2
+ *                     are used when pm_kick gets the same position pointer
+ *                     as the deposit and need the sorted deposit and the
+ *                     real-space gradient
  * one knob at a time, keeps the fastest and writes HOST tuned[4] = {wide_y,
  * wide_z, ctas_per_sm, gather_rows} (may be NULL).  a, a_hist, sqrtPM_hist, n_hist: as
  * pm_nu_response (the tuning kicks need a response).  Results are bit-identical
@@ -397,7 +404,8 @@ NUPM_API int pm_autotune(pm_ctx* ctx, const void* pos, void* vel, double a, cons
                          const double* sqrtPM_hist, int32_t n_hist, int32_t reps, int32_t* tuned);
 /* Set the four knobs directly, HOST tuned[4] (-1 = built-in choice for wide_y / wide_z).
  * PM_ERR_INVALID for a value out of range, PM_ERR_UNSUPPORTED for wide_z = 2
- * on a grid that does not offer it. */
+ * on a grid that does not offer it, PM_ERR_ALLOC when gather_rows = 2 cannot
+ * allocate its buffers (the tuning is then unchanged). */
 NUPM_API int pm_set_tuning(pm_ctx* ctx, const int32_t* tuned);
 
 /* ---- CUDA graphs of whole kicks (batched form) ----

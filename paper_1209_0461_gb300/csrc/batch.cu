@@ -165,7 +165,7 @@ struct PScatter {
     for (int k = 0; k < kSortSteps; ++k) {
       const int64_t base = (int64_t)item * kSortChunk + (k * 256 + (threadIdx.x & ~31)) * kSortBatch;
       if (base < b.g.np)
-        row_scatter_warp<T>(b.pos, b.g.np, b.g.n, b.g.delta, b.g.row_cursor, b.g.perm, b.g.rec, base);
+        row_scatter_warp<T>(b.pos, b.g.np, b.g.n, b.g.delta, b.g.row_cursor, b.g.perm, b.g.rec, base, nullptr);
     }
   }
 };

@@ -278,7 +278,8 @@ int NUPM_FN(row_sort)(const GridArgs& g, const void* pos, cudaStream_t s) {
   k_scan_blocks<<<nb, kScanBlock, 0, s>>>(g.row_count, g.row_start, g.scan_tot, len);
   k_scan_totals<<<1, kScanBlock, 0, s>>>(g.scan_tot, nb);
   k_scan_add<<<(len + 255) / 256, 256, 0, s>>>(g.row_start, g.scan_tot, len, g.row_cursor);
-  if (g.np > 0) k_row_scatter<T><<<blocks, 256, 0, s>>>(pos, g.np, g.n, g.delta, g.row_cursor, g.perm, g.rec);
+  if (g.np > 0)
+    k_row_scatter<T><<<blocks, 256, 0, s>>>(pos, g.np, g.n, g.delta, g.row_cursor, g.perm, g.rec, g.inv);
   return PM_OK;
 }
 
@@ -352,6 +353,16 @@ int NUPM_FN(green)(const GridArgs& g, cudaStream_t s) {
 }
 
 int NUPM_FN(interp)(const GridArgs& g, const void* pos, void* vel, double kick, void* acc_out, cudaStream_t s) {
+  if (g.np > 0 && g.fd_grad && g.rows_ready && g.gather_rows == 2) {
+    // forces in the sort's row order by sorted slot, then the velocities in particle order
+    k_interp_rows_acc<T><<<(unsigned)((g.np + kGatherTPB * kGatherChunk - 1) / (kGatherTPB * kGatherChunk)),
+                           kGatherTPB, 0, s>>>(g.rec, g.row_start, g.n, g.delta, reinterpret_cast<const T*>(g.g),
+                                               reinterpret_cast<T*>(g.accs));
+    k_kick_inv<T><<<grid_blocks(g.np, 256, g.part_ctas_per_sm), 256, 0, s>>>(
+        g.inv, reinterpret_cast<const T*>(g.accs), g.np, reinterpret_cast<T*>(vel), (T)kick,
+        reinterpret_cast<T*>(acc_out));
+    return PM_OK;
+  }
   if (g.np > 0 && g.fd_grad && g.rows_ready) {   // row order of the deposit's sort: a warp per row
     k_interp_rows_fd<T><<<(unsigned)(((int64_t)g.n * g.n + kRowsPerCta - 1) / kRowsPerCta), kGatherTPB, 0, s>>>(
         g.rec, g.row_start, g.perm, g.np, g.n, g.delta, reinterpret_cast<const T*>(g.g), reinterpret_cast<T*>(vel),

@@ -912,6 +912,88 @@ k_interp_rows_fd(const unsigned long long* __restrict__ rec, const int* __restri
   }
 }
 
+// The row-order gather without its scattered velocity update (clustered
+// particles, far from their storage order, make the update through perm[] a
+// random read and write of six words a particle): the forces of the sorted
+// records are written by sorted slot, four values a slot (one 16- or 32-byte
+// store), and k_kick_inv then walks the particles in storage order, reading
+// each one's force through its slot inv[p] (one random 16- or 32-byte read)
+// and updating its velocity with coalesced accesses.  fd_stencil's arithmetic
+// and the same update expression: bit-identical to the particle-order gather.
+// Work order: the sorted records in contiguous chunks of kGatherTPB x
+// kGatherChunk (a CTA's threads kGatherTPB apart, as the particle-order
+// gather), CTAs dispatched in index order.  The CTA finds the row of its first
+// record by bisection of row_start; each thread then advances its row as its
+// records advance (rows are sorted), so empty rows cost nothing.
+template <typename T>
+__global__ void __launch_bounds__(kGatherTPB, sizeof(T) == 4 ? 12 : 8)
+k_interp_rows_acc(const unsigned long long* __restrict__ rec, const int* __restrict__ row_start, int n,
+                  double delta, const T* __restrict__ phi, T* __restrict__ accs) {
+  __shared__ int s_row;
+  const T scale = (T)(-1.0 / (12.0 * delta));
+  const int rows = n * n;
+  const int nrec = row_start[rows];                 // the sorted (valid) records
+  const int64_t i0 = (int64_t)blockIdx.x * kGatherTPB * kGatherChunk;
+  if (i0 >= nrec) return;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = rows;                          // row_start[lo] <= i0 < row_start[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (row_start[mid] <= i0) lo = mid; else hi = mid;
+    }
+    s_row = lo;
+  }
+  __syncthreads();
+  int r = s_row;
+#pragma unroll 1
+  for (int u = 0; u < kGatherChunk; ++u) {
+    const int64_t i = i0 + threadIdx.x + (int64_t)u * kGatherTPB;
+    if (i >= nrec) break;
+    while (row_start[r + 1] <= i) ++r;              // r + 1 <= rows: i < row_start[rows]
+    const int cz = r / n, cy = r - cz * n;
+    const unsigned long long rr = rec[i];
+    const int c[3] = {(int)(rr >> 48) & 0x7ff, cy, cz};
+    const int w[3] = {(int)(rr & 0xffffu), (int)((rr >> 16) & 0xffffu), (int)((rr >> 32) & 0xffffu)};
+    T a[3];
+    fd_stencil<T>(phi, n, c, w, a);
+    if constexpr (sizeof(T) == 4) {
+      reinterpret_cast<float4*>(accs)[i] = make_float4(a[0] * scale, a[1] * scale, a[2] * scale, 0.0f);
+    } else {
+      double2* q = reinterpret_cast<double2*>(accs) + 2 * i;
+      q[0] = make_double2(a[0] * scale, a[1] * scale);
+      q[1] = make_double2(a[2] * scale, 0.0);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_kick_inv(const int* __restrict__ inv, const T* __restrict__ accs, int64_t np,
+                           T* __restrict__ vel, T kick, T* __restrict__ acc_out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
+    const int slot = inv[p];
+    if (slot < 0) continue;   // skipped by the sort (PM_ERR_RANGE recorded there)
+    T ad[3];
+    if constexpr (sizeof(T) == 4) {
+      const float4 q = reinterpret_cast<const float4*>(accs)[slot];
+      ad[0] = q.x;
+      ad[1] = q.y;
+      ad[2] = q.z;
+    } else {
+      const double2* q = reinterpret_cast<const double2*>(accs) + 2 * (int64_t)slot;
+      const double2 q0 = q[0], q1 = q[1];
+      ad[0] = q0.x;
+      ad[1] = q0.y;
+      ad[2] = q1.x;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      vel[d * np + p] = vel[d * np + p] + ad[d] * kick;
+      if (acc_out) acc_out[d * np + p] = ad[d];
+    }
+  }
+}
+
 // Inspection: one component of acc = -S phi on the whole grid (real [N][N][N]).
 template <typename T>
 __global__ void k_fd_force_field(const T* __restrict__ phi, int n, int comp, double delta, T* __restrict__ out) {

@@ -154,6 +154,8 @@ struct GridArgs {
   int* row_cursor;                 // [N^2 + 1]
   int* scan_tot;                   // [2 * 1024] block totals of the scan
   int* perm;                       // [npart] particle indices sorted by row (fused gather only, else null)
+  int* inv;                        // [npart] each particle's sorted slot, -1 if skipped (gather_rows 2, else null)
+  void* accs;                      // [npart][4] forces in sorted order (gather_rows 2)
   unsigned long long* rec;         // [npart] packed particle records sorted by row
   const CUtensorMap* tmap_spec_y;  // TMA maps of the column passes (nullptr: plain kernels)
   const CUtensorMap* tmap_spec_z;
@@ -174,7 +176,9 @@ struct GridArgs {
   // applied by the gather (one inverse transform)
   bool fd_grad = false;
   // tuning: 1 = gather in the row order of the deposit's sort (records +
-  // perm), used when rows_ready (same positions as the deposit, perm written)
+  // perm), 2 = the same order writing forces by sorted slot, then the
+  // velocity update in particle order through inv; used when rows_ready (same
+  // positions as the deposit, perm or inv written)
   int gather_rows = 0;
   bool rows_ready = false;
 };

@@ -106,6 +106,9 @@ struct pm_ctx {
   int wide_y = -1, wide_z = -1, part_cps = 16;   // tuning (pm_autotune)
   int gather_rows = 0;                            // tuning: gather in the sort's row order
   bool perm_valid = false;                        // the last deposit's sort wrote perm
+  bool inv_valid = false;                         // the last deposit's sort wrote inv
+  int* d_inv = nullptr;                           // gather_rows 2: sorted slot of each particle
+  void* d_accs = nullptr;                         // gather_rows 2: [npart][4] forces by sorted slot
   const void* dep_pos = nullptr;                  // positions of the last deposit
   double* d_bins_lattice = nullptr;   // [2][nk] lattice count / ksum, restored after pm_set_power
   float* d_X = nullptr;           // [nk][12] surrogate features
@@ -481,6 +484,8 @@ GridArgs grid_args(const pm_ctx* c) {
   g.row_cursor = c->d_rowcur;
   g.scan_tot = c->d_scantot;
   g.perm = ((c->p.flags & PM_FUSED_GATHER) || c->gather_rows == 1) ? c->d_perm : nullptr;
+  g.inv = c->gather_rows == 2 ? c->d_inv : nullptr;
+  g.accs = c->d_accs;
   g.gather_rows = c->gather_rows;
   g.rec = c->d_rec;
   g.tmap_spec_y = c->tma ? &c->tm_spec_y : nullptr;
@@ -501,7 +506,7 @@ void release(pm_ctx* c) {
                   c->d_stab, c->d_hist_u, c->d_gl, c->d_parts, c->d_R, c->d_pnu, c->d_pm, c->d_rlist, c->d_gtab,
                   c->d_dtab, c->d_wtab, c->d_plane0, c->d_fac, c->d_rowc, c->d_rows, c->d_rowcur,
                   c->d_scantot, c->d_perm, c->d_rec, c->d_status, c->d_hist_u2, c->d_rtab, c->d_icheb, c->d_hist_own,
-                  c->d_prev[0], c->d_prev[1]};
+                  c->d_prev[0], c->d_prev[1], c->d_inv, c->d_accs};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_hist_u) cudaFreeHost(c->h_hist_u);
@@ -896,6 +901,7 @@ int pm_deposit(pm_ctx* c, const void* pos) {
   c->deposited = true;
   c->deposit_grid_valid = unfused || keep;   // the fixed-point grid stays intact until pm_kick
   c->perm_valid = !unfused && g.perm != nullptr;
+  c->inv_valid = !unfused && g.inv != nullptr;
   c->dep_pos = pos;
   c->have_response = false;
   c->have_kick = false;
@@ -1205,7 +1211,8 @@ int pm_kick(pm_ctx* c, const void* pos, void* vel, double a, double kick_factor,
   }
   c->deposit_grid_valid = false;
   // the row-order gather walks the deposit's sort: only for the same positions
-  g.rows_ready = c->gather_rows == 1 && c->perm_valid && pos == c->dep_pos && g.fd_grad;
+  g.rows_ready = ((c->gather_rows == 1 && c->perm_valid) || (c->gather_rows == 2 && c->inv_valid)) &&
+                 pos == c->dep_pos && g.fd_grad;
   // the fused gather walks the row sort of pm_deposit, absent on the unfused path
   const bool separate = !(c->p.flags & PM_FUSED_GATHER) || (c->p.flags & PM_UNFUSED_DEPOSIT);
   const int inv[3] = {kPassZInv, kPassYInv, kPassXInv};
@@ -1220,7 +1227,7 @@ int pm_kick(pm_ctx* c, const void* pos, void* vel, double a, double kick_factor,
       rc = c->fp64 ? fft_pass_f64(g, inv[2], c->stream) : fft_pass_f32(g, inv[2], c->stream);
     }
     if (rc == PM_OK) {
-      Stage st(c, PM_ST_INTERP, 1);
+      Stage st(c, PM_ST_INTERP, g.rows_ready && c->gather_rows == 2 ? 2 : 1);
       rc = c->fp64 ? interp_f64(g, pos, vel, kick_factor, acc_out, c->stream)
                    : interp_f32(g, pos, vel, kick_factor, acc_out, c->stream);
     }
@@ -1249,6 +1256,7 @@ int pm_drift(pm_ctx* c, void* pos, const void* vel, double drift_factor) {
   }
   // the particles moved: a sort of the old positions no longer describes them
   c->perm_valid = false;
+  c->inv_valid = false;
   return cuda_check(c, cudaGetLastError(), "pm_drift launch");
 }
 
@@ -1488,6 +1496,16 @@ int pm_get_timing(pm_ctx* c, double* ms, int64_t* launches, int64_t* calls) {
 
 int64_t pm_device_bytes(const pm_ctx* c) { return c ? c->bytes : 0; }
 
+// gather_rows 2 needs the inverse permutation and the sorted forces (4 + 16
+// bytes a particle in FP32, 4 + 32 in FP64), allocated on first use.
+static int ensure_rows_acc(pm_ctx* c) {
+  int rc = PM_OK;
+  if (!c->d_inv) rc = dalloc(c, (void**)&c->d_inv, (size_t)c->np * sizeof(int), "inverse row permutation");
+  if (rc == PM_OK && !c->d_accs)
+    rc = dalloc(c, &c->d_accs, (size_t)c->np * 4 * (c->fp64 ? sizeof(double) : sizeof(float)), "sorted forces");
+  return rc;
+}
+
 int pm_autotune(pm_ctx* c, const void* pos, void* vel, double a, const double* a_hist, const double* sqrtPM_hist,
                 int32_t n_hist, int32_t reps, int32_t* tuned) {
   if (!c) return PM_ERR_INVALID;
@@ -1555,14 +1573,23 @@ int pm_autotune(pm_ctx* c, const void* pos, void* vel, double a, const double* a
   // gather order: particle order, or the row order of the deposit's sort
   // (records + permutation; the default real-space gradient on the sorted path)
   if (rc == PM_OK && c->d_perm && !(c->p.flags & (PM_SPECTRAL_GRADIENT | PM_FUSED_GATHER | PM_TMA_COLUMNS))) {
-    double t0 = 0.0, t1 = 0.0;
+    double t[3] = {0.0, 1e300, 1e300};
     c->gather_rows = 0;
-    rc = measure(kStP, 2, &t0);
+    rc = measure(kStP, 2, &t[0]);
     if (rc == PM_OK) {
       c->gather_rows = 1;
-      rc = measure(kStP, 2, &t1);
+      rc = measure(kStP, 2, &t[1]);
     }
-    c->gather_rows = (rc == PM_OK && t1 < t0) ? 1 : 0;
+    // the forces-by-slot form only where its 20 (FP32) or 36 (FP64) bytes a
+    // particle can be had; otherwise it is left out of the comparison
+    if (rc == PM_OK && ensure_rows_acc(c) == PM_OK) {
+      c->gather_rows = 2;
+      rc = measure(kStP, 2, &t[2]);
+    }
+    int best = 0;
+    for (int k = 1; k < 3; ++k)
+      if (t[k] < t[best]) best = k;
+    c->gather_rows = rc == PM_OK ? best : 0;
   }
   const int rc2 = pm_timing(c, was_timing ? 1 : 0);
   if (rc != PM_OK) return rc;
@@ -1580,11 +1607,15 @@ int pm_autotune(pm_ctx* c, const void* pos, void* vel, double a, const double* a
 int pm_set_tuning(pm_ctx* c, const int32_t* tuned) {
   if (!c || !tuned) return PM_ERR_INVALID;
   if (tuned[0] < -1 || tuned[0] > 1 || tuned[1] < -1 || tuned[1] > 2 || tuned[2] < 1 || tuned[2] > 64 ||
-      tuned[3] < 0 || tuned[3] > 1)
+      tuned[3] < 0 || tuned[3] > 2)
     return fail(c, PM_ERR_INVALID,
-                "pm_set_tuning: wide_y in -1..1, wide_z in -1..2, ctas_per_sm in 1..64, gather_rows 0 or 1");
+                "pm_set_tuning: wide_y in -1..1, wide_z in -1..2, ctas_per_sm in 1..64, gather_rows 0..2");
   if (tuned[1] == 2 && !c->tma_z16)
     return fail(c, PM_ERR_UNSUPPORTED, "pm_set_tuning: wide_z = 2 needs a power-of-two grid of 256 or more");
+  if (tuned[3] == 2) {
+    const int rc = ensure_rows_acc(c);
+    if (rc != PM_OK) return rc;
+  }
   c->wide_y = tuned[0];
   c->wide_z = tuned[1];
   c->part_cps = tuned[2];
@@ -1856,6 +1887,7 @@ int pm_batch_kick(pm_batch* B, const void* const* pos, void* const* vel, const d
     c->have_kick = true;
     c->deposit_grid_valid = false;
     c->perm_valid = c->d_perm != nullptr && grid_args(c).perm != nullptr;
+    c->inv_valid = false;   // the batched sort writes no inverse permutation
     c->dep_pos = pos[b];
   }
   return PM_OK;

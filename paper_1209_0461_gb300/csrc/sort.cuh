@@ -110,7 +110,8 @@ __global__ void k_row_count(const void* __restrict__ pos, int64_t np, int n, dou
 template <typename T>
 __device__ __forceinline__ void row_scatter_warp(const void* __restrict__ pos, int64_t np, int n, double delta,
                                                  int* __restrict__ cursor, int* __restrict__ perm,
-                                                 unsigned long long* __restrict__ rec, int64_t base) {
+                                                 unsigned long long* __restrict__ rec, int64_t base,
+                                                 int* __restrict__ inv = nullptr) {
   constexpr int U = kSortBatch;
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -135,20 +136,24 @@ __device__ __forceinline__ void row_scatter_warp(const void* __restrict__ pos, i
       const int slot = start + __popc(peers & ((1u << lane) - 1));
       rec[slot] = pack_record(c, w);
       if (perm) perm[slot] = (int)p;
+      if (inv) inv[p] = slot;
+    } else if (inv && p < np) {
+      inv[p] = -1;   // skipped particle (PM_ERR_RANGE): no slot
     }
   }
 }
 
 // Place each valid particle at its row's cursor: the packed record (and, when
-// perm is given, the particle index) at the same sorted slot.
+// perm is given, the particle index) at the same sorted slot; with inv given,
+// each particle's slot (-1 for a skipped particle) in particle order.
 template <typename T>
 __global__ void k_row_scatter(const void* __restrict__ pos, int64_t np, int n, double delta,
                               int* __restrict__ cursor, int* __restrict__ perm,
-                              unsigned long long* __restrict__ rec) {
+                              unsigned long long* __restrict__ rec, int* __restrict__ inv) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x * kSortBatch;
   for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * kSortBatch; base < np;
        base += stride)
-    row_scatter_warp<T>(pos, np, n, delta, cursor, perm, rec, base);
+    row_scatter_warp<T>(pos, np, n, delta, cursor, perm, rec, base, inv);
 }
 
 // Exclusive scan of n values in three launches: per-block scans of 2048

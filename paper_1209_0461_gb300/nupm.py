@@ -366,7 +366,9 @@ class PM:
     # -- tuning
     def autotune(self, pos, vel, a, a_hist, sqrtPM_hist, reps=2):
         """pm_autotune: returns (wide_y, wide_z, ctas_per_sm, gather_rows); wide_z = 2
-        is the TMA-staged z pass, gather_rows = 1 the gather in the sort's row order."""
+        is the TMA-staged z pass, gather_rows = 1 the gather in the sort's row order,
+        2 the same order with forces by sorted slot and the velocity update in
+        particle order."""
         self._check_pos(pos)
         ah, n = self._history(a_hist, sqrtPM_hist)
         t = (C.c_int32 * 4)()

@@ -76,7 +76,15 @@ def test_persistent_batch_matches_direct_kicks_and_graphs_to_few_nodes():
     ref = _dv(direct)
     ref_bins = [it["pm"].bins() for it in direct.items]
     direct.close()
-    b = batch.Batch(boxes, persistent=True)
+    # two sub-batches per grid size on their own streams: the same velocities
+    b = batch.Batch(boxes, persistent=True, split=2)
+    assert len(b.groups) == 6
+    b.eager_step()
+    b.check()
+    for d0, d1 in zip(ref, _dv(b)):
+        assert np.abs(d1 - d0).max() <= 1e-5 * np.abs(d0).max()
+    b.close()
+    b = batch.Batch(boxes, persistent=True, split=1)
     assert len(b.groups) == 3
     b.eager_step()
     b.check()

@@ -192,10 +192,11 @@ def test_prepared_response_is_identical(prec, n):
 @pytest.mark.parametrize("prec,n,case", [("fp32", 64, "lattice"), ("fp64", 32, "lattice"), ("fp32", 64, "shuffled"),
                                          ("fp32", 64, "clustered"), ("fp32", 192, "lattice")])
 def test_row_order_gather(prec, n, case):
-    # gather_rows = 1 walks the deposit's row sort (records + permutation): the
-    # same stencil arithmetic, so the same forces and velocities bit for bit as
-    # the particle-order gather, for lattice-ordered, shuffled and clustered
-    # particles; and against the oracle
+    # gather_rows = 1 walks the deposit's row sort (records + permutation), 2
+    # the same order writing forces by sorted slot and then the velocities in
+    # particle order (inverse permutation): the same stencil arithmetic, so the
+    # same forces and velocities bit for bit as the particle-order gather, for
+    # lattice-ordered, shuffled and clustered particles; and against the oracle
     w = synth.with_(synth.WORKLOADS["pm32_fp64"], name=f"rows{n}{case}", ngrid=n, npart_side=n // 2 if n > 32 else n,
                     precision=prec, n_hist=6, clustered=(case == "clustered"))
     inp = make_inputs(w)
@@ -204,8 +205,11 @@ def test_row_order_gather(prec, n, case):
         inp = dict(inp, pos64=inp["pos64"][:, perm].copy(), vel=inp["vel"][:, perm].copy())
     a = gpu_kick(w, inp, tuning=(-1, -1, 16, 0))
     b = gpu_kick(w, inp, tuning=(-1, -1, 16, 1))
+    c = gpu_kick(w, inp, tuning=(-1, -1, 16, 2))
     assert np.array_equal(a["acc"], b["acc"])
     assert np.array_equal(a["vel"], b["vel"])
+    assert np.array_equal(a["acc"], c["acc"])
+    assert np.array_equal(a["vel"], c["vel"])
     _check_common(w, b, oracle_kick(w, inp), prec == "fp64")
 
 
@@ -220,7 +224,7 @@ def test_row_order_gather_needs_the_deposit_positions():
     pos = torch.from_numpy(synth.to_cell_offset(inp["pos64"], w.box, w.ngrid)).cuda()
     h = torch.from_numpy(np.ascontiguousarray(inp["hist"])).cuda()
     out = []
-    for rows, other in ((0, False), (1, True), (1, False)):
+    for rows, other in ((0, False), (1, True), (1, False), (2, True), (2, False)):
         pm.set_tuning(-1, -1, 16, rows)
         vel = torch.from_numpy(inp["vel"].astype(np.float32)).cuda()
         acc = torch.empty_like(vel)
@@ -229,7 +233,40 @@ def test_row_order_gather_needs_the_deposit_positions():
         pm.kick(pos.clone() if other else pos, vel, w.a_kick, 0.01, acc_out=acc)
         pm.check()
         out.append(acc.cpu().numpy())
-    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    for o in out[1:]:
+        assert np.array_equal(out[0], o)
+    pm.close()
+
+
+def test_forces_by_slot_leave_a_skipped_particle():
+    # gather_rows = 2 with one particle whose offset is outside [0, 1): the sort
+    # skips it (PM_ERR_RANGE), its velocity stays as it was, and every other
+    # velocity equals the particle-order gather's
+    w = synth.with_(synth.WORKLOADS["pm32_fp64"], name="rows2bad", ngrid=64, npart_side=32, precision="fp32",
+                    n_hist=4)
+    inp = make_inputs(w)
+    pm = nupm.PM(w.ngrid, w.npart, w.box, w.omega_cdm, w.omega_nu, w.h, w.m_nu_total, w.n_species,
+                 a_init=w.a_init, n_kbins=w.n_kbins, n_hist_max=4, precision="fp32",
+                 sqrtPnu_init=inp["pi"], theta_over_delta_init=inp["ti"])
+    bad = synth.to_cell_offset(inp["pos64"], w.box, w.ngrid)
+    bad[3, 5] = np.float32(1.0).view(np.int32)
+    pos = torch.from_numpy(bad).cuda()
+    h = torch.from_numpy(np.ascontiguousarray(inp["hist"])).cuda()
+    v0 = inp["vel"].astype(np.float32)
+    out = []
+    for rows in (0, 2):
+        pm.set_tuning(-1, -1, 16, rows)
+        vel = torch.from_numpy(v0).cuda()
+        pm.deposit(pos)
+        pm.nu_response(w.a_kick, inp["a_hist"], h)
+        pm.kick(pos, vel, w.a_kick, 0.01)
+        with pytest.raises(nupm.PMError) as e:
+            pm.check()
+        assert e.value.code == -2                        # PM_ERR_RANGE
+        out.append(vel.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[1][:, 5], v0[:, 5])
+    assert not np.array_equal(out[1][:, 6], v0[:, 6])
     pm.close()
 
 
