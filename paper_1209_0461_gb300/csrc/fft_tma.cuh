@@ -371,4 +371,124 @@ k_col_tma_z(const __grid_constant__ CUtensorMap map, ColTmaArgs<T> A) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 forward z pass with the exchange in a buffer of its own.  The staged
+// tile (N x 16 columns, 128-byte row segments, the same tensor map as
+// k_col_tma_z) is read into registers and the next tile's copy is issued at
+// once, so that it travels during this tile's butterflies and stores
+// (k_col_tma_z can issue it only once the exchange, which reuses the tile
+// buffer, has been read back).  The exchange buffer holds 8 of the 16
+// columns: the two halves exchange in turn.  The same butterflies as fft_regs
+// for the two-stage plans of 256, 512 and 1024 points (one exchange).
+// ---------------------------------------------------------------------------
+template <int N>
+struct ColTmaZFwdCfg {
+  using T = float;
+  using P = Plan<T, N>;
+  static constexpr int M = N / 2;
+  static constexpr int E = P::R1, R2 = P::R2;
+  static constexpr int NT = N / E;
+  static constexpr int W = ColTmaZCfg<T, N>::W, WH = W / 2;
+  static constexpr int THREADS = W * NT;
+  static constexpr int PAD = ColTmaZCfg<T, N>::PAD;
+  static constexpr int BOX = ColTmaZCfg<T, N>::BOX;
+  static constexpr int NBOX = N / BOX;
+  static constexpr size_t TILE_BYTES = (size_t)N * W * sizeof(cx<T>);
+  static constexpr size_t XCH_BYTES = (size_t)ColSmem<T, WH, PAD>::words(N) * sizeof(cx<T>);
+  static constexpr size_t SMEM = TILE_BYTES + XCH_BYTES + 64;
+  static constexpr int TILES_PER_ROW = M / W;
+  static_assert(P::R3 == 1 && R2 > 1 && E % R2 == 0, "two-stage plans only");
+  static_assert(THREADS % 32 == 0 && THREADS <= 1024, "whole warps");
+  static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
+  static_assert(TILE_BYTES % 128 == 0 && (TILE_BYTES + XCH_BYTES) % 8 == 0, "buffer alignment");
+};
+
+template <int N>
+__global__ void __launch_bounds__(ColTmaZFwdCfg<N>::THREADS, 1)
+k_col_tma_z_fwd(const __grid_constant__ CUtensorMap map, ColTmaArgs<float> A) {
+  using T = float;
+  using Cfg = ColTmaZFwdCfg<N>;
+  constexpr int M = N / 2, E = Cfg::E, R2 = Cfg::R2, NT = Cfg::NT, W = Cfg::W, WH = Cfg::WH;
+  constexpr int64_t ES = (int64_t)N * M;      // element stride along z
+  constexpr int DIR = -1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* xch = reinterpret_cast<cx<T>*>(smem_raw + Cfg::TILE_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::TILE_BYTES + Cfg::XCH_BYTES);
+  const int items = Cfg::TILES_PER_ROW * N;   // (x2 tile, y)
+  const int c = threadIdx.x % W;
+  const int t = threadIdx.x / W;
+  const int half = c / WH;
+  ColSmem<T, WH, Cfg::PAD> xs{xch, c % WH};
+
+  auto issue = [&](int item) {
+    const int xt = item % Cfg::TILES_PER_ROW, y = item / Cfg::TILES_PER_ROW;
+    mbar_expect_tx(bar, (uint32_t)Cfg::TILE_BYTES);
+#pragma unroll
+    for (int bx = 0; bx < Cfg::NBOX; ++bx)
+      tma_load_4d(tile + (size_t)bx * Cfg::BOX * W, &map, bar, xt * W, y, bx * Cfg::BOX, 0);
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int first = blockIdx.x, step = gridDim.x;
+  if (threadIdx.x == 0 && first < items) issue(first);
+  int k = 0;
+  for (int item = first; item < items; item += step, ++k) {
+    const bool ok = mbar_wait_bounded(bar, (uint32_t)(k & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicCAS(A.status, 0, PM_ERR_TIMEOUT);
+        mbar_wait_bounded(bar, (uint32_t)(k & 1));   // this CTA's one copy in flight (bounded)
+      }
+      return;
+    }
+    const int xt = item % Cfg::TILES_PER_ROW, y = item / Cfg::TILES_PER_ROW;
+    const int x2 = xt * W + c;
+    cx<T> v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = tile[(t + NT * i) * W + c];   // the staged tile (dense)
+    fence_proxy_async_shared();
+    __syncthreads();   // every read of the tile is done: it may take the next copy
+    if (threadIdx.x == 0 && item + step < items) issue(item + step);
+    // first stage: radix-E butterfly on the thread's elements t + NT i
+    dft<E, DIR>(v);
+    // the exchange, one half of the columns at a time
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (half == h) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) xs.st(t * E + i, v[i]);
+      }
+      __syncthreads();
+      if (half == h) {
+#pragma unroll
+        for (int b = 0; b < E / R2; ++b) {
+          const int j = t + NT * b;
+#pragma unroll
+          for (int i = 0; i < R2; ++i) v[b * R2 + i] = xs.ld(j + i * (N / R2));
+        }
+      }
+      __syncthreads();
+    }
+    // second stage: twiddles W_N^{i k}, k = j mod E, and radix-R2 butterflies
+#pragma unroll
+    for (int b = 0; b < E / R2; ++b) {
+      const int j = t + NT * b;
+      const int kk = j % E;
+#pragma unroll
+      for (int i = 1; i < R2; ++i) v[b * R2 + i] = cmul(v[b * R2 + i], twid_table<DIR>(A.tw, i * kk * (N / (E * R2))));
+      dft<R2, DIR>(&v[b * R2]);
+    }
+    cx<T>* dst = A.spec + (int64_t)y * M + x2;
+#pragma unroll
+    for (int b = 0; b < E / R2; ++b)
+#pragma unroll
+      for (int i = 0; i < R2; ++i) dst[(int64_t)(t + NT * b + i * (N / R2)) * ES] = v[b * R2 + i];
+  }
+}
+
 }  // namespace nupm

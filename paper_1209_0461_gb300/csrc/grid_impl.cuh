@@ -147,6 +147,21 @@ void col_tma_z_n(const GridArgs& g, cudaStream_t s) {
   a.status = g.status;
   const int items = Cfg::TILES_PER_ROW * N;
   const int grid = items < g.sm_count ? items : g.sm_count;
+  if constexpr (sizeof(T) == 4 && MODE == kColFwdZ) {
+    // FP32 forward: the form with its own exchange buffer (the next tile's copy
+    // issued before the transform): 1.81 against 2.02 ms at 1024^3 on GB300.
+    // The Green pass keeps k_col_tma_z, whose Green factors are computed while
+    // its copy travels (2.27 against 2.46 ms with the factors computed inline
+    // in a split-buffer form).
+    using FC = ColTmaZFwdCfg<N>;
+    static bool fattr = false;
+    if (!fattr) {
+      cudaFuncSetAttribute(k_col_tma_z_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FC::SMEM);
+      fattr = true;
+    }
+    k_col_tma_z_fwd<N><<<grid, FC::THREADS, FC::SMEM, s>>>(*g.tmap_z16, a);
+    return;
+  }
   k_col_tma_z<T, N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*g.tmap_z16, a);
 }
 
