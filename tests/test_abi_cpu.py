@@ -83,3 +83,23 @@ def test_host_background_against_the_oracle(L, masses):
                               flags=nupm.PM_RELATIVISTIC if rel else 0)
             want = float(O.hubble(a, cos))
             assert abs(got / want - 1) < (1e-15 if not rel else 2e-12), (rel, a, got, want)
+
+
+def test_step_batch_and_peak_entry_points_validate_without_gpu(L):
+    # the step loop, the persistent batch and the FP64 peak reject missing
+    # arguments on the host, before any device work
+    assert L.pm_drift(None, None, None, 0.1) == -1
+    assert L.pm_history_set(None, None, None, 0, None) == -1
+    assert L.pm_history_get(None, None, None, None, None) == -1
+    assert L.pm_step(None, None, None, 0.1, 0.01, 0.01, None) == -1
+    out = C.c_void_p(123)
+    assert L.pm_batch_create(None, 0, None, C.byref(out)) == -1
+    assert out.value is None
+    assert L.pm_batch_create(None, 1, None, None) == -1
+    assert L.pm_batch_kick(None, None, None, None, None, None, None, None) == -1
+    assert L.pm_batch_launches(None) == 0
+    assert L.pm_batch_last_error(None) == b"null batch"
+    L.pm_batch_free(None)
+    t = C.c_double(-1.0)
+    assert L.pm_measure_fp64_fma(0, C.byref(t), None) == -1
+    assert L.pm_measure_fp64_fma(8, None, None) == -1
