@@ -49,7 +49,9 @@ extern "C" {
 #define PM_OK               0
 #define PM_ERR_INVALID     -1   /* bad argument (NULL, size, non-finite parameter) */
 #define PM_ERR_RANGE       -2   /* value outside its domain (offset not in [0,1), a < a_init, ...) */
-#define PM_ERR_OVERFLOW    -3   /* fixed-point deposit cannot hold the particle count */
+#define PM_ERR_OVERFLOW    -3   /* a cell of the fixed-point deposit passed 2^64 - 1 (more than 65535
+                                   particles' full weight in one cell): reported by pm_check after the
+                                   deposit, whose grid is then wrong */
 #define PM_ERR_CUDA        -4   /* a CUDA runtime call failed */
 #define PM_ERR_ALLOC       -5   /* device allocation failed */
 #define PM_ERR_TIMEOUT     -6   /* a bounded device wait gave up (reserved) */

@@ -179,7 +179,7 @@ struct PDeposit {
     constexpr int NX = N / F::TY;
     deposit_fft_x_tile<T, N>(b.g.rec, b.g.row_start, reinterpret_cast<C*>(b.g.spec), b.g.scale,
                              reinterpret_cast<const C*>(b.g.tw_m), reinterpret_cast<const C*>(b.g.tw_n), nullptr,
-                             item % NX, item / NX);
+                             item % NX, item / NX, b.g.status);
   }
 };
 

@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include "consts.cuh"
+#include "../../include/nupm.h"
 
 namespace nupm {
 
@@ -589,7 +590,7 @@ __device__ __forceinline__ void deposit_fft_x_tile(const unsigned long long* __r
                                                    const int* __restrict__ row_start, cx<T>* __restrict__ spec,
                                                    double scale, const cx<T>* __restrict__ tw_m,
                                                    const cx<T>* __restrict__ tw_n, unsigned long long* __restrict__ keep,
-                                                   int bx, int by) {
+                                                   int bx, int by, int* status) {
   using Cfg = FusedCfg<T, N>;
   using P = typename Cfg::P;
   constexpr int TZ = Cfg::TZ, TY = Cfg::TY, ROWS = Cfg::ROWS, M = N / 2, E = Cfg::E, NT = Cfg::NT;
@@ -652,6 +653,11 @@ __device__ __forceinline__ void deposit_fft_x_tile(const unsigned long long* __r
   static_assert(N < 32 || N % 32 == 0, "the y window is identified mod 32");
   constexpr int YM = (N < 32 ? N : 32) - 1;
   const int ws = (ty0 - 1 + N) % N;
+  // A cell's sum wraps past 2^64 only with 65536 or more contributions of up
+  // to 2^48 each; a tile with fewer records cannot overflow, and only a tile
+  // with more reads back its high-word adds to detect a wrap (PM_ERR_OVERFLOW).
+  const bool careful = total >= 65536;
+  bool ovf = false;
   constexpr int U = 4;
   for (int j0 = threadIdx.x; j0 < total; j0 += blockDim.x * U) {
     unsigned long long rr[U];
@@ -709,11 +715,18 @@ __device__ __forceinline__ void deposit_fft_x_tile(const unsigned long long* __r
       for (int k = 0; k < 8; ++k)
         if (lo[k] | hi[k]) {
           const unsigned int h = hi[k] + carry_of(old[k], lo[k]);
-          if (h) atomicAdd(accw + PLANE + slot[k], h);
+          if (h) {
+            if (careful) {
+              const unsigned int oh = atomicAdd(accw + PLANE + slot[k], h);
+              ovf = ovf || (oh + h < oh);
+            } else {
+              atomicAdd(accw + PLANE + slot[k], h);
+            }
+          }
         }
     }
   }
-  __syncthreads();
+  if (__syncthreads_or(ovf) && threadIdx.x == 0 && status) atomicCAS(status, 0, PM_ERR_OVERFLOW);
   // forward x transform of the tile's rows (as k_fft_x_fwd)
   const int t = threadIdx.x % NT;
   const int r = threadIdx.x / NT;
@@ -783,8 +796,8 @@ template <typename T, int N>
 __global__ void __launch_bounds__(FusedCfg<T, N>::THREADS, FusedCfg<T, N>::MIN_BLOCKS)
 k_deposit_fft_x(const unsigned long long* __restrict__ rec, const int* __restrict__ row_start,
                 cx<T>* __restrict__ spec, double scale, const cx<T>* __restrict__ tw_m, const cx<T>* __restrict__ tw_n,
-                unsigned long long* __restrict__ keep) {
-  deposit_fft_x_tile<T, N>(rec, row_start, spec, scale, tw_m, tw_n, keep, blockIdx.x, blockIdx.y);
+                unsigned long long* __restrict__ keep, int* status) {
+  deposit_fft_x_tile<T, N>(rec, row_start, spec, scale, tw_m, tw_n, keep, blockIdx.x, blockIdx.y, status);
 }
 
 // ---------------------------------------------------------------------------

@@ -228,7 +228,7 @@ void deposit_fft_x_n(const GridArgs& g, const void* pos, bool keep, cudaStream_t
   }
   k_deposit_fft_x<T, N><<<dim3(N / F::TY, N / F::TZ), F::THREADS, F::SMEM, s>>>(
       g.rec, g.row_start, reinterpret_cast<C*>(g.spec), g.scale, reinterpret_cast<const C*>(g.tw_m),
-      reinterpret_cast<const C*>(g.tw_n), keep ? reinterpret_cast<unsigned long long*>(g.g) : nullptr);
+      reinterpret_cast<const C*>(g.tw_n), keep ? reinterpret_cast<unsigned long long*>(g.g) : nullptr, g.status);
 }
 
 // Fused inverse x + interpolation + kick of size N (persistent grid).

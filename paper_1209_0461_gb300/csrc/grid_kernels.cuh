@@ -144,7 +144,10 @@ __global__ void k_deposit(const void* __restrict__ pos, int64_t np, int n, doubl
 #pragma unroll
           for (int dx = 0; dx < 2; ++dx) {
             const unsigned long long wt = wzy * wx[dx];
-            if (wt) atomicAdd(grid + rowi + xs[dx], wt);
+            if (wt) {
+              const unsigned long long o = atomicAdd(grid + rowi + xs[dx], wt);
+              if (o + wt < o) set_status(status, PM_ERR_OVERFLOW);   // the cell's sum wrapped past 2^64
+            }
           }
         }
     }

@@ -270,6 +270,31 @@ def test_forces_by_slot_leave_a_skipped_particle():
     pm.close()
 
 
+@pytest.mark.parametrize("flags", [KEEP_DEPOSIT, KEEP_DEPOSIT | UNFUSED_DEPOSIT])
+def test_deposit_overflow_is_reported(flags):
+    # a cell's fixed-point sum is an unsigned 64-bit integer and a particle at
+    # a node gives it 2^48: 40000 particles there are deposited exactly
+    # (40000 * 2^48 at the node, nothing elsewhere), 70000 pass 2^64 and
+    # pm_check reports PM_ERR_OVERFLOW (fused tile sums and global sums)
+    n = 32
+    for npart, overflow in ((40000, False), (70000, True)):
+        pos = np.zeros((6, npart), dtype=np.int32)
+        pos[0:3] = 5                                          # cell (5, 5, 5), offsets 0
+        pm = nupm.PM(n, npart, 64.0, 0.3, m_nu_total=0.0, a_init=0.02, n_kbins=8, precision="fp32", flags=flags)
+        pm.deposit(torch.from_numpy(pos).cuda())
+        if overflow:
+            with pytest.raises(nupm.PMError) as e:
+                pm.check()
+            assert e.value.code == -3                        # PM_ERR_OVERFLOW
+        else:
+            pm.check()
+            F = pm.field(nupm.FIELD_DEPOSIT).cpu().numpy().view(np.uint64).reshape(n, n, n)
+            assert int(F[5, 5, 5]) == npart * 2 ** 48
+            F[5, 5, 5] = 0
+            assert not F.any()
+        pm.close()
+
+
 def test_prepare_twice_is_an_order_error():
     w = synth.with_(synth.WORKLOADS["pm32_fp64"], n_hist=4)
     inp = make_inputs(w)
