@@ -103,14 +103,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def stage_bytes(w, stage, fused_interp=True, spectral=False):
+def bins_in_z(w, tuning):
+    """True when the FP32 bin power sums ride in the TMA-staged forward z pass
+    (wide_z = 2 on a power-of-two grid of 256 or more, at most 256 bins): the
+    bins stage then reads only the packed x2 = 0 column."""
+    n = w.ngrid
+    return (bool(tuning) and tuning[1] == 2 and w.precision == "fp32" and w.n_kbins <= 256
+            and n >= 256 and (n & (n - 1)) == 0)
+
+
+def stage_bytes(w, stage, fused_interp=True, spectral=False, bins_fused=False):
     """Algorithmic (compulsory) HBM bytes of ONE launch of a stage: each pass
     reads its inputs and writes its outputs once at stored precision.  By
     default the inverse passes carry the potential alone and the gather reads
     the real potential grid (its 4-point stencil); with the gradient in
     Fourier space (spectral) they carry three force fields.  With the fused
     interpolation the inverse x stage reads the three fields and the
-    particles (positions, row permutation) and updates the velocities."""
+    particles (positions, row permutation) and updates the velocities.  With
+    the bin sums in the forward z pass (bins_fused) the bins stage reads the
+    packed x2 = 0 column alone."""
+    if bins_fused and stage == "bins":
+        return (8 if w.precision == "fp32" else 16) * w.ngrid * w.ngrid
     n = w.ngrid
     M = n ** 3
     Mc = n * n * (n // 2)                 # packed complex elements per field
@@ -449,14 +462,15 @@ def run_gpu(args, w, rank, world):
         per_launch_ms = tot_ms / max(calls, 1)     # memset/reduce ride along in the stage
     fused = stages["interp"][1] == 0
     spectral = bool(args.spectral_gradient)
-    alg = stage_bytes(wr, dom, fused, spectral)
+    bz = bins_in_z(wr, tuning)
+    alg = stage_bytes(wr, dom, fused, spectral, bz)
     achieved = alg / (per_launch_ms / 1e3) / 1e9
     roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
             "traffic": traffic_from_profiles(dom, wr.name), "alg_bytes_per_launch": int(alg),
             "ms_per_launch": round(per_launch_ms, 4)}
     total_launch = sum(v[1] for v in stages.values())
-    step_alg = sum(stage_bytes(wr, k, fused, spectral) * (v[2] if k in ("deposit", "bins") else v[1])
+    step_alg = sum(stage_bytes(wr, k, fused, spectral, bz) * (v[2] if k in ("deposit", "bins") else v[1])
                    for k, v in stages.items() if k != "response" and v[1] > 0) / args.steps
     res = dict(value=whole_job_rate(wr.npart, world, ms), ms_per_step=ms, ms_per_step_median=ms_median,
                graph=graph, e2e=e2e, roofline=roof,

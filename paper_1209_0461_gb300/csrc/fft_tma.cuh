@@ -17,6 +17,7 @@
 
 #include "async_copy.cuh"
 #include "fft.cuh"
+#include "grid_kernels.cuh"
 
 namespace nupm {
 
@@ -37,6 +38,11 @@ struct ColTmaArgs {
   const float* fac;       // FP32 fac table
   float fac_inv_du, coeff;
   int* status;
+  // bin power sums fused into the forward z pass (k_col_tma_z_fwd<N, true>)
+  const int* thr;         // bin thresholds T_0..T_nk of n^2
+  float inv_lr;
+  int nk;                 // <= kZBinsMaxBins
+  double* partials;       // [gridDim.x][nk]: one row per CTA
 };
 
 template <typename T, int N>
@@ -380,8 +386,18 @@ k_col_tma_z(const __grid_constant__ CUtensorMap map, ColTmaArgs<T> A) {
 // buffer, has been read back).  The exchange buffer holds 8 of the 16
 // columns: the two halves exchange in turn.  The same butterflies as fft_regs
 // for the two-stage plans of 256, 512 and 1024 points (one exchange).
+//
+// BINS: the power sums of the spectrum's bins (a3) in the same pass.  A
+// tile's |delta_k|^2 go to the exchange buffer (free after the exchange), and
+// one warp per column folds them at kz = 0 into rings j = |kz| (n^2 =
+// ky^2 + x2^2 + j^2, weight 2 for the +-kx pair) for bin_rings_warp; the
+// packed column x2 = 0 is left to k_bin_plane0.  Each CTA keeps one
+// float-pair accumulator per warp and writes their sum in FP64, in warp
+// order, to its row of partials at the end: a fixed order for a fixed grid.
 // ---------------------------------------------------------------------------
-template <int N>
+constexpr int kZBinsMaxBins = 256;
+
+template <int N, bool BINS>
 struct ColTmaZFwdCfg {
   using T = float;
   using P = Plan<T, N>;
@@ -390,35 +406,41 @@ struct ColTmaZFwdCfg {
   static constexpr int NT = N / E;
   static constexpr int W = ColTmaZCfg<T, N>::W, WH = W / 2;
   static constexpr int THREADS = W * NT;
+  static constexpr int WARPS = THREADS / 32;
   static constexpr int PAD = ColTmaZCfg<T, N>::PAD;
   static constexpr int BOX = ColTmaZCfg<T, N>::BOX;
   static constexpr int NBOX = N / BOX;
   static constexpr size_t TILE_BYTES = (size_t)N * W * sizeof(cx<T>);
   static constexpr size_t XCH_BYTES = (size_t)ColSmem<T, WH, PAD>::words(N) * sizeof(cx<T>);
-  static constexpr size_t SMEM = TILE_BYTES + XCH_BYTES + 64;
+  static constexpr size_t ACC_BYTES = BINS ? (size_t)WARPS * kZBinsMaxBins * sizeof(float2) : 0;
+  static constexpr size_t SMEM = TILE_BYTES + XCH_BYTES + ACC_BYTES + 64;
   static constexpr int TILES_PER_ROW = M / W;
   static_assert(P::R3 == 1 && R2 > 1 && E % R2 == 0, "two-stage plans only");
   static_assert(THREADS % 32 == 0 && THREADS <= 1024, "whole warps");
   static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
-  static_assert(TILE_BYTES % 128 == 0 && (TILE_BYTES + XCH_BYTES) % 8 == 0, "buffer alignment");
+  static_assert(TILE_BYTES % 128 == 0 && (TILE_BYTES + XCH_BYTES + ACC_BYTES) % 8 == 0, "buffer alignment");
+  static_assert(!BINS || (size_t)W * N * sizeof(float) <= XCH_BYTES, "the powers fit the exchange buffer");
+  static_assert(!BINS || (N / 2) % 32 == 0, "rings per lane");
 };
 
-template <int N>
-__global__ void __launch_bounds__(ColTmaZFwdCfg<N>::THREADS, 1)
+template <int N, bool BINS>
+__global__ void __launch_bounds__(ColTmaZFwdCfg<N, BINS>::THREADS, 1)
 k_col_tma_z_fwd(const __grid_constant__ CUtensorMap map, ColTmaArgs<float> A) {
   using T = float;
-  using Cfg = ColTmaZFwdCfg<N>;
+  using Cfg = ColTmaZFwdCfg<N, BINS>;
   constexpr int M = N / 2, E = Cfg::E, R2 = Cfg::R2, NT = Cfg::NT, W = Cfg::W, WH = Cfg::WH;
   constexpr int64_t ES = (int64_t)N * M;      // element stride along z
   constexpr int DIR = -1;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* xch = reinterpret_cast<cx<T>*>(smem_raw + Cfg::TILE_BYTES);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::TILE_BYTES + Cfg::XCH_BYTES);
+  float2* acc_all = reinterpret_cast<float2*>(smem_raw + Cfg::TILE_BYTES + Cfg::XCH_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::TILE_BYTES + Cfg::XCH_BYTES + Cfg::ACC_BYTES);
   const int items = Cfg::TILES_PER_ROW * N;   // (x2 tile, y)
   const int c = threadIdx.x % W;
   const int t = threadIdx.x / W;
   const int half = c / WH;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   ColSmem<T, WH, Cfg::PAD> xs{xch, c % WH};
 
   auto issue = [&](int item) {
@@ -433,6 +455,8 @@ k_col_tma_z_fwd(const __grid_constant__ CUtensorMap map, ColTmaArgs<float> A) {
     mbar_init(bar, 1);
     fence_mbar_init();
   }
+  if constexpr (BINS)
+    for (int i = threadIdx.x; i < Cfg::WARPS * A.nk; i += blockDim.x) acc_all[i] = make_float2(0.0f, 0.0f);
   __syncthreads();
   const int first = blockIdx.x, step = gridDim.x;
   if (threadIdx.x == 0 && first < items) issue(first);
@@ -488,6 +512,47 @@ k_col_tma_z_fwd(const __grid_constant__ CUtensorMap map, ColTmaArgs<float> A) {
     for (int b = 0; b < E / R2; ++b)
 #pragma unroll
       for (int i = 0; i < R2; ++i) dst[(int64_t)(t + NT * b + i * (N / R2)) * ES] = v[b * R2 + i];
+    if constexpr (BINS) {
+      constexpr int J = N / 2, ER = J / 32;
+      // |delta_k|^2 of this tile, element iz of column c at iz W + ((c + iz / ER) mod W):
+      // the stores of a warp (16 columns, two consecutive iz) and the ring
+      // loads of a warp (one column, lanes ER apart in iz) fall in distinct
+      // banks, two lanes a bank for the loads
+      static_assert(W == 16, "the rotation assumes 16 columns");
+      float* pw = reinterpret_cast<float*>(xch);
+      auto at = [&](int iz, int col) { return iz * W + ((col + iz / ER) & (W - 1)); };
+#pragma unroll
+      for (int b = 0; b < E / R2; ++b)
+#pragma unroll
+        for (int i = 0; i < R2; ++i) {
+          const cx<T> q = v[b * R2 + i];
+          pw[at(t + NT * b + i * (N / R2), c)] = q.x * q.x + q.y * q.y;
+        }
+      __syncthreads();
+      const int ky = y < N / 2 ? y : y - N;
+      for (int col = warp; col < W; col += Cfg::WARPS) {
+        const int x2c = xt * W + col;
+        if (x2c == 0) continue;                      // the packed column: k_bin_plane0
+        float r[ER];
+#pragma unroll
+        for (int i = 0; i < ER; ++i) {
+          const int j = lane * ER + i;                // j < J: kz = j and kz = -j
+          r[i] = 2.0f * (j > 0 ? pw[at(j, col)] + pw[at(N - j, col)] : pw[at(0, col)]);
+        }
+        const int base2 = ky * ky + x2c * x2c;
+        bin_rings_warp<ER>(r, base2, true, base2 + J * J, 2.0f * pw[at(J, col)], A.thr, A.nk, A.inv_lr,
+                           acc_all + warp * A.nk);
+      }
+      __syncthreads();   // the powers are read before the next tile's exchange
+    }
+  }
+  if constexpr (BINS) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.nk; i += blockDim.x) {
+      double sum = 0.0;
+      for (int w = 0; w < Cfg::WARPS; ++w) sum += (double)acc_all[w * A.nk + i].x + (double)acc_all[w * A.nk + i].y;
+      A.partials[(int64_t)blockIdx.x * A.nk + i] = sum;
+    }
   }
 }
 

@@ -122,6 +122,13 @@ void col_tma_n(const GridArgs& g, const CUtensorMap* map, cudaStream_t s) {
   k_col_tma<T, N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*map, a);
 }
 
+// Persistent grid of the TMA-staged forward z pass (one CTA per SM, at most
+// one per tile): the number of partial rows its fused bin sums write.
+static inline int z_fwd_grid(const GridArgs& g) {
+  const int items = (g.n / 2 / ColTmaZCfg<float, 1024>::W) * g.n;
+  return items < g.sm_count ? items : g.sm_count;
+}
+
 // TMA-staged z pass of size N with 128-byte segments (one resident CTA per
 // SM; a persistent grid of one CTA per SM).
 template <int N, int MODE>
@@ -152,14 +159,28 @@ void col_tma_z_n(const GridArgs& g, cudaStream_t s) {
     // issued before the transform): 1.81 against 2.02 ms at 1024^3 on GB300.
     // The Green pass keeps k_col_tma_z, whose Green factors are computed while
     // its copy travels (2.27 against 2.46 ms with the factors computed inline
-    // in a split-buffer form).
-    using FC = ColTmaZFwdCfg<N>;
-    static bool fattr = false;
-    if (!fattr) {
-      cudaFuncSetAttribute(k_col_tma_z_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FC::SMEM);
-      fattr = true;
+    // in a split-buffer form).  With bins_in_z it also sums the bins' power.
+    if (g.bins_in_z) {
+      using FC = ColTmaZFwdCfg<N, true>;
+      static bool battr = false;
+      if (!battr) {
+        cudaFuncSetAttribute(k_col_tma_z_fwd<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FC::SMEM);
+        battr = true;
+      }
+      a.thr = g.bin_thr;
+      a.inv_lr = g.bin_inv_lr;
+      a.nk = g.bin_nk;
+      a.partials = g.bin_partials;
+      k_col_tma_z_fwd<N, true><<<grid, FC::THREADS, FC::SMEM, s>>>(*g.tmap_z16, a);
+    } else {
+      using FC = ColTmaZFwdCfg<N, false>;
+      static bool fattr = false;
+      if (!fattr) {
+        cudaFuncSetAttribute(k_col_tma_z_fwd<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FC::SMEM);
+        fattr = true;
+      }
+      k_col_tma_z_fwd<N, false><<<grid, FC::THREADS, FC::SMEM, s>>>(*g.tmap_z16, a);
     }
-    k_col_tma_z_fwd<N><<<grid, FC::THREADS, FC::SMEM, s>>>(*g.tmap_z16, a);
     return;
   }
   k_col_tma_z<T, N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*g.tmap_z16, a);
@@ -334,8 +355,23 @@ int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const int* thr, float
   };
   bool done = false;
   if constexpr (sizeof(T) == 4) {
+    // FP32 power sums made by the forward z pass (one partial row per CTA of
+    // its persistent grid): the packed x2 = 0 column here, then the reduce
+    if (!lattice && g.bins_in_z) {
+      const int zgrid = z_fwd_grid(g);
+      const int nplane = (g.n + kPlaneBinWarps - 1) / kPlaneBinWarps;
+      const size_t sh = (size_t)kPlaneBinWarps * nk * sizeof(double);
+      switch (g.n) {
+        case 256: k_bin_plane0<256><<<nplane, kPlaneBinWarps * 32, sh, s>>>(reinterpret_cast<const cx<float>*>(spec), nk, thr, inv_lr, partials, zgrid); break;
+        case 512: k_bin_plane0<512><<<nplane, kPlaneBinWarps * 32, sh, s>>>(reinterpret_cast<const cx<float>*>(spec), nk, thr, inv_lr, partials, zgrid); break;
+        case 1024: k_bin_plane0<1024><<<nplane, kPlaneBinWarps * 32, sh, s>>>(reinterpret_cast<const cx<float>*>(spec), nk, thr, inv_lr, partials, zgrid); break;
+        default: return PM_ERR_UNSUPPORTED;
+      }
+      nblk = zgrid + nplane;
+      done = true;
+    }
     // FP32 power sums of grids with a bins tensor map: rows staged by TMA
-    if (!lattice && g.tmap_bins && (E == 2 || E == 4 || E == 8 || E == 16)) {
+    if (!done && !lattice && g.tmap_bins && (E == 2 || E == 4 || E == 8 || E == 16)) {
       decltype(&k_bin_power_tma<16>) kern = E == 2 ? k_bin_power_tma<2> : E == 4 ? k_bin_power_tma<4>
                                             : E == 8 ? k_bin_power_tma<8> : k_bin_power_tma<16>;
       const size_t sh = bin_tma_smem(nk, E);

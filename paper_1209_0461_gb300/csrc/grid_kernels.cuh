@@ -194,7 +194,7 @@ __device__ __forceinline__ int bin_of_n2(int n2, const int* T, int nk, float inv
   return (T[b] <= n2 && n2 < T[b + 1]) ? b : -1;
 }
 
-// FP32 power sums accumulate per bin as an unevaluated pair hi + lo of
+// FP32 power sums accumulate per bin as an unevaluated pair hi + lo of// FP32 power sums accumulate per bin as an unevaluated pair hi + lo of
 // floats (error-free two-sum of each added run or segment): about twice
 // float precision without GB300's narrow FP64 pipe, which otherwise limits
 // the kernel.  The pair is summed into FP64 once per CTA.
@@ -209,6 +209,131 @@ __device__ __forceinline__ void pair_add(float2* a, float x) {
   v.x = s;
   v.y += err;
   *a = v;
+}
+
+// Power sums of one warp over "rings" j of a line of modes whose n^2 =
+// base2 + j^2 grows with j (the modes along z of one (x2, y) column, folded
+// at kz = 0, or along y of one kz row): lane l holds the values r[i] of rings
+// j = l ER + i, and the last lane also `extra` for the ring n2x after all of
+// them.  The bins of a lane's rings are monotone and the lanes' ranges follow
+// each other, so each lane sums its runs of equal bin in order, a bin met only
+// inside one lane is added at once, and the runs that cross lanes are joined
+// by one segmented scan (as bin_row_staged); every bin gets its adds in a fixed
+// order, into the warp's float-pair accumulator acc[nk] (pair_add).
+template <int ER>
+__device__ __forceinline__ void bin_rings_warp(const float (&r)[ER], int base2, bool has_extra, int n2x,
+                                               float extra, const int* __restrict__ T, int nk, float inv_lr,
+                                               float2* acc) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int j0 = lane * ER;
+  const int n20 = base2 + j0 * j0;
+  int bL = bin_of_n2(n20 > 0 ? n20 : 1, T, nk, inv_lr);   // n^2 = 0 (the mean) carries no power
+  const int bF = bL;
+  int tnext = T[bL + 1];
+  bool multi = false;
+  float sF = 0.0f, c = 0.0f;
+  auto ring = [&](int n2m, float v) {
+    if (n2m >= tnext) {
+      if (!multi) {          // the first run waits for the lane combine
+        sF = c;
+        multi = true;
+      } else {               // an inner run: a bin no other lane has
+        pair_add(acc + bL, c);
+      }
+      c = 0.0f;
+      do {
+        ++bL;
+        tnext = T[bL + 1];
+      } while (n2m >= tnext);
+    }
+    c += v;
+  };
+#pragma unroll
+  for (int i = 0; i < ER; ++i) {
+    const int j = j0 + i;
+    ring(base2 + j * j, r[i]);
+  }
+  if (lane == 31 && has_extra) ring(n2x, extra);
+  int kk = (bL << 1) | (multi ? 0 : 1);   // key, open (a single-run lane continues the previous one)
+  float s0 = c;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int pkk = __shfl_up_sync(full, kk, off);
+    const float p0 = __shfl_up_sync(full, s0, off);
+    if (lane >= off && (kk & 1) && (pkk >> 1) == (kk >> 1)) {
+      s0 += p0;
+      kk = (kk & ~1) | (pkk & 1);
+    }
+  }
+  const int k = kk >> 1;
+  const int qk = __shfl_up_sync(full, k, 1);
+  const float q0 = __shfl_up_sync(full, s0, 1);
+  const int nextF = __shfl_down_sync(full, bF, 1);
+  __syncwarp();
+  if (multi) pair_add(acc + bF, sF + ((lane > 0 && qk == bF) ? q0 : 0.0f));
+  __syncwarp();
+  if (lane == 31 || nextF != k) pair_add(acc + k, s0);
+  __syncwarp();
+}
+
+// The packed column x2 = 0 of an FP32 spectrum (the kx = 0 and kx = N/2
+// planes, A + iB) into bins: warp w of CTA b takes the row kz of iz = b W + w
+// and rings j = |ky|, unpacking each slot with its partner at (-z, -y); the
+// kx = 0 and kx = N/2 modes are two ring lines (n^2 = kz^2 + j^2 and
+// kz^2 + (N/2)^2 + j^2).  The CTA's warp sums go to partials[slot0 + b].
+constexpr int kPlaneBinWarps = 8;
+template <int N>
+__global__ void __launch_bounds__(kPlaneBinWarps * 32)
+k_bin_plane0(const cx<float>* __restrict__ spec, int nk, const int* __restrict__ thr, float inv_lr,
+             double* __restrict__ partials, int slot0) {
+  constexpr int M = N / 2, J = N / 2, ER = J / 32;
+  static_assert(J % 32 == 0, "rings per lane");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* acc_all = reinterpret_cast<float2*>(smem_raw);   // [kPlaneBinWarps][nk] float pairs
+  for (int i = threadIdx.x; i < kPlaneBinWarps * nk; i += blockDim.x) acc_all[i] = make_float2(0.0f, 0.0f);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int iz = blockIdx.x * kPlaneBinWarps + warp;
+  if (iz < N) {
+    const int kz = signed_freq(iz, N);
+    const int pz = partner_index(iz, N);
+    auto unpack = [&](int iy, float& pa, float& pb) {
+      const cx<float> f = spec[((int64_t)iz * N + iy) * M];
+      const cx<float> g = spec[((int64_t)pz * N + partner_index(iy, N)) * M];
+      const float ax = 0.5f * (f.x + g.x), ay = 0.5f * (f.y - g.y);
+      const float bx = 0.5f * (f.y + g.y), by = -0.5f * (f.x - g.x);
+      pa = ax * ax + ay * ay;
+      pb = bx * bx + by * by;
+    };
+    float ra[ER], rb[ER];
+#pragma unroll
+    for (int i = 0; i < ER; ++i) {
+      const int j = lane * ER + i;   // j < J
+      float a1, b1;
+      unpack(j, a1, b1);
+      if (j > 0) {
+        float a2, b2;
+        unpack(N - j, a2, b2);
+        a1 += a2;
+        b1 += b2;
+      }
+      ra[i] = (kz == 0 && j == 0) ? 0.0f : a1;   // the mean carries no power
+      rb[i] = b1;
+    }
+    float ea = 0.0f, eb = 0.0f;
+    if (lane == 31) unpack(J, ea, eb);           // ky = N/2: one mode
+    float2* acc = acc_all + warp * nk;
+    bin_rings_warp<ER>(ra, kz * kz, true, kz * kz + J * J, ea, thr, nk, inv_lr, acc);
+    bin_rings_warp<ER>(rb, kz * kz + M * M, true, kz * kz + M * M + J * J, eb, thr, nk, inv_lr, acc);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+    double sum = 0.0;
+#pragma unroll
+    for (int w = 0; w < kPlaneBinWarps; ++w) sum += (double)acc_all[w * nk + i].x + (double)acc_all[w * nk + i].y;
+    partials[(int64_t)(slot0 + blockIdx.x) * nk + i] = sum;
+  }
 }
 
 // One row's modes into the warp's accumulator acc (see above).  f: this

@@ -181,6 +181,14 @@ struct GridArgs {
   // positions as the deposit, perm or inv written)
   int gather_rows = 0;
   bool rows_ready = false;
+  // FP32 bin power sums inside the TMA-staged forward z pass (wide_z = 2,
+  // n_kbins <= 256): the z pass writes one partial row per CTA, the bins step
+  // adds the packed x2 = 0 column and reduces
+  bool bins_in_z = false;
+  const int* bin_thr = nullptr;
+  float bin_inv_lr = 0;
+  int bin_nk = 0;
+  double* bin_partials = nullptr;
 };
 #define NUPM_DECLARE_GRID(SFX)                                                              \
   int deposit##SFX(const GridArgs& g, const void* pos, cudaStream_t s);                     \

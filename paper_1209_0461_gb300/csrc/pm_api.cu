@@ -485,6 +485,11 @@ GridArgs grid_args(const pm_ctx* c) {
   g.scan_tot = c->d_scantot;
   g.perm = ((c->p.flags & PM_FUSED_GATHER) || c->gather_rows == 1) ? c->d_perm : nullptr;
   g.inv = c->gather_rows == 2 ? c->d_inv : nullptr;
+  g.bins_in_z = !c->fp64 && c->tma_z16 && c->wide_z == 2 && c->nk <= 256;
+  g.bin_thr = c->d_thr;
+  g.bin_inv_lr = c->bin_inv_lr;
+  g.bin_nk = c->nk;
+  g.bin_partials = c->d_partials;
   g.accs = c->d_accs;
   g.gather_rows = c->gather_rows;
   g.rec = c->d_rec;

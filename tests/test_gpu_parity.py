@@ -473,6 +473,33 @@ def test_tma_staged_z_passes(prec, flags):
         assert erms < (1e-6 if flags & SPECTRAL_GRADIENT else 1e-5)
 
 
+@pytest.mark.parametrize("n,nk", [(256, 256), (512, 64), (1024, 256)])
+def test_bin_sums_fused_in_the_z_pass(n, nk):
+    # wide_z = 2 with FP32 and at most 256 bins: the forward z pass sums the
+    # bins' power (rings along kz, the packed x2 = 0 column by its own
+    # kernel); the same counts and Sigma |k| as the lattice, and the power
+    # sums of the separate bin pass to float rounding, on the same deposit
+    w = synth.Workload(f"zbins{n}", n, n // 4, 2.0 * n, 0.15, 3, 4, nk, "fp32")
+    inp = make_inputs(w)
+    pm = nupm.PM(w.ngrid, w.npart, w.box, w.omega_cdm, w.omega_nu, w.h, w.m_nu_total, w.n_species,
+                 a_init=w.a_init, n_kbins=nk, n_hist_max=4, precision="fp32")
+    pos = torch.from_numpy(synth.to_cell_offset(inp["pos64"], w.box, w.ngrid)).cuda()
+    out = []
+    for wide_z in (1, 2, 2):
+        pm.set_tuning(-1, wide_z, 16)
+        pm.deposit(pos)
+        pm.check()
+        out.append([np.array(x) for x in pm.bins()])
+    pm.close()
+    (c1, k1, p1), (c2, k2, p2), (c3, k3, p3) = out
+    assert np.array_equal(c1, c2) and np.array_equal(k1, k2)
+    ne = c1 > 0
+    rel = np.abs(p2[ne] / p1[ne] - 1)
+    print(f"n={n} nk={nk}: fused vs separate bin sums, max rel {rel.max():.2e}")
+    assert rel.max() < 2e-6
+    assert np.array_equal(p2, p3)                         # deterministic
+
+
 @pytest.mark.parametrize("prec,n,npart", [("fp64", 32, 32 ** 3), ("fp32", 64, 64 ** 3 - 37),
                                           ("fp32", 128, 64 ** 3), ("fp64", 16, 8 ** 3)])
 def test_fused_interpolation_equals_separate(prec, n, npart):
