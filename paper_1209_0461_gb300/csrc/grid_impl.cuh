@@ -122,6 +122,25 @@ void col_tma_n(const GridArgs& g, const CUtensorMap* map, cudaStream_t s) {
   k_col_tma<T, N, MODE><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*map, a);
 }
 
+// The packed x2 = 0 column's bins after a forward z pass that summed the
+// rest (FP32 grids of 256, 512 or 1024 points; false otherwise).  A template,
+// so that the FP64 unit does not instantiate the FP32 kernels.
+template <typename U>
+bool bins_plane0(const GridArgs& g, int nk, const int* thr, float inv_lr, double* partials, int zgrid,
+                 int nplane, cudaStream_t s) {
+  if constexpr (sizeof(U) == 4) {
+    const cx<float>* spec = reinterpret_cast<const cx<float>*>(g.spec);
+    const size_t sh = (size_t)kPlaneBinWarps * nk * sizeof(float2);
+    switch (g.n) {
+      case 256: k_bin_plane0<256><<<nplane, kPlaneBinWarps * 32, sh, s>>>(spec, nk, thr, inv_lr, partials, zgrid); return true;
+      case 512: k_bin_plane0<512><<<nplane, kPlaneBinWarps * 32, sh, s>>>(spec, nk, thr, inv_lr, partials, zgrid); return true;
+      case 1024: k_bin_plane0<1024><<<nplane, kPlaneBinWarps * 32, sh, s>>>(spec, nk, thr, inv_lr, partials, zgrid); return true;
+      default: return false;
+    }
+  }
+  return false;
+}
+
 // Persistent grid of the TMA-staged forward z pass (one CTA per SM, at most
 // one per tile): the number of partial rows its fused bin sums write.
 static inline int z_fwd_grid(const GridArgs& g) {
@@ -360,13 +379,7 @@ int NUPM_FN(bins)(const GridArgs& g, bool lattice, int nk, const int* thr, float
     if (!lattice && g.bins_in_z) {
       const int zgrid = z_fwd_grid(g);
       const int nplane = (g.n + kPlaneBinWarps - 1) / kPlaneBinWarps;
-      const size_t sh = (size_t)kPlaneBinWarps * nk * sizeof(double);
-      switch (g.n) {
-        case 256: k_bin_plane0<256><<<nplane, kPlaneBinWarps * 32, sh, s>>>(reinterpret_cast<const cx<float>*>(spec), nk, thr, inv_lr, partials, zgrid); break;
-        case 512: k_bin_plane0<512><<<nplane, kPlaneBinWarps * 32, sh, s>>>(reinterpret_cast<const cx<float>*>(spec), nk, thr, inv_lr, partials, zgrid); break;
-        case 1024: k_bin_plane0<1024><<<nplane, kPlaneBinWarps * 32, sh, s>>>(reinterpret_cast<const cx<float>*>(spec), nk, thr, inv_lr, partials, zgrid); break;
-        default: return PM_ERR_UNSUPPORTED;
-      }
+      if (!bins_plane0<T>(g, nk, thr, inv_lr, partials, zgrid, nplane, s)) return PM_ERR_UNSUPPORTED;
       nblk = zgrid + nplane;
       done = true;
     }
