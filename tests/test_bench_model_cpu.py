@@ -30,3 +30,20 @@ def test_spectral_gradient_carries_three_fields():
     y = bench.stage_bytes(W, "fft_y_inv", False, True)
     x = bench.stage_bytes(W, "fft_x_inv", False, True)
     assert z == 3 * CPLX and y == 5 * CPLX and x == 3 * (CPLX + REAL)
+
+
+def test_bin_sums_in_the_z_pass():
+    # FP32, wide_z = 2 (TMA-staged z passes), at most 256 bins, a power-of-two
+    # grid of 256 or more: the bins stage reads the packed x2 = 0 column only
+    assert bench.bins_in_z(W, [0, 2, 4, 0])
+    assert not bench.bins_in_z(W, [0, 1, 4, 0])
+    assert not bench.bins_in_z(W, None)
+    assert not bench.bins_in_z(synth.with_(W, precision="fp64"), [0, 2, 4, 0])
+    assert not bench.bins_in_z(synth.with_(W, n_kbins=512), [0, 2, 4, 0])
+    assert not bench.bins_in_z(synth.with_(W, ngrid=192), [0, 2, 4, 0])
+    assert bench.stage_bytes(W, "bins", False, False, True) == 8 * N * N
+    assert bench.stage_bytes(W, "fft_z_fwd", False, False, True) == 2 * CPLX
+    total = sum(bench.stage_bytes(W, k, False, False, True) for k in
+                ("deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_fwd", "bins", "fft_z_inv", "fft_y_inv",
+                 "fft_x_inv", "interp")) + 3 * 8 * N * N
+    assert abs(total / 1e9 - 63.4) < 0.1
